@@ -1,0 +1,216 @@
+"""CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Thin ctypes wrapper over ``nhp_oracle.c``, a plain, slow, single-threaded C
+restatement of the paper's graph (Section V), obstacle rendering (Section VI),
+kernel-style layered relaxation (Section VIII.B, Insert 1), Dijkstra (Section
+VIII.A) and forward-tracking extraction (Section X).  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
+this package; the planner library never does, and this package never imports
+the planner library.
+
+Every function cites the passage it follows in the C source.  All of them are
+pinned by ``tests/test_oracle_pins.py`` (hand-worked table values, closed
+forms, brute-force enumeration, Dijkstra convergence, symmetries, an
+independent library distance transform).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_lib", "libnhp_oracle.so")
+_SRC = os.path.join(_HERE, "nhp_oracle.c")
+_HDR = os.path.join(_HERE, "nhp_oracle.h")
+
+INF = 0xFFFFFFFF
+HARD = 0xFFFF
+NONE = 0xFFFF
+LF, SF, RB, RF, SB, LB = range(6)
+CYCLE_ORDER = (LF, SF, RB, RF, SB, LB)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_lib (idempotent)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(_SRC),
+                                                                       os.path.getmtime(_HDR)):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        p = C.c_void_p
+        L.orc_create.restype = p
+        L.orc_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.orc_destroy.argtypes = [p]
+        L.orc_tables.argtypes = [p] + [p] * 7
+        L.orc_footprint.restype = C.c_int
+        L.orc_footprint.argtypes = [p, C.c_int, C.c_int, C.c_int, C.c_int, p, p, C.c_int]
+        L.orc_render.restype = C.c_int
+        L.orc_render.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p]
+        L.orc_render_cells.restype = C.c_int
+        L.orc_render_cells.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p, C.c_int64, p]
+        L.orc_succ.restype = C.c_int64
+        L.orc_succ.argtypes = [p, C.c_int, C.c_int64]
+        L.orc_edge.restype = C.c_uint32
+        L.orc_edge.argtypes = [p, p, C.c_int, C.c_int64]
+        L.orc_sweep.restype = C.c_int
+        L.orc_sweep.argtypes = [p, p, C.c_int64, C.c_int, C.c_int, p, p, p]
+        L.orc_layers.restype = C.c_int
+        L.orc_layers.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p, p, p]
+        L.orc_dijkstra.restype = C.c_int
+        L.orc_dijkstra.argtypes = [p, p, C.c_int64, p]
+        L.orc_bruteforce.restype = C.c_int
+        L.orc_bruteforce.argtypes = [p, p, C.c_int64, C.c_int, p]
+        L.orc_extract.restype = C.c_int
+        L.orc_extract.argtypes = [p, p, p, C.c_int64, p, C.c_int]
+        L.orc_soft_image.argtypes = [C.c_int, p, C.c_int, C.c_int, p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Oracle:
+    """One grid shape + vehicle turn radius + integer costs."""
+
+    def __init__(self, nx_log2: int, nt_log2: int, turn_radius: float, half_shift: int = 1,
+                 step_straight: int = 100, step_scale: int = 100, transition: int = 500):
+        self.nx_log2, self.nt_log2 = nx_log2, nt_log2
+        self.nx, self.nt = 1 << nx_log2, 1 << nt_log2
+        self.nr = self.nx * self.nx * self.nt
+        self.ct = transition
+        self._c = lib().orc_create(nx_log2, nt_log2, float(turn_radius), int(half_shift),
+                                   step_straight, step_scale, transition)
+        if not self._c:
+            raise ValueError("oracle: invalid grid description")
+
+    def __del__(self):
+        if getattr(self, "_c", None):
+            lib().orc_destroy(self._c)
+            self._c = None
+
+    def cell(self, pose) -> int:
+        i, j, t = pose
+        return int(i) + self.nx * (int(j) + self.nx * int(t))
+
+    def pose(self, cell: int):
+        cell = int(cell)
+        return (cell & (self.nx - 1), (cell >> self.nx_log2) & (self.nx - 1), cell >> (2 * self.nx_log2))
+
+    # ----------------------------------------------------------- eqs. 11-24
+    def tables(self):
+        nt, nx = self.nt, self.nx
+        beta = np.zeros(nt, np.int32)
+        psi2 = np.zeros(nt, np.uint8)
+        iflag = np.zeros(nt, np.uint8)
+        jsign = np.zeros(nt, np.int8)
+        bsh = np.zeros((nt, nx), np.int32)
+        wS = np.zeros(nt, np.uint32)
+        wA = np.zeros(1, np.uint32)
+        lib().orc_tables(self._c, _ptr(beta), _ptr(psi2), _ptr(iflag), _ptr(jsign), _ptr(bsh), _ptr(wS), _ptr(wA))
+        return dict(beta=beta, psi2=psi2, iflag=iflag, jsign=jsign, bshear=bsh, wS=wS, wA=int(wA[0]))
+
+    # ----------------------------------------------------------- Section VI
+    def footprint(self, front: int, rear: int, hw: int, theta: int):
+        cap = 1 << 18
+        dx = np.zeros(cap, np.int32)
+        dy = np.zeros(cap, np.int32)
+        n = lib().orc_footprint(self._c, front, rear, hw, theta, _ptr(dx), _ptr(dy), cap)
+        if n < 0:
+            raise ValueError("footprint too large")
+        return dx[:n].copy(), dy[:n].copy()
+
+    def render(self, img: np.ndarray, footprint) -> np.ndarray:
+        img = np.ascontiguousarray(img, dtype=np.uint16)
+        B = np.zeros(self.nr, np.uint16)
+        if lib().orc_render(self._c, _ptr(img), *[int(v) for v in footprint], _ptr(B)) != 0:
+            raise MemoryError
+        return B
+
+    def render_cells(self, img: np.ndarray, footprint, cells) -> np.ndarray:
+        img = np.ascontiguousarray(img, dtype=np.uint16)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(len(cells), np.uint16)
+        if lib().orc_render_cells(self._c, _ptr(img), *[int(v) for v in footprint], _ptr(cells),
+                                  len(cells), _ptr(out)) != 0:
+            raise ValueError("render_cells failed")
+        return out
+
+    # ----------------------------------------------------------- eqs. 25-31
+    def succ(self, mu: int, cell: int) -> int:
+        return int(lib().orc_succ(self._c, mu, int(cell)))
+
+    def edge(self, B: np.ndarray, mu: int, cell: int) -> int:
+        return int(lib().orc_edge(self._c, _ptr(B), mu, int(cell)))
+
+    # ----------------------------------------------------------- Section VIII
+    def sweep(self, B: np.ndarray, start: int, n_cycles: int, mode: int = 0):
+        B = np.ascontiguousarray(B, dtype=np.uint16)
+        V = np.zeros(self.nr, np.uint32)
+        L = np.zeros(self.nr, np.uint16)
+        imp = np.zeros(max(1, 6 * n_cycles), np.int64)
+        rc = lib().orc_sweep(self._c, _ptr(B), int(start), int(n_cycles), int(mode), _ptr(V), _ptr(L), _ptr(imp))
+        if rc != 0:
+            raise ValueError(f"oracle sweep failed ({rc})")
+        return V, L, imp[:6 * n_cycles]
+
+    def layers(self, B, V, L, first_layer: int, n_layers: int, mode: int = 0):
+        V = np.array(V, dtype=np.uint32, copy=True)
+        L = np.array(L, dtype=np.uint16, copy=True)
+        imp = np.zeros(max(1, n_layers), np.int64)
+        rc = lib().orc_layers(self._c, _ptr(np.ascontiguousarray(B, dtype=np.uint16)), first_layer, n_layers,
+                              mode, _ptr(V), _ptr(L), _ptr(imp))
+        if rc != 0:
+            raise ValueError("oracle layers failed")
+        return V, L, imp[:n_layers]
+
+    def dijkstra(self, B: np.ndarray, start: int) -> np.ndarray:
+        V = np.zeros(self.nr, np.uint32)
+        if lib().orc_dijkstra(self._c, _ptr(np.ascontiguousarray(B, dtype=np.uint16)), int(start), _ptr(V)) != 0:
+            raise ValueError("dijkstra failed")
+        return V
+
+    def bruteforce(self, B: np.ndarray, start: int, n_cycles: int) -> np.ndarray:
+        V = np.zeros(self.nr, np.uint32)
+        if lib().orc_bruteforce(self._c, _ptr(np.ascontiguousarray(B, dtype=np.uint16)), int(start),
+                                int(n_cycles), _ptr(V)) != 0:
+            raise ValueError("bruteforce failed")
+        return V
+
+    # ----------------------------------------------------------- Section X
+    def extract(self, V: np.ndarray, L: np.ndarray, goal: int, cap: int = 4096):
+        seg = np.zeros((cap, 6), np.int64)
+        n = lib().orc_extract(self._c, _ptr(np.ascontiguousarray(V, np.uint32)),
+                              _ptr(np.ascontiguousarray(L, np.uint16)), int(goal), _ptr(seg), cap)
+        if n == -1:
+            return None
+        if n < 0:
+            raise ValueError(f"extract failed ({n})")
+        return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3]),
+                     cost=int(r[4]) | (int(r[5]) << 16)) for r in seg[:n]]
+
+
+def soft_image(occupancy: np.ndarray, radius: int, soft_max: int) -> np.ndarray:
+    """Section VII soft-obstacle image from a binary occupancy map."""
+    occ = np.ascontiguousarray(occupancy, dtype=np.uint8)
+    nx = occ.shape[0]
+    img = np.zeros((nx, nx), np.uint16)
+    lib().orc_soft_image(nx, _ptr(occ), int(radius), int(soft_max), _ptr(img))
+    return img

@@ -1,0 +1,695 @@
+/*
+ * nhp_oracle.c -- TEST INFRASTRUCTURE ONLY (see nhp_oracle.h).
+ *
+ * A plain restatement of the paper's graph and its kernel-style processing,
+ * written for a reader who checks it against the paper by eye:
+ *   - geometry tables               Section V.C, eqs. 11-24
+ *   - maneuver edges                Section V.D, eqs. 25-28, 30-31
+ *   - obstacle rendering            Section VI (walls: Section V.C)
+ *   - Star transition subgraph      Section V.A, Fig. 9, Table 1 (7 vertices,
+ *                                   18 edges per cell)
+ *   - maneuver-kernel relaxation    Section VIII.B, Insert 1 (two loops for
+ *                                   turns, one for straights)
+ *   - cycle order                   Section XVI.A
+ *   - Dijkstra                      Section VIII.A
+ *   - forward-tracking labels       Section X
+ *   - soft obstacle image           Section VII
+ * Readings where the paper is silent are stated where they are used.
+ */
+#include "nhp_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_INF 0xFFFFFFFFu
+#define ORC_HARD 0xFFFFu
+#define ORC_NONE 0xFFFFu
+#define ORC_PI 3.14159265358979323846
+
+enum { LF = 0, SF = 1, RB = 2, RF = 3, SB = 4, LB = 5 };
+
+struct orc_ctx {
+    int lx, lt, nx, nt, mx, mt;
+    int64_t nr;
+    double R;
+    int half;
+    uint32_t step_s, step_a, ct;
+    int32_t* beta;  /* beta(T), eq. 13 context */
+    uint8_t* psi2;  /* 2*Psi(T), eq. 13 */
+    uint8_t* iflag; /* I(T), eq. 19 */
+    int8_t* jsign;  /* J(T), eq. 24 */
+    int32_t* bsh;   /* B(y',T), eq. 22, stored [T*nx + y'] */
+    uint32_t* wS;   /* straight step weight per heading */
+    uint32_t wA;    /* turn step weight */
+};
+
+/* saturating uint32 addition: INF absorbs */
+static uint32_t sadd(uint32_t a, uint32_t b) {
+    uint64_t s = (uint64_t)a + (uint64_t)b;
+    return s >= ORC_INF ? ORC_INF : (uint32_t)s;
+}
+
+static int64_t floor_half(int64_t z) { return z >= 0 ? z / 2 : -((-z + 1) / 2); }
+
+static double heading(int T, int nt) { return (2.0 * ORC_PI) * (double)T / (double)nt; }
+
+orc_ctx* orc_create(int nx_log2, int nt_log2, double R, int half_shift,
+                    uint32_t step_straight, uint32_t step_scale, uint32_t ct) {
+    if (nx_log2 < 2 || nx_log2 > 12 || nt_log2 < 2 || nt_log2 > 12 || !(R > 0)) return NULL;
+    orc_ctx* c = (orc_ctx*)calloc(1, sizeof(orc_ctx));
+    if (!c) return NULL;
+    c->lx = nx_log2; c->lt = nt_log2;
+    c->nx = 1 << nx_log2; c->nt = 1 << nt_log2;
+    c->mx = c->nx - 1; c->mt = c->nt - 1;
+    c->nr = (int64_t)c->nx * c->nx * c->nt;
+    c->R = R; c->half = half_shift ? 1 : 0;
+    c->step_s = step_straight; c->step_a = step_scale; c->ct = ct;
+    int nt = c->nt, nx = c->nx;
+    c->beta = (int32_t*)malloc(sizeof(int32_t) * nt);
+    c->psi2 = (uint8_t*)malloc(nt);
+    c->iflag = (uint8_t*)malloc(nt);
+    c->jsign = (int8_t*)malloc(nt);
+    c->bsh = (int32_t*)malloc(sizeof(int32_t) * (size_t)nt * nx);
+    c->wS = (uint32_t*)malloc(sizeof(uint32_t) * nt);
+    if (!c->beta || !c->psi2 || !c->iflag || !c->jsign || !c->bsh || !c->wS) {
+        orc_destroy(c);
+        return NULL;
+    }
+    for (int T = 0; T < nt; T++) {
+        double th = heading(T, nt);
+        double s = sin(th), co = cos(th);
+        /* eqs. 11-13: alpha = R sin(theta); zeta(x) = round(2x)/2;
+         * beta = floor(zeta(alpha)); Psi = zeta(alpha) - beta.  Without the
+         * half-cell option beta is alpha rounded the usual way and Psi = 0. */
+        double alpha = R * s;
+        if (c->half) {
+            long z = lround(2.0 * alpha);
+            c->beta[T] = (int32_t)floor_half(z);
+            c->psi2[T] = (uint8_t)(z & 1 ? 1 : 0);
+        } else {
+            c->beta[T] = (int32_t)lround(alpha);
+            c->psi2[T] = 0;
+        }
+        /* eq. 19: I = 0 iff |tan theta| <= 1, decided on the integer heading:
+         * the angular distance to the nearest multiple of pi is m*2pi/nt, and
+         * m*2pi/nt <= pi/4  <=>  8m <= nt. */
+        int r = T % (nt / 2);
+        int m = r < nt / 2 - r ? r : nt / 2 - r;
+        c->iflag[T] = (uint8_t)(8 * m <= nt ? 0 : 1);
+        /* eq. 24: J = sign(cos) when I = 0, sign(sin) when I = 1. */
+        if (c->iflag[T] == 0) {
+            int d0 = T < nt - T ? T : nt - T; /* cos > 0 iff d0 < nt/4 */
+            c->jsign[T] = (int8_t)(4 * d0 < nt ? 1 : -1);
+        } else {
+            c->jsign[T] = (int8_t)(2 * T < nt ? 1 : -1); /* sin > 0 iff 0 < T < nt/2 */
+        }
+        /* eq. 20: K = tan when I = 0, cot when I = 1;  eq. 22: B = round(y' K). */
+        double K = c->iflag[T] == 0 ? s / co : co / s;
+        for (int y = 0; y < nx; y++) c->bsh[(size_t)T * nx + y] = (int32_t)lround((double)y * K);
+        /* Section V.D: a straight edge spans 1/|cos| (I = 0) or 1/|sin| (I = 1)
+         * cells, i.e. 1/max(|cos|,|sin|); the weight is that length times the
+         * straight step unit, rounded. */
+        double len = 1.0 / fmax(fabs(co), fabs(s));
+        c->wS[T] = (uint32_t)lround((double)step_straight * len);
+    }
+    /* Section V.D: a turn edge spans 2 pi R / N_theta. */
+    c->wA = (uint32_t)lround((double)step_scale * (2.0 * ORC_PI) * R / (double)nt);
+    return c;
+}
+
+void orc_destroy(orc_ctx* c) {
+    if (!c) return;
+    free(c->beta); free(c->psi2); free(c->iflag); free(c->jsign); free(c->bsh); free(c->wS);
+    free(c);
+}
+
+void orc_tables(const orc_ctx* c, int32_t* beta, uint8_t* psi2, uint8_t* iflag,
+                int8_t* jsign, int32_t* bshear, uint32_t* wS, uint32_t* wA) {
+    if (beta) memcpy(beta, c->beta, sizeof(int32_t) * c->nt);
+    if (psi2) memcpy(psi2, c->psi2, c->nt);
+    if (iflag) memcpy(iflag, c->iflag, c->nt);
+    if (jsign) memcpy(jsign, c->jsign, c->nt);
+    if (bshear) memcpy(bshear, c->bsh, sizeof(int32_t) * (size_t)c->nt * c->nx);
+    if (wS) memcpy(wS, c->wS, sizeof(uint32_t) * c->nt);
+    if (wA) *wA = c->wA;
+}
+
+/* ---------------------------------------------------------------- indexing */
+
+static int64_t cell_of(const orc_ctx* c, int i, int j, int T) {
+    return (int64_t)(i & c->mx) + (int64_t)c->nx * ((int64_t)(j & c->mx) + (int64_t)c->nx * (T & c->mt));
+}
+static void coords(const orc_ctx* c, int64_t cell, int* i, int* j, int* T) {
+    *i = (int)(cell & c->mx);
+    *j = (int)((cell >> c->lx) & c->mx);
+    *T = (int)(cell >> (2 * c->lx));
+}
+static int beta_at(const orc_ctx* c, int T) { return c->beta[T & c->mt]; }
+
+/* ---------------------------------------------------------------- footprint
+ * Reading of Section VI with Fig. 6: the vehicle is the closed rectangle
+ * [-rear, front] x [-hw, hw] in vehicle coordinates (origin at the rear axle).
+ * Pose (i, j, T) stands for the continuum pose (i + Psi_0, j + Psi_1, theta)
+ * (eq. 16).  World cell (i+dx, j+dy) belongs to the footprint when its centre,
+ * expressed in vehicle coordinates, lies in the rectangle (with a 1e-9-cell
+ * tolerance so that exact rotations by multiples of 90 degrees keep their
+ * boundary cells); the cell under the origin always belongs. */
+static double psi_x(const orc_ctx* c, int T) { return c->psi2[T & c->mt] * 0.5; }
+static double psi_y(const orc_ctx* c, int T) { return c->psi2[(T + c->nt / 4) & c->mt] * 0.5; }
+
+static int in_footprint(const orc_ctx* c, int front, int rear, int hw, int T, int dx, int dy) {
+    if (dx == 0 && dy == 0) return 1;
+    const double eps = 1e-9;
+    double th = heading(T, c->nt);
+    double co = cos(th), s = sin(th);
+    double px = (double)dx - psi_x(c, T), py = (double)dy - psi_y(c, T);
+    double xv = co * px + s * py;
+    double yv = -s * px + co * py;
+    return xv >= -(double)rear - eps && xv <= (double)front + eps &&
+           yv >= -(double)hw - eps && yv <= (double)hw + eps;
+}
+
+static int footprint_reach(int front, int rear, int hw) {
+    int ext = front > rear ? front : rear;
+    return (int)ceil(sqrt((double)ext * ext + (double)hw * hw)) + 2;
+}
+
+int orc_footprint(const orc_ctx* c, int front, int rear, int hw, int T,
+                  int32_t* dx, int32_t* dy, int cap) {
+    int lim = footprint_reach(front, rear, hw);
+    int n = 0;
+    for (int y = -lim; y <= lim; y++)
+        for (int x = -lim; x <= lim; x++)
+            if (in_footprint(c, front, rear, hw, T, x, y)) {
+                if (n < cap) { dx[n] = x; dy[n] = y; }
+                n++;
+            }
+    return n <= cap ? n : -n;
+}
+
+/* Section VI + walls of Section V.C: a one-cell hard wall at i = 0 and j = 0,
+ * all coordinates modulo N_x; B is the maximum of the image over the
+ * footprint (HARD = 0xFFFF is the largest value, so any hard cell wins). */
+static uint16_t img_at(const orc_ctx* c, const uint16_t* img, int x, int y) {
+    x &= c->mx; y &= c->mx;
+    if (x == 0 || y == 0) return ORC_HARD;
+    return img[(size_t)y * c->nx + x];
+}
+
+static uint16_t render_one(const orc_ctx* c, const uint16_t* img, const int32_t* dx,
+                           const int32_t* dy, int n, int i, int j) {
+    uint16_t m = 0;
+    for (int k = 0; k < n; k++) {
+        uint16_t v = img_at(c, img, i + dx[k], j + dy[k]);
+        if (v > m) m = v;
+    }
+    return m;
+}
+
+int orc_render(const orc_ctx* c, const uint16_t* img, int front, int rear, int hw, uint16_t* B) {
+    int lim = footprint_reach(front, rear, hw);
+    int cap = (2 * lim + 1) * (2 * lim + 1);
+    int32_t* dx = (int32_t*)malloc(sizeof(int32_t) * cap);
+    int32_t* dy = (int32_t*)malloc(sizeof(int32_t) * cap);
+    if (!dx || !dy) { free(dx); free(dy); return -1; }
+    for (int T = 0; T < c->nt; T++) {
+        int n = orc_footprint(c, front, rear, hw, T, dx, dy, cap);
+        for (int j = 0; j < c->nx; j++)
+            for (int i = 0; i < c->nx; i++)
+                B[cell_of(c, i, j, T)] = render_one(c, img, dx, dy, n, i, j);
+    }
+    free(dx); free(dy);
+    return 0;
+}
+
+int orc_render_cells(const orc_ctx* c, const uint16_t* img, int front, int rear, int hw,
+                     const int64_t* cells, int64_t n, uint16_t* out) {
+    int lim = footprint_reach(front, rear, hw);
+    int cap = (2 * lim + 1) * (2 * lim + 1);
+    int32_t* dx = (int32_t*)malloc(sizeof(int32_t) * cap);
+    int32_t* dy = (int32_t*)malloc(sizeof(int32_t) * cap);
+    if (!dx || !dy) { free(dx); free(dy); return -1; }
+    for (int64_t k = 0; k < n; k++) {
+        int i, j, T;
+        if (cells[k] < 0 || cells[k] >= c->nr) { free(dx); free(dy); return -1; }
+        coords(c, cells[k], &i, &j, &T);
+        int m = orc_footprint(c, front, rear, hw, T, dx, dy, cap);
+        out[k] = render_one(c, img, dx, dy, m, i, j);
+    }
+    free(dx); free(dy);
+    return 0;
+}
+
+/* ------------------------------------------------------------ maneuver edges */
+
+static int is_turn(int mu) { return mu == LF || mu == LB || mu == RF || mu == RB; }
+
+int64_t orc_succ(const orc_ctx* c, int mu, int64_t cell) {
+    int i, j, T;
+    coords(c, cell, &i, &j, &T);
+    int q = c->nt / 4;
+    if (is_turn(mu)) {
+        /* eqs. 25-28: LEFT uses (beta_0, beta_3), RIGHT uses (beta_2, beta_1);
+         * LF and RB step to T+1, LB and RF to T-1; beta_q^{+/-}(T) =
+         * beta(T + qN/4 +/- 1) - beta(T + qN/4). */
+        int qa = (mu == LF || mu == LB) ? 0 : 2;
+        int qb = (mu == LF || mu == LB) ? 3 : 1;
+        int step = (mu == LF || mu == RB) ? 1 : -1;
+        int T2 = (T + step) & c->mt;
+        int di = beta_at(c, T + step + qa * q) - beta_at(c, T + qa * q);
+        int dj = beta_at(c, T + step + qb * q) - beta_at(c, T + qb * q);
+        return cell_of(c, i + di, j + dj, T2);
+    }
+    /* eqs. 30-31; eq. 24 picks which of them is forward. */
+    int plus = (c->jsign[T] >= 0) == (mu == SF);
+    int step = plus ? 1 : -1;
+    const int32_t* Bs = c->bsh + (size_t)T * c->nx;
+    if (c->iflag[T] == 0) {
+        int i2 = (i + step) & c->mx;
+        return cell_of(c, i2, j + Bs[i2] - Bs[i], T);
+    } else {
+        int j2 = (j + step) & c->mx;
+        return cell_of(c, i + Bs[j2] - Bs[j], j2, T);
+    }
+}
+
+/* Edge weight of the maneuver edge leaving `cell` (Insert 1 charges the
+ * obstacle value of the vertex being left): w * B >> 8 with B in Q8, or INF
+ * when the cell is hard. */
+uint32_t orc_edge(const orc_ctx* c, const uint16_t* B, int mu, int64_t cell) {
+    uint16_t b = B[cell];
+    if (b == ORC_HARD) return ORC_INF;
+    uint32_t w = is_turn(mu) ? c->wA : c->wS[cell >> (2 * c->lx)];
+    return (uint32_t)(((uint64_t)w * b) >> 8);
+}
+
+/* ------------------------------------------------- explicit Star graph (Fig. 9)
+ * Per cell X: vertex T(X) (transition state) and M_mu(X) for the six
+ * maneuvers; edges T->M_mu (weight ct), M_mu->T (weight 0), and the maneuver
+ * edge M_mu(X) -> M_mu(succ_mu(X)) (weight orc_edge).  A hard cell has no
+ * transition vertex: its T<->M edges are absent (weight INF). */
+typedef struct {
+    int64_t nr;
+    uint32_t* succ[6];   /* maneuver edge targets  */
+    uint32_t* w_mm[6];   /* maneuver edge weights  */
+    uint32_t* w_tm[6];   /* T -> M_mu weights      */
+    uint32_t* w_mt[6];   /* M_mu -> T weights      */
+} star_graph;
+
+static void graph_free(star_graph* g) {
+    for (int m = 0; m < 6; m++) { free(g->succ[m]); free(g->w_mm[m]); free(g->w_tm[m]); free(g->w_mt[m]); }
+}
+
+static int graph_build(const orc_ctx* c, const uint16_t* B, star_graph* g) {
+    memset(g, 0, sizeof(*g));
+    if (c->nr > 0xFFFFFFFFll) return -1;
+    g->nr = c->nr;
+    for (int m = 0; m < 6; m++) {
+        g->succ[m] = (uint32_t*)malloc(sizeof(uint32_t) * c->nr);
+        g->w_mm[m] = (uint32_t*)malloc(sizeof(uint32_t) * c->nr);
+        g->w_tm[m] = (uint32_t*)malloc(sizeof(uint32_t) * c->nr);
+        g->w_mt[m] = (uint32_t*)malloc(sizeof(uint32_t) * c->nr);
+        if (!g->succ[m] || !g->w_mm[m] || !g->w_tm[m] || !g->w_mt[m]) { graph_free(g); return -1; }
+        for (int64_t x = 0; x < c->nr; x++) {
+            int hard = B[x] == ORC_HARD;
+            g->succ[m][x] = (uint32_t)orc_succ(c, m, x);
+            g->w_mm[m][x] = orc_edge(c, B, m, x);
+            g->w_tm[m][x] = hard ? ORC_INF : c->ct;
+            g->w_mt[m][x] = hard ? ORC_INF : 0u;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------ relaxation along one maneuver cycle
+ * Running a maneuver kernel (Section VIII.B) means: from any transition state
+ * at its current value, enter the maneuver, follow its edges, and return to
+ * the transition state wherever that improves the value.  On a cycle
+ * c_0 .. c_{n-1} (c_{k+1} = succ(c_k)) this is, for each position p,
+ *     V'(c_p) = min( V(c_p),  min_{d=1..n-1} V(c_{p-d}) + w_tm(c_{p-d})
+ *                              + sum_{k=p-d}^{p-1} w_mm(c_k) + w_mt(c_p) )
+ * with all V read at the start of the layer.  Longer segments wrap a full
+ * cycle and cannot improve (every finite edge costs at least 1).
+ * Tie reading: a label is written only on strict improvement, and among
+ * equal-cost entries the one furthest upstream (largest d) is recorded; for
+ * the straight lines, which start at the wall, this is exactly what the
+ * sequential Insert 1 loop with a strict comparison records. */
+typedef struct {
+    const uint32_t* Vin;
+    uint32_t* Vout;
+    uint16_t* L;
+    int mu;
+    int64_t improved;
+} layer_io;
+
+/* The definition above, evaluated directly: O(n^2) per cycle. */
+static void relax_cycle_definition(layer_io* io, int n, const int64_t* cell, const uint32_t* w_tm,
+                                   const uint32_t* w_mm, const uint32_t* w_mt) {
+    for (int p = 0; p < n; p++) {
+        uint32_t best = ORC_INF;
+        int bd = 0;
+        uint32_t path = 0; /* sum of w_mm over positions p-d .. p-1 */
+        for (int d = 1; d < n; d++) {
+            int s = ((p - d) % n + n) % n;
+            path = sadd(path, w_mm[s]);
+            uint32_t cand = sadd(sadd(sadd(io->Vin[cell[s]], w_tm[s]), path), w_mt[p]);
+            if (cand != ORC_INF && cand <= best) { best = cand; bd = d; }
+        }
+        if (best < io->Vin[cell[p]]) {
+            io->Vout[cell[p]] = best;
+            io->L[cell[p]] = (uint16_t)((io->mu << 13) | bd);
+            io->improved++;
+        }
+    }
+}
+
+/* The same relaxation as the sequential loop of Insert 1 run over the cycle
+ * twice (Section VIII.B): the first loop warms the carried value up, the
+ * second stores.  The carry keeps the entry position; a new entry replaces it
+ * only when strictly cheaper, so ties keep the earlier (further upstream)
+ * entry. */
+static void relax_cycle_scan(layer_io* io, int n, const int64_t* cell, const uint32_t* w_tm,
+                             const uint32_t* w_mm, const uint32_t* w_mt) {
+    uint32_t v = ORC_INF;
+    int qe = 0;
+    for (int q = 0; q < 2 * n; q++) {
+        int k = q % n;
+        uint32_t u = io->Vin[cell[k]];
+        if (q >= n) {
+            uint32_t cand = sadd(v, w_mt[k]);
+            if (cand < u) {
+                io->Vout[cell[k]] = cand;
+                io->L[cell[k]] = (uint16_t)((io->mu << 13) | (q - qe));
+                io->improved++;
+            }
+        }
+        uint32_t t = sadd(u, w_tm[k]);
+        if (t < v) { v = t; qe = q; }
+        v = sadd(v, w_mm[k]);
+    }
+}
+
+/* mode 0 / 2: explicit edge list, cycles found by following succ pointers. */
+static int layer_edgelist(const star_graph* g, int mu, layer_io* io, int use_definition) {
+    int64_t nr = g->nr;
+    uint8_t* seen = (uint8_t*)calloc((size_t)nr, 1);
+    int64_t* cyc = (int64_t*)malloc(sizeof(int64_t) * 8192);
+    uint32_t* a = (uint32_t*)malloc(sizeof(uint32_t) * 3 * 8192);
+    if (!seen || !cyc || !a) { free(seen); free(cyc); free(a); return -1; }
+    uint32_t *wtm = a, *wmm = a + 8192, *wmt = a + 2 * 8192;
+    for (int64_t x0 = 0; x0 < nr; x0++) {
+        if (seen[x0]) continue;
+        int n = 0;
+        int64_t x = x0;
+        while (!seen[x]) {
+            if (n >= 8192) { free(seen); free(cyc); free(a); return -1; }
+            seen[x] = 1;
+            cyc[n] = x;
+            wtm[n] = g->w_tm[mu][x];
+            wmm[n] = g->w_mm[mu][x];
+            wmt[n] = g->w_mt[mu][x];
+            n++;
+            x = g->succ[mu][x];
+        }
+        if (x != x0) { free(seen); free(cyc); free(a); return -1; } /* not a permutation */
+        if (use_definition) relax_cycle_definition(io, n, cyc, wtm, wmm, wmt);
+        else relax_cycle_scan(io, n, cyc, wtm, wmm, wmt);
+    }
+    free(seen); free(cyc); free(a);
+    return 0;
+}
+
+/* mode 1: edges evaluated on the fly; all cycles of the maneuver advance in
+ * lockstep (as the paper's threads do), each started at one cell of its own:
+ * turn chains at their heading-0 cell, straight lines at their wall cell.
+ * Each chain is checked to close after n steps. */
+static int layer_lockstep(const orc_ctx* c, const uint16_t* B, int mu, layer_io* io) {
+    int nx = c->nx;
+    int64_t nchains;
+    int n;
+    if (is_turn(mu)) { nchains = (int64_t)nx * nx; n = c->nt; }
+    else { nchains = nx; n = nx; }
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * nchains);
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * nchains);
+    uint32_t* v = (uint32_t*)malloc(sizeof(uint32_t) * nchains);
+    int32_t* qe = (int32_t*)malloc(sizeof(int32_t) * nchains);
+    if (!start || !cur || !v || !qe) { free(start); free(cur); free(v); free(qe); return -1; }
+    int rc = 0;
+    int nplanes = is_turn(mu) ? 1 : c->nt;
+    for (int plane = 0; plane < nplanes && rc == 0; plane++) {
+        for (int64_t k = 0; k < nchains; k++) {
+            if (is_turn(mu)) start[k] = k; /* cells of heading plane 0 */
+            else start[k] = c->iflag[plane] == 0 ? cell_of(c, 0, (int)k, plane) : cell_of(c, (int)k, 0, plane);
+            cur[k] = start[k];
+            v[k] = ORC_INF;
+            qe[k] = 0;
+        }
+        for (int q = 0; q < 2 * n; q++) {
+            for (int64_t k = 0; k < nchains; k++) {
+                int64_t x = cur[k];
+                int hard = B[x] == ORC_HARD;
+                uint32_t u = io->Vin[x];
+                if (q >= n) {
+                    uint32_t cand = hard ? ORC_INF : v[k];
+                    if (cand < u) {
+                        io->Vout[x] = cand;
+                        io->L[x] = (uint16_t)((io->mu << 13) | (q - qe[k]));
+                        io->improved++;
+                    }
+                }
+                uint32_t t = hard ? ORC_INF : sadd(u, c->ct);
+                if (t < v[k]) { v[k] = t; qe[k] = q; }
+                v[k] = sadd(v[k], orc_edge(c, B, mu, x));
+                cur[k] = orc_succ(c, mu, x);
+            }
+            if (q == n - 1)
+                for (int64_t k = 0; k < nchains; k++)
+                    if (cur[k] != start[k]) rc = -1;
+        }
+    }
+    free(start); free(cur); free(v); free(qe);
+    return rc;
+}
+
+static const int cycle_order[6] = {LF, SF, RB, RF, SB, LB}; /* Section XVI.A */
+
+int orc_layers(const orc_ctx* c, const uint16_t* B, int first_layer, int n_layers, int mode,
+               uint32_t* V, uint16_t* L, int64_t* improved) {
+    if (mode < 0 || mode > 2 || n_layers < 0 || first_layer < 0) return -1;
+    star_graph g;
+    int have_graph = 0;
+    if (mode != 1) {
+        if (graph_build(c, B, &g) != 0) return -1;
+        have_graph = 1;
+    }
+    uint32_t* Vin = (uint32_t*)malloc(sizeof(uint32_t) * c->nr);
+    if (!Vin) { if (have_graph) graph_free(&g); return -1; }
+    int rc = 0;
+    for (int l = 0; l < n_layers && rc == 0; l++) {
+        int mu = cycle_order[(first_layer + l) % 6];
+        memcpy(Vin, V, sizeof(uint32_t) * c->nr);
+        layer_io io = {Vin, V, L, mu, 0};
+        if (mode == 1) rc = layer_lockstep(c, B, mu, &io);
+        else rc = layer_edgelist(&g, mu, &io, mode == 2);
+        if (improved) improved[l] = io.improved;
+    }
+    free(Vin);
+    if (have_graph) graph_free(&g);
+    return rc;
+}
+
+int orc_sweep(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, int mode,
+              uint32_t* V, uint16_t* L, int64_t* improved) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD || n_cycles < 0) return -1;
+    for (int64_t x = 0; x < c->nr; x++) { V[x] = ORC_INF; L[x] = ORC_NONE; }
+    V[start] = 0;
+    return orc_layers(c, B, 0, 6 * n_cycles, mode, V, L, improved);
+}
+
+/* ----------------------------------------------------- Dijkstra (Section VIII.A)
+ * Indexed binary heap kept in two arrays, heap position of a vertex and the
+ * vertex at a heap position, keyed by the value array itself. */
+typedef struct {
+    uint32_t* key;
+    int64_t* heap;
+    int64_t* pos;
+    int64_t n;
+} iheap;
+
+static void heap_swap(iheap* h, int64_t a, int64_t b) {
+    int64_t va = h->heap[a], vb = h->heap[b];
+    h->heap[a] = vb; h->heap[b] = va;
+    h->pos[vb] = a; h->pos[va] = b;
+}
+static void heap_up(iheap* h, int64_t k) {
+    while (k > 0) {
+        int64_t p = (k - 1) / 2;
+        if (h->key[h->heap[p]] <= h->key[h->heap[k]]) break;
+        heap_swap(h, p, k);
+        k = p;
+    }
+}
+static void heap_down(iheap* h, int64_t k) {
+    for (;;) {
+        int64_t l = 2 * k + 1, r = l + 1, m = k;
+        if (l < h->n && h->key[h->heap[l]] < h->key[h->heap[m]]) m = l;
+        if (r < h->n && h->key[h->heap[r]] < h->key[h->heap[m]]) m = r;
+        if (m == k) break;
+        heap_swap(h, m, k);
+        k = m;
+    }
+}
+
+int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* Vinf) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD) return -1;
+    star_graph g;
+    if (graph_build(c, B, &g) != 0) return -1;
+    int64_t nr = c->nr, nv = 7 * nr; /* vertex 0..nr-1: T(X); (1+mu)*nr + X: M_mu(X) */
+    iheap h;
+    h.key = (uint32_t*)malloc(sizeof(uint32_t) * nv);
+    h.heap = (int64_t*)malloc(sizeof(int64_t) * nv);
+    h.pos = (int64_t*)malloc(sizeof(int64_t) * nv);
+    uint8_t* done = (uint8_t*)calloc((size_t)nv, 1);
+    if (!h.key || !h.heap || !h.pos || !done) {
+        free(h.key); free(h.heap); free(h.pos); free(done); graph_free(&g); return -1;
+    }
+    for (int64_t v = 0; v < nv; v++) { h.key[v] = ORC_INF; h.pos[v] = -1; }
+    h.key[start] = 0;
+    h.heap[0] = start; h.pos[start] = 0; h.n = 1;
+#define RELAX(dst, w)                                                   \
+    do {                                                                \
+        uint32_t nd_ = sadd(du, (w));                                   \
+        int64_t d_ = (dst);                                             \
+        if (nd_ < h.key[d_] && !done[d_]) {                             \
+            h.key[d_] = nd_;                                            \
+            if (h.pos[d_] < 0) { h.heap[h.n] = d_; h.pos[d_] = h.n; h.n++; } \
+            heap_up(&h, h.pos[d_]);                                     \
+        }                                                               \
+    } while (0)
+    while (h.n > 0) {
+        int64_t u = h.heap[0];
+        heap_swap(&h, 0, h.n - 1);
+        h.n--;
+        h.pos[u] = -1;
+        if (h.n > 0) heap_down(&h, 0);
+        done[u] = 1;
+        uint32_t du = h.key[u];
+        if (du == ORC_INF) break;
+        if (u < nr) {
+            for (int m = 0; m < 6; m++) RELAX((1 + m) * nr + u, g.w_tm[m][u]);
+        } else {
+            int m = (int)(u / nr) - 1;
+            int64_t x = u % nr;
+            RELAX(x, g.w_mt[m][x]);
+            RELAX((1 + m) * nr + g.succ[m][x], g.w_mm[m][x]);
+        }
+    }
+#undef RELAX
+    for (int64_t x = 0; x < nr; x++) Vinf[x] = B[x] == ORC_HARD ? ORC_INF : h.key[x];
+    free(h.key); free(h.heap); free(h.pos); free(done); graph_free(&g);
+    return 0;
+}
+
+/* ------------------------------------------------------------ brute force
+ * Enumerate every sequence of at most one maneuver segment per layer (layers
+ * in the cycle order), every segment length 1..n-1, starting at T(start);
+ * a path prefix that reaches (layer, cell) no cheaper than an earlier one is
+ * dropped, because what can follow depends only on (layer, cell). */
+typedef struct {
+    const orc_ctx* c;
+    const uint16_t* B;
+    int layers;
+    uint32_t* seen; /* [layer][cell] */
+    uint32_t* best;
+} bf_state;
+
+static void bf_explore(bf_state* s, int layer, int64_t x, uint32_t cost) {
+    const orc_ctx* c = s->c;
+    uint32_t* sl = s->seen + (size_t)layer * c->nr;
+    if (cost >= sl[x]) return;
+    sl[x] = cost;
+    if (cost < s->best[x]) s->best[x] = cost;
+    if (layer == s->layers) return;
+    bf_explore(s, layer + 1, x, cost); /* no segment in this layer */
+    int mu = cycle_order[layer % 6];
+    int n = is_turn(mu) ? c->nt : c->nx;
+    uint32_t run = sadd(cost, c->ct);
+    int64_t y = x;
+    for (int d = 1; d < n; d++) {
+        run = sadd(run, orc_edge(c, s->B, mu, y));
+        y = orc_succ(c, mu, y);
+        if (run == ORC_INF) break;
+        if (s->B[y] != ORC_HARD) bf_explore(s, layer + 1, y, run);
+    }
+}
+
+int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* Vbest) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD) return -1;
+    bf_state s = {c, B, 6 * n_cycles, NULL, Vbest};
+    s.seen = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(s.layers + 1) * c->nr);
+    if (!s.seen) return -1;
+    for (int64_t k = 0; k < (int64_t)(s.layers + 1) * c->nr; k++) s.seen[k] = ORC_INF;
+    for (int64_t x = 0; x < c->nr; x++) Vbest[x] = ORC_INF;
+    bf_explore(&s, 0, start, 0);
+    free(s.seen);
+    return 0;
+}
+
+/* ------------------------------------------------------------ extraction
+ * Forward tracking (Section X): each label names the maneuver and how many
+ * steps back its entry lies.  The entry is reached by walking the reverse
+ * maneuver (eqs. 25-31 are exactly reversible: LF<->LB, RF<->RB, SF<->SB,
+ * which in cycle-order numbering is mu -> 5 - mu). */
+int orc_extract(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal,
+                int64_t* seg, int cap) {
+    if (goal < 0 || goal >= c->nr) return -3;
+    if (V[goal] == ORC_INF) return -1;
+    int n = 0;
+    int64_t x = goal;
+    int guard = 0;
+    while (L[x] != ORC_NONE) {
+        if (++guard > 1 << 20) return -3;
+        int mu = L[x] >> 13, d = L[x] & 8191;
+        if (mu > 5 || d == 0) return -3;
+        int64_t e = x;
+        for (int k = 0; k < d; k++) e = orc_succ(c, 5 - mu, e);
+        if (n < cap) {
+            int64_t* r = seg + 6 * (size_t)n;
+            r[0] = mu; r[1] = e; r[2] = x; r[3] = d;
+            r[4] = (int64_t)(V[x] & 0xFFFF); r[5] = (int64_t)(V[x] >> 16);
+        }
+        n++;
+        x = e;
+    }
+    if (V[x] != 0) return -3;
+    if (n > cap) return -2;
+    for (int a = 0, b = n - 1; a < b; a++, b--)
+        for (int k = 0; k < 6; k++) {
+            int64_t t = seg[6 * a + k];
+            seg[6 * a + k] = seg[6 * b + k];
+            seg[6 * b + k] = t;
+        }
+    return n;
+}
+
+/* ----------------------------------------------------------- soft obstacles
+ * Only distances below the radius matter, and any occupied cell at squared
+ * distance < r^2 lies inside the (2r-1)^2 window, so the window search gives
+ * the exact penalty.  Cells outside the image do not count as occupied. */
+void orc_soft_image(int nx, const uint8_t* occ, int radius, int soft_max, uint16_t* img) {
+    int r2 = radius * radius;
+    for (int y = 0; y < nx; y++)
+        for (int x = 0; x < nx; x++) {
+            if (occ[(size_t)y * nx + x]) { img[(size_t)y * nx + x] = ORC_HARD; continue; }
+            int best = -1;
+            for (int yy = y - radius + 1; yy <= y + radius - 1; yy++)
+                for (int xx = x - radius + 1; xx <= x + radius - 1; xx++)
+                    if (yy >= 0 && yy < nx && xx >= 0 && xx < nx && occ[(size_t)yy * nx + xx]) {
+                        int d2 = (xx - x) * (xx - x) + (yy - y) * (yy - y);
+                        if (best < 0 || d2 < best) best = d2;
+                    }
+            int pen = (best >= 0 && best < r2) ? soft_max * (r2 - best) / r2 : 0;
+            img[(size_t)y * nx + x] = (uint16_t)(256 + pen);
+        }
+}

@@ -1,0 +1,93 @@
+/*
+ * nhp_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, single-threaded CPU oracle for the kernel-style N-turn sweep of
+ * Nister et al., "Nonholonomic Motion Planning as Efficient as Piano Mover's"
+ * (arXiv 2306.01301).  It exists to check the CUDA library bit for bit.  It
+ * shares no code, header, table or constant with the library under
+ * paper_2306_01301_b300/; only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline leg may load it.
+ *
+ * Conventions (all integer, all exact):
+ *   cell index  idx = i + Nx*(j + Nx*T)   (i = x column, j = y row, T = heading)
+ *   value INF   0xFFFFFFFF, saturating uint32 addition
+ *   obstacle    uint16 Q8 reciprocal velocity, 256 = free, 0xFFFF = HARD
+ *   label       (mu << 13) | d, NONE = 0xFFFF; mu is the cycle-order index
+ *               LF=0 SF=1 RB=2 RF=3 SB=4 LB=5 (Section XVI.A), d = steps
+ *               from the entry cell of the maneuver segment to this cell.
+ */
+#ifndef NHP_ORACLE_H
+#define NHP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_ctx orc_ctx;
+
+/* Grid + vehicle + cost description.  R in cells, costs in integer units. */
+orc_ctx* orc_create(int nx_log2, int nt_log2, double R, int half_shift,
+                    uint32_t step_straight, uint32_t step_scale, uint32_t ct);
+void     orc_destroy(orc_ctx* c);
+
+/* Geometry tables (Section V.C, eqs. 11-24).  Arrays are caller-owned:
+ * beta[nt], psi2[nt] (2*Psi), iflag[nt], jsign[nt], bshear[nt*nx] (B(y',T) at
+ * [T*nx + y']), wS[nt]; *wA gets the turn step weight. */
+void orc_tables(const orc_ctx* c, int32_t* beta, uint8_t* psi2, uint8_t* iflag,
+                int8_t* jsign, int32_t* bshear, uint32_t* wS, uint32_t* wA);
+
+/* Footprint offsets of heading T (Section VI; rectangle read of Fig. 6):
+ * writes up to cap (dx,dy) pairs, returns the count (or -needed if cap small). */
+int orc_footprint(const orc_ctx* c, int front, int rear, int hw, int T,
+                  int32_t* dx, int32_t* dy, int cap);
+
+/* Obstacle volume B (Section VI), full volume or selected cells. */
+int orc_render(const orc_ctx* c, const uint16_t* img, int front, int rear, int hw,
+               uint16_t* B);
+int orc_render_cells(const orc_ctx* c, const uint16_t* img, int front, int rear,
+                     int hw, const int64_t* cells, int64_t n, uint16_t* out);
+
+/* Successor of cell under maneuver mu (eqs. 25-28, 30-31). */
+int64_t orc_succ(const orc_ctx* c, int mu, int64_t cell);
+
+/* Edge weight leaving cell under maneuver mu (Section V.D + Insert 1). */
+uint32_t orc_edge(const orc_ctx* c, const uint16_t* B, int mu, int64_t cell);
+
+/* Layered relaxation (Section VIII.B), N cycles in the order of Section XVI.A.
+ * mode 0: explicit Star-graph edge list, cycles found by pointer following;
+ * mode 1: same relaxation, edges evaluated on the fly, chains in lockstep;
+ * mode 2: explicit edge list, each cycle relaxed by the O(n^2) definition.
+ * improved[6N] (optional) receives the number of strictly improved cells per
+ * layer.  Returns 0, or -1 on bad input / allocation failure. */
+int orc_sweep(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles,
+              int mode, uint32_t* V, uint16_t* L, int64_t* improved);
+
+/* Continue an existing (V, L) by more layers starting at layer index
+ * first_layer (so first_layer % 6 selects the maneuver). */
+int orc_layers(const orc_ctx* c, const uint16_t* B, int first_layer, int n_layers,
+               int mode, uint32_t* V, uint16_t* L, int64_t* improved);
+
+/* Full Dijkstra on the explicit Star graph (Section VIII.A): V_inf. */
+int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* Vinf);
+
+/* Exhaustive search over layer-ordered segment sequences (tiny grids). */
+int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles,
+                   uint32_t* Vbest);
+
+/* Label walk from goal (Section X, forward tracking).  Writes segments in
+ * driving order: seg[k*6 + {mu, entry, exit, d, cost_lo16, cost_hi16}] as
+ * int64.  Returns segment count, -1 unreachable, -2 cap too small, -3
+ * malformed labels. */
+int orc_extract(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal,
+                int64_t* seg, int cap);
+
+/* Soft-obstacle image (Section VII): HARD where occ != 0, else 256 + pen with
+ * pen = soft_max*(r2-d2)/r2 for squared Euclidean distance d2 < r2 to the
+ * nearest occupied cell, else 256. */
+void orc_soft_image(int nx, const uint8_t* occ, int radius, int soft_max, uint16_t* img);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
