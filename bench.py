@@ -1,0 +1,289 @@
+"""Benchmark: the 512^3 parallel-parking plan (N = 8 maneuver cycles).
+
+One step = one whole plan through the hot path: c-space obstacle rendering,
+4N + 1 fused maneuver sweeps (6N maneuver layers) and goal lookup + label
+walk.  Metric: pose-cell updates per second, one update being one pose cell
+processed by one maneuver layer (6 * N * Nx^2 * N_theta per plan); plans/s is
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU; the planner does
+not shard, so every rank plans its own replica (weak scaling) and no
+collective touches the data path.  --impl reference times the CPU oracle
+(the repository's own plain restatement of the method) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pose-cell updates/s"
+WORKLOAD = "parallel_parking_512x512x512_N8"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("sweep.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2306_01301_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per turn-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since it was captured."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("source_hash") == source_hash():
+            return t.get("turn_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only query)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(sc, img):
+    """The oracle, as it stands, on a bounded sample: one maneuver cycle (6
+    layers) of the same 512^3 workload on one host core."""
+    import oracle as O
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    B = o.render_rows(img, sc.footprint)
+    t0 = time.perf_counter()
+    o.sweep(B, o.cell(sc.start), 1, mode=1)
+    dt = time.perf_counter() - t0
+    return {"value": 6 * sc.cells / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"1 maneuver cycle (6 layers) of {WORKLOAD}, single-threaded C oracle, "
+                      f"{dt:.1f} s; host has {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2306_01301_b300 import scenes
+    sc = scenes.parallel_parking()
+    img = sc.hard_image()
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    B = o.render_rows(img, sc.footprint)
+    V, L, _ = o.sweep(B, o.cell(sc.start), 0, mode=1)
+    # each step: one maneuver layer of the oracle (a bounded sample of a plan)
+    for k in range(args.warmup):
+        V, L, _ = o.layers(B, V, L, k, 1, mode=1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        V, L, _ = o.layers(B, V, L, args.warmup + k, 1, mode=1)
+    dt = time.perf_counter() - t0
+    value = args.steps * sc.cells / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "step": "one maneuver layer", "threads": 1},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} maneuver layers of {WORKLOAD}"},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2306_01301_b300 import binding, scenes
+    sc = scenes.parallel_parking()
+    img = sc.hard_image()
+    N = sc.n_cycles
+    updates = 6 * N * sc.cells
+    stream = torch.cuda.current_stream()
+    p = binding.Planner.from_scene(sc, img, stream=stream)
+
+    def step():
+        p.render()
+        p.sweep(sc.start, N)
+        return p.extract(sc.goal)
+
+    res = None
+    for _ in range(max(3, args.warmup)):
+        res = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timing (image already in HBM)
+    clocks = ClockSampler(dev)
+    p.profile(True)
+    l0 = p.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = p.kernel_launches() - l0
+    prof = p.profile_read()
+    p.profile(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    value = updates * args.steps * world / sec
+
+    # ---- end to end through the C ABI: host image in, host plan out
+    pinned = torch.from_numpy(img).pin_memory()
+    host_img = pinned.numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nseg = 0
+    for _ in range(args.steps):
+        p.set_image(host_img)
+        r = step()
+        nseg = len(r.segments) if r else 0
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = img.nbytes
+    d2h = 8 + 36 * nseg
+
+    peak, peak_kind = load_peaks()
+    turn_launch_ms = prof["turn_ms"] / max(1, prof["turn_passes"])
+    turn_bytes = sc.cells * 6 + 6 * prof["turn_improved"] / max(1, prof["turn_passes"])
+    achieved = turn_bytes / (turn_launch_ms / 1e3) / 1e9
+    straight_launch_ms = prof["straight_ms"] / max(1, prof["straight_passes"])
+    straight_bytes = sc.cells * 6 + 6 * prof["straight_improved"] / max(1, prof["straight_passes"])
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "512x512x512", "n_cycles": N, "vehicle_cells": "96x38",
+                   "turn_radius_cells": sc.turn_radius, "gear_cost": sc.transition,
+                   "parallelism": f"replicas{world}", "l2": "inputs_larger_than_L2 (V+L+B = 1 GiB)"},
+        "plans_per_s": args.steps * world / sec,
+        "plan_cost": res.cost if res else None, "plan_maneuvers": len(res.segments) if res else 0,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "k_turn (fused turn-pair sweep)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(), "bytes_per_launch": turn_bytes, "launch_ms": turn_launch_ms},
+        "kernels": {"turn_ms_per_launch": turn_launch_ms, "straight_ms_per_launch": straight_launch_ms,
+                    "straight_GBps": straight_bytes / (straight_launch_ms / 1e3) / 1e9,
+                    "render_ms_per_step": prof["render_ms"] / max(1, prof["render_passes"]),
+                    "init_ms_per_step": prof["init_ms"] / max(1, prof["init_passes"])},
+        "e2e": {"value": updates * args.steps * world / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "plans_per_s": args.steps * world / e2e_s},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, img)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    p.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * nhplan.h -- C ABI of the B300 kernel-style nonholonomic planner.
+ *
+ * Implements the data-parallel hot path of Nister et al., "Nonholonomic
+ * Motion Planning as Efficient as Piano Mover's" (arXiv 2306.01301):
+ * configuration-space obstacle rendering (Section VI), kernel-style
+ * processing of the Star graph by maneuver sweeps (Section VIII.B-C, Insert
+ * 1, cycle order of Section XVI.A) and forward-tracking plan extraction
+ * (Sections IX-X).  All compute runs in hand-written sm_103a CUDA kernels;
+ * there is no CPU fallback.
+ *
+ * Data model
+ *   Grid      Nx = Ny = 2^nx_log2 cells, N_theta = 2^ntheta_log2 headings
+ *             (Section V.C).  Heading T stands for theta = 2*pi*T/N_theta.
+ *   Layout    every volume is theta-major, x fastest:
+ *             idx(i, j, T) = i + Nx*(j + Nx*T)  (i = x column, j = y row).
+ *   Image     uint16 [Nx][Nx] (row j, column i), Q8 reciprocal of the highest
+ *             velocity (Section VI): 256 = free, larger = slower, 0xFFFF =
+ *             hard.  Non-hard values must be >= 256.
+ *   B         uint16 obstacle volume: max of the image over the vehicle
+ *             footprint at that pose, 0xFFFF where the footprint touches a
+ *             hard cell or the one-cell walls at i = 0 and j = 0 (Section V.C).
+ *   V         uint32 value of the transition state (Section V.A: the only
+ *             volume kernel-style processing keeps), PLAN_INF = unreached.
+ *             Costs are fixed-point integers with saturating addition.
+ *   L         uint16 forward-tracking label (Section X): (mu << 13) | d, where
+ *             mu is the maneuver in cycle-order numbering
+ *             LF=0 SF=1 RB=2 RF=3 SB=4 LB=5 and d (1 <= d < 8192) the number of
+ *             steps from the segment's entry cell; PLAN_LABEL_NONE where V was
+ *             never improved.  Labels are written only on strict improvement;
+ *             among equally cheap entries the one furthest upstream wins.
+ *   Edge cost leaving a non-hard cell X along maneuver mu:
+ *             (w_mu * B(X)) >> 8, w = round(step_scale * 2*pi*R / N_theta) for
+ *             turns and round(step_straight / max(|cos|,|sin|)) for straights
+ *             (Section V.D); entering any maneuver costs `transition` (Star
+ *             graph transition edges, Section V.A).
+ *
+ * Ownership and threading
+ *   Host inputs are copied during the call; the caller keeps them.  Device
+ *   volumes belong to the plan until plan_destroy.  A plan is not re-entrant;
+ *   all its work is ordered on the stream given at creation.  Calls marked
+ *   "async" enqueue work and return; plan_extract and plan_copy_volumes
+ *   synchronise the plan's stream.
+ *
+ * Errors
+ *   Every entry point returns PLAN_OK (0) or a negative PLAN_E* code; no
+ *   entry point aborts the process.  plan_strerror() names the code.
+ */
+#ifndef NHPLAN_H
+#define NHPLAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PLAN_OK 0
+#define PLAN_EINVAL (-1)       /* bad dimensions, pose, radius, costs, image value */
+#define PLAN_ENOMEM (-2)       /* allocator returned NULL */
+#define PLAN_ECUDA (-3)        /* a CUDA runtime call failed */
+#define PLAN_ETIMEOUT (-4)     /* a bounded device wait gave up */
+#define PLAN_EUNREACHABLE (-5) /* goal value is PLAN_INF */
+#define PLAN_ERANGE (-6)       /* output capacity too small, or costs could overflow */
+#define PLAN_EINTERNAL (-7)    /* device-side consistency check failed */
+#define PLAN_ESTATE (-8)       /* call out of order (e.g. sweep before render) */
+
+#define PLAN_INF 0xFFFFFFFFu
+#define PLAN_HARD 0xFFFFu
+#define PLAN_LABEL_NONE 0xFFFFu
+
+#define PLAN_FLAG_HALF_SHIFT 1u /* eqs. 13-16: quarter-cell turn rounding */
+
+typedef struct plan_s plan_t;
+
+typedef struct {
+    int32_t x, y, theta; /* integer cell indices: 0 <= x, y < Nx, 0 <= theta < N_theta */
+} plan_pose;
+
+typedef struct {
+    uint32_t step_straight; /* cost of one unit straight step at theta = 0 (e.g. 100) */
+    uint32_t step_scale;    /* cost per cell of arc length (e.g. 100) */
+    uint32_t transition;    /* ct: cost of entering any maneuver (gear/steer change), < 2^28 */
+    uint32_t flags;         /* PLAN_FLAG_* */
+} plan_costs;
+
+typedef struct {
+    int32_t nx_log2;       /* 2..12 */
+    int32_t ntheta_log2;   /* 2..10 */
+    const uint16_t* image; /* host pointer, Nx*Nx values, see "Image" above */
+} plan_grid;
+
+typedef struct {
+    /* Closed rectangle [-rear, front] x [-half_width, half_width] in cells,
+     * origin at the rear axle (Fig. 6); all zero = point vehicle. */
+    int32_t front, rear, half_width;
+} plan_footprint;
+
+typedef struct {
+    /* Device memory provider.  alloc returns NULL on failure; free receives
+     * the same byte count.  `stream` is the plan's cudaStream_t. */
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} plan_allocator;
+
+typedef struct {
+    int32_t maneuver;   /* cycle-order id LF=0 SF=1 RB=2 RF=3 SB=4 LB=5 */
+    plan_pose entry;    /* transition point where the maneuver starts */
+    plan_pose exit;     /* transition point where it ends */
+    int32_t steps;      /* maneuver edges followed */
+    uint32_t cost;      /* V at the exit pose */
+} plan_segment;
+
+/* Create a plan for one grid shape, vehicle and cost model (the role of
+ * Appendix G's `ini`).  turn_radius_cells = R = 1/k_max in cells (> 0).
+ * allocator NULL uses cudaMalloc/cudaFree.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream).  Copies the image to the device.  On
+ * success *out owns the device volumes V, L, B (8 bytes per pose cell) plus
+ * an image-sized scratch table. */
+int plan_create(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
+                const plan_costs* costs, const plan_allocator* allocator, void* cuda_stream,
+                plan_t** out);
+
+/* Replace the obstacle image (host pointer, Nx*Nx uint16).  The copy is
+ * enqueued on the plan's stream; the host buffer may be reused on return. */
+int plan_set_image(plan_t* plan, const uint16_t* image);
+
+/* Section VI: render the obstacle volume B from the image and the footprint
+ * (walls of Section V.C included).  Async. */
+int plan_render_cspace(plan_t* plan);
+
+/* Section VIII.B: V <- INF, L <- NONE, V[start] <- 0, then n_cycles cycles of
+ * the six maneuver sweeps in the order LF, SF, RB, RF, SB, LB (Section XVI.A).
+ * Requires a rendered obstacle volume (PLAN_ESTATE otherwise) and a non-hard
+ * start (PLAN_EINVAL; checked on the host from the image and the footprint).
+ * Async.  Returns
+ * PLAN_ERANGE if finite costs could reach 2^30 for this image and cycle
+ * count. */
+int plan_sweep(plan_t* plan, plan_pose start, int n_cycles);
+
+/* Sections IX-X: read V at the exact goal pose and follow the labels back to
+ * the start.  Writes at most `cap` segments in driving order to `out` (host),
+ * sets *n_out to the number of segments (also when cap is too small:
+ * PLAN_ERANGE) and *cost to V(goal).  Synchronises.  PLAN_EUNREACHABLE (with
+ * *n_out = 0, *cost = PLAN_INF) if the goal was not reached. */
+int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out,
+                 uint32_t* cost);
+
+/* Copy the device volumes to host buffers (any may be NULL): V (uint32),
+ * L (uint16), B (uint16), Nx*Nx*N_theta entries each.  Synchronises. */
+int plan_copy_volumes(plan_t* plan, uint32_t* V, uint16_t* L, uint16_t* B);
+
+/* Device pointers of the volumes (owned by the plan). */
+int plan_device_volumes(plan_t* plan, uint32_t** V, uint16_t** L, uint16_t** B);
+
+/* Per-pass timing and work counters, for roofline accounting.  While
+ * profiling is on, plan_render_cspace and plan_sweep record a CUDA event pair
+ * around each kernel pass on the plan's stream, and the sweep kernels count
+ * the cells whose value strictly decreased (the cells they write).  Counting
+ * adds one atomic per warp; timing adds two event records per pass. */
+typedef struct {
+    int64_t turn_passes;      /* fused or single turn sweeps */
+    int64_t straight_passes;
+    int64_t render_passes;    /* sparse table + render */
+    int64_t init_passes;
+    double turn_ms, straight_ms, render_ms, init_ms; /* summed event times */
+    uint64_t turn_improved;   /* cells written by turn passes */
+    uint64_t straight_improved;
+} plan_profile_stats;
+
+/* Turn profiling on (enable != 0) or off; either way the counters restart. */
+int plan_profile(plan_t* plan, int enable);
+
+/* Read the counters accumulated since plan_profile(plan, 1).  Synchronises. */
+int plan_profile_read(plan_t* plan, plan_profile_stats* out);
+
+/* Number of CUDA kernels launched by this plan since creation. */
+int plan_kernel_launches(plan_t* plan, int64_t* count);
+
+int plan_destroy(plan_t* plan);
+
+const char* plan_strerror(int code);
+
+/* Section VII, host helper: soft-obstacle image from a binary occupancy map
+ * [nx][nx] (nonzero = obstacle).  Obstacle cells become 0xFFFF; a free cell at
+ * squared Euclidean distance d2 from the nearest obstacle gets
+ * 256 + soft_max*(r2 - d2)/r2 (integer division) when d2 < r2 = radius^2, else
+ * 256.  radius 0 gives the hard-only image.  Returns PLAN_EINVAL for bad
+ * arguments (nx <= 0, radius < 0 or > 255, soft_max < 0 or > 65000). */
+int plan_soft_image(int nx, const uint8_t* occupancy, int radius, int soft_max, uint16_t* image);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NHPLAN_H */

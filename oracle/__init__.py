@@ -61,6 +61,8 @@ def lib():
         L.orc_footprint.argtypes = [p, C.c_int, C.c_int, C.c_int, C.c_int, p, p, C.c_int]
         L.orc_render.restype = C.c_int
         L.orc_render.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p]
+        L.orc_render_rows.restype = C.c_int
+        L.orc_render_rows.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p]
         L.orc_render_cells.restype = C.c_int
         L.orc_render_cells.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p, C.c_int64, p]
         L.orc_succ.restype = C.c_int64
@@ -141,6 +143,14 @@ class Oracle:
         img = np.ascontiguousarray(img, dtype=np.uint16)
         B = np.zeros(self.nr, np.uint16)
         if lib().orc_render(self._c, _ptr(img), *[int(v) for v in footprint], _ptr(B)) != 0:
+            raise MemoryError
+        return B
+
+    def render_rows(self, img: np.ndarray, footprint) -> np.ndarray:
+        """Same volume as render(), by row runs and sliding maxima (fast)."""
+        img = np.ascontiguousarray(img, dtype=np.uint16)
+        B = np.zeros(self.nr, np.uint16)
+        if lib().orc_render_rows(self._c, _ptr(img), *[int(v) for v in footprint], _ptr(B)) != 0:
             raise MemoryError
         return B
 

@@ -223,6 +223,80 @@ int orc_render(const orc_ctx* c, const uint16_t* img, int front, int rear, int h
     return 0;
 }
 
+/* Same volume, grouped by footprint rows: each row of the footprint is a run
+ * of cells [lo, lo+w) at offset dy, and the maximum over a run is a sliding
+ * window maximum of width w along image rows, which Section VI notes costs a
+ * constant number of comparisons per sample regardless of the width (the van
+ * Herk / Gil-Werman block method: prefix maxima from each block start and
+ * suffix maxima from each block end, window = max(suffix at x, prefix at
+ * x+w-1)).  Rows are cyclic (coordinates modulo Nx). */
+static void window_max_rows(const orc_ctx* c, const uint16_t* img, int w, uint16_t* out,
+                            uint16_t* ext, uint16_t* pre, uint16_t* suf) {
+    int nx = c->nx;
+    int len = nx + w - 1; /* the row extended cyclically */
+    int nblk = (len + w - 1) / w;
+    int plen = nblk * w;
+    for (int y = 0; y < nx; y++) {
+        for (int x = 0; x < plen; x++) ext[x] = x < len ? img_at(c, img, x, y) : 0;
+        for (int b = 0; b < nblk; b++) {
+            int a = b * w;
+            pre[a] = ext[a];
+            for (int x = a + 1; x < a + w; x++) pre[x] = ext[x] > pre[x - 1] ? ext[x] : pre[x - 1];
+            suf[a + w - 1] = ext[a + w - 1];
+            for (int x = a + w - 2; x >= a; x--) suf[x] = ext[x] > suf[x + 1] ? ext[x] : suf[x + 1];
+        }
+        for (int x = 0; x < nx; x++) {
+            uint16_t s1 = suf[x], p1 = pre[x + w - 1];
+            out[(size_t)y * nx + x] = s1 > p1 ? s1 : p1;
+        }
+    }
+}
+
+int orc_render_rows(const orc_ctx* c, const uint16_t* img, int front, int rear, int hw, uint16_t* B) {
+    int lim = footprint_reach(front, rear, hw);
+    int cap = (2 * lim + 1) * (2 * lim + 1);
+    int nx = c->nx;
+    size_t plane = (size_t)nx * nx;
+    int wmax = 2 * lim + 1;
+    int32_t* dx = (int32_t*)malloc(sizeof(int32_t) * cap);
+    int32_t* dy = (int32_t*)malloc(sizeof(int32_t) * cap);
+    uint16_t* win = (uint16_t*)malloc(sizeof(uint16_t) * plane * (size_t)(wmax + 1));
+    uint8_t* have = (uint8_t*)malloc((size_t)wmax + 1);
+    int buf = 2 * (nx + wmax) + 2 * wmax;
+    uint16_t* ext = (uint16_t*)malloc(sizeof(uint16_t) * buf);
+    uint16_t* pre = (uint16_t*)malloc(sizeof(uint16_t) * buf);
+    uint16_t* suf = (uint16_t*)malloc(sizeof(uint16_t) * buf);
+    if (!dx || !dy || !win || !have || !ext || !pre || !suf) {
+        free(dx); free(dy); free(win); free(have); free(ext); free(pre); free(suf);
+        return -1;
+    }
+    memset(have, 0, (size_t)wmax + 1);
+    for (int T = 0; T < c->nt; T++) {
+        int n = orc_footprint(c, front, rear, hw, T, dx, dy, cap);
+        uint16_t* Bt = B + (size_t)T * plane;
+        memset(Bt, 0, plane * sizeof(uint16_t));
+        /* cells come sorted by dy then dx: split each dy into maximal runs */
+        for (int k = 0; k < n;) {
+            int e = k;
+            while (e + 1 < n && dy[e + 1] == dy[k] && dx[e + 1] == dx[e] + 1) e++;
+            int lo = dx[k], w = dx[e] - dx[k] + 1, ry = dy[k];
+            if (!have[w]) { window_max_rows(c, img, w, win + (size_t)w * plane, ext, pre, suf); have[w] = 1; }
+            const uint16_t* W = win + (size_t)w * plane;
+            for (int j = 0; j < nx; j++) {
+                const uint16_t* row = W + (size_t)((j + ry) & c->mx) * nx;
+                uint16_t* out = Bt + (size_t)j * nx;
+                for (int i = 0; i < nx; i++) {
+                    uint16_t v = row[(i + lo) & c->mx];
+                    if (v > out[i]) out[i] = v;
+                }
+            }
+            k = e + 1;
+        }
+    }
+    free(dx); free(dy); free(win); free(have); free(ext); free(pre); free(suf);
+    return 0;
+}
+
 int orc_render_cells(const orc_ctx* c, const uint16_t* img, int front, int rear, int hw,
                      const int64_t* cells, int64_t n, uint16_t* out) {
     int lim = footprint_reach(front, rear, hw);

@@ -45,6 +45,10 @@ int orc_footprint(const orc_ctx* c, int front, int rear, int hw, int T,
 /* Obstacle volume B (Section VI), full volume or selected cells. */
 int orc_render(const orc_ctx* c, const uint16_t* img, int front, int rear, int hw,
                uint16_t* B);
+/* The same B computed row run by row run with sliding-window maxima
+ * (Section VI's constant-cost max filter); used for large grids. */
+int orc_render_rows(const orc_ctx* c, const uint16_t* img, int front, int rear,
+                    int hw, uint16_t* B);
 int orc_render_cells(const orc_ctx* c, const uint16_t* img, int front, int rear,
                      int hw, const int64_t* cells, int64_t n, uint16_t* out);
 

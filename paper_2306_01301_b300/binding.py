@@ -1,0 +1,268 @@
+"""Thin Python binding of the nhplan C ABI (include/nhplan.h).
+
+Argument marshalling only: every step of the planner runs in the library's
+CUDA kernels.  PyTorch provides the device memory (its caching allocator,
+through the C ABI's allocator callbacks) and the CUDA stream.  If the
+compiled library is missing or no CUDA device is present, the calls raise;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libnhplan.so")
+
+PLAN_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNREACHABLE", -6: "ERANGE",
+          -7: "EINTERNAL", -8: "ESTATE"}
+PLAN_EUNREACHABLE = -5
+PLAN_FLAG_HALF_SHIFT = 1
+INF = 0xFFFFFFFF
+MANEUVERS = ("LF", "SF", "RB", "RF", "SB", "LB")
+
+
+class PlanError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})")
+
+
+class Pose(C.Structure):
+    _fields_ = [("x", C.c_int32), ("y", C.c_int32), ("theta", C.c_int32)]
+
+
+class Costs(C.Structure):
+    _fields_ = [("step_straight", C.c_uint32), ("step_scale", C.c_uint32), ("transition", C.c_uint32),
+                ("flags", C.c_uint32)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx_log2", C.c_int32), ("ntheta_log2", C.c_int32), ("image", C.c_void_p)]
+
+
+class Footprint(C.Structure):
+    _fields_ = [("front", C.c_int32), ("rear", C.c_int32), ("half_width", C.c_int32)]
+
+
+class ProfileStats(C.Structure):
+    _fields_ = [("turn_passes", C.c_int64), ("straight_passes", C.c_int64), ("render_passes", C.c_int64),
+                ("init_passes", C.c_int64), ("turn_ms", C.c_double), ("straight_ms", C.c_double),
+                ("render_ms", C.c_double), ("init_ms", C.c_double), ("turn_improved", C.c_uint64),
+                ("straight_improved", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class Segment(C.Structure):
+    _fields_ = [("maneuver", C.c_int32), ("entry", Pose), ("exit", Pose), ("steps", C.c_int32),
+                ("cost", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2306_01301_b300._build`")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.plan_create.restype = C.c_int
+        L.plan_create.argtypes = [C.POINTER(Grid), C.POINTER(Footprint), C.c_double, C.POINTER(Costs),
+                                  C.POINTER(Allocator), vp, C.POINTER(vp)]
+        L.plan_set_image.restype = C.c_int
+        L.plan_set_image.argtypes = [vp, vp]
+        L.plan_render_cspace.restype = C.c_int
+        L.plan_render_cspace.argtypes = [vp]
+        L.plan_sweep.restype = C.c_int
+        L.plan_sweep.argtypes = [vp, Pose, C.c_int]
+        L.plan_extract.restype = C.c_int
+        L.plan_extract.argtypes = [vp, Pose, C.POINTER(Segment), C.c_int, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_uint32)]
+        L.plan_copy_volumes.restype = C.c_int
+        L.plan_copy_volumes.argtypes = [vp, vp, vp, vp]
+        L.plan_device_volumes.restype = C.c_int
+        L.plan_device_volumes.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+        L.plan_profile.restype = C.c_int
+        L.plan_profile.argtypes = [vp, C.c_int]
+        L.plan_profile_read.restype = C.c_int
+        L.plan_profile_read.argtypes = [vp, C.POINTER(ProfileStats)]
+        L.plan_kernel_launches.restype = C.c_int
+        L.plan_kernel_launches.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.plan_destroy.restype = C.c_int
+        L.plan_destroy.argtypes = [vp]
+        L.plan_strerror.restype = C.c_char_p
+        L.plan_strerror.argtypes = [C.c_int]
+        L.plan_soft_image.restype = C.c_int
+        L.plan_soft_image.argtypes = [C.c_int, vp, C.c_int, C.c_int, vp]
+        _lib = L
+    return _lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().plan_strerror(code).decode()
+    except Exception:  # library not loadable while formatting an error
+        return "?"
+
+
+def _check(rc: int, where: str):
+    if rc != PLAN_OK:
+        raise PlanError(rc, where)
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def soft_image(occupancy: np.ndarray, radius: int, soft_max: int) -> np.ndarray:
+    """Section VII soft-obstacle image (library host helper)."""
+    occ = np.ascontiguousarray(occupancy, dtype=np.uint8)
+    img = np.zeros(occ.shape, np.uint16)
+    _check(lib().plan_soft_image(int(occ.shape[0]), _ptr(occ), int(radius), int(soft_max), _ptr(img)),
+           "plan_soft_image")
+    return img
+
+
+@dataclass
+class PlanResult:
+    cost: int
+    segments: List[dict]
+
+
+class _TorchAllocator:
+    """C-ABI allocator callbacks bound to torch's CUDA caching allocator."""
+
+    def __init__(self, torch, stream):
+        self.torch = torch
+        self.stream = stream
+        self.device = stream.device
+
+        def _alloc(nbytes, _stream, _ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _free(ptr, _nbytes, _stream, _ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._fa = ALLOC_FN(_alloc)
+        self._ff = FREE_FN(_free)
+        self.struct = Allocator(self._fa, self._ff, None)
+
+
+class Planner:
+    """One plan: grid shape + image + vehicle + costs, volumes on the GPU."""
+
+    def __init__(self, nx_log2: int, nt_log2: int, image: np.ndarray, footprint: Tuple[int, int, int],
+                 turn_radius: float, transition: int, step_straight: int = 100, step_scale: int = 100,
+                 half_shift: int = 1, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("nhplan needs a CUDA device; there is no CPU fallback")
+        self.torch = torch
+        self.nx_log2, self.nt_log2 = nx_log2, nt_log2
+        self.nx, self.nt = 1 << nx_log2, 1 << nt_log2
+        self.cells = self.nx * self.nx * self.nt
+        self.stream = stream or torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(torch, self.stream)
+        img = np.ascontiguousarray(image, dtype=np.uint16)
+        assert img.shape == (self.nx, self.nx)
+        grid = Grid(nx_log2, nt_log2, img.ctypes.data_as(C.c_void_p))
+        fp = Footprint(*[int(v) for v in footprint])
+        costs = Costs(step_straight, step_scale, transition, PLAN_FLAG_HALF_SHIFT if half_shift else 0)
+        h = C.c_void_p()
+        _check(lib().plan_create(C.byref(grid), C.byref(fp), float(turn_radius), C.byref(costs),
+                                 C.byref(self._alloc.struct), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "plan_create")
+        self._h = h
+
+    @classmethod
+    def from_scene(cls, sc, image: Optional[np.ndarray] = None, stream=None) -> "Planner":
+        if image is None:
+            image = soft_image(sc.occupancy, sc.soft_radius, sc.soft_max) if sc.soft_radius else sc.hard_image()
+        return cls(sc.nx_log2, sc.nt_log2, image, sc.footprint, sc.turn_radius, sc.transition,
+                   sc.step_straight, sc.step_scale, sc.half_shift, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ steps
+    def set_image(self, image: np.ndarray):
+        img = np.ascontiguousarray(image, dtype=np.uint16)
+        _check(lib().plan_set_image(self._h, _ptr(img)), "plan_set_image")
+
+    def render(self):
+        _check(lib().plan_render_cspace(self._h), "plan_render_cspace")
+
+    def sweep(self, start, n_cycles: int):
+        _check(lib().plan_sweep(self._h, Pose(*[int(v) for v in start]), int(n_cycles)), "plan_sweep")
+
+    def extract(self, goal, cap: int = 1024) -> Optional[PlanResult]:
+        segs = (Segment * cap)()
+        n = C.c_int(0)
+        cost = C.c_uint32(0)
+        rc = lib().plan_extract(self._h, Pose(*[int(v) for v in goal]), segs, cap, C.byref(n), C.byref(cost))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_extract")
+        out = [dict(mu=s.maneuver, entry=(s.entry.x, s.entry.y, s.entry.theta),
+                    exit=(s.exit.x, s.exit.y, s.exit.theta), steps=s.steps, cost=s.cost) for s in segs[:n.value]]
+        return PlanResult(int(cost.value), out)
+
+    def plan(self, start, goal, n_cycles: int) -> Optional[PlanResult]:
+        self.render()
+        self.sweep(start, n_cycles)
+        return self.extract(goal)
+
+    # ------------------------------------------------------------ inspection
+    def volumes(self, V=True, L=True, B=True):
+        v = np.empty(self.cells, np.uint32) if V else None
+        l_ = np.empty(self.cells, np.uint16) if L else None
+        b = np.empty(self.cells, np.uint16) if B else None
+        _check(lib().plan_copy_volumes(self._h, _ptr(v) if V else None, _ptr(l_) if L else None,
+                                       _ptr(b) if B else None), "plan_copy_volumes")
+        return v, l_, b
+
+    def device_pointers(self):
+        v, l_, b = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(lib().plan_device_volumes(self._h, C.byref(v), C.byref(l_), C.byref(b)), "plan_device_volumes")
+        return v.value, l_.value, b.value
+
+    def profile(self, enable: bool = True):
+        _check(lib().plan_profile(self._h, 1 if enable else 0), "plan_profile")
+
+    def profile_read(self) -> dict:
+        st = ProfileStats()
+        _check(lib().plan_profile_read(self._h, C.byref(st)), "plan_profile_read")
+        return {f: getattr(st, f) for f, _ in ProfileStats._fields_}
+
+    def kernel_launches(self) -> int:
+        c = C.c_int64(0)
+        _check(lib().plan_kernel_launches(self._h, C.byref(c)), "plan_kernel_launches")
+        return int(c.value)

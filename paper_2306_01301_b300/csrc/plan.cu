@@ -1,0 +1,606 @@
+// plan.cu -- host side of the nhplan C ABI: geometry tables, footprint runs,
+// device memory, the maneuver-cycle schedule and plan extraction.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace nhp;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kDevSegCap = 4096;
+
+void* default_alloc(size_t bytes, void*, void*) {
+    void* p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+void default_free(void* p, size_t, void*, void*) { cudaFree(p); }
+
+size_t round16(size_t b) { return (b + 15) & ~size_t(15); }
+
+}  // namespace
+
+struct plan_s {
+    int lx = 0, lt = 0, nx = 0, nt = 0;
+    int64_t nxy = 0, nr = 0;
+    double R = 0;
+    plan_costs costs{};
+    plan_footprint fp{};
+    cudaStream_t stream = nullptr;
+    plan_allocator alloc{};
+    // host copies
+    std::vector<int4> beta4;
+    std::vector<PlaneInfo> planes;
+    std::vector<int16_t> bshear;
+    std::vector<int32_t> run_off;
+    std::vector<Run> runs;
+    std::vector<int32_t> fp_dx, fp_dy;  // footprint cells of every heading, concatenated
+    std::vector<int32_t> fp_off;
+    std::vector<unsigned char> blob;    // staged table upload
+    std::vector<uint16_t> img;
+    int max_runs = 0;
+    uint32_t wA = 0, w_max = 0;
+    uint32_t img_max_soft = 256;
+    // device
+    unsigned char* d_blob = nullptr;
+    size_t blob_bytes = 0;
+    uint16_t* d_img = nullptr;
+    uint16_t* d_table = nullptr;
+    size_t table_bytes = 0;
+    uint32_t* d_V = nullptr;
+    uint16_t* d_L = nullptr;
+    uint16_t* d_B = nullptr;
+    plan_segment* d_seg = nullptr;
+    int* d_status = nullptr;
+    bool rendered = false;
+    int64_t launches = 0;
+    DevGrid g{};
+    // profiling (plan_profile)
+    bool prof = false;
+    unsigned long long* d_cnt = nullptr;  // [0] turn, [1] straight improved cells
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> spare;
+    plan_profile_stats acc{};
+
+    void* dalloc(size_t bytes) { return alloc.alloc(bytes, (void*)stream, alloc.ctx); }
+    void dfree(void* p, size_t bytes) {
+        if (p) alloc.free(p, bytes, (void*)stream, alloc.ctx);
+    }
+};
+
+namespace {
+
+// ------------------------------------------------------------ geometry tables
+// Section V.C.  Heading T stands for theta = 2 pi T / N_theta.
+//   eq. 11-13: alpha = R sin(theta); with the half-cell option
+//              zeta(alpha) = round(2 alpha)/2, beta = floor(zeta), Psi = zeta -
+//              beta; without it beta = round(alpha), Psi = 0.
+//   eq. 19:    I = 0 iff |tan theta| <= 1, decided on the integer heading
+//              (angular distance m*2pi/N to the nearest multiple of pi is at
+//              most pi/4 iff 8m <= N).
+//   eq. 20-22: K = tan (I = 0) or cot (I = 1); B(y', T) = round(y' K).
+//   eq. 24:    J = sign(cos) (I = 0) or sign(sin) (I = 1).
+//   Section V.D edge lengths: turn 2 pi R / N_theta, straight
+//              1/max(|cos|,|sin|), scaled by the integer step units and rounded.
+void build_tables(plan_s* p, std::vector<int>& beta, std::vector<int>& psi2) {
+    const int nt = p->nt, nx = p->nx;
+    const bool half = (p->costs.flags & PLAN_FLAG_HALF_SHIFT) != 0;
+    beta.assign(nt, 0);
+    psi2.assign(nt, 0);
+    p->planes.assign(nt, PlaneInfo{});
+    p->bshear.assign((size_t)nt * nx, 0);
+    uint32_t wmax = 0;
+    for (int T = 0; T < nt; T++) {
+        const double th = (2.0 * kPi) * (double)T / (double)nt;
+        const double s = sin(th), c = cos(th);
+        const double alpha = p->R * s;
+        if (half) {
+            const long z = lround(2.0 * alpha);
+            beta[T] = (int)(z >= 0 ? z / 2 : -((-z + 1) / 2));
+            psi2[T] = (int)(z & 1);
+        } else {
+            beta[T] = (int)lround(alpha);
+        }
+        const int halfN = nt / 2;
+        const int r = T % halfN;
+        const int m = std::min(r, halfN - r);
+        PlaneInfo& pi = p->planes[T];
+        pi.iflag = 8 * m <= nt ? 0 : 1;
+        if (pi.iflag == 0) {
+            const int d0 = std::min(T, nt - T);
+            pi.jsign = 4 * d0 < nt ? 1 : -1;
+        } else {
+            pi.jsign = 2 * T < nt ? 1 : -1;
+        }
+        const double K = pi.iflag == 0 ? s / c : c / s;
+        for (int y = 0; y < nx; y++) p->bshear[(size_t)T * nx + y] = (int16_t)lround((double)y * K);
+        pi.wS = (uint32_t)lround((double)p->costs.step_straight * (1.0 / fmax(fabs(c), fabs(s))));
+        wmax = std::max(wmax, pi.wS);
+    }
+    p->wA = (uint32_t)lround((double)p->costs.step_scale * (2.0 * kPi) * p->R / (double)nt);
+    p->w_max = std::max(wmax, p->wA);
+    p->beta4.resize(nt);
+    const int q = nt / 4;
+    for (int T = 0; T < nt; T++)
+        p->beta4[T] = make_int4(beta[T], beta[(T + 3 * q) % nt], beta[(T + 2 * q) % nt], beta[(T + q) % nt]);
+}
+
+// Footprint (Section VI, Fig. 6): the closed rectangle [-rear, front] x
+// [-hw, hw] in vehicle coordinates, placed at the continuum pose of eq. 16
+// (i + Psi_0, j + Psi_1, theta).  World cell (i+dx, j+dy) is covered when its
+// centre lies in the rectangle (1e-9-cell tolerance, so exact multiples of 90
+// degrees keep their edge cells); the cell under the origin is always covered.
+void build_runs(plan_s* p, const std::vector<int>& psi2) {
+    const int nt = p->nt;
+    const plan_footprint& f = p->fp;
+    const int ext = std::max(f.front, f.rear);
+    const int lim = (int)ceil(sqrt((double)ext * ext + (double)f.half_width * f.half_width)) + 2;
+    p->run_off.assign(nt + 1, 0);
+    p->runs.clear();
+    p->fp_off.assign(nt + 1, 0);
+    p->fp_dx.clear();
+    p->fp_dy.clear();
+    p->max_runs = 0;
+    const double eps = 1e-9;
+    std::vector<char> row(2 * lim + 1);
+    for (int T = 0; T < nt; T++) {
+        const double th = (2.0 * kPi) * (double)T / (double)nt;
+        const double c = cos(th), s = sin(th);
+        const double px0 = 0.5 * psi2[T], py0 = 0.5 * psi2[(T + nt / 4) % nt];
+        const int first = (int)p->runs.size();
+        for (int dy = -lim; dy <= lim; dy++) {
+            for (int dx = -lim; dx <= lim; dx++) {
+                bool in = dx == 0 && dy == 0;
+                if (!in) {
+                    const double ax = (double)dx - px0, ay = (double)dy - py0;
+                    const double xv = c * ax + s * ay, yv = -s * ax + c * ay;
+                    in = xv >= -(double)f.rear - eps && xv <= (double)f.front + eps &&
+                         yv >= -(double)f.half_width - eps && yv <= (double)f.half_width + eps;
+                }
+                row[dx + lim] = in;
+                if (in) {
+                    p->fp_dx.push_back(dx);
+                    p->fp_dy.push_back(dy);
+                }
+            }
+            for (int a = 0; a <= 2 * lim;) {
+                if (!row[a]) { a++; continue; }
+                int b = a;
+                while (b + 1 <= 2 * lim && row[b + 1]) b++;
+                const int lo = a - lim, hi = b - lim, w = hi - lo + 1;
+                Run r;
+                r.dy = (int16_t)dy;
+                r.lo = (int16_t)lo;
+                if (w >= p->nx) {  // covers the whole (cyclic) row
+                    r.lvl = (int16_t)p->lx;
+                    r.hi2 = (int16_t)lo;
+                } else {
+                    int lvl = 0;
+                    while ((2 << lvl) <= w) lvl++;
+                    r.lvl = (int16_t)lvl;
+                    r.hi2 = (int16_t)(hi - (1 << lvl) + 1);
+                }
+                p->runs.push_back(r);
+                a = b + 1;
+            }
+        }
+        p->run_off[T + 1] = (int32_t)p->runs.size();
+        p->fp_off[T + 1] = (int32_t)p->fp_dx.size();
+        p->max_runs = std::max(p->max_runs, (int)p->runs.size() - first);
+    }
+}
+
+int check_image(const uint16_t* img, int64_t n, uint32_t* max_soft) {
+    uint32_t m = 256;
+    for (int64_t k = 0; k < n; k++) {
+        const uint16_t v = img[k];
+        if (v == PLAN_HARD) continue;
+        if (v < 256) return PLAN_EINVAL;
+        if (v > m) m = v;
+    }
+    *max_soft = m;
+    return PLAN_OK;
+}
+
+bool pose_ok(const plan_s* p, plan_pose q) {
+    return q.x >= 0 && q.y >= 0 && q.theta >= 0 && q.x < p->nx && q.y < p->nx && q.theta < p->nt;
+}
+
+int64_t cell_index(const plan_s* p, plan_pose q) {
+    return (int64_t)q.x + ((int64_t)q.y << p->lx) + ((int64_t)q.theta << (2 * p->lx));
+}
+
+// Is pose q hard?  Same definition as the render kernel, evaluated on the
+// host copy of the image for one pose.
+bool pose_hard(const plan_s* p, plan_pose q) {
+    const int M = p->nx - 1;
+    for (int k = p->fp_off[q.theta]; k < p->fp_off[q.theta + 1]; k++) {
+        const int x = (q.x + p->fp_dx[k]) & M, y = (q.y + p->fp_dy[k]) & M;
+        if (x == 0 || y == 0 || p->img[(size_t)y * p->nx + x] == PLAN_HARD) return true;
+    }
+    return false;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : PLAN_ECUDA; }
+
+void release(plan_s* p) {
+    p->dfree(p->d_blob, p->blob_bytes);
+    p->dfree(p->d_img, (size_t)p->nxy * 2);
+    p->dfree(p->d_table, p->table_bytes);
+    p->dfree(p->d_V, (size_t)p->nr * 4);
+    p->dfree(p->d_L, (size_t)p->nr * 2);
+    p->dfree(p->d_B, (size_t)p->nr * 2);
+    p->dfree(p->d_seg, sizeof(plan_segment) * kDevSegCap);
+    p->dfree(p->d_status, 16);
+    p->dfree(p->d_cnt, 16);
+    for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto e : p->spare) cudaEventDestroy(e);
+    p->marks.clear();
+    p->spare.clear();
+}
+
+enum { K_TURN = 0, K_STRAIGHT = 1, K_RENDER = 2, K_INIT = 3 };
+
+cudaEvent_t take_event(plan_s* p) {
+    if (!p->spare.empty()) {
+        cudaEvent_t e = p->spare.back();
+        p->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Bracket one pass with an event pair when profiling; returns the start mark.
+int mark_begin(plan_s* p, int kind) {
+    if (!p->prof) return -1;
+    plan_s::Mark m{kind, take_event(p), take_event(p)};
+    if (!m.a || !m.b) return -1;
+    cudaEventRecord(m.a, p->stream);
+    p->marks.push_back(m);
+    return (int)p->marks.size() - 1;
+}
+void mark_end(plan_s* p, int idx) {
+    if (idx >= 0) cudaEventRecord(p->marks[idx].b, p->stream);
+}
+unsigned long long* counter(plan_s* p, int kind) { return p->prof ? p->d_cnt + kind : nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+int plan_create(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
+                const plan_costs* costs, const plan_allocator* allocator, void* cuda_stream, plan_t** out) {
+    if (!out) return PLAN_EINVAL;
+    *out = nullptr;
+    if (!grid || !footprint || !costs || !grid->image) return PLAN_EINVAL;
+    if (grid->nx_log2 < 2 || grid->nx_log2 > 12 || grid->ntheta_log2 < 2 || grid->ntheta_log2 > 10)
+        return PLAN_EINVAL;
+    if (!(turn_radius_cells > 0) || turn_radius_cells > 1e6) return PLAN_EINVAL;
+    if (footprint->front < 0 || footprint->rear < 0 || footprint->half_width < 0 || footprint->front > 2000 ||
+        footprint->rear > 2000 || footprint->half_width > 2000)
+        return PLAN_EINVAL;
+    if (costs->transition >= (1u << 28) || costs->step_straight == 0 || costs->step_scale == 0)
+        return PLAN_EINVAL;
+    if (allocator && (!allocator->alloc || !allocator->free)) return PLAN_EINVAL;
+
+    plan_s* p = new (std::nothrow) plan_s();
+    if (!p) return PLAN_ENOMEM;
+    p->lx = grid->nx_log2;
+    p->lt = grid->ntheta_log2;
+    p->nx = 1 << p->lx;
+    p->nt = 1 << p->lt;
+    p->nxy = (int64_t)p->nx * p->nx;
+    p->nr = p->nxy * p->nt;
+    p->R = turn_radius_cells;
+    p->costs = *costs;
+    p->fp = *footprint;
+    p->stream = (cudaStream_t)cuda_stream;
+    if (allocator) p->alloc = *allocator;
+    else p->alloc = plan_allocator{default_alloc, default_free, nullptr};
+
+    int rc = check_image(grid->image, p->nxy, &p->img_max_soft);
+    if (rc != PLAN_OK) { delete p; return rc; }
+    p->img.assign(grid->image, grid->image + p->nxy);
+
+    std::vector<int> beta, psi2;
+    build_tables(p, beta, psi2);
+    if (p->wA == 0 || p->w_max > 0xFFFF) { delete p; return PLAN_EINVAL; }
+    build_runs(p, psi2);
+
+    // table blob: beta4 | planes | bshear | run_off | runs
+    const size_t o_beta = 0;
+    const size_t o_plane = o_beta + round16(sizeof(int4) * p->nt);
+    const size_t o_bsh = o_plane + round16(sizeof(PlaneInfo) * p->nt);
+    const size_t o_roff = o_bsh + round16(sizeof(int16_t) * p->bshear.size());
+    const size_t o_runs = o_roff + round16(sizeof(int32_t) * p->run_off.size());
+    p->blob_bytes = o_runs + round16(sizeof(Run) * std::max<size_t>(1, p->runs.size()));
+    p->blob.assign(p->blob_bytes, 0);
+    memcpy(p->blob.data() + o_beta, p->beta4.data(), sizeof(int4) * p->nt);
+    memcpy(p->blob.data() + o_plane, p->planes.data(), sizeof(PlaneInfo) * p->nt);
+    memcpy(p->blob.data() + o_bsh, p->bshear.data(), sizeof(int16_t) * p->bshear.size());
+    memcpy(p->blob.data() + o_roff, p->run_off.data(), sizeof(int32_t) * p->run_off.size());
+    if (!p->runs.empty()) memcpy(p->blob.data() + o_runs, p->runs.data(), sizeof(Run) * p->runs.size());
+
+    p->table_bytes = (size_t)(p->lx + 1) * p->nxy * 2;
+    p->d_blob = (unsigned char*)p->dalloc(p->blob_bytes);
+    p->d_img = (uint16_t*)p->dalloc((size_t)p->nxy * 2);
+    p->d_table = (uint16_t*)p->dalloc(p->table_bytes);
+    p->d_V = (uint32_t*)p->dalloc((size_t)p->nr * 4);
+    p->d_L = (uint16_t*)p->dalloc((size_t)p->nr * 2);
+    p->d_B = (uint16_t*)p->dalloc((size_t)p->nr * 2);
+    p->d_seg = (plan_segment*)p->dalloc(sizeof(plan_segment) * kDevSegCap);
+    p->d_status = (int*)p->dalloc(16);
+    p->d_cnt = (unsigned long long*)p->dalloc(16);
+    if (!p->d_cnt ||
+        !p->d_blob || !p->d_img || !p->d_table || !p->d_V || !p->d_L || !p->d_B || !p->d_seg || !p->d_status) {
+        release(p);
+        delete p;
+        return PLAN_ENOMEM;
+    }
+    rc = cuda_rc(cudaMemcpyAsync(p->d_blob, p->blob.data(), p->blob_bytes, cudaMemcpyHostToDevice, p->stream));
+    if (rc == PLAN_OK)
+        rc = cuda_rc(cudaMemcpyAsync(p->d_img, p->img.data(), (size_t)p->nxy * 2, cudaMemcpyHostToDevice, p->stream));
+    if (rc != PLAN_OK) {
+        release(p);
+        delete p;
+        return rc;
+    }
+    DevGrid& g = p->g;
+    g.lx = p->lx; g.lt = p->lt; g.nx = p->nx; g.nt = p->nt; g.mx = p->nx - 1; g.mt = p->nt - 1;
+    g.wA = p->wA;
+    g.ct = p->costs.transition;
+    g.beta4 = (const int4*)(p->d_blob + o_beta);
+    g.plane = (const PlaneInfo*)(p->d_blob + o_plane);
+    g.bshear = (const int16_t*)(p->d_blob + o_bsh);
+    g.run_off = (const int32_t*)(p->d_blob + o_roff);
+    g.runs = (const Run*)(p->d_blob + o_runs);
+    *out = p;
+    return PLAN_OK;
+}
+
+int plan_set_image(plan_t* p, const uint16_t* image) {
+    if (!p || !image) return PLAN_EINVAL;
+    uint32_t m;
+    int rc = check_image(image, p->nxy, &m);
+    if (rc != PLAN_OK) return rc;
+    // the previous upload may still read the host copy: finish it first
+    rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc != PLAN_OK) return rc;
+    p->img_max_soft = m;
+    p->img.assign(image, image + p->nxy);
+    p->rendered = false;
+    return cuda_rc(cudaMemcpyAsync(p->d_img, p->img.data(), (size_t)p->nxy * 2, cudaMemcpyHostToDevice, p->stream));
+}
+
+int plan_render_cspace(plan_t* p) {
+    if (!p) return PLAN_EINVAL;
+    const int mk = mark_begin(p, K_RENDER);
+    int rc = cuda_rc(launch_sparse_table(p->d_img, p->d_table, p->lx, p->stream));
+    p->launches += p->lx + 1;
+    if (rc != PLAN_OK) return rc;
+    rc = cuda_rc(launch_render(p->g, p->d_table, p->d_B, std::max(1, p->max_runs), p->stream));
+    p->launches += 1;
+    mark_end(p, mk);
+    if (rc == PLAN_OK) p->rendered = true;
+    return rc;
+}
+
+int plan_sweep(plan_t* p, plan_pose start, int n_cycles) {
+    if (!p || n_cycles < 0 || n_cycles > 4096 || !pose_ok(p, start)) return PLAN_EINVAL;
+    if (!p->rendered) return PLAN_ESTATE;
+    if (pose_hard(p, start)) return PLAN_EINVAL;
+    // Every finite value is a sum over at most 6N segments of ct plus at most
+    // max(Nx, N_theta) - 1 edges; it must stay below the kernels' TH.
+    const double e_max = (double)(((uint64_t)p->w_max * p->img_max_soft) >> 8);
+    const double bound = 6.0 * n_cycles * ((double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max);
+    if (bound >= (double)TH) return PLAN_ERANGE;
+    Volumes vt{p->d_V, p->d_L, p->d_B, counter(p, K_TURN)};
+    Volumes vs{p->d_V, p->d_L, p->d_B, counter(p, K_STRAIGHT)};
+    const DevGrid& g = p->g;
+    cudaStream_t s = p->stream;
+    int mk = mark_begin(p, K_INIT);
+    int rc = cuda_rc(launch_init(g, vt, cell_index(p, start), s));
+    mark_end(p, mk);
+    p->launches++;
+    if (rc != PLAN_OK || n_cycles == 0) return rc;
+    auto turn = [&](int family, int asc, int mu1, int mu2) {
+        const int m = mark_begin(p, K_TURN);
+        const int r = cuda_rc(launch_turn(g, vt, family, asc, mu1, mu2, s));
+        mark_end(p, m);
+        p->launches++;
+        return r;
+    };
+    auto straight = [&](int mu) {
+        const int m = mark_begin(p, K_STRAIGHT);
+        const int r = cuda_rc(launch_straight(g, vs, mu, s));
+        mark_end(p, m);
+        p->launches++;
+        return r;
+    };
+    // Cycle order LF, SF, RB, RF, SB, LB (Section XVI.A).  Consecutive turns on
+    // the same curve family share one pass: {RB, RF} and {LB of cycle n, LF
+    // of cycle n+1}; a lone LF opens the run and a lone LB closes it, so N
+    // cycles take 4N + 1 passes over the volume instead of 6N.
+    rc = turn(0, 1, LF, -1);
+    for (int c = 0; c < n_cycles && rc == PLAN_OK; c++) {
+        rc = straight(SF);
+        if (rc == PLAN_OK) rc = turn(1, 1, RB, RF);
+        if (rc == PLAN_OK) rc = straight(SB);
+        if (rc == PLAN_OK) rc = turn(0, 0, LB, c + 1 < n_cycles ? LF : -1);
+    }
+    return rc;
+}
+
+int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_out, uint32_t* cost) {
+    if (!p || !n_out || !cost || cap < 0 || (cap > 0 && !out) || !pose_ok(p, goal)) return PLAN_EINVAL;
+    *n_out = 0;
+    *cost = PLAN_INF;
+    Volumes v{p->d_V, p->d_L, p->d_B, nullptr};
+    int rc = cuda_rc(launch_extract(p->g, v, cell_index(p, goal), p->d_seg, kDevSegCap, p->d_status, p->stream));
+    p->launches++;
+    if (rc != PLAN_OK) return rc;
+    int status = 0;
+    uint32_t vg = PLAN_INF;
+    rc = cuda_rc(cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK)
+        rc = cuda_rc(cudaMemcpyAsync(&vg, p->d_V + cell_index(p, goal), 4, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc != PLAN_OK) return rc;
+    if (status == -1) return PLAN_EUNREACHABLE;
+    if (status < 0) return PLAN_EINTERNAL;
+    *cost = vg;
+    *n_out = status;
+    if (status > cap || status > kDevSegCap) return PLAN_ERANGE;
+    if (status > 0) {
+        rc = cuda_rc(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status, cudaMemcpyDeviceToHost, p->stream));
+        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+        if (rc != PLAN_OK) return rc;
+        std::reverse(out, out + status);  // the walk runs goal -> start
+    }
+    return PLAN_OK;
+}
+
+int plan_copy_volumes(plan_t* p, uint32_t* V, uint16_t* L, uint16_t* B) {
+    if (!p) return PLAN_EINVAL;
+    int rc = PLAN_OK;
+    if (V) rc = cuda_rc(cudaMemcpyAsync(V, p->d_V, (size_t)p->nr * 4, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK && L) rc = cuda_rc(cudaMemcpyAsync(L, p->d_L, (size_t)p->nr * 2, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK && B) rc = cuda_rc(cudaMemcpyAsync(B, p->d_B, (size_t)p->nr * 2, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    return rc;
+}
+
+int plan_device_volumes(plan_t* p, uint32_t** V, uint16_t** L, uint16_t** B) {
+    if (!p) return PLAN_EINVAL;
+    if (V) *V = p->d_V;
+    if (L) *L = p->d_L;
+    if (B) *B = p->d_B;
+    return PLAN_OK;
+}
+
+int plan_profile(plan_t* p, int enable) {
+    if (!p) return PLAN_EINVAL;
+    int rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc != PLAN_OK) return rc;
+    for (auto& m : p->marks) { p->spare.push_back(m.a); p->spare.push_back(m.b); }
+    p->marks.clear();
+    p->acc = plan_profile_stats{};
+    p->prof = enable != 0;
+    return cuda_rc(cudaMemsetAsync(p->d_cnt, 0, 16, p->stream));
+}
+
+int plan_profile_read(plan_t* p, plan_profile_stats* out) {
+    if (!p || !out) return PLAN_EINVAL;
+    unsigned long long cnt[2] = {0, 0};
+    int rc = cuda_rc(cudaMemcpyAsync(cnt, p->d_cnt, 16, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc != PLAN_OK) return rc;
+    for (auto& m : p->marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) != cudaSuccess) return PLAN_ECUDA;
+        switch (m.kind) {
+            case K_TURN: p->acc.turn_passes++; p->acc.turn_ms += ms; break;
+            case K_STRAIGHT: p->acc.straight_passes++; p->acc.straight_ms += ms; break;
+            case K_RENDER: p->acc.render_passes++; p->acc.render_ms += ms; break;
+            default: p->acc.init_passes++; p->acc.init_ms += ms; break;
+        }
+        p->spare.push_back(m.a);
+        p->spare.push_back(m.b);
+    }
+    p->marks.clear();
+    p->acc.turn_improved = cnt[0];
+    p->acc.straight_improved = cnt[1];
+    *out = p->acc;
+    return PLAN_OK;
+}
+
+int plan_kernel_launches(plan_t* p, int64_t* count) {
+    if (!p || !count) return PLAN_EINVAL;
+    *count = p->launches;
+    return PLAN_OK;
+}
+
+int plan_destroy(plan_t* p) {
+    if (!p) return PLAN_EINVAL;
+    cudaStreamSynchronize(p->stream);
+    release(p);
+    delete p;
+    return PLAN_OK;
+}
+
+const char* plan_strerror(int code) {
+    switch (code) {
+        case PLAN_OK: return "ok";
+        case PLAN_EINVAL: return "invalid argument";
+        case PLAN_ENOMEM: return "device allocation failed";
+        case PLAN_ECUDA: return "CUDA runtime error";
+        case PLAN_ETIMEOUT: return "device wait timed out";
+        case PLAN_EUNREACHABLE: return "goal unreachable";
+        case PLAN_ERANGE: return "capacity or cost range exceeded";
+        case PLAN_EINTERNAL: return "internal consistency check failed";
+        case PLAN_ESTATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+// Section VII: soft obstacle costs from the distance to the nearest obstacle.
+// Exact squared Euclidean distance transform by two passes of the 1-D lower
+// envelope of parabolas (Felzenszwalb & Huttenlocher), the linear-time family
+// of methods the paper points to (Meijster et al.).
+int plan_soft_image(int nx, const uint8_t* occ, int radius, int soft_max, uint16_t* image) {
+    if (nx <= 0 || nx > 65536 || !occ || !image || radius < 0 || radius > 255 || soft_max < 0 || soft_max > 65000)
+        return PLAN_EINVAL;
+    const int64_t n = (int64_t)nx * nx;
+    const int64_t big = 4ll * nx * nx + 1;  // larger than any in-image squared distance
+    std::vector<int64_t> d2(n), f(nx), out(nx);
+    std::vector<int> vpos(nx);
+    std::vector<double> z(nx + 1);
+    auto dt1 = [&](int64_t* line, int64_t stride) {
+        for (int q = 0; q < nx; q++) f[q] = line[q * stride];
+        int k = 0;
+        vpos[0] = 0;
+        z[0] = -1e300;
+        z[1] = 1e300;
+        for (int q = 1; q < nx; q++) {
+            double sv;
+            for (;;) {  // z[0] = -inf, so this stops at k = 0 at the latest
+                const int r = vpos[k];
+                sv = ((double)(f[q] + (int64_t)q * q) - (double)(f[r] + (int64_t)r * r)) / (2.0 * (q - r));
+                if (sv > z[k]) break;
+                k--;
+            }
+            k++;
+            vpos[k] = q;
+            z[k] = sv;
+            z[k + 1] = 1e300;
+        }
+        k = 0;
+        for (int q = 0; q < nx; q++) {
+            while (z[k + 1] < q) k++;
+            const int64_t dq = q - vpos[k];
+            out[q] = dq * dq + f[vpos[k]];
+        }
+        for (int q = 0; q < nx; q++) line[q * stride] = std::min(out[q], big);
+    };
+    for (int64_t k = 0; k < n; k++) d2[k] = occ[k] ? 0 : big;
+    for (int x = 0; x < nx; x++) dt1(d2.data() + x, nx);           // columns
+    for (int y = 0; y < nx; y++) dt1(d2.data() + (int64_t)y * nx, 1);  // rows
+    const int64_t r2 = (int64_t)radius * radius;
+    for (int64_t k = 0; k < n; k++) {
+        if (occ[k]) { image[k] = PLAN_HARD; continue; }
+        const int64_t pen = d2[k] < r2 ? (int64_t)soft_max * (r2 - d2[k]) / r2 : 0;
+        image[k] = (uint16_t)(256 + pen);
+    }
+    return PLAN_OK;
+}
+
+}  // extern "C"

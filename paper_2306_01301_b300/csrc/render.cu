@@ -1,0 +1,84 @@
+// render.cu -- configuration-space obstacle rendering (Section VI).
+//
+// B(i, j, T) is the maximum of the obstacle image over the vehicle footprint
+// placed at pose (i, j, T), with the one-cell hard walls at i = 0 and j = 0
+// inserted first (Section V.C) and all coordinates taken modulo Nx.  Because
+// HARD = 0xFFFF is the largest uint16, a plain maximum also marks every pose
+// whose footprint touches a hard cell.
+//
+// The footprint of heading T is stored as maximal row runs (dy, [lo, hi]).
+// A row maximum over any run costs two lookups in a per-row sparse table
+// S_k[y][x] = max(img[y][x .. x + 2^k - 1]) (cyclic in x): the paper's
+// separable dilation idea (cost independent of the run length), but exact
+// for the rotated rectangle's rasterisation.
+#include "internal.h"
+
+namespace nhp {
+namespace {
+
+// level 0: the image with the walls inserted
+__global__ void k_table_level0(const uint16_t* img, uint16_t* t0, int lx) {
+    const int n = 1 << lx;
+    const int64_t total = (int64_t)n * n;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k & (n - 1)), y = (int)(k >> lx);
+        t0[k] = (x == 0 || y == 0) ? HARD : img[k];
+    }
+}
+
+// level k from level k-1: window 2^k = two windows of 2^(k-1)
+__global__ void k_table_level(const uint16_t* prev, uint16_t* cur, int lx, int half) {
+    const int n = 1 << lx;
+    const int64_t total = (int64_t)n * n;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k & (n - 1));
+        const int64_t row = k - x;
+        const uint16_t a = prev[k], b = prev[row + ((x + half) & (n - 1))];
+        cur[k] = a > b ? a : b;
+    }
+}
+
+// One thread per pose cell of heading blockIdx.y; the heading's runs are
+// staged in shared memory.
+__global__ void __launch_bounds__(256) k_render(DevGrid g, const uint16_t* __restrict__ table,
+                                                uint16_t* __restrict__ B) {
+    extern __shared__ Run runs[];
+    const int T = blockIdx.y;
+    const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
+    __syncthreads();
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nxy) return;
+    const int i = (int)(cell & g.mx), j = (int)(cell >> g.lx);
+    uint16_t m = 0;
+    for (int r = 0; r < nr; r++) {
+        const Run ru = runs[r];
+        const uint16_t* row = table + (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+        const uint16_t a = __ldg(row + ((i + ru.lo) & g.mx));
+        const uint16_t b = __ldg(row + ((i + ru.hi2) & g.mx));
+        m = max(m, max(a, b));
+    }
+    B[(int64_t)T * nxy + cell] = m;
+}
+
+}  // namespace
+
+cudaError_t launch_sparse_table(const uint16_t* img, uint16_t* table, int lx, cudaStream_t s) {
+    const int64_t nxy = (int64_t)1 << (2 * lx);
+    int64_t blocks = (nxy + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_table_level0<<<(unsigned)blocks, 256, 0, s>>>(img, table, lx);
+    for (int k = 1; k <= lx; k++)
+        k_table_level<<<(unsigned)blocks, 256, 0, s>>>(table + (k - 1) * nxy, table + k * nxy, lx, 1 << (k - 1));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render(const DevGrid& g, const uint16_t* table, uint16_t* B, int max_runs, cudaStream_t s) {
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    dim3 grid((unsigned)((nxy + 255) / 256), (unsigned)g.nt);
+    k_render<<<grid, 256, (size_t)max_runs * sizeof(Run), s>>>(g, table, B);
+    return cudaGetLastError();
+}
+
+}  // namespace nhp

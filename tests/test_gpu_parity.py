@@ -1,0 +1,173 @@
+"""GPU path (through the C ABI) against the CPU oracle: bit-exact obstacle
+volume B, value volume V, labels L and extracted plans.
+
+Small cases cover every turn-kernel shape (N_theta 4 .. 512), grids narrower
+than a warp (Nx = 4, 8, 16), soft costs, rectangles, with and without the
+half-cell shift.  Full-size cases run the 512^3 parallel-parking and maze
+workloads in the launch configuration the benchmark uses: the full B and one
+full cycle of V and L are compared cell by cell, and the full-N run is
+checked for properties that hold at any size (monotone in N, a consistent
+extracted plan ending at V(goal)).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_01301_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+
+
+def planner(sc, img):
+    from paper_2306_01301_b300 import binding
+    return binding.Planner(sc.nx_log2, sc.nt_log2, img, sc.footprint, sc.turn_radius, sc.transition,
+                           sc.step_straight, sc.step_scale, sc.half_shift)
+
+
+def first_free(o, B, cands):
+    for c in cands:
+        if B[o.cell(c)] != O.HARD:
+            return c
+    raise AssertionError("no free candidate pose")
+
+
+SMALL = [
+    # lx, lt, R, footprint, soft, half, N
+    (2, 2, 1.5, (0, 0, 0), True, 1, 2),
+    (3, 3, 2.0, (0, 0, 0), False, 1, 1),
+    (3, 3, 2.0, (0, 0, 0), True, 1, 3),
+    (4, 4, 2.5, (1, 0, 0), True, 0, 2),
+    (4, 5, 3.0, (2, 1, 1), True, 1, 3),
+    (5, 3, 4.0, (0, 0, 0), True, 1, 2),
+    (5, 6, 6.0, (3, 1, 1), True, 1, 2),
+    (5, 7, 7.5, (2, 1, 1), False, 1, 2),
+    (4, 8, 5.0, (2, 1, 1), True, 1, 2),
+    (5, 9, 9.0, (3, 1, 1), True, 0, 1),
+    (6, 5, 10.0, (4, 1, 2), True, 1, 3),
+]
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[f"nx{1 << c[0]}_nt{1 << c[1]}" for c in SMALL])
+def test_small_grids_bit_exact(case):
+    lx, lt, R, fp, soft, half, N = case
+    sc, img = scenes.tiny(100 + lx * 16 + lt, lx, lt, fill=0.08, turn_radius=R, footprint=fp, soft=soft,
+                          half_shift=half, transition=300)
+    o = O.Oracle(lx, lt, R, half_shift=half, transition=sc.transition)
+    Bo = o.render(img, fp)
+    start = first_free(o, Bo, sc.pose_candidates)
+    Vo, Lo, _ = o.sweep(Bo, o.cell(start), N, mode=1)
+    p = planner(sc, img)
+    p.render()
+    p.sweep(start, N)
+    V, L, B = p.volumes()
+    assert np.array_equal(B, Bo), "obstacle volume"
+    assert np.array_equal(V, Vo), f"values differ at {np.flatnonzero(V != Vo)[:5]}"
+    assert np.array_equal(L, Lo), f"labels differ at {np.flatnonzero(L != Lo)[:5]}"
+    # plans to every reached cell of a random sample
+    reached = np.flatnonzero(Vo != INF)
+    rng = np.random.default_rng(lx + lt)
+    for g in rng.choice(reached, size=min(25, len(reached)), replace=False):
+        ref = o.extract(Vo, Lo, int(g))
+        got = p.extract(o.pose(int(g)))
+        assert got.cost == Vo[g]
+        assert [(s["mu"], s["entry"], s["exit"], s["steps"], s["cost"]) for s in got.segments] == \
+               [(s["mu"], o.pose(s["entry"]), o.pose(s["exit"]), s["steps"], s["cost"]) for s in ref]
+    p.close()
+
+
+def test_single_query_64cubed_bit_exact():
+    """The plain single-query workload: 64^3, point vehicle, N = 4."""
+    sc = scenes.single_query(0)
+    img = sc.hard_image()
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    Bo = o.render(img, sc.footprint)
+    Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
+    p = planner(sc, img)
+    p.render()
+    p.sweep(sc.start, sc.n_cycles)
+    V, L, B = p.volumes()
+    assert np.array_equal(B, Bo) and np.array_equal(V, Vo) and np.array_equal(L, Lo)
+    ref = o.extract(Vo, Lo, o.cell(sc.goal))
+    got = p.extract(sc.goal)
+    if ref is None:
+        assert got is None
+    else:
+        assert got.cost == Vo[o.cell(sc.goal)]
+        assert [(s["mu"], s["steps"], s["cost"]) for s in got.segments] == \
+               [(s["mu"], s["steps"], s["cost"]) for s in ref]
+    # other start poses of the same scene, same plan object (state reset by sweep)
+    for st in sc.pose_candidates[2:6]:
+        Vo, Lo, _ = o.sweep(Bo, o.cell(st), sc.n_cycles, mode=1)
+        p.sweep(st, sc.n_cycles)
+        V, L, _ = p.volumes(B=False)
+        assert np.array_equal(V, Vo) and np.array_equal(L, Lo)
+    p.close()
+
+
+def test_errors_are_reported_not_raised_on_device():
+    from paper_2306_01301_b300 import binding
+    sc, img = scenes.tiny(5, 4, 4, fill=0.1, soft=True)
+    p = planner(sc, img)
+    with pytest.raises(binding.PlanError) as e:
+        p.sweep(sc.start, 1)  # before rendering
+    assert e.value.code == -8
+    p.render()
+    hard = np.argwhere(img == 0xFFFF)
+    if len(hard):
+        y, x = hard[0]
+        with pytest.raises(binding.PlanError) as e:
+            p.sweep((int(x), int(y), 0), 1)
+        assert e.value.code == -1
+    with pytest.raises(binding.PlanError):
+        p.sweep((99, 0, 0), 1)
+    p.sweep(sc.start, 0)  # zero cycles: only the start is reached
+    V, L, _ = p.volumes(B=False)
+    assert (V != INF).sum() == 1 and (L != 0xFFFF).sum() == 0
+    assert p.extract((0, 0, 0)) is None  # wall cell: unreachable
+    p.close()
+
+
+def _full_size(sc, img, n_check=1):
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    Bo = o.render_rows(img, sc.footprint)
+    p = planner(sc, img)
+    p.render()
+    p.sweep(sc.start, n_check)
+    V1, L1, B = p.volumes()
+    assert np.array_equal(B, Bo), "obstacle volume"
+    Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), n_check, mode=1)
+    assert np.array_equal(V1, Vo), f"values differ at {np.flatnonzero(V1 != Vo)[:5]}"
+    assert np.array_equal(L1, Lo), f"labels differ at {np.flatnonzero(L1 != Lo)[:5]}"
+    del Vo, Lo, Bo
+    # the benchmark's full cycle count: properties that hold at any size
+    p.sweep(sc.start, sc.n_cycles)
+    VN, LN, _ = p.volumes(B=False)
+    assert np.all(VN <= V1), "more cycles raised a value"
+    res = p.extract(sc.goal)
+    g = o.cell(sc.goal)
+    if res is None:
+        assert VN[g] == INF
+    else:
+        assert res.cost == VN[g]
+        segs = res.segments
+        assert segs[0]["entry"] == tuple(sc.start) and segs[-1]["exit"] == tuple(sc.goal)
+        for a, b in zip(segs, segs[1:]):
+            assert b["entry"] == a["exit"] and b["cost"] > a["cost"]
+        assert segs[-1]["cost"] == res.cost
+    p.close()
+    return res
+
+
+def test_parallel_parking_512cubed_full_size():
+    sc = scenes.parallel_parking()
+    _full_size(sc, sc.hard_image())
+
+
+def test_maze_512cubed_full_size_soft_costs():
+    from paper_2306_01301_b300 import binding
+    sc = scenes.maze()
+    img = binding.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max)
+    assert np.array_equal(img, O.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max))
+    _full_size(sc, img)

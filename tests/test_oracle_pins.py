@@ -303,6 +303,14 @@ def test_render_against_maximum_filter():
     del ref
 
 
+@pytest.mark.parametrize("lx,lt,fp,half", [(5, 4, (5, 2, 2), 1), (4, 5, (9, 3, 4), 0), (3, 3, (6, 2, 3), 1),
+                                           (6, 4, (0, 0, 0), 1)])
+def test_row_run_render_equals_definition(lx, lt, fp, half):
+    sc, img = scenes.tiny(13 + lx, lx, lt, fill=0.1, soft=True)
+    o = O.Oracle(lx, lt, 4.0, half_shift=half)
+    assert np.array_equal(o.render_rows(img, fp), o.render(img, fp))
+
+
 def test_render_cells_matches_full_render():
     sc, img = scenes.tiny(12, 5, 4, fill=0.1, soft=True)
     o = O.Oracle(5, 4, 4.0)
