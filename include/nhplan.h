@@ -183,6 +183,27 @@ int plan_destroy(plan_t* plan);
 
 const char* plan_strerror(int code);
 
+/* Obstacle rendering for callers that cannot allocate device memory -- for
+ * example a runtime that owns all device memory through a fixed memory plan,
+ * or a control loop that forbids allocation once it is running.  The paper
+ * has no counterpart; this is the same computation as plan_render_cspace
+ * without a plan object.  image_dev: device pointer, Nx*Nx uint16 (as in
+ * plan_grid.image); B_dev: device pointer, Nx*Nx*N_theta uint16, written.
+ * footprint, turn radius and flags as in plan_create (the radius and the
+ * half-shift flag fix the footprint's sub-cell placement).  Work is enqueued
+ * on cuda_stream.  The call allocates nothing: its scratch (sparse table and
+ * footprint runs, about 5.8 MB) is one fixed device array that every GPU which
+ * loads this library holds until the process exits, so Nx is limited to 512
+ * (larger grids return PLAN_ERANGE before any work) and the footprint to 65536
+ * row runs over all headings.  The first call on a device looks up that
+ * array's device address with the device current; make it before any stream
+ * capture.  All calls share the one array: two calls whose work overlaps on a
+ * GPU (other streams, other host threads) race and may produce wrong volumes.
+ * Returns PLAN_EINVAL for bad arguments and PLAN_ECUDA if a CUDA call fails. */
+int plan_render_cspace_static(const uint16_t* image_dev, int nx_log2, int ntheta_log2,
+                              const plan_footprint* footprint, double turn_radius_cells, uint32_t flags,
+                              uint16_t* B_dev, void* cuda_stream);
+
 /* Section VII, host helper: soft-obstacle image from a binary occupancy map
  * [nx][nx] (nonzero = obstacle).  Obstacle cells become 0xFFFF; a free cell at
  * squared Euclidean distance d2 from the nearest obstacle gets
