@@ -52,12 +52,20 @@ __global__ void __launch_bounds__(256) k_render(DevGrid g, const uint16_t* __res
     if (cell >= nxy) return;
     const int i = (int)(cell & g.mx), j = (int)(cell >> g.lx);
     uint16_t m = 0;
-    for (int r = 0; r < nr; r++) {
-        const Run ru = runs[r];
-        const uint16_t* row = table + (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
-        const uint16_t a = __ldg(row + ((i + ru.lo) & g.mx));
-        const uint16_t b = __ldg(row + ((i + ru.hi2) & g.mx));
-        m = max(m, max(a, b));
+    // HARD is the largest value: once every lane of the warp has met a hard
+    // cell, no later run can change the result.
+    for (int r0 = 0; r0 < nr; r0 += 4) {
+#pragma unroll
+        for (int r = r0; r < r0 + 4; r++) {
+            if (r < nr) {
+                const Run ru = runs[r];
+                const uint16_t* row = table + (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+                const uint16_t a = __ldg(row + ((i + ru.lo) & g.mx));
+                const uint16_t b = __ldg(row + ((i + ru.hi2) & g.mx));
+                m = max(m, max(a, b));
+            }
+        }
+        if (__all_sync(__activemask(), m == HARD)) break;
     }
     B[(int64_t)T * nxy + cell] = m;
 }

@@ -53,12 +53,16 @@ __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t
 // chain in registers.  Scan-order positions: ascending r = T, descending
 // r = NT-1-T; positions of the storing (second) loop are r + NT.
 
+// Section-map arrays are [section][chain].  The carry scan reads them with
+// lanes spread over (section, chain) = (l % S, l / S); a row pitch of
+// 32 + 32/S words puts those 32 reads in 32 different banks.
 template <int K, int S>
 struct TurnSmem {
+    static constexpr int P = 32 + 32 / S;
     int2 beta[K * S];
-    uint32_t sa[S][32];
-    uint32_t sb[S][32];
-    int32_t sp[S][32];
+    uint32_t sa[S][P];
+    uint32_t sb[S][P];
+    int32_t sp[S][P];
 };
 
 // Compose an earlier stretch X with a later one Y (in place into Y):
@@ -212,7 +216,7 @@ cudaError_t launch_turn_t(const DevGrid& g, Volumes v, int family, int asc, int 
 
 // ---------------------------------------------------------------- straights
 template <int CH>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_straight(DevGrid g, Volumes vol, int mu) {
     const int T = blockIdx.y;
     const int xq = blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,7 +289,7 @@ cudaError_t launch_turn(const DevGrid& g, Volumes v, int family, int asc, int mu
 cudaError_t launch_straight(const DevGrid& g, Volumes v, int mu, cudaStream_t s) {
     const int tpb = g.nx < 256 ? g.nx : 256;
     dim3 grid((unsigned)((g.nx + tpb - 1) / tpb), (unsigned)g.nt);
-    if (g.nx >= 16) k_straight<16><<<grid, tpb, 0, s>>>(g, v, mu);
+    if (g.nx >= 8) k_straight<8><<<grid, tpb, 0, s>>>(g, v, mu);
     else k_straight<4><<<grid, tpb, 0, s>>>(g, v, mu);
     return cudaGetLastError();
 }
