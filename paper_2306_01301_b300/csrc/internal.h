@@ -56,6 +56,13 @@ struct Volumes {
 cudaError_t launch_sparse_table(const uint16_t* img, uint16_t* table, int lx, cudaStream_t s);
 cudaError_t launch_render(const DevGrid& g, const uint16_t* table, uint16_t* B, int max_runs,
                           cudaStream_t s);
+// Rendering with a bit-parallel hard test (Nx >= 32): builds the per-row OR
+// table `bits` ((lx+1) * Nx * Nx/32 words), writes HARD / 256 into B; with
+// soft = true the maximum of the image (sparse `table`, already built) is
+// then filled in for the non-hard poses.  Launches lx + 3 kernels (lx + 4
+// with soft).
+cudaError_t launch_render_bits(const DevGrid& g, const uint16_t* img, uint32_t* bits, uint16_t* B, bool soft,
+                               const uint16_t* table, int max_runs, cudaStream_t s);
 cudaError_t launch_init(const DevGrid& g, Volumes v, int64_t start, cudaStream_t s);
 // Turn chains: family 0 = LEFT (beta_0, beta_3), 1 = RIGHT (beta_2, beta_1).
 // First scan direction asc (1: T increasing) with maneuver mu1; if mu2 >= 0 a

@@ -53,6 +53,8 @@ struct plan_s {
     uint16_t* d_img = nullptr;
     uint16_t* d_table = nullptr;
     size_t table_bytes = 0;
+    uint32_t* d_bits = nullptr;  // bit-parallel hard table (Nx >= 32)
+    size_t bits_bytes = 0;
     uint32_t* d_V = nullptr;
     uint16_t* d_L = nullptr;
     uint16_t* d_B = nullptr;
@@ -234,6 +236,7 @@ void release(plan_s* p) {
     p->dfree(p->d_blob, p->blob_bytes);
     p->dfree(p->d_img, (size_t)p->nxy * 2);
     p->dfree(p->d_table, p->table_bytes);
+    p->dfree(p->d_bits, p->bits_bytes);
     p->dfree(p->d_V, (size_t)p->nr * 4);
     p->dfree(p->d_L, (size_t)p->nr * 2);
     p->dfree(p->d_B, (size_t)p->nr * 2);
@@ -331,6 +334,7 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     if (!p->runs.empty()) memcpy(p->blob.data() + o_runs, p->runs.data(), sizeof(Run) * p->runs.size());
 
     p->table_bytes = (size_t)(p->lx + 1) * p->nxy * 2;
+    p->bits_bytes = p->nx >= 32 ? (size_t)(p->lx + 1) * p->nxy / 8 : 0;
     p->d_blob = (unsigned char*)p->dalloc(p->blob_bytes);
     p->d_img = (uint16_t*)p->dalloc((size_t)p->nxy * 2);
     p->d_table = (uint16_t*)p->dalloc(p->table_bytes);
@@ -340,7 +344,8 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     p->d_seg = (plan_segment*)p->dalloc(sizeof(plan_segment) * kDevSegCap);
     p->d_status = (int*)p->dalloc(16);
     p->d_cnt = (unsigned long long*)p->dalloc(16);
-    if (!p->d_cnt ||
+    if (p->bits_bytes) p->d_bits = (uint32_t*)p->dalloc(p->bits_bytes);
+    if ((p->bits_bytes && !p->d_bits) || !p->d_cnt ||
         !p->d_blob || !p->d_img || !p->d_table || !p->d_V || !p->d_L || !p->d_B || !p->d_seg || !p->d_status) {
         release(p);
         delete p;
@@ -384,11 +389,21 @@ int plan_set_image(plan_t* p, const uint16_t* image) {
 int plan_render_cspace(plan_t* p) {
     if (!p) return PLAN_EINVAL;
     const int mk = mark_begin(p, K_RENDER);
-    int rc = cuda_rc(launch_sparse_table(p->d_img, p->d_table, p->lx, p->stream));
-    p->launches += p->lx + 1;
-    if (rc != PLAN_OK) return rc;
-    rc = cuda_rc(launch_render(p->g, p->d_table, p->d_B, std::max(1, p->max_runs), p->stream));
-    p->launches += 1;
+    const bool soft = p->img_max_soft > 256;
+    int rc = PLAN_OK;
+    if (soft || p->nx < 32) {
+        rc = cuda_rc(launch_sparse_table(p->d_img, p->d_table, p->lx, p->stream));
+        p->launches += p->lx + 1;
+    }
+    if (rc == PLAN_OK && p->nx >= 32) {
+        // bit-parallel hard test; soft maxima only for the non-hard poses
+        rc = cuda_rc(launch_render_bits(p->g, p->d_img, p->d_bits, p->d_B, soft, p->d_table,
+                                        std::max(1, p->max_runs), p->stream));
+        p->launches += p->lx + 2 + (soft ? 1 : 0);
+    } else if (rc == PLAN_OK) {
+        rc = cuda_rc(launch_render(p->g, p->d_table, p->d_B, std::max(1, p->max_runs), p->stream));
+        p->launches += 1;
+    }
     mark_end(p, mk);
     if (rc == PLAN_OK) p->rendered = true;
     return rc;

@@ -70,7 +70,125 @@ __global__ void __launch_bounds__(256) k_render(DevGrid g, const uint16_t* __res
     B[(int64_t)T * nxy + cell] = m;
 }
 
+// ----------------------------------------------------------- bit-parallel
+// The hard test alone: bit x of word row Hk[y] is 1 when any of the cells
+// x .. x + 2^k - 1 of image row y (cyclic) is hard or a wall.  One 32-bit
+// word covers 32 neighbouring poses, so one thread tests 32 poses per
+// footprint run with two funnel-shifted word pairs.
+
+// bits [p, p+32) of a cyclic row of nw words
+__device__ __forceinline__ uint32_t row_window(const uint32_t* row, int p, int nw_mask) {
+    const int w0 = p >> 5, sh = p & 31;
+    const uint32_t lo = __ldg(row + (w0 & nw_mask)), hi = __ldg(row + ((w0 + 1) & nw_mask));
+    return __funnelshift_r(lo, hi, sh);
+}
+
+__global__ void k_bits_level0(const uint16_t* __restrict__ img, uint32_t* __restrict__ h0, int lx) {
+    const int n = 1 << lx, nw = n >> 5;
+    const int64_t total = (int64_t)n * nw;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / nw), w = (int)(k % nw);
+        const uint16_t* r = img + (int64_t)y * n + 32 * w;
+        uint32_t bits = 0;
+#pragma unroll 8
+        for (int t = 0; t < 32; t++) {
+            const int x = 32 * w + t;
+            if (x == 0 || y == 0 || r[t] == HARD) bits |= 1u << t;
+        }
+        h0[k] = bits;
+    }
+}
+
+__global__ void k_bits_level(const uint32_t* __restrict__ prev, uint32_t* __restrict__ cur, int lx, int half) {
+    const int n = 1 << lx, nw = n >> 5;
+    const int64_t total = (int64_t)n * nw;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / nw), w = (int)(k % nw);
+        const uint32_t* row = prev + (int64_t)y * nw;
+        cur[k] = row[w] | row_window(row, 32 * w + half, nw - 1);
+    }
+}
+
+// One thread per (32-pose word, row j) of heading blockIdx.y.  Writes HARD
+// where the footprint meets a hard cell; elsewhere `free_value` (256 for a
+// hard-only image, 0 as a placeholder when a soft pass follows).
+__global__ void __launch_bounds__(256) k_render_bits(DevGrid g, const uint32_t* __restrict__ bits,
+                                                      uint16_t* __restrict__ B, uint16_t free_value) {
+    extern __shared__ Run runs[];
+    const int T = blockIdx.y;
+    const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
+    __syncthreads();
+    const int nw = g.nx >> 5;
+    const int64_t words = (int64_t)g.nx * nw;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= words) return;
+    const int j = (int)(k / nw), w = (int)(k % nw);
+    const int64_t plane_words = (int64_t)g.nx * nw;
+    uint32_t hard = 0;
+    for (int r = 0; r < nr && hard != 0xFFFFFFFFu; r++) {
+        const Run ru = runs[r];
+        const uint32_t* row = bits + (int64_t)ru.lvl * plane_words + (int64_t)((j + ru.dy) & g.mx) * nw;
+        hard |= row_window(row, ((32 * w + ru.lo) & g.mx), nw - 1) | row_window(row, ((32 * w + ru.hi2) & g.mx), nw - 1);
+    }
+    uint4* out = (uint4*)(B + (int64_t)T * g.nx * g.nx + (int64_t)j * g.nx + 32 * w);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        uint32_t v[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const int t = 8 * q + 2 * h;
+            const uint32_t a = (hard >> t) & 1u ? HARD : free_value;
+            const uint32_t b = (hard >> (t + 1)) & 1u ? HARD : free_value;
+            v[h] = a | (b << 16);
+        }
+        out[q] = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// Soft values for the poses the bit pass left non-hard.
+__global__ void __launch_bounds__(256) k_render_soft(DevGrid g, const uint16_t* __restrict__ table,
+                                                     uint16_t* __restrict__ B) {
+    extern __shared__ Run runs[];
+    const int T = blockIdx.y;
+    const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
+    __syncthreads();
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nxy) return;
+    uint16_t* dst = B + (int64_t)T * nxy + cell;
+    const bool hard = *dst == HARD;
+    if (__all_sync(__activemask(), hard)) return;
+    const int i = (int)(cell & g.mx), j = (int)(cell >> g.lx);
+    uint16_t m = 0;
+    for (int r = 0; r < nr; r++) {
+        const Run ru = runs[r];
+        const uint16_t* row = table + (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+        m = max(m, max(__ldg(row + ((i + ru.lo) & g.mx)), __ldg(row + ((i + ru.hi2) & g.mx))));
+    }
+    if (!hard) *dst = m;
+}
+
 }  // namespace
+
+cudaError_t launch_render_bits(const DevGrid& g, const uint16_t* img, uint32_t* bits, uint16_t* B, bool soft,
+                               const uint16_t* table, int max_runs, cudaStream_t s) {
+    const int64_t words = (int64_t)g.nx * (g.nx >> 5);
+    int64_t blocks = (words + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_bits_level0<<<(unsigned)blocks, 256, 0, s>>>(img, bits, g.lx);
+    for (int k = 1; k <= g.lx; k++)
+        k_bits_level<<<(unsigned)blocks, 256, 0, s>>>(bits + (k - 1) * words, bits + k * words, g.lx, 1 << (k - 1));
+    dim3 grid((unsigned)((words + 255) / 256), (unsigned)g.nt);
+    k_render_bits<<<grid, 256, (size_t)max_runs * sizeof(Run), s>>>(g, bits, B, soft ? 0 : 256);
+    if (soft) {
+        const int64_t nxy = (int64_t)g.nx * g.nx;
+        dim3 g2((unsigned)((nxy + 255) / 256), (unsigned)g.nt);
+        k_render_soft<<<g2, 256, (size_t)max_runs * sizeof(Run), s>>>(g, table, B);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sparse_table(const uint16_t* img, uint16_t* table, int lx, cudaStream_t s) {
     const int64_t nxy = (int64_t)1 << (2 * lx);

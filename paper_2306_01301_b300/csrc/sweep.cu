@@ -215,14 +215,103 @@ cudaError_t launch_turn_t(const DevGrid& g, Volumes v, int family, int asc, int 
 }
 
 // ---------------------------------------------------------------- straights
-template <int CH>
-__global__ void __launch_bounds__(256, 4)
+// One thread per line (x', T); a block owns `lines` neighbouring lines of one
+// heading plane and walks them 16 steps at a time.  Each 16-step chunk of the
+// block's lines is a sheared parallelogram of cells: Bs changes by at most 1
+// per step (|slope| <= 1), so the chunk fits in a (lines + 15) x 16 tile.
+//   shallow (I = 0): cell (line, step y') = row x' + Bs(y'), column y';
+//                    tile rows = grid rows, tile columns = the 16 steps.
+//   steep   (I = 1): cell = row y', column x' + Bs(y');
+//                    tile rows = the 16 steps, tile columns = grid columns.
+// Tiles are filled with 4-byte cp.async copies (whole row segments, so
+// global reads coalesce in both cases), two stages deep: the next chunk is in
+// flight while the current one is scanned.  Changed cells are marked in the
+// tile (bit 31 of the value, the label in place of the obstacle value) and
+// written back row segment by row segment.
+constexpr int kSteps = 16;
+constexpr int kMaxLines = 256;
+constexpr int kSpan = kMaxLines + kSteps;           // tile extent across lines
+constexpr int kVWords = kSpan * (kSteps + 1);       // >= kSteps * (kSpan + 1)
+constexpr int kBHalves = kSpan * (kSteps + 2);      // >= kSteps * (kSpan + 4)
+constexpr uint32_t kMark = 0x80000000u;             // changed; stored values are < TH
+
+struct StraightStage {
+    uint32_t v[kVWords];
+    uint16_t b[kBHalves];
+};
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct ChunkGeom {
+    int y0;     // first step of the chunk (ascending y')
+    int bmin;   // min of Bs over the chunk
+    int span;   // lines + (max - min of Bs)
+    int base;   // grid coordinate of tile index 0 across lines (masked)
+};
+
+__device__ __forceinline__ ChunkGeom chunk_geom(const int16_t* bs, int ch, int dir, int nx, int X0, int lines,
+                                                int mx) {
+    ChunkGeom c;
+    c.y0 = dir > 0 ? ch * kSteps : nx - (ch + 1) * kSteps;
+    const int b0 = bs[c.y0], b1 = bs[c.y0 + kSteps - 1];
+    c.bmin = min(b0, b1);
+    c.span = lines + max(b0, b1) - c.bmin;
+    c.base = (X0 + c.bmin) & mx;
+    return c;
+}
+
+// Issue the copies of one chunk into a stage.
+__device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeom& c, bool steep,
+                                               const uint32_t* Vp, const uint16_t* Bp, int lx, int mx) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (!steep) {
+        // rows r in [0, span), columns s in [0, 16): V words and B word pairs
+        for (int k = tid; k < c.span * kSteps; k += nt) {
+            const int r = k >> 4, s = k & 15;
+            const int64_t row = (int64_t)((c.base + r) & mx) << lx;
+            cp_async4(&st.v[r * (kSteps + 1) + s], Vp + row + c.y0 + s);
+        }
+        for (int k = tid; k < c.span * (kSteps / 2); k += nt) {
+            const int r = k >> 3, s2 = (k & 7) * 2;
+            const int64_t row = (int64_t)((c.base + r) & mx) << lx;
+            cp_async4(&st.b[r * (kSteps + 2) + s2], Bp + row + c.y0 + s2);
+        }
+    } else {
+        // step rows s in [0, 16), columns x in [0, span) starting at base
+        for (int k = tid; k < kSteps * c.span; k += nt) {
+            const int s = k / c.span, x = k - s * c.span;
+            const int64_t row = (int64_t)(c.y0 + s) << lx;
+            cp_async4(&st.v[s * (kSpan + 1) + x], Vp + row + ((c.base + x) & mx));
+        }
+        // B as aligned word pairs covering [base, base + span): halfword
+        // index h of tile row s holds column (base & ~1) + h
+        const int a = c.base & ~1;
+        const int words = (c.span + 2) >> 1;
+        for (int k = tid; k < kSteps * words; k += nt) {
+            const int s = k / words, wd = k - s * words;
+            const int64_t row = (int64_t)(c.y0 + s) << lx;
+            cp_async4(&st.b[s * (kSpan + 4) + 2 * wd], Bp + row + ((a + 2 * wd) & mx));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMaxLines, 3)
 k_straight(DevGrid g, Volumes vol, int mu) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StraightStage* stage = reinterpret_cast<StraightStage*>(smem_raw);
     const int T = blockIdx.y;
-    const int xq = blockIdx.x * blockDim.x + threadIdx.x;
-    if (xq >= g.nx) return;
+    const int lines = blockDim.x;  // min(Nx, 256)
+    const int X0 = blockIdx.x * lines;
+    const int t = threadIdx.x;
     const PlaneInfo pi = g.plane[T];
-    const int dir = mu == SF ? pi.jsign : -pi.jsign;
+    const bool steep = pi.iflag != 0;
+    const int dir = mu == SF ? pi.jsign : -pi.jsign;  // direction of y' along the sweep
     const int16_t* bs = g.bshear + (int64_t)T * g.nx;
     const int64_t nxy = (int64_t)g.nx * g.nx;
     uint32_t* Vp = vol.V + (int64_t)T * nxy;
@@ -230,33 +319,116 @@ k_straight(DevGrid g, Volumes vol, int mu) {
     const uint16_t* Bp = vol.B + (int64_t)T * nxy;
     const uint32_t w = pi.wS, ct = g.ct;
     const uint32_t mtag = (uint32_t)mu << 13;
+    // Sweep order: dir > 0 visits y' = 0, 1, .., Nx-1 (q = y'); dir < 0
+    // visits Nx-1, .., 1, 0 (q = Nx - y').  Starting at Nx-1 with nothing
+    // carried equals starting at the wall cell y' = 0, which carries nothing.
     uint32_t v = 0xFFFFFFFFu;
     int pv = 0;
     uint32_t nimp = 0;
-    for (int k0 = 0; k0 < g.nx; k0 += CH) {
-        uint32_t id[CH], u[CH], e[CH];
-#pragma unroll
-        for (int c = 0; c < CH; c++) {
-            const int y = (dir * (k0 + c)) & g.mx;
-            const int col = (xq + bs[y]) & g.mx;
-            id[c] = pi.iflag ? (uint32_t)(col | (y << g.lx)) : (uint32_t)(y | (col << g.lx));
-            const uint16_t ob = __ldg(Bp + id[c]);
-            const uint32_t vv = __ldg(Vp + id[c]);
-            e[c] = edge_cost(ob, w);
-            u[c] = ob == HARD ? 0u : min(vv, TH);
-        }
-#pragma unroll
-        for (int c = 0; c < CH; c++) {
-            const int q = k0 + c;
-            if (v < u[c]) {
-                Vp[id[c]] = v;
-                Lp[id[c]] = (uint16_t)(mtag | (uint32_t)(q - pv));
-                nimp++;
+    const int nch = g.nx / kSteps;
+
+    ChunkGeom geo0 = chunk_geom(bs, 0, dir, g.nx, X0, lines, g.mx), geo1 = geo0;
+    straight_issue(stage[0], geo0, steep, Vp, Bp, g.lx, g.mx);
+    cp_async_commit();
+    if (nch > 1) {
+        geo1 = chunk_geom(bs, 1, dir, g.nx, X0, lines, g.mx);
+        straight_issue(stage[1], geo1, steep, Vp, Bp, g.lx, g.mx);
+    }
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ch++) {
+        const int sb = ch & 1;
+        StraightStage& st = stage[sb];
+        const ChunkGeom c = sb ? geo1 : geo0;
+        cp_async_wait1();
+        __syncthreads();
+        // ---- scan this thread's line over the chunk
+        const int bofs = steep ? (c.base & 1) : 0;
+#pragma unroll 4
+        for (int kk = 0; kk < kSteps; kk++) {
+            const int s = dir > 0 ? kk : kSteps - 1 - kk;
+            const int y = c.y0 + s;
+            const int q = dir > 0 ? y : g.nx - y;
+            const int a = t + bs[y] - c.bmin;  // tile index across lines, in [0, span)
+            const int vi = steep ? s * (kSpan + 1) + a : a * (kSteps + 1) + s;
+            const int bi = steep ? s * (kSpan + 4) + a + bofs : a * (kSteps + 2) + s;
+            const uint16_t ob = st.b[bi];
+            const uint32_t e = edge_cost(ob, w);
+            const uint32_t u = ob == HARD ? 0u : min(st.v[vi], TH);
+            if (v < u) {
+                st.v[vi] = v | kMark;
+                st.b[bi] = (uint16_t)(mtag | (uint32_t)(q - pv));
             }
-            const uint32_t t = u[c] + ct;
-            if (t < v) { v = t; pv = q; }
-            v += e[c];
+            const uint32_t tt = u + ct;
+            if (tt < v) { v = tt; pv = q; }
+            v += e;
         }
+        __syncthreads();
+        // ---- write back the marked cells, row segment by row segment
+        if (!steep) {
+            for (int k = t; k < c.span * kSteps; k += lines) {
+                const int r = k >> 4, s = k & 15;
+                const uint32_t x = st.v[r * (kSteps + 1) + s];
+                if ((x >> 30) == 2u) {
+                    const int64_t id = ((int64_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
+                    Vp[id] = x & ~kMark;
+                    Lp[id] = st.b[r * (kSteps + 2) + s];
+                    nimp++;
+                }
+            }
+        } else {
+            for (int k = t; k < kSteps * c.span; k += lines) {
+                const int s = k / c.span, xx = k - s * c.span;
+                const uint32_t x = st.v[s * (kSpan + 1) + xx];
+                if ((x >> 30) == 2u) {
+                    const int64_t id = ((int64_t)(c.y0 + s) << g.lx) + ((c.base + xx) & g.mx);
+                    Vp[id] = x & ~kMark;
+                    Lp[id] = st.b[s * (kSpan + 4) + xx + bofs];
+                    nimp++;
+                }
+            }
+        }
+        __syncthreads();
+        if (ch + 2 < nch) {
+            const ChunkGeom nxt = chunk_geom(bs, ch + 2, dir, g.nx, X0, lines, g.mx);
+            if (sb) geo1 = nxt;
+            else geo0 = nxt;
+            straight_issue(stage[sb], nxt, steep, Vp, Bp, g.lx, g.mx);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait0();
+    if (vol.improved) count_improved(vol.improved, nimp);
+}
+
+// Grids narrower than one 16-step chunk: the plain per-thread loop.
+__global__ void k_straight_small(DevGrid g, Volumes vol, int mu) {
+    const int T = blockIdx.y;
+    const int xq = threadIdx.x;
+    const PlaneInfo pi = g.plane[T];
+    const int dir = mu == SF ? pi.jsign : -pi.jsign;
+    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    uint32_t* Vp = vol.V + (int64_t)T * nxy;
+    uint16_t* Lp = vol.L + (int64_t)T * nxy;
+    const uint16_t* Bp = vol.B + (int64_t)T * nxy;
+    const uint32_t mtag = (uint32_t)mu << 13;
+    uint32_t v = 0xFFFFFFFFu, nimp = 0;
+    int pv = 0;
+    for (int q = 0; q < g.nx; q++) {
+        const int y = (dir * q) & g.mx;
+        const int col = (xq + bs[y]) & g.mx;
+        const uint32_t id = pi.iflag ? (uint32_t)(col | (y << g.lx)) : (uint32_t)(y | (col << g.lx));
+        const uint16_t ob = Bp[id];
+        const uint32_t e = edge_cost(ob, pi.wS);
+        const uint32_t u = ob == HARD ? 0u : min(Vp[id], TH);
+        if (v < u) {
+            Vp[id] = v;
+            Lp[id] = (uint16_t)(mtag | (uint32_t)(q - pv));
+            nimp++;
+        }
+        const uint32_t tt = u + g.ct;
+        if (tt < v) { v = tt; pv = q; }
+        v += e;
     }
     if (vol.improved) count_improved(vol.improved, nimp);
 }
@@ -287,10 +459,23 @@ cudaError_t launch_turn(const DevGrid& g, Volumes v, int family, int asc, int mu
 }
 
 cudaError_t launch_straight(const DevGrid& g, Volumes v, int mu, cudaStream_t s) {
-    const int tpb = g.nx < 256 ? g.nx : 256;
-    dim3 grid((unsigned)((g.nx + tpb - 1) / tpb), (unsigned)g.nt);
-    if (g.nx >= 8) k_straight<8><<<grid, tpb, 0, s>>>(g, v, mu);
-    else k_straight<4><<<grid, tpb, 0, s>>>(g, v, mu);
+    if (g.nx < kSteps) {
+        k_straight_small<<<dim3(1, (unsigned)g.nt), g.nx, 0, s>>>(g, v, mu);
+        return cudaGetLastError();
+    }
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const size_t smem = 2 * sizeof(StraightStage);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_straight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const int tpb = g.nx < kMaxLines ? g.nx : kMaxLines;
+    dim3 grid((unsigned)(g.nx / tpb), (unsigned)g.nt);
+    k_straight<<<grid, tpb, smem, s>>>(g, v, mu);
     return cudaGetLastError();
 }
 
