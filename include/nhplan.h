@@ -87,7 +87,7 @@ typedef struct {
 
 typedef struct {
     int32_t nx_log2;       /* 2..12 */
-    int32_t ntheta_log2;   /* 2..10 */
+    int32_t ntheta_log2;   /* 2..10, with 2*nx_log2 + ntheta_log2 <= 32 */
     const uint16_t* image; /* host pointer, Nx*Nx values, see "Image" above */
 } plan_grid;
 

@@ -285,7 +285,8 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     if (!out) return PLAN_EINVAL;
     *out = nullptr;
     if (!grid || !footprint || !costs || !grid->image) return PLAN_EINVAL;
-    if (grid->nx_log2 < 2 || grid->nx_log2 > 12 || grid->ntheta_log2 < 2 || grid->ntheta_log2 > 10)
+    if (grid->nx_log2 < 2 || grid->nx_log2 > 12 || grid->ntheta_log2 < 2 || grid->ntheta_log2 > 10 ||
+        2 * grid->nx_log2 + grid->ntheta_log2 > 32)  // at most 2^32 pose cells
         return PLAN_EINVAL;
     if (!(turn_radius_cells > 0) || turn_radius_cells > 1e6) return PLAN_EINVAL;
     if (footprint->front < 0 || footprint->rear < 0 || footprint->half_width < 0 || footprint->front > 2000 ||

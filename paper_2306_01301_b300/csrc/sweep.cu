@@ -29,6 +29,8 @@
 // u = 0 for hard cells (a hard cell is never stored because v < 0 is
 // impossible, and its entry is cancelled by its edge cost TH before it can
 // reach another cell).
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace nhp {
@@ -37,6 +39,14 @@ namespace {
 __device__ __forceinline__ uint32_t edge_cost(uint16_t b, uint32_t w) {
     return b == HARD ? TH : (w * (uint32_t)b) >> 8;
 }
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Profiling only: add this warp's improved-cell count to the plan counter.
 __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t n) {
@@ -49,20 +59,25 @@ __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t
 }
 
 // ------------------------------------------------------------------- turns
-// CTA = 32 chains x S sections; warp s holds headings [sK, sK+K) of its lane's
-// chain in registers.  Scan-order positions: ascending r = T, descending
-// r = NT-1-T; positions of the storing (second) loop are r + NT.
+// A block owns 32 chains (lanes: 32 neighbouring x' of one y', so every
+// heading plane is read as one rotated 128-byte row segment) and SL sections
+// of K headings each (warps).  With CL = 2 a thread-block cluster of two
+// blocks shares the chains: block rank r holds headings [r*NT/2, (r+1)*NT/2)
+// and the two halves exchange their composite section maps through
+// distributed shared memory, so two independent 512-thread blocks fit on an
+// SM and overlap each other's load and compute phases.
+// Scan-order positions: ascending r = T, descending r = NT-1-T; positions of
+// the storing (second) loop are r + NT.
 
-// Section-map arrays are [section][chain].  The carry scan reads them with
-// lanes spread over (section, chain) = (l % S, l / S); a row pitch of
-// 32 + 32/S words puts those 32 reads in 32 different banks.
-template <int K, int S>
+template <int K, int SL, int CL>
 struct TurnSmem {
-    static constexpr int P = 32 + 32 / S;
-    int2 beta[K * S];
-    uint32_t sa[S][P];
-    uint32_t sb[S][P];
-    int32_t sp[S][P];
+    static constexpr int P = 32 + 32 / SL;  // pitch: the carry scan's reads hit 32 banks
+    int2 cell[K * SL];   // per heading: (offset of the chain row in the volume, x shift)
+    uint32_t sa[SL][P];
+    uint32_t sb[SL][P];
+    int32_t sp[SL][P];
+    uint32_t tot[2][3][32];                 // per scan: this block's composite (A, B, P)
+    uint16_t lab[K][32 * SL];               // labels of improved cells
 };
 
 // Compose an earlier stretch X with a later one Y (in place into Y):
@@ -74,105 +89,195 @@ __device__ __forceinline__ void combine(uint32_t xa, uint32_t xb, int xp, uint32
     ya = min(xa + ya, TH);
 }
 
-template <int K, int S, bool ASC>
-__device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t (&lab)[(K + 1) / 2],
-                                          uint32_t& chg, int mu, uint32_t ct, int sec, int lane,
-                                          TurnSmem<K, S>& sm) {
-    constexpr int NT = K * S;
-    const int ss = ASC ? sec : S - 1 - sec;  // section index in scan order
-    // 1) this section's map (first-loop positions in [0, NT)).
-    uint32_t a = 0, b = 0xFFFFFFFFu;
+template <int K, int SL, int CL, bool ASC>
+__device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t& chg, int mu,
+                                          uint32_t ct, int sec, int lane, int rank, int scan, uint32_t a,
+                                          bool live, TurnSmem<K, SL, CL>& sm) {
+    constexpr int S = SL * CL, NT = K * S;
+    const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);  // this block's place in scan order
+    const int sl = ASC ? sec : SL - 1 - sec;                     // section index in scan order, local
+    const int ss = sr * SL + sl;                                 // ... global
+    // 1) this section's map (first-loop positions in [0, NT)); its slope
+    //    `a`, the section's summed edge costs, is the same in both directions.
+    // "nothing produced" must stay within the composition bound (<= 2TH + ct)
+    uint32_t b = TH;
     int pb = 0;
+    if (__any_sync(0xFFFFFFFFu, live)) {
+        b = 0xFFFFFFFFu;  // lowered to <= TH + ct by the first cell
 #pragma unroll
-    for (int kk = 0; kk < K; kk++) {
-        const int k = ASC ? kk : K - 1 - kk;
-        const uint32_t t = u[k] + ct;
-        if (t < b) { b = t; pb = ss * K + kk; }
-        b += e[k];
-        a = min(a + e[k], TH);
+        for (int kk = 0; kk < K; kk++) {
+            const int k = ASC ? kk : K - 1 - kk;
+            const uint32_t t = u[k] + ct;
+            if (t < b) { b = t; pb = ss * K + kk; }
+            b += e[k];
+        }
     }
-    sm.sa[ss][lane] = a;
-    sm.sb[ss][lane] = b;
-    sm.sp[ss][lane] = pb;
+    sm.sa[sl][lane] = a;
+    sm.sb[sl][lane] = b;
+    sm.sp[sl][lane] = pb;
     __syncthreads();
-    // 2) carry into each section of the second loop: segmented warp scan
-    //    over the S section maps of each chain (32/S chains per warp).
+    // 2) segmented warp scan over the SL local section maps of each chain
+    //    (32/SL chains per warp), then the carry into each section of the
+    //    second loop.
     {
-        const int c = sec * (32 / S) + lane / S;
-        const int s = lane % S;
+        const int c = sec * (32 / SL) + lane / SL;
+        const int s = lane % SL;
         uint32_t A = sm.sa[s][c], B = sm.sb[s][c];
         int P = sm.sp[s][c];
 #pragma unroll
-        for (int off = 1; off < S; off <<= 1) {
-            const uint32_t xa = __shfl_up_sync(0xFFFFFFFFu, A, off, S);
-            const uint32_t xb = __shfl_up_sync(0xFFFFFFFFu, B, off, S);
-            const int xp = __shfl_up_sync(0xFFFFFFFFu, P, off, S);
+        for (int off = 1; off < SL; off <<= 1) {
+            const uint32_t xa = __shfl_up_sync(0xFFFFFFFFu, A, off, SL);
+            const uint32_t xb = __shfl_up_sync(0xFFFFFFFFu, B, off, SL);
+            const int xp = __shfl_up_sync(0xFFFFFFFFu, P, off, SL);
             if (s >= off) combine(xa, xb, xp, A, B, P);
         }
-        // the whole first loop applied to 'nothing carried'
-        const uint32_t bF = __shfl_sync(0xFFFFFFFFu, B, S - 1, S);
-        const int pF = __shfl_sync(0xFFFFFFFFu, P, S - 1, S);
-        // map of sections 0..s-1 of the second loop
-        const uint32_t eA = __shfl_up_sync(0xFFFFFFFFu, A, 1, S);
-        const uint32_t eB = __shfl_up_sync(0xFFFFFFFFu, B, 1, S);
-        const int eP = __shfl_up_sync(0xFFFFFFFFu, P, 1, S);
-        uint32_t cv = bF;
-        int cp = pF;
+        // this block's whole stretch (inclusive map of its last section)
+        const uint32_t tA = __shfl_sync(0xFFFFFFFFu, A, SL - 1, SL);
+        const uint32_t tB = __shfl_sync(0xFFFFFFFFu, B, SL - 1, SL);
+        const int tP = __shfl_sync(0xFFFFFFFFu, P, SL - 1, SL);
+        // map of the local sections before s
+        const uint32_t eA = __shfl_up_sync(0xFFFFFFFFu, A, 1, SL);
+        const uint32_t eB = __shfl_up_sync(0xFFFFFFFFu, B, 1, SL);
+        const int eP = __shfl_up_sync(0xFFFFFFFFu, P, 1, SL);
+        uint32_t cv;  // carry into the first local section of the second loop
+        int cp;
+        if (CL == 1) {
+            cv = tB;
+            cp = tP;
+        } else {
+            if (s == 0) {
+                sm.tot[scan][0][c] = tA;
+                sm.tot[scan][1][c] = tB;
+                sm.tot[scan][2][c] = tP;
+            }
+            cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+            cluster.sync();
+            // composites of the blocks in scan order: j-th block holds scan
+            // positions [j*NT/CL, (j+1)*NT/CL)
+            uint32_t rA[CL], rB[CL];
+            int rP[CL];
+#pragma unroll
+            for (int j = 0; j < CL; j++) {
+                const int rk = ASC ? j : CL - 1 - j;  // cluster rank of scan-order block j
+                const TurnSmem<K, SL, CL>* o = cluster.map_shared_rank(&sm, rk);
+                rA[j] = o->tot[scan][0][c];
+                rB[j] = o->tot[scan][1][c];
+                rP[j] = o->tot[scan][2][c];
+            }
+            // the whole first loop applied to 'nothing carried'
+            uint32_t fA = rA[0], fB = rB[0];
+            int fP = rP[0];
+#pragma unroll
+            for (int j = 1; j < CL; j++) {
+                uint32_t a2 = rA[j], b2 = rB[j];
+                int p2 = rP[j];
+                combine(fA, fB, fP, a2, b2, p2);
+                fA = a2; fB = b2; fP = p2;
+            }
+            // then the second loop's blocks before this one
+            cv = fB;
+            cp = fP;
+#pragma unroll
+            for (int j = 0; j < CL - 1; j++) {
+                if (j < sr) {
+                    const uint32_t cand = cv + rA[j];
+                    if (!(cand <= rB[j])) { cv = rB[j]; cp = rP[j] + NT; }
+                    else cv = cand;
+                }
+            }
+        }
+        uint32_t iv = cv;
+        int ip = cp;
         if (s > 0) {
-            const uint32_t cand = bF + eA;  // first-loop entries are further upstream
-            if (cand <= eB) { cv = cand; cp = pF; }
-            else { cv = eB; cp = eP + NT; }
+            const uint32_t cand = cv + eA;  // entries before this block's loop-2 sections are further upstream
+            if (cand <= eB) { iv = cand; ip = cp; }
+            else { iv = eB; ip = eP + NT; }
         }
         __syncwarp();
-        sm.sb[s][c] = cv;
-        sm.sp[s][c] = cp;
+        sm.sb[s][c] = iv;
+        sm.sp[s][c] = ip;
     }
     __syncthreads();
     // 3) second loop: store where strictly better.
-    uint32_t v = sm.sb[ss][lane];
-    int pv = sm.sp[ss][lane];
-    const uint32_t mtag = (uint32_t)mu << 13;
+    const uint32_t v0 = sm.sb[sl][lane];
+    const int p0 = sm.sp[sl][lane];
+    // Lean pass: the carried value alone, and whether any cell improves.
+    // Improvements are rare once the front has passed, so the pass that also
+    // tracks entry positions and writes labels runs only in warps that need it.
+    bool any = false;
+    if (__any_sync(0xFFFFFFFFu, live || v0 < TH)) {
+        uint32_t v = v0;
 #pragma unroll
-    for (int kk = 0; kk < K; kk++) {
-        const int k = ASC ? kk : K - 1 - kk;
-        const int q = NT + ss * K + kk;
-        const uint32_t uk = u[k];
-        if (v < uk) {
-            u[k] = v;
-            const uint32_t l = mtag | (uint32_t)(q - pv);
-            lab[k >> 1] = (k & 1) ? ((lab[k >> 1] & 0xFFFFu) | (l << 16)) : ((lab[k >> 1] & 0xFFFF0000u) | l);
-            chg |= 1u << k;
+        for (int kk = 0; kk < K; kk++) {
+            const int k = ASC ? kk : K - 1 - kk;
+            any |= v < u[k];
+            v = min(v, u[k] + ct) + e[k];
         }
-        const uint32_t t = uk + ct;
-        if (t < v) { v = t; pv = q; }
-        v += e[k];
     }
-    __syncthreads();  // the shared summaries are reused by the next scan
+    if (__any_sync(0xFFFFFFFFu, any)) {
+        uint32_t v = v0;
+        int pv = p0;
+        const uint32_t mtag = (uint32_t)mu << 13;
+        const int tid = sec * 32 + lane;
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = ASC ? kk : K - 1 - kk;
+            const int q = NT + ss * K + kk;
+            const uint32_t uk = u[k];
+            if (v < uk) {
+                u[k] = v;
+                sm.lab[k][tid] = (uint16_t)(mtag | (uint32_t)(q - pv));
+                chg |= 1u << k;
+            }
+            const uint32_t t = uk + ct;
+            if (t < v) { v = t; pv = q; }
+            v += e[k];
+        }
+    }
+    __syncthreads();  // the section arrays are reused by the next scan
 }
 
-template <int K, int S>
-__global__ void __launch_bounds__(32 * S, 1)
+template <int K, int SL, int CL>
+__global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : (1024 / (32 * SL) < 1 ? 1 : 1024 / (32 * SL)))
 k_turn(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
-    constexpr int NT = K * S;
-    __shared__ TurnSmem<K, S> sm;
+    constexpr int NTL = K * SL;  // headings held by this block
+    __shared__ TurnSmem<K, SL, CL> sm;
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
-    for (int t = tid; t < NT; t += 32 * S) {
-        const int4 b = g.beta4[t];
-        sm.beta[t] = family ? make_int2(b.z, b.w) : make_int2(b.x, b.y);
-    }
-    __syncthreads();
+    const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
+    const int tile = CL == 1 ? (int)blockIdx.x : (int)(blockIdx.x / CL);
+    const int T0 = rank * NTL;
     const int64_t nxy = (int64_t)g.nx * g.nx;
-    const int64_t chain = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t chain = (int64_t)tile * 32 + lane;
     const bool valid = chain < nxy;
     const int xq = (int)(chain & g.mx), yq = (int)((chain >> g.lx) & g.mx);
+    // With Nx >= 32 all 32 chains of the block share y', so each heading's
+    // chain row has one offset: precompute (row offset, x shift) per heading.
+    const bool row_uniform = g.nx >= 32;
+    for (int t = tid; t < NTL; t += 32 * SL) {
+        const int4 b = g.beta4[T0 + t];
+        const int bx = family ? b.z : b.x, by = family ? b.w : b.y;
+        const int ybase = row_uniform ? (int)(((int64_t)tile * 32 >> g.lx) & g.mx) : 0;
+        // volumes hold at most 2^32 cells, so 32-bit offsets suffice
+        if (row_uniform)
+            sm.cell[t] = make_int2((int)(uint32_t)((((ybase + by) & g.mx) << g.lx) + (int64_t)(T0 + t) * nxy), bx);
+        else
+            sm.cell[t] = make_int2((int)(uint32_t)((int64_t)(T0 + t) * nxy), (bx & g.mx) | ((by & g.mx) << 16));
+    }
+    __syncthreads();
     const uint32_t w = g.wA, ct = g.ct;
+    auto cell_index = [&](int T) -> uint32_t {
+        const int2 c = sm.cell[T];
+        if (row_uniform) return (uint32_t)c.x + (uint32_t)((xq + c.y) & g.mx);
+        const int bx = c.y & 0xFFFF, by = c.y >> 16;
+        return (uint32_t)c.x + (uint32_t)(((xq + bx) & g.mx) | (((yq + by) & g.mx) << g.lx));
+    };
 
-    uint32_t u[K], e[K], lab[(K + 1) / 2];
+    uint32_t u[K], e[K];
+    uint32_t a = 0;     // summed edge costs of this thread's section
+    bool live = false;  // the section holds a reached, non-hard cell
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        const int T = sec * K + k;
-        const int2 bb = sm.beta[T];
-        const int64_t id = (int64_t)(((xq + bb.x) & g.mx) | (((yq + bb.y) & g.mx) << g.lx)) + (int64_t)T * nxy;
+        const uint32_t id = cell_index(sec * K + k);
         uint32_t vv = 0xFFFFFFFFu;
         uint16_t ob = HARD;
         if (valid) {
@@ -181,37 +286,340 @@ k_turn(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
         }
         e[k] = edge_cost(ob, w);
         u[k] = ob == HARD ? 0u : min(vv, TH);
+        a = min(a + e[k], TH);
+        live |= ob != HARD && vv < TH;
     }
-#pragma unroll
-    for (int k = 0; k < (K + 1) / 2; k++) lab[k] = 0;
     uint32_t chg = 0;
-    if (asc) turn_scan<K, S, true>(u, e, lab, chg, mu1, ct, sec, lane, sm);
-    else turn_scan<K, S, false>(u, e, lab, chg, mu1, ct, sec, lane, sm);
+    if (asc) turn_scan<K, SL, CL, true>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm);
+    else turn_scan<K, SL, CL, false>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm);
     if (mu2 >= 0) {
-        if (asc) turn_scan<K, S, false>(u, e, lab, chg, mu2, ct, sec, lane, sm);
-        else turn_scan<K, S, true>(u, e, lab, chg, mu2, ct, sec, lane, sm);
+        live = live || chg != 0;
+        if (asc) turn_scan<K, SL, CL, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm);
+        else turn_scan<K, SL, CL, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm);
     }
     if (vol.improved) count_improved(vol.improved, __popc(chg));
-    if (!valid || chg == 0) return;
+    if (valid && chg) {
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        if (chg & (1u << k)) {
-            const int T = sec * K + k;
-            const int2 bb = sm.beta[T];
-            const int64_t id =
-                (int64_t)(((xq + bb.x) & g.mx) | (((yq + bb.y) & g.mx) << g.lx)) + (int64_t)T * nxy;
-            vol.V[id] = u[k];
-            vol.L[id] = (uint16_t)((k & 1) ? (lab[k >> 1] >> 16) : (lab[k >> 1] & 0xFFFFu));
+        for (int k = 0; k < K; k++) {
+            if (chg & (1u << k)) {
+                const uint32_t id = cell_index(sec * K + k);
+                vol.V[id] = u[k];
+                vol.L[id] = sm.lab[k][tid];
+            }
+        }
+    }
+    // the partner block reads this block's shared memory: leave together
+    if (CL > 1) cooperative_groups::this_cluster().sync();
+}
+
+// ------------------------------------------------------ pipelined turn sweep
+// Persistent form of the turn kernel for Nx >= 32 (all 32 chains of a tile
+// share y'): each cluster walks chain tiles tile0, tile0 + #clusters, ...;
+// while it scans tile i from registers, cp.async streams tile i + 2 into
+// the other shared-memory stage, so HBM traffic overlaps the scans.
+template <int K, int SL>
+struct TurnStage {
+    static constexpr int NTL = K * SL;
+    uint32_t v[NTL][32];      // V of the tile's chains, one row per heading
+    uint16_t b[NTL][36];      // B as aligned word pairs: lane l at [l + (shift & 1)]
+};
+
+template <int K, int SL, int CL>
+struct TurnPipeSmem {
+    static constexpr int P = 32 + 32 / SL;
+    TurnStage<K, SL> stage[2];
+    int2 beta[K * SL];        // this block's headings: (beta_x, beta_y) of the family
+    uint32_t sa[SL][P];
+    uint32_t sb[SL][P];
+    int32_t sp[SL][P];
+    uint32_t tot[4][3][32];   // composite exchange slots, rotating per scan
+    uint16_t lab[K][32 * SL];
+};
+
+// The scan (identical arithmetic to turn_scan) with the exchange slot and
+// shared layout of the pipelined kernel.
+// `live`: this thread's section holds a reached, non-hard cell.  A warp whose
+// sections hold none has no entries (its maps are "nothing produced") and,
+// when nothing is carried in either, cannot improve any of its cells, so it
+// skips those loops; the results are the same cell for cell.
+template <int K, int SL, int CL, bool ASC>
+__device__ __forceinline__ void turn_scan_pipe(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t& chg, int mu,
+                                               uint32_t ct, int sec, int lane, int rank, int slot, uint32_t a,
+                                               bool live, TurnPipeSmem<K, SL, CL>& sm) {
+    constexpr int S = SL * CL, NT = K * S;
+    const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);
+    const int sl = ASC ? sec : SL - 1 - sec;
+    const int ss = sr * SL + sl;
+    // "nothing produced" must stay within the composition bound (<= 2TH + ct)
+    uint32_t b = TH;
+    int pb = 0;
+    if (__any_sync(0xFFFFFFFFu, live)) {
+        b = 0xFFFFFFFFu;  // lowered to <= TH + ct by the first cell
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = ASC ? kk : K - 1 - kk;
+            const uint32_t t = u[k] + ct;
+            if (t < b) { b = t; pb = ss * K + kk; }
+            b += e[k];
+        }
+    }
+    sm.sa[sl][lane] = a;
+    sm.sb[sl][lane] = b;
+    sm.sp[sl][lane] = pb;
+    __syncthreads();
+    {
+        const int c = sec * (32 / SL) + lane / SL;
+        const int s = lane % SL;
+        uint32_t A = sm.sa[s][c], B = sm.sb[s][c];
+        int P = sm.sp[s][c];
+#pragma unroll
+        for (int off = 1; off < SL; off <<= 1) {
+            const uint32_t xa = __shfl_up_sync(0xFFFFFFFFu, A, off, SL);
+            const uint32_t xb = __shfl_up_sync(0xFFFFFFFFu, B, off, SL);
+            const int xp = __shfl_up_sync(0xFFFFFFFFu, P, off, SL);
+            if (s >= off) combine(xa, xb, xp, A, B, P);
+        }
+        const uint32_t tA = __shfl_sync(0xFFFFFFFFu, A, SL - 1, SL);
+        const uint32_t tB = __shfl_sync(0xFFFFFFFFu, B, SL - 1, SL);
+        const int tP = __shfl_sync(0xFFFFFFFFu, P, SL - 1, SL);
+        const uint32_t eA = __shfl_up_sync(0xFFFFFFFFu, A, 1, SL);
+        const uint32_t eB = __shfl_up_sync(0xFFFFFFFFu, B, 1, SL);
+        const int eP = __shfl_up_sync(0xFFFFFFFFu, P, 1, SL);
+        uint32_t cv;
+        int cp;
+        if (CL == 1) {
+            cv = tB;
+            cp = tP;
+        } else {
+            if (s == 0) {
+                sm.tot[slot][0][c] = tA;
+                sm.tot[slot][1][c] = tB;
+                sm.tot[slot][2][c] = tP;
+            }
+            cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+            cluster.sync();
+            uint32_t rA[CL], rB[CL];
+            int rP[CL];
+#pragma unroll
+            for (int j = 0; j < CL; j++) {
+                const int rk = ASC ? j : CL - 1 - j;
+                const TurnPipeSmem<K, SL, CL>* o = cluster.map_shared_rank(&sm, rk);
+                rA[j] = o->tot[slot][0][c];
+                rB[j] = o->tot[slot][1][c];
+                rP[j] = o->tot[slot][2][c];
+            }
+            uint32_t fA = rA[0], fB = rB[0];
+            int fP = rP[0];
+#pragma unroll
+            for (int j = 1; j < CL; j++) {
+                uint32_t a2 = rA[j], b2 = rB[j];
+                int p2 = rP[j];
+                combine(fA, fB, fP, a2, b2, p2);
+                fA = a2; fB = b2; fP = p2;
+            }
+            cv = fB;
+            cp = fP;
+#pragma unroll
+            for (int j = 0; j < CL - 1; j++) {
+                if (j < sr) {
+                    const uint32_t cand = cv + rA[j];
+                    if (!(cand <= rB[j])) { cv = rB[j]; cp = rP[j] + NT; }
+                    else cv = cand;
+                }
+            }
+        }
+        uint32_t iv = cv;
+        int ip = cp;
+        if (s > 0) {
+            const uint32_t cand = cv + eA;
+            if (cand <= eB) { iv = cand; ip = cp; }
+            else { iv = eB; ip = eP + NT; }
+        }
+        __syncwarp();
+        sm.sb[s][c] = iv;
+        sm.sp[s][c] = ip;
+    }
+    __syncthreads();
+    uint32_t v = sm.sb[sl][lane];
+    int pv = sm.sp[sl][lane];
+    const uint32_t mtag = (uint32_t)mu << 13;
+    const int tid = sec * 32 + lane;
+    if (__any_sync(0xFFFFFFFFu, live || v < TH)) {
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = ASC ? kk : K - 1 - kk;
+            const int q = NT + ss * K + kk;
+            const uint32_t uk = u[k];
+            if (v < uk) {
+                u[k] = v;
+                sm.lab[k][tid] = (uint16_t)(mtag | (uint32_t)(q - pv));
+                chg |= 1u << k;
+            }
+            const uint32_t t = uk + ct;
+            if (t < v) { v = t; pv = q; }
+            v += e[k];
+        }
+    }
+    __syncthreads();
+}
+
+// Copy one tile's V and B rows of this block's headings into a stage; warp
+// `sec` copies headings [sec*K, sec*K + K).
+template <int K, int SL, int CL>
+__device__ __forceinline__ void turn_issue(TurnPipeSmem<K, SL, CL>& sm, TurnStage<K, SL>& st, const DevGrid& g,
+                                           const Volumes& vol, int tile, int T0, int sec, int lane) {
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int x0 = (tile * 32) & g.mx;
+    const int y0 = ((tile * 32) >> g.lx) & g.mx;
+    const int hw = g.nx >> 1;  // words per B row
+#pragma unroll 4
+    for (int kk = 0; kk < K; kk++) {
+        const int T = sec * K + kk;
+        const int2 bb = sm.beta[T];
+        const int64_t row = (((int64_t)((y0 + bb.y) & g.mx)) << g.lx) + (int64_t)(T0 + T) * nxy;
+        const int c0 = (x0 + bb.x) & g.mx;
+        cp_async4(&st.v[T][lane], vol.V + row + ((c0 + lane) & g.mx));
+        if (lane < 17) {
+            const int wd = ((c0 >> 1) + lane) & (hw - 1);
+            cp_async4(&st.b[T][2 * lane], vol.B + row + 2 * wd);
         }
     }
 }
 
-template <int K, int S>
+template <int K, int SL, int CL>
+__global__ void __launch_bounds__(32 * SL, 3)
+k_turn_pipe(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
+    constexpr int NTL = K * SL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TurnPipeSmem<K, SL, CL>& sm = *reinterpret_cast<TurnPipeSmem<K, SL, CL>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
+    const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
+    const int cid = (int)(blockIdx.x / CL), ncl = (int)(gridDim.x / CL);
+    const int T0 = rank * NTL;
+    for (int t = tid; t < NTL; t += 32 * SL) {
+        const int4 b = g.beta4[T0 + t];
+        sm.beta[t] = family ? make_int2(b.z, b.w) : make_int2(b.x, b.y);
+    }
+    __syncthreads();
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int ntiles = (int)(nxy / 32);
+    const uint32_t w = g.wA, ct = g.ct;
+    int tile = cid;
+    if (tile < ntiles) turn_issue(sm, sm.stage[0], g, vol, tile, T0, sec, lane);
+    cp_async_commit();
+    if (tile + ncl < ntiles) turn_issue(sm, sm.stage[1], g, vol, tile + ncl, T0, sec, lane);
+    cp_async_commit();
+    uint64_t nimp = 0;
+    for (int it = 0; tile < ntiles; it++, tile += ncl) {
+        TurnStage<K, SL>& st = sm.stage[it & 1];
+        cp_async_wait1();
+        __syncthreads();
+        const int x0 = (tile * 32) & g.mx;
+        const int y0 = ((tile * 32) >> g.lx) & g.mx;
+        uint32_t u[K], e[K];
+        uint32_t a = 0;
+        bool live = false;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int T = sec * K + k;
+            const int c0 = (x0 + sm.beta[T].x) & g.mx;
+            const uint16_t ob = st.b[T][lane + (c0 & 1)];
+            const uint32_t vv = st.v[T][lane];
+            e[k] = edge_cost(ob, w);
+            u[k] = ob == HARD ? 0u : min(vv, TH);
+            a = min(a + e[k], TH);
+            live |= ob != HARD && vv < TH;
+        }
+        __syncthreads();  // stage consumed: refill it with tile it + 2
+        if (tile + 2 * ncl < ntiles) turn_issue(sm, st, g, vol, tile + 2 * ncl, T0, sec, lane);
+        cp_async_commit();
+        uint32_t chg = 0;
+        if (asc) turn_scan_pipe<K, SL, CL, true>(u, e, chg, mu1, ct, sec, lane, rank, (2 * it) & 3, a, live, sm);
+        else turn_scan_pipe<K, SL, CL, false>(u, e, chg, mu1, ct, sec, lane, rank, (2 * it) & 3, a, live, sm);
+        if (mu2 >= 0) {
+            live = live || chg != 0;
+            if (asc)
+                turn_scan_pipe<K, SL, CL, false>(u, e, chg, mu2, ct, sec, lane, rank, (2 * it + 1) & 3, a, live, sm);
+            else
+                turn_scan_pipe<K, SL, CL, true>(u, e, chg, mu2, ct, sec, lane, rank, (2 * it + 1) & 3, a, live, sm);
+        }
+        nimp += __popc(chg);
+        if (chg) {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (chg & (1u << k)) {
+                    const int T = sec * K + k;
+                    const int2 bb = sm.beta[T];
+                    const int64_t id = (((int64_t)((y0 + bb.y) & g.mx)) << g.lx) + (int64_t)(T0 + T) * nxy +
+                                       ((x0 + lane + bb.x) & g.mx);
+                    vol.V[id] = u[k];
+                    vol.L[id] = sm.lab[k][tid];
+                }
+            }
+        }
+    }
+    cp_async_wait0();
+    if (vol.improved) count_improved(vol.improved, (uint32_t)nimp);
+    if (CL > 1) cooperative_groups::this_cluster().sync();
+}
+
+template <int K, int SL, int CL>
+cudaError_t launch_turn_pipe(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
+    static int clusters[64] = {};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const size_t smem = sizeof(TurnPipeSmem<K, SL, CL>);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(32 * SL);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (dev < 0 || dev >= 64 || clusters[dev] == 0) {
+        err = cudaFuncSetAttribute(k_turn_pipe<K, SL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        int n = 0;
+        cfg.gridDim = dim3(CL);
+        err = cudaOccupancyMaxActiveClusters(&n, k_turn_pipe<K, SL, CL>, &cfg);
+        if (err != cudaSuccess) return err;
+        if (n < 1) n = 1;
+        if (dev >= 0 && dev < 64) clusters[dev] = n;
+        else clusters[0] = n;
+    }
+    const int64_t ntiles = (int64_t)g.nx * g.nx / 32;
+    int64_t ncl = clusters[(dev >= 0 && dev < 64) ? dev : 0];
+    if (ncl > ntiles) ncl = ntiles;
+    cfg.gridDim = dim3((unsigned)(ncl * CL));
+    return cudaLaunchKernelEx(&cfg, k_turn_pipe<K, SL, CL>, g, v, family, asc, mu1, mu2);
+}
+
+template <int K, int SL, int CL>
 cudaError_t launch_turn_t(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
     const int64_t chains = (int64_t)g.nx * g.nx;
-    const unsigned blocks = (unsigned)((chains + 31) / 32);
-    k_turn<K, S><<<blocks, 32 * S, 0, s>>>(g, v, family, asc, mu1, mu2);
-    return cudaGetLastError();
+    const unsigned tiles = (unsigned)((chains + 31) / 32);
+    if (CL == 1) {
+        k_turn<K, SL, CL><<<tiles, 32 * SL, 0, s>>>(g, v, family, asc, mu1, mu2);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles * CL);
+    cfg.blockDim = dim3(32 * SL);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, g, v, family, asc, mu1, mu2);
 }
 
 // ---------------------------------------------------------------- straights
@@ -238,20 +646,12 @@ constexpr uint32_t kMark = 0x80000000u;             // changed; stored values ar
 struct StraightStage {
     uint32_t v[kVWords];
     uint16_t b[kBHalves];
+    int16_t bs[kSteps];  // Bs(y0 + s) - bmin, s = 0..15
 };
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 struct ChunkGeom {
     int y0;     // first step of the chunk (ascending y')
-    int bmin;   // min of Bs over the chunk
-    int span;   // lines + (max - min of Bs)
+    int span;   // lines + (max - min of Bs over the chunk)
     int base;   // grid coordinate of tile index 0 across lines (masked)
 };
 
@@ -260,58 +660,61 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const int16_t* bs, int ch, int d
     ChunkGeom c;
     c.y0 = dir > 0 ? ch * kSteps : nx - (ch + 1) * kSteps;
     const int b0 = bs[c.y0], b1 = bs[c.y0 + kSteps - 1];
-    c.bmin = min(b0, b1);
-    c.span = lines + max(b0, b1) - c.bmin;
-    c.base = (X0 + c.bmin) & mx;
+    c.span = lines + max(b0, b1) - min(b0, b1);
+    c.base = (X0 + min(b0, b1)) & mx;
     return c;
 }
 
-// Issue the copies of one chunk into a stage.
-__device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeom& c, bool steep,
+// Tile layouts.  Shallow: v[r][s] pitch 17 words, b[r][s] pitch 18 halves
+// (r = grid row offset, s = step).  Steep: v[s][x] pitch 273 words,
+// b[s][h] pitch 276 halves with h = x + (base & 1) (B is copied in aligned
+// word pairs).  Both put the 32 cells a warp reads in one step into 32
+// different banks.
+template <bool STEEP>
+__device__ __forceinline__ int vidx(int s, int a) { return STEEP ? s * (kSpan + 1) + a : a * (kSteps + 1) + s; }
+template <bool STEEP>
+__device__ __forceinline__ int bidx(int s, int a, int bofs) {
+    return STEEP ? s * (kSpan + 4) + a + bofs : a * (kSteps + 2) + s;
+}
+
+template <bool STEEP>
+__device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeom& c, const int16_t* bs,
                                                const uint32_t* Vp, const uint16_t* Bp, int lx, int mx) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (!steep) {
-        // rows r in [0, span), columns s in [0, 16): V words and B word pairs
-        for (int k = tid; k < c.span * kSteps; k += nt) {
-            const int r = k >> 4, s = k & 15;
-            const int64_t row = (int64_t)((c.base + r) & mx) << lx;
-            cp_async4(&st.v[r * (kSteps + 1) + s], Vp + row + c.y0 + s);
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t < kSteps) st.bs[t] = (int16_t)(bs[c.y0 + t] - min(bs[c.y0], bs[c.y0 + kSteps - 1]));
+    if (!STEEP) {
+        // thread t copies step s = t % 16 of rows t/16, t/16 + nt/16, ...
+        const int s = t & 15, rstep = nt >> 4;
+        for (int r = t >> 4; r < c.span; r += rstep) {
+            const uint32_t* src = Vp + ((int64_t)((c.base + r) & mx) << lx) + c.y0 + s;
+            cp_async4(&st.v[r * (kSteps + 1) + s], src);
         }
-        for (int k = tid; k < c.span * (kSteps / 2); k += nt) {
-            const int r = k >> 3, s2 = (k & 7) * 2;
-            const int64_t row = (int64_t)((c.base + r) & mx) << lx;
-            cp_async4(&st.b[r * (kSteps + 2) + s2], Bp + row + c.y0 + s2);
+        const int s2 = (t & 7) * 2, rstep2 = nt >> 3;
+        for (int r = t >> 3; r < c.span; r += rstep2) {
+            const uint16_t* src = Bp + ((int64_t)((c.base + r) & mx) << lx) + c.y0 + s2;
+            cp_async4(&st.b[r * (kSteps + 2) + s2], src);
         }
     } else {
-        // step rows s in [0, 16), columns x in [0, span) starting at base
-        for (int k = tid; k < kSteps * c.span; k += nt) {
-            const int s = k / c.span, x = k - s * c.span;
-            const int64_t row = (int64_t)(c.y0 + s) << lx;
-            cp_async4(&st.v[s * (kSpan + 1) + x], Vp + row + ((c.base + x) & mx));
-        }
-        // B as aligned word pairs covering [base, base + span): halfword
-        // index h of tile row s holds column (base & ~1) + h
         const int a = c.base & ~1;
         const int words = (c.span + 2) >> 1;
-        for (int k = tid; k < kSteps * words; k += nt) {
-            const int s = k / words, wd = k - s * words;
-            const int64_t row = (int64_t)(c.y0 + s) << lx;
-            cp_async4(&st.b[s * (kSpan + 4) + 2 * wd], Bp + row + ((a + 2 * wd) & mx));
+#pragma unroll 4
+        for (int s = 0; s < kSteps; s++) {
+            const uint32_t* vrow = Vp + ((int64_t)(c.y0 + s) << lx);
+            const uint16_t* brow = Bp + ((int64_t)(c.y0 + s) << lx);
+            for (int x = t; x < c.span; x += nt) cp_async4(&st.v[s * (kSpan + 1) + x], vrow + ((c.base + x) & mx));
+            for (int wd = t; wd < words; wd += nt)
+                cp_async4(&st.b[s * (kSpan + 4) + 2 * wd], brow + ((a + 2 * wd) & mx));
         }
     }
 }
 
-__global__ void __launch_bounds__(kMaxLines, 3)
-k_straight(DevGrid g, Volumes vol, int mu) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    StraightStage* stage = reinterpret_cast<StraightStage*>(smem_raw);
-    const int T = blockIdx.y;
+template <bool STEEP, bool FWD>
+__device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, int T, StraightStage* stage,
+                                              const PlaneInfo& pi) {
     const int lines = blockDim.x;  // min(Nx, 256)
     const int X0 = blockIdx.x * lines;
     const int t = threadIdx.x;
-    const PlaneInfo pi = g.plane[T];
-    const bool steep = pi.iflag != 0;
-    const int dir = mu == SF ? pi.jsign : -pi.jsign;  // direction of y' along the sweep
+    constexpr int dir = FWD ? 1 : -1;  // direction of y' along the sweep
     const int16_t* bs = g.bshear + (int64_t)T * g.nx;
     const int64_t nxy = (int64_t)g.nx * g.nx;
     uint32_t* Vp = vol.V + (int64_t)T * nxy;
@@ -328,11 +731,11 @@ k_straight(DevGrid g, Volumes vol, int mu) {
     const int nch = g.nx / kSteps;
 
     ChunkGeom geo0 = chunk_geom(bs, 0, dir, g.nx, X0, lines, g.mx), geo1 = geo0;
-    straight_issue(stage[0], geo0, steep, Vp, Bp, g.lx, g.mx);
+    straight_issue<STEEP>(stage[0], geo0, bs, Vp, Bp, g.lx, g.mx);
     cp_async_commit();
     if (nch > 1) {
         geo1 = chunk_geom(bs, 1, dir, g.nx, X0, lines, g.mx);
-        straight_issue(stage[1], geo1, steep, Vp, Bp, g.lx, g.mx);
+        straight_issue<STEEP>(stage[1], geo1, bs, Vp, Bp, g.lx, g.mx);
     }
     cp_async_commit();
     for (int ch = 0; ch < nch; ch++) {
@@ -341,19 +744,17 @@ k_straight(DevGrid g, Volumes vol, int mu) {
         const ChunkGeom c = sb ? geo1 : geo0;
         cp_async_wait1();
         __syncthreads();
-        // ---- scan this thread's line over the chunk
-        const int bofs = steep ? (c.base & 1) : 0;
-#pragma unroll 4
+        const int bofs = STEEP ? (c.base & 1) : 0;
+        const int qbase = FWD ? c.y0 : g.nx - c.y0;  // q = qbase + dir * s
+#pragma unroll
         for (int kk = 0; kk < kSteps; kk++) {
-            const int s = dir > 0 ? kk : kSteps - 1 - kk;
-            const int y = c.y0 + s;
-            const int q = dir > 0 ? y : g.nx - y;
-            const int a = t + bs[y] - c.bmin;  // tile index across lines, in [0, span)
-            const int vi = steep ? s * (kSpan + 1) + a : a * (kSteps + 1) + s;
-            const int bi = steep ? s * (kSpan + 4) + a + bofs : a * (kSteps + 2) + s;
+            const int s = FWD ? kk : kSteps - 1 - kk;
+            const int a = t + st.bs[s];  // tile index across lines, in [0, span)
+            const int vi = vidx<STEEP>(s, a), bi = bidx<STEEP>(s, a, bofs);
             const uint16_t ob = st.b[bi];
             const uint32_t e = edge_cost(ob, w);
             const uint32_t u = ob == HARD ? 0u : min(st.v[vi], TH);
+            const int q = qbase + (FWD ? s : -s);
             if (v < u) {
                 st.v[vi] = v | kMark;
                 st.b[bi] = (uint16_t)(mtag | (uint32_t)(q - pv));
@@ -363,10 +764,10 @@ k_straight(DevGrid g, Volumes vol, int mu) {
             v += e;
         }
         __syncthreads();
-        // ---- write back the marked cells, row segment by row segment
-        if (!steep) {
-            for (int k = t; k < c.span * kSteps; k += lines) {
-                const int r = k >> 4, s = k & 15;
+        // write back the marked cells, row segment by row segment
+        if (!STEEP) {
+            const int s = t & 15, rstep = lines >> 4;
+            for (int r = t >> 4; r < c.span; r += rstep) {
                 const uint32_t x = st.v[r * (kSteps + 1) + s];
                 if ((x >> 30) == 2u) {
                     const int64_t id = ((int64_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
@@ -376,14 +777,15 @@ k_straight(DevGrid g, Volumes vol, int mu) {
                 }
             }
         } else {
-            for (int k = t; k < kSteps * c.span; k += lines) {
-                const int s = k / c.span, xx = k - s * c.span;
-                const uint32_t x = st.v[s * (kSpan + 1) + xx];
-                if ((x >> 30) == 2u) {
-                    const int64_t id = ((int64_t)(c.y0 + s) << g.lx) + ((c.base + xx) & g.mx);
-                    Vp[id] = x & ~kMark;
-                    Lp[id] = st.b[s * (kSpan + 4) + xx + bofs];
-                    nimp++;
+            for (int s = 0; s < kSteps; s++) {
+                for (int xx = t; xx < c.span; xx += lines) {
+                    const uint32_t x = st.v[s * (kSpan + 1) + xx];
+                    if ((x >> 30) == 2u) {
+                        const int64_t id = ((int64_t)(c.y0 + s) << g.lx) + ((c.base + xx) & g.mx);
+                        Vp[id] = x & ~kMark;
+                        Lp[id] = st.b[s * (kSpan + 4) + xx + bofs];
+                        nimp++;
+                    }
                 }
             }
         }
@@ -392,12 +794,28 @@ k_straight(DevGrid g, Volumes vol, int mu) {
             const ChunkGeom nxt = chunk_geom(bs, ch + 2, dir, g.nx, X0, lines, g.mx);
             if (sb) geo1 = nxt;
             else geo0 = nxt;
-            straight_issue(stage[sb], nxt, steep, Vp, Bp, g.lx, g.mx);
+            straight_issue<STEEP>(stage[sb], nxt, bs, Vp, Bp, g.lx, g.mx);
         }
         cp_async_commit();
     }
     cp_async_wait0();
     if (vol.improved) count_improved(vol.improved, nimp);
+}
+
+__global__ void __launch_bounds__(kMaxLines, 3)
+k_straight(DevGrid g, Volumes vol, int mu) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StraightStage* stage = reinterpret_cast<StraightStage*>(smem_raw);
+    const int T = blockIdx.y;
+    const PlaneInfo pi = g.plane[T];
+    const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
+    if (pi.iflag) {
+        if (fwd) straight_body<true, true>(g, vol, mu, T, stage, pi);
+        else straight_body<true, false>(g, vol, mu, T, stage, pi);
+    } else {
+        if (fwd) straight_body<false, true>(g, vol, mu, T, stage, pi);
+        else straight_body<false, false>(g, vol, mu, T, stage, pi);
+    }
 }
 
 // Grids narrower than one 16-step chunk: the plain per-thread loop.
@@ -443,17 +861,37 @@ __global__ void k_init(Volumes vol, int64_t n, int64_t start) {
 
 }  // namespace
 
+// Shape of the 512-heading turn kernel: K headings per thread, SL sections
+// (warps) per block, CL blocks per cluster, K * SL * CL = 512.
+#ifndef TURN_PIPE
+#define TURN_PIPE 0  // the persistent cp.async-pipelined variant (slower while the scans are issue-bound)
+#endif
+#ifndef TURN512_K
+#define TURN512_K 16
+#define TURN512_SL 8
+#define TURN512_CL 4
+#endif
+
 cudaError_t launch_turn(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
+    if (TURN_PIPE && g.nx >= 32) {
+        switch (g.nt) {
+            case 128: return launch_turn_pipe<16, 8, 1>(g, v, family, asc, mu1, mu2, s);
+            case 256: return launch_turn_pipe<16, 8, 2>(g, v, family, asc, mu1, mu2, s);
+            case 512: return launch_turn_pipe<TURN512_K, TURN512_SL, TURN512_CL>(g, v, family, asc, mu1, mu2, s);
+            case 1024: return launch_turn_pipe<16, 8, 8>(g, v, family, asc, mu1, mu2, s);
+            default: break;
+        }
+    }
     switch (g.nt) {
-        case 4: return launch_turn_t<1, 4>(g, v, family, asc, mu1, mu2, s);
-        case 8: return launch_turn_t<2, 4>(g, v, family, asc, mu1, mu2, s);
-        case 16: return launch_turn_t<4, 4>(g, v, family, asc, mu1, mu2, s);
-        case 32: return launch_turn_t<8, 4>(g, v, family, asc, mu1, mu2, s);
-        case 64: return launch_turn_t<16, 4>(g, v, family, asc, mu1, mu2, s);
-        case 128: return launch_turn_t<16, 8>(g, v, family, asc, mu1, mu2, s);
-        case 256: return launch_turn_t<16, 16>(g, v, family, asc, mu1, mu2, s);
-        case 512: return launch_turn_t<16, 32>(g, v, family, asc, mu1, mu2, s);
-        case 1024: return launch_turn_t<32, 32>(g, v, family, asc, mu1, mu2, s);
+        case 4: return launch_turn_t<1, 4, 1>(g, v, family, asc, mu1, mu2, s);
+        case 8: return launch_turn_t<2, 4, 1>(g, v, family, asc, mu1, mu2, s);
+        case 16: return launch_turn_t<4, 4, 1>(g, v, family, asc, mu1, mu2, s);
+        case 32: return launch_turn_t<8, 4, 1>(g, v, family, asc, mu1, mu2, s);
+        case 64: return launch_turn_t<8, 8, 1>(g, v, family, asc, mu1, mu2, s);
+        case 128: return launch_turn_t<8, 16, 1>(g, v, family, asc, mu1, mu2, s);
+        case 256: return launch_turn_t<8, 16, 2>(g, v, family, asc, mu1, mu2, s);
+        case 512: return launch_turn_t<TURN512_K, TURN512_SL, TURN512_CL>(g, v, family, asc, mu1, mu2, s);
+        case 1024: return launch_turn_t<8, 16, 8>(g, v, family, asc, mu1, mu2, s);
         default: return cudaErrorInvalidValue;
     }
 }
