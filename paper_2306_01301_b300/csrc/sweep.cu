@@ -638,16 +638,27 @@ cudaError_t launch_turn_t(const DevGrid& g, Volumes v, int family, int asc, int 
 // written back row segment by row segment.
 constexpr int kSteps = 16;
 constexpr int kMaxLines = 256;
-constexpr int kSpan = kMaxLines + kSteps;           // tile extent across lines
-constexpr int kVWords = kSpan * (kSteps + 1);       // >= kSteps * (kSpan + 1)
-constexpr int kBHalves = kSpan * (kSteps + 2);      // >= kSteps * (kSpan + 4)
-constexpr uint32_t kMark = 0x80000000u;             // changed; stored values are < TH
+constexpr int kSpan = kMaxLines + kSteps;  // tile extent across lines (>= lines + 15)
+// Shallow tiles: rows = grid rows, 16 step columns, 16-byte aligned rows.
+constexpr int kShV = 20;                   // word pitch   (banks: 8 row classes)
+constexpr int kShB = 24;                   // half pitch
+// Steep tiles: 16 step rows, columns = an aligned superset of the segment.
+constexpr int kStV = kSpan + 8;            // word pitch   (segment + up to 3 lead + tail chunk)
+constexpr int kStB = kSpan + 16;           // half pitch
+constexpr int kVWords = (kSpan * kShV > kSteps * kStV) ? kSpan * kShV : kSteps * kStV;
+constexpr int kBHalves = (kSpan * kShB > kSteps * kStB) ? kSpan * kShB : kSteps * kStB;
+constexpr uint32_t kMark = 0x80000000u;    // changed; stored values are < TH
 
 struct StraightStage {
     uint32_t v[kVWords];
     uint16_t b[kBHalves];
-    int16_t bs[kSteps];  // Bs(y0 + s) - bmin, s = 0..15
+    int16_t bs[kSteps];  // Bs(y0 + s) - min over the chunk, s = 0..15
 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 
 struct ChunkGeom {
     int y0;     // first step of the chunk (ascending y')
@@ -665,16 +676,14 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const int16_t* bs, int ch, int d
     return c;
 }
 
-// Tile layouts.  Shallow: v[r][s] pitch 17 words, b[r][s] pitch 18 halves
-// (r = grid row offset, s = step).  Steep: v[s][x] pitch 273 words,
-// b[s][h] pitch 276 halves with h = x + (base & 1) (B is copied in aligned
-// word pairs).  Both put the 32 cells a warp reads in one step into 32
-// different banks.
+// Word / half index of tile element (step s, index a across lines).
 template <bool STEEP>
-__device__ __forceinline__ int vidx(int s, int a) { return STEEP ? s * (kSpan + 1) + a : a * (kSteps + 1) + s; }
+__device__ __forceinline__ int vidx(int s, int a, int base) {
+    return STEEP ? s * kStV + a + (base & 3) : a * kShV + s;
+}
 template <bool STEEP>
-__device__ __forceinline__ int bidx(int s, int a, int bofs) {
-    return STEEP ? s * (kSpan + 4) + a + bofs : a * (kSteps + 2) + s;
+__device__ __forceinline__ int bidx(int s, int a, int base) {
+    return STEEP ? s * kStB + a + (base & 7) : a * kShB + s;
 }
 
 template <bool STEEP>
@@ -683,27 +692,26 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
     const int t = threadIdx.x, nt = blockDim.x;
     if (t < kSteps) st.bs[t] = (int16_t)(bs[c.y0 + t] - min(bs[c.y0], bs[c.y0 + kSteps - 1]));
     if (!STEEP) {
-        // thread t copies step s = t % 16 of rows t/16, t/16 + nt/16, ...
-        const int s = t & 15, rstep = nt >> 4;
-        for (int r = t >> 4; r < c.span; r += rstep) {
-            const uint32_t* src = Vp + ((int64_t)((c.base + r) & mx) << lx) + c.y0 + s;
-            cp_async4(&st.v[r * (kSteps + 1) + s], src);
-        }
-        const int s2 = (t & 7) * 2, rstep2 = nt >> 3;
-        for (int r = t >> 3; r < c.span; r += rstep2) {
-            const uint16_t* src = Bp + ((int64_t)((c.base + r) & mx) << lx) + c.y0 + s2;
-            cp_async4(&st.b[r * (kSteps + 2) + s2], src);
+        // row r: 16 V words = 4 chunks, 16 B halves = 2 chunks, all aligned
+        for (int k = t; k < c.span * 6; k += nt) {
+            const int r = k / 6, j = k - r * 6;
+            const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
+            if (j < 4) cp_async16(&st.v[r * kShV + 4 * j], Vp + row + 4 * j);
+            else cp_async16(&st.b[r * kShB + 8 * (j - 4)], Bp + row + 8 * (j - 4));
         }
     } else {
-        const int a = c.base & ~1;
-        const int words = (c.span + 2) >> 1;
-#pragma unroll 4
-        for (int s = 0; s < kSteps; s++) {
-            const uint32_t* vrow = Vp + ((int64_t)(c.y0 + s) << lx);
-            const uint16_t* brow = Bp + ((int64_t)(c.y0 + s) << lx);
-            for (int x = t; x < c.span; x += nt) cp_async4(&st.v[s * (kSpan + 1) + x], vrow + ((c.base + x) & mx));
-            for (int wd = t; wd < words; wd += nt)
-                cp_async4(&st.b[s * (kSpan + 4) + 2 * wd], brow + ((a + 2 * wd) & mx));
+        // step row s: the aligned chunks covering columns [base, base + span)
+        const int a4 = c.base & ~3, nv = ((c.base & 3) + c.span + 3) >> 2;
+        const int a8 = c.base & ~7, nb = ((c.base & 7) + c.span + 7) >> 3;
+        const int per = nv + nb;                   // chunks per step row (< blockDim for Nx >= 16)
+        const int rpp = max(1, nt / per);          // step rows copied per pass of the block
+        const int s0 = t / per, j = t - s0 * per;  // one division per thread and chunk
+        if (s0 < rpp) {
+            for (int s = s0; s < kSteps; s += rpp) {
+                const uint32_t row = (uint32_t)(c.y0 + s) << lx;
+                if (j < nv) cp_async16(&st.v[s * kStV + 4 * j], Vp + row + ((a4 + 4 * j) & mx));
+                else cp_async16(&st.b[s * kStB + 8 * (j - nv)], Bp + row + ((a8 + 8 * (j - nv)) & mx));
+            }
         }
     }
 }
@@ -744,13 +752,13 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
         const ChunkGeom c = sb ? geo1 : geo0;
         cp_async_wait1();
         __syncthreads();
-        const int bofs = STEEP ? (c.base & 1) : 0;
         const int qbase = FWD ? c.y0 : g.nx - c.y0;  // q = qbase + dir * s
+        bool marked = false;
 #pragma unroll
         for (int kk = 0; kk < kSteps; kk++) {
             const int s = FWD ? kk : kSteps - 1 - kk;
             const int a = t + st.bs[s];  // tile index across lines, in [0, span)
-            const int vi = vidx<STEEP>(s, a), bi = bidx<STEEP>(s, a, bofs);
+            const int vi = vidx<STEEP>(s, a, c.base), bi = bidx<STEEP>(s, a, c.base);
             const uint16_t ob = st.b[bi];
             const uint32_t e = edge_cost(ob, w);
             const uint32_t u = ob == HARD ? 0u : min(st.v[vi], TH);
@@ -758,38 +766,40 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
             if (v < u) {
                 st.v[vi] = v | kMark;
                 st.b[bi] = (uint16_t)(mtag | (uint32_t)(q - pv));
+                marked = true;
             }
             const uint32_t tt = u + ct;
             if (tt < v) { v = tt; pv = q; }
             v += e;
         }
-        __syncthreads();
-        // write back the marked cells, row segment by row segment
-        if (!STEEP) {
-            const int s = t & 15, rstep = lines >> 4;
-            for (int r = t >> 4; r < c.span; r += rstep) {
-                const uint32_t x = st.v[r * (kSteps + 1) + s];
-                if ((x >> 30) == 2u) {
-                    const int64_t id = ((int64_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
-                    Vp[id] = x & ~kMark;
-                    Lp[id] = st.b[r * (kSteps + 2) + s];
-                    nimp++;
-                }
-            }
-        } else {
-            for (int s = 0; s < kSteps; s++) {
-                for (int xx = t; xx < c.span; xx += lines) {
-                    const uint32_t x = st.v[s * (kSpan + 1) + xx];
+        // write back the marked cells (only when the block has any)
+        if (__syncthreads_or(marked)) {
+            if (!STEEP) {
+                const int s = t & 15, rstep = lines >> 4;
+                for (int r = t >> 4; r < c.span; r += rstep) {
+                    const uint32_t x = st.v[r * kShV + s];
                     if ((x >> 30) == 2u) {
-                        const int64_t id = ((int64_t)(c.y0 + s) << g.lx) + ((c.base + xx) & g.mx);
+                        const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
                         Vp[id] = x & ~kMark;
-                        Lp[id] = st.b[s * (kSpan + 4) + xx + bofs];
+                        Lp[id] = st.b[r * kShB + s];
                         nimp++;
                     }
                 }
+            } else {
+                for (int s = 0; s < kSteps; s++) {
+                    for (int xx = t; xx < c.span; xx += lines) {
+                        const uint32_t x = st.v[vidx<true>(s, xx, c.base)];
+                        if ((x >> 30) == 2u) {
+                            const uint32_t id = ((uint32_t)(c.y0 + s) << g.lx) + ((c.base + xx) & g.mx);
+                            Vp[id] = x & ~kMark;
+                            Lp[id] = st.b[bidx<true>(s, xx, c.base)];
+                            nimp++;
+                        }
+                    }
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
         if (ch + 2 < nch) {
             const ChunkGeom nxt = chunk_geom(bs, ch + 2, dir, g.nx, X0, lines, g.mx);
             if (sb) geo1 = nxt;
