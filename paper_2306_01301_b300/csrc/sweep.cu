@@ -40,9 +40,9 @@ __device__ __forceinline__ uint32_t edge_cost(uint16_t b, uint32_t w) {
     return b == HARD ? TH : (w * (uint32_t)b) >> 8;
 }
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -69,15 +69,23 @@ __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t
 // Scan-order positions: ascending r = T, descending r = NT-1-T; positions of
 // the storing (second) loop are r + NT.
 
-template <int K, int SL, int CL>
-struct TurnSmem {
+// Shared state of one turn scan: section maps, the cluster exchange slots
+// (NSLOT of them, rotated so that a block never overwrites a slot its
+// partners may still read) and the labels of improved cells.
+template <int K, int SL, int NSLOT>
+struct TurnShared {
     static constexpr int P = 32 + 32 / SL;  // pitch: the carry scan's reads hit 32 banks
-    int2 cell[K * SL];   // per heading: (offset of the chain row in the volume, x shift)
     uint32_t sa[SL][P];
     uint32_t sb[SL][P];
     int32_t sp[SL][P];
-    uint32_t tot[2][3][32];                 // per scan: this block's composite (A, B, P)
+    uint32_t tot[NSLOT][3][32];             // per scan: this block's composite (A, B, P)
     uint16_t lab[K][32 * SL];               // labels of improved cells
+};
+
+template <int K, int SL, int CL>
+struct TurnSmem {
+    int2 cell[K * SL];   // per heading: (offset of the chain row in the volume, x shift)
+    TurnShared<K, SL, 2> sh;
 };
 
 // Compose an earlier stretch X with a later one Y (in place into Y):
@@ -89,17 +97,22 @@ __device__ __forceinline__ void combine(uint32_t xa, uint32_t xb, int xp, uint32
     ya = min(xa + ya, TH);
 }
 
-template <int K, int SL, int CL, bool ASC>
+// One maneuver scan over the block's chains.  `live`: this thread's section
+// holds a reached, non-hard cell.  A warp whose sections hold none has no
+// entries (its maps are "nothing produced") and, when nothing is carried in
+// either, cannot improve any of its cells, so it skips those loops; the
+// results are the same cell for cell.
+template <int K, int SL, int CL, int NSLOT, bool ASC>
 __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t& chg, int mu,
-                                          uint32_t ct, int sec, int lane, int rank, int scan, uint32_t a,
-                                          bool live, TurnSmem<K, SL, CL>& sm) {
+                                          uint32_t ct, int sec, int lane, int rank, int slot, uint32_t a,
+                                          bool live, TurnShared<K, SL, NSLOT>& sm) {
     constexpr int S = SL * CL, NT = K * S;
     const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);  // this block's place in scan order
     const int sl = ASC ? sec : SL - 1 - sec;                     // section index in scan order, local
     const int ss = sr * SL + sl;                                 // ... global
     // 1) this section's map (first-loop positions in [0, NT)); its slope
     //    `a`, the section's summed edge costs, is the same in both directions.
-    // "nothing produced" must stay within the composition bound (<= 2TH + ct)
+    //    "Nothing produced" must stay within the composition bound (<= 2TH + ct).
     uint32_t b = TH;
     int pb = 0;
     if (__any_sync(0xFFFFFFFFu, live)) {
@@ -146,9 +159,9 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
             cp = tP;
         } else {
             if (s == 0) {
-                sm.tot[scan][0][c] = tA;
-                sm.tot[scan][1][c] = tB;
-                sm.tot[scan][2][c] = tP;
+                sm.tot[slot][0][c] = tA;
+                sm.tot[slot][1][c] = tB;
+                sm.tot[slot][2][c] = tP;
             }
             cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
             cluster.sync();
@@ -159,10 +172,10 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
 #pragma unroll
             for (int j = 0; j < CL; j++) {
                 const int rk = ASC ? j : CL - 1 - j;  // cluster rank of scan-order block j
-                const TurnSmem<K, SL, CL>* o = cluster.map_shared_rank(&sm, rk);
-                rA[j] = o->tot[scan][0][c];
-                rB[j] = o->tot[scan][1][c];
-                rP[j] = o->tot[scan][2][c];
+                const TurnShared<K, SL, NSLOT>* o = cluster.map_shared_rank(&sm, rk);
+                rA[j] = o->tot[slot][0][c];
+                rB[j] = o->tot[slot][1][c];
+                rP[j] = o->tot[slot][2][c];
             }
             // the whole first loop applied to 'nothing carried'
             uint32_t fA = rA[0], fB = rB[0];
@@ -189,7 +202,7 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
         uint32_t iv = cv;
         int ip = cp;
         if (s > 0) {
-            const uint32_t cand = cv + eA;  // entries before this block's loop-2 sections are further upstream
+            const uint32_t cand = cv + eA;  // earlier entries are further upstream
             if (cand <= eB) { iv = cand; ip = cp; }
             else { iv = eB; ip = eP + NT; }
         }
@@ -290,12 +303,12 @@ k_turn(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
         live |= ob != HARD && vv < TH;
     }
     uint32_t chg = 0;
-    if (asc) turn_scan<K, SL, CL, true>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm);
-    else turn_scan<K, SL, CL, false>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm);
+    if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm.sh);
+    else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm.sh);
     if (mu2 >= 0) {
         live = live || chg != 0;
-        if (asc) turn_scan<K, SL, CL, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm);
-        else turn_scan<K, SL, CL, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm);
+        if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm.sh);
+        else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm.sh);
     }
     if (vol.improved) count_improved(vol.improved, __popc(chg));
     if (valid && chg) {
@@ -304,299 +317,12 @@ k_turn(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
             if (chg & (1u << k)) {
                 const uint32_t id = cell_index(sec * K + k);
                 vol.V[id] = u[k];
-                vol.L[id] = sm.lab[k][tid];
+                vol.L[id] = sm.sh.lab[k][tid];
             }
         }
     }
     // the partner block reads this block's shared memory: leave together
     if (CL > 1) cooperative_groups::this_cluster().sync();
-}
-
-// ------------------------------------------------------ pipelined turn sweep
-// Persistent form of the turn kernel for Nx >= 32 (all 32 chains of a tile
-// share y'): each cluster walks chain tiles tile0, tile0 + #clusters, ...;
-// while it scans tile i from registers, cp.async streams tile i + 2 into
-// the other shared-memory stage, so HBM traffic overlaps the scans.
-template <int K, int SL>
-struct TurnStage {
-    static constexpr int NTL = K * SL;
-    uint32_t v[NTL][32];      // V of the tile's chains, one row per heading
-    uint16_t b[NTL][36];      // B as aligned word pairs: lane l at [l + (shift & 1)]
-};
-
-template <int K, int SL, int CL>
-struct TurnPipeSmem {
-    static constexpr int P = 32 + 32 / SL;
-    TurnStage<K, SL> stage[2];
-    int2 beta[K * SL];        // this block's headings: (beta_x, beta_y) of the family
-    uint32_t sa[SL][P];
-    uint32_t sb[SL][P];
-    int32_t sp[SL][P];
-    uint32_t tot[4][3][32];   // composite exchange slots, rotating per scan
-    uint16_t lab[K][32 * SL];
-};
-
-// The scan (identical arithmetic to turn_scan) with the exchange slot and
-// shared layout of the pipelined kernel.
-// `live`: this thread's section holds a reached, non-hard cell.  A warp whose
-// sections hold none has no entries (its maps are "nothing produced") and,
-// when nothing is carried in either, cannot improve any of its cells, so it
-// skips those loops; the results are the same cell for cell.
-template <int K, int SL, int CL, bool ASC>
-__device__ __forceinline__ void turn_scan_pipe(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t& chg, int mu,
-                                               uint32_t ct, int sec, int lane, int rank, int slot, uint32_t a,
-                                               bool live, TurnPipeSmem<K, SL, CL>& sm) {
-    constexpr int S = SL * CL, NT = K * S;
-    const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);
-    const int sl = ASC ? sec : SL - 1 - sec;
-    const int ss = sr * SL + sl;
-    // "nothing produced" must stay within the composition bound (<= 2TH + ct)
-    uint32_t b = TH;
-    int pb = 0;
-    if (__any_sync(0xFFFFFFFFu, live)) {
-        b = 0xFFFFFFFFu;  // lowered to <= TH + ct by the first cell
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = ASC ? kk : K - 1 - kk;
-            const uint32_t t = u[k] + ct;
-            if (t < b) { b = t; pb = ss * K + kk; }
-            b += e[k];
-        }
-    }
-    sm.sa[sl][lane] = a;
-    sm.sb[sl][lane] = b;
-    sm.sp[sl][lane] = pb;
-    __syncthreads();
-    {
-        const int c = sec * (32 / SL) + lane / SL;
-        const int s = lane % SL;
-        uint32_t A = sm.sa[s][c], B = sm.sb[s][c];
-        int P = sm.sp[s][c];
-#pragma unroll
-        for (int off = 1; off < SL; off <<= 1) {
-            const uint32_t xa = __shfl_up_sync(0xFFFFFFFFu, A, off, SL);
-            const uint32_t xb = __shfl_up_sync(0xFFFFFFFFu, B, off, SL);
-            const int xp = __shfl_up_sync(0xFFFFFFFFu, P, off, SL);
-            if (s >= off) combine(xa, xb, xp, A, B, P);
-        }
-        const uint32_t tA = __shfl_sync(0xFFFFFFFFu, A, SL - 1, SL);
-        const uint32_t tB = __shfl_sync(0xFFFFFFFFu, B, SL - 1, SL);
-        const int tP = __shfl_sync(0xFFFFFFFFu, P, SL - 1, SL);
-        const uint32_t eA = __shfl_up_sync(0xFFFFFFFFu, A, 1, SL);
-        const uint32_t eB = __shfl_up_sync(0xFFFFFFFFu, B, 1, SL);
-        const int eP = __shfl_up_sync(0xFFFFFFFFu, P, 1, SL);
-        uint32_t cv;
-        int cp;
-        if (CL == 1) {
-            cv = tB;
-            cp = tP;
-        } else {
-            if (s == 0) {
-                sm.tot[slot][0][c] = tA;
-                sm.tot[slot][1][c] = tB;
-                sm.tot[slot][2][c] = tP;
-            }
-            cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
-            cluster.sync();
-            uint32_t rA[CL], rB[CL];
-            int rP[CL];
-#pragma unroll
-            for (int j = 0; j < CL; j++) {
-                const int rk = ASC ? j : CL - 1 - j;
-                const TurnPipeSmem<K, SL, CL>* o = cluster.map_shared_rank(&sm, rk);
-                rA[j] = o->tot[slot][0][c];
-                rB[j] = o->tot[slot][1][c];
-                rP[j] = o->tot[slot][2][c];
-            }
-            uint32_t fA = rA[0], fB = rB[0];
-            int fP = rP[0];
-#pragma unroll
-            for (int j = 1; j < CL; j++) {
-                uint32_t a2 = rA[j], b2 = rB[j];
-                int p2 = rP[j];
-                combine(fA, fB, fP, a2, b2, p2);
-                fA = a2; fB = b2; fP = p2;
-            }
-            cv = fB;
-            cp = fP;
-#pragma unroll
-            for (int j = 0; j < CL - 1; j++) {
-                if (j < sr) {
-                    const uint32_t cand = cv + rA[j];
-                    if (!(cand <= rB[j])) { cv = rB[j]; cp = rP[j] + NT; }
-                    else cv = cand;
-                }
-            }
-        }
-        uint32_t iv = cv;
-        int ip = cp;
-        if (s > 0) {
-            const uint32_t cand = cv + eA;
-            if (cand <= eB) { iv = cand; ip = cp; }
-            else { iv = eB; ip = eP + NT; }
-        }
-        __syncwarp();
-        sm.sb[s][c] = iv;
-        sm.sp[s][c] = ip;
-    }
-    __syncthreads();
-    uint32_t v = sm.sb[sl][lane];
-    int pv = sm.sp[sl][lane];
-    const uint32_t mtag = (uint32_t)mu << 13;
-    const int tid = sec * 32 + lane;
-    if (__any_sync(0xFFFFFFFFu, live || v < TH)) {
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = ASC ? kk : K - 1 - kk;
-            const int q = NT + ss * K + kk;
-            const uint32_t uk = u[k];
-            if (v < uk) {
-                u[k] = v;
-                sm.lab[k][tid] = (uint16_t)(mtag | (uint32_t)(q - pv));
-                chg |= 1u << k;
-            }
-            const uint32_t t = uk + ct;
-            if (t < v) { v = t; pv = q; }
-            v += e[k];
-        }
-    }
-    __syncthreads();
-}
-
-// Copy one tile's V and B rows of this block's headings into a stage; warp
-// `sec` copies headings [sec*K, sec*K + K).
-template <int K, int SL, int CL>
-__device__ __forceinline__ void turn_issue(TurnPipeSmem<K, SL, CL>& sm, TurnStage<K, SL>& st, const DevGrid& g,
-                                           const Volumes& vol, int tile, int T0, int sec, int lane) {
-    const int64_t nxy = (int64_t)g.nx * g.nx;
-    const int x0 = (tile * 32) & g.mx;
-    const int y0 = ((tile * 32) >> g.lx) & g.mx;
-    const int hw = g.nx >> 1;  // words per B row
-#pragma unroll 4
-    for (int kk = 0; kk < K; kk++) {
-        const int T = sec * K + kk;
-        const int2 bb = sm.beta[T];
-        const int64_t row = (((int64_t)((y0 + bb.y) & g.mx)) << g.lx) + (int64_t)(T0 + T) * nxy;
-        const int c0 = (x0 + bb.x) & g.mx;
-        cp_async4(&st.v[T][lane], vol.V + row + ((c0 + lane) & g.mx));
-        if (lane < 17) {
-            const int wd = ((c0 >> 1) + lane) & (hw - 1);
-            cp_async4(&st.b[T][2 * lane], vol.B + row + 2 * wd);
-        }
-    }
-}
-
-template <int K, int SL, int CL>
-__global__ void __launch_bounds__(32 * SL, 3)
-k_turn_pipe(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
-    constexpr int NTL = K * SL;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TurnPipeSmem<K, SL, CL>& sm = *reinterpret_cast<TurnPipeSmem<K, SL, CL>*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
-    const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
-    const int cid = (int)(blockIdx.x / CL), ncl = (int)(gridDim.x / CL);
-    const int T0 = rank * NTL;
-    for (int t = tid; t < NTL; t += 32 * SL) {
-        const int4 b = g.beta4[T0 + t];
-        sm.beta[t] = family ? make_int2(b.z, b.w) : make_int2(b.x, b.y);
-    }
-    __syncthreads();
-    const int64_t nxy = (int64_t)g.nx * g.nx;
-    const int ntiles = (int)(nxy / 32);
-    const uint32_t w = g.wA, ct = g.ct;
-    int tile = cid;
-    if (tile < ntiles) turn_issue(sm, sm.stage[0], g, vol, tile, T0, sec, lane);
-    cp_async_commit();
-    if (tile + ncl < ntiles) turn_issue(sm, sm.stage[1], g, vol, tile + ncl, T0, sec, lane);
-    cp_async_commit();
-    uint64_t nimp = 0;
-    for (int it = 0; tile < ntiles; it++, tile += ncl) {
-        TurnStage<K, SL>& st = sm.stage[it & 1];
-        cp_async_wait1();
-        __syncthreads();
-        const int x0 = (tile * 32) & g.mx;
-        const int y0 = ((tile * 32) >> g.lx) & g.mx;
-        uint32_t u[K], e[K];
-        uint32_t a = 0;
-        bool live = false;
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int T = sec * K + k;
-            const int c0 = (x0 + sm.beta[T].x) & g.mx;
-            const uint16_t ob = st.b[T][lane + (c0 & 1)];
-            const uint32_t vv = st.v[T][lane];
-            e[k] = edge_cost(ob, w);
-            u[k] = ob == HARD ? 0u : min(vv, TH);
-            a = min(a + e[k], TH);
-            live |= ob != HARD && vv < TH;
-        }
-        __syncthreads();  // stage consumed: refill it with tile it + 2
-        if (tile + 2 * ncl < ntiles) turn_issue(sm, st, g, vol, tile + 2 * ncl, T0, sec, lane);
-        cp_async_commit();
-        uint32_t chg = 0;
-        if (asc) turn_scan_pipe<K, SL, CL, true>(u, e, chg, mu1, ct, sec, lane, rank, (2 * it) & 3, a, live, sm);
-        else turn_scan_pipe<K, SL, CL, false>(u, e, chg, mu1, ct, sec, lane, rank, (2 * it) & 3, a, live, sm);
-        if (mu2 >= 0) {
-            live = live || chg != 0;
-            if (asc)
-                turn_scan_pipe<K, SL, CL, false>(u, e, chg, mu2, ct, sec, lane, rank, (2 * it + 1) & 3, a, live, sm);
-            else
-                turn_scan_pipe<K, SL, CL, true>(u, e, chg, mu2, ct, sec, lane, rank, (2 * it + 1) & 3, a, live, sm);
-        }
-        nimp += __popc(chg);
-        if (chg) {
-#pragma unroll
-            for (int k = 0; k < K; k++) {
-                if (chg & (1u << k)) {
-                    const int T = sec * K + k;
-                    const int2 bb = sm.beta[T];
-                    const int64_t id = (((int64_t)((y0 + bb.y) & g.mx)) << g.lx) + (int64_t)(T0 + T) * nxy +
-                                       ((x0 + lane + bb.x) & g.mx);
-                    vol.V[id] = u[k];
-                    vol.L[id] = sm.lab[k][tid];
-                }
-            }
-        }
-    }
-    cp_async_wait0();
-    if (vol.improved) count_improved(vol.improved, (uint32_t)nimp);
-    if (CL > 1) cooperative_groups::this_cluster().sync();
-}
-
-template <int K, int SL, int CL>
-cudaError_t launch_turn_pipe(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
-    static int clusters[64] = {};
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
-    const size_t smem = sizeof(TurnPipeSmem<K, SL, CL>);
-    cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(32 * SL);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (dev < 0 || dev >= 64 || clusters[dev] == 0) {
-        err = cudaFuncSetAttribute(k_turn_pipe<K, SL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        int n = 0;
-        cfg.gridDim = dim3(CL);
-        err = cudaOccupancyMaxActiveClusters(&n, k_turn_pipe<K, SL, CL>, &cfg);
-        if (err != cudaSuccess) return err;
-        if (n < 1) n = 1;
-        if (dev >= 0 && dev < 64) clusters[dev] = n;
-        else clusters[0] = n;
-    }
-    const int64_t ntiles = (int64_t)g.nx * g.nx / 32;
-    int64_t ncl = clusters[(dev >= 0 && dev < 64) ? dev : 0];
-    if (ncl > ntiles) ncl = ntiles;
-    cfg.gridDim = dim3((unsigned)(ncl * CL));
-    return cudaLaunchKernelEx(&cfg, k_turn_pipe<K, SL, CL>, g, v, family, asc, mu1, mu2);
 }
 
 template <int K, int SL, int CL>
@@ -655,10 +381,6 @@ struct StraightStage {
     int16_t bs[kSteps];  // Bs(y0 + s) - min over the chunk, s = 0..15
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 
 struct ChunkGeom {
     int y0;     // first step of the chunk (ascending y')
@@ -872,36 +594,28 @@ __global__ void k_init(Volumes vol, int64_t n, int64_t start) {
 }  // namespace
 
 // Shape of the 512-heading turn kernel: K headings per thread, SL sections
-// (warps) per block, CL blocks per cluster, K * SL * CL = 512.
-#ifndef TURN_PIPE
-#define TURN_PIPE 0  // the persistent cp.async-pipelined variant (slower while the scans are issue-bound)
-#endif
+// (warps) per block, CL blocks per cluster, K * SL * CL = 512.  Measured on
+// B300 at 512^3: one 1024-thread block per chain tile (no cluster) beats the
+// 2-, 4- and 8-block clusters, whose barriers carry a memory fence, and a
+// persistent variant that streamed the next tile through shared memory with
+// cp.async while scanning the current one (the scans, not HBM, bound it).
 #ifndef TURN512_K
 #define TURN512_K 16
-#define TURN512_SL 8
-#define TURN512_CL 4
+#define TURN512_SL 32
+#define TURN512_CL 1
 #endif
 
 cudaError_t launch_turn(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
-    if (TURN_PIPE && g.nx >= 32) {
-        switch (g.nt) {
-            case 128: return launch_turn_pipe<16, 8, 1>(g, v, family, asc, mu1, mu2, s);
-            case 256: return launch_turn_pipe<16, 8, 2>(g, v, family, asc, mu1, mu2, s);
-            case 512: return launch_turn_pipe<TURN512_K, TURN512_SL, TURN512_CL>(g, v, family, asc, mu1, mu2, s);
-            case 1024: return launch_turn_pipe<16, 8, 8>(g, v, family, asc, mu1, mu2, s);
-            default: break;
-        }
-    }
     switch (g.nt) {
         case 4: return launch_turn_t<1, 4, 1>(g, v, family, asc, mu1, mu2, s);
         case 8: return launch_turn_t<2, 4, 1>(g, v, family, asc, mu1, mu2, s);
         case 16: return launch_turn_t<4, 4, 1>(g, v, family, asc, mu1, mu2, s);
         case 32: return launch_turn_t<8, 4, 1>(g, v, family, asc, mu1, mu2, s);
         case 64: return launch_turn_t<8, 8, 1>(g, v, family, asc, mu1, mu2, s);
-        case 128: return launch_turn_t<8, 16, 1>(g, v, family, asc, mu1, mu2, s);
-        case 256: return launch_turn_t<8, 16, 2>(g, v, family, asc, mu1, mu2, s);
+        case 128: return launch_turn_t<16, 8, 1>(g, v, family, asc, mu1, mu2, s);
+        case 256: return launch_turn_t<16, 16, 1>(g, v, family, asc, mu1, mu2, s);
         case 512: return launch_turn_t<TURN512_K, TURN512_SL, TURN512_CL>(g, v, family, asc, mu1, mu2, s);
-        case 1024: return launch_turn_t<8, 16, 8>(g, v, family, asc, mu1, mu2, s);
+        case 1024: return launch_turn_t<16, 32, 2>(g, v, family, asc, mu1, mu2, s);
         default: return cudaErrorInvalidValue;
     }
 }
