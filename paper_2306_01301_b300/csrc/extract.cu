@@ -50,8 +50,17 @@ __device__ int64_t entry_cell(const DevGrid& g, int64_t c, int mu, int d) {
     return cell_of(g, xq + (left ? be.x : be.z), yq + (left ? be.y : be.w), Te);
 }
 
-__global__ void k_extract(DevGrid g, Volumes vol, int64_t goal, plan_segment* seg, int cap, int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void k_extract(const QueryDesc* __restrict__ qd) {
+    if (threadIdx.x != 0) return;
+    const QueryDesc& Q = qd[blockIdx.x];
+    const DevGrid g = Q.g;
+    const Volumes vol = Q.v;
+    const int64_t goal = Q.goal;
+    plan_segment* seg = Q.seg;
+    int32_t* status = Q.status;
+    const int cap = Q.seg_cap;
+    status[1] = (int32_t)(vol.V[goal] & 0xFFFFu);
+    status[2] = (int32_t)(vol.V[goal] >> 16);
     if (vol.V[goal] == 0xFFFFFFFFu) { status[0] = -1; return; }
     int64_t x = goal;
     int n = 0;
@@ -79,9 +88,8 @@ __global__ void k_extract(DevGrid g, Volumes vol, int64_t goal, plan_segment* se
 
 }  // namespace
 
-cudaError_t launch_extract(const DevGrid& g, Volumes v, int64_t goal, plan_segment* seg, int cap, int* status,
-                           cudaStream_t s) {
-    k_extract<<<1, 32, 0, s>>>(g, v, goal, seg, cap, status);
+cudaError_t launch_extract(const Group& gr, cudaStream_t s) {
+    k_extract<<<(unsigned)gr.nq, 32, 0, s>>>(gr.d);
     return cudaGetLastError();
 }
 

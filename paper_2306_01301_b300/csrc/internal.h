@@ -52,28 +52,62 @@ struct Volumes {
     unsigned long long* improved;  // optional counter of strictly improved cells
 };
 
-// Kernel launchers (each returns cudaGetLastError()).
-cudaError_t launch_sparse_table(const uint16_t* img, uint16_t* table, int lx, cudaStream_t s);
-cudaError_t launch_render(const DevGrid& g, const uint16_t* table, uint16_t* B, int max_runs,
-                          cudaStream_t s);
-// Rendering with a bit-parallel hard test (Nx >= 32): builds the per-row OR
-// table `bits` ((lx+1) * Nx * Nx/32 words), writes HARD / 256 into B; with
-// soft = true the maximum of the image (sparse `table`, already built) is
-// then filled in for the non-hard poses.  Launches lx + 3 kernels (lx + 4
-// with soft).
-cudaError_t launch_render_bits(const DevGrid& g, const uint16_t* img, uint32_t* bits, uint16_t* B, bool soft,
-                               const uint16_t* table, int max_runs, cudaStream_t s);
-cudaError_t launch_init(const DevGrid& g, Volumes v, int64_t start, cudaStream_t s);
-// Turn chains: family 0 = LEFT (beta_0, beta_3), 1 = RIGHT (beta_2, beta_1).
-// First scan direction asc (1: T increasing) with maneuver mu1; if mu2 >= 0 a
-// second scan in the opposite direction with maneuver mu2 follows on the same
-// chains (fused pair).
-cudaError_t launch_turn(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2,
-                        cudaStream_t s);
-cudaError_t launch_straight(const DevGrid& g, Volumes v, int mu, cudaStream_t s);
-// Label walk from goal; writes up to cap plan_segment records (goal first)
-// and status[0] = count, or -1 unreachable, -3 malformed labels.
-cudaError_t launch_extract(const DevGrid& g, Volumes v, int64_t goal, plan_segment* seg, int cap,
-                           int* status, cudaStream_t s);
+// Everything a kernel needs about one planning query.  Kernels take a device
+// array of these, so one launch serves a single plan, a batch of plans of
+// one grid shape, or one step of the server with each query at its own pass.
+struct QueryDesc {
+    DevGrid g;
+    Volumes v;
+    int64_t start;            // start cell (init)
+    int64_t goal;             // goal cell (extract)
+    int32_t n_cycles;         // N: the query runs passes 0 .. 4N
+    int32_t pass;             // this query's pass when a launch says "per query"
+    const uint16_t* img;      // obstacle image (Nx*Nx)
+    uint32_t* bits;           // bit-parallel hard table, (lx+1) * Nx * Nx/32 words
+    uint16_t* table;          // uint16 sparse max table, (lx+1) * Nx * Nx
+    plan_segment* seg;        // label walk output (goal first)
+    int32_t* status;          // [0] segment count or error, [1] V(goal) low, [2] high
+    int32_t seg_cap;
+    int32_t max_runs;         // footprint runs of the widest heading
+};
+
+// One launch group: nq descriptors of a single grid shape on the device.
+struct Group {
+    const QueryDesc* d;
+    int nq;
+    int lx, lt;
+    int max_runs;             // max over the group
+};
+
+// Cycle schedule (Section XVI.A) with the turn pairs fused: N cycles are the
+// passes p = 0 .. 4N:
+//   p = 0      LF              (a lone opening left-forward)
+//   p = 4c+1   SF              p = 4c+3   SB
+//   p = 4c+2   RB then RF      (right chains, heading up then down)
+//   p = 4c+4   LB then LF      (left chains, heading down then up; the LF
+//                               belongs to cycle c+1 and is dropped when
+//                               c = N-1)
+inline int pass_count(int n_cycles) { return n_cycles > 0 ? 4 * n_cycles + 1 : 0; }
+inline bool pass_is_turn(int p) { return (p & 1) == 0; }
+
+// Launchers.  `pass` < 0 means "each query's own QueryDesc::pass"; queries
+// whose pass is outside 0 .. 4N do nothing.  Each returns cudaGetLastError().
+cudaError_t launch_init(const Group& gr, cudaStream_t s);
+// Rendering: bit-parallel hard test for Nx >= 32 (uint16 maxima for the
+// non-hard poses when `soft`), uint16 sparse-table path otherwise.  Returns
+// the number of kernels launched through *launches.
+cudaError_t launch_render(const Group& gr, bool soft, cudaStream_t s, int* launches);
+// Turn pass with kernel shape `variant` (index into the shapes available for
+// the group's N_theta, -1 = the measured default).
+cudaError_t launch_turn(const Group& gr, int pass, int variant, cudaStream_t s);
+int turn_variants(int nt);
+// Straight pass with `lines` (128 or 256, 0 = default) lines per block.
+cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s);
+// Label walk from each query's goal into its seg/status buffers.
+cudaError_t launch_extract(const Group& gr, cudaStream_t s);
+
+// Rendering pieces used by the allocation-free entry point.
+cudaError_t launch_sparse_table(const Group& gr, cudaStream_t s);
+cudaError_t launch_render_table(const Group& gr, cudaStream_t s);
 
 }  // namespace nhp

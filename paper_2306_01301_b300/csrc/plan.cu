@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "internal.h"
+#include "plan_state.h"
 
 using namespace nhp;
 
@@ -26,56 +26,6 @@ size_t round16(size_t b) { return (b + 15) & ~size_t(15); }
 
 }  // namespace
 
-struct plan_s {
-    int lx = 0, lt = 0, nx = 0, nt = 0;
-    int64_t nxy = 0, nr = 0;
-    double R = 0;
-    plan_costs costs{};
-    plan_footprint fp{};
-    cudaStream_t stream = nullptr;
-    plan_allocator alloc{};
-    // host copies
-    std::vector<int4> beta4;
-    std::vector<PlaneInfo> planes;
-    std::vector<int16_t> bshear;
-    std::vector<int32_t> run_off;
-    std::vector<Run> runs;
-    std::vector<int32_t> fp_dx, fp_dy;  // footprint cells of every heading, concatenated
-    std::vector<int32_t> fp_off;
-    std::vector<unsigned char> blob;    // staged table upload
-    std::vector<uint16_t> img;
-    int max_runs = 0;
-    uint32_t wA = 0, w_max = 0;
-    uint32_t img_max_soft = 256;
-    // device
-    unsigned char* d_blob = nullptr;
-    size_t blob_bytes = 0;
-    uint16_t* d_img = nullptr;
-    uint16_t* d_table = nullptr;
-    size_t table_bytes = 0;
-    uint32_t* d_bits = nullptr;  // bit-parallel hard table (Nx >= 32)
-    size_t bits_bytes = 0;
-    uint32_t* d_V = nullptr;
-    uint16_t* d_L = nullptr;
-    uint16_t* d_B = nullptr;
-    plan_segment* d_seg = nullptr;
-    int* d_status = nullptr;
-    bool rendered = false;
-    int64_t launches = 0;
-    DevGrid g{};
-    // profiling (plan_profile)
-    bool prof = false;
-    unsigned long long* d_cnt = nullptr;  // [0] turn, [1] straight improved cells
-    struct Mark { int kind; cudaEvent_t a, b; };
-    std::vector<Mark> marks;
-    std::vector<cudaEvent_t> spare;
-    plan_profile_stats acc{};
-
-    void* dalloc(size_t bytes) { return alloc.alloc(bytes, (void*)stream, alloc.ctx); }
-    void dfree(void* p, size_t bytes) {
-        if (p) alloc.free(p, bytes, (void*)stream, alloc.ctx);
-    }
-};
 
 namespace {
 
@@ -211,6 +161,10 @@ int check_image(const uint16_t* img, int64_t n, uint32_t* max_soft) {
     return PLAN_OK;
 }
 
+}  // namespace
+
+namespace nhp {
+
 bool pose_ok(const plan_s* p, plan_pose q) {
     return q.x >= 0 && q.y >= 0 && q.theta >= 0 && q.x < p->nx && q.y < p->nx && q.theta < p->nt;
 }
@@ -232,6 +186,23 @@ bool pose_hard(const plan_s* p, plan_pose q) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : PLAN_ECUDA; }
 
+int range_check(const plan_s* p, int n_cycles) {
+    // Every finite value is a sum over at most 6N segments of ct plus at most
+    // max(Nx, N_theta) - 1 edges; it must stay below the kernels' TH.
+    const double e_max = (double)(((uint64_t)p->w_max * p->img_max_soft) >> 8);
+    const double bound =
+        6.0 * n_cycles * ((double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max);
+    return bound >= (double)TH ? PLAN_ERANGE : PLAN_OK;
+}
+
+int upload_desc(plan_s* p) {
+    return cuda_rc(cudaMemcpyAsync(p->d_qd, &p->qd, sizeof(QueryDesc), cudaMemcpyHostToDevice, p->stream));
+}
+
+}  // namespace nhp
+
+namespace {
+
 void release(plan_s* p) {
     p->dfree(p->d_blob, p->blob_bytes);
     p->dfree(p->d_img, (size_t)p->nxy * 2);
@@ -243,6 +214,7 @@ void release(plan_s* p) {
     p->dfree(p->d_seg, sizeof(plan_segment) * kDevSegCap);
     p->dfree(p->d_status, 16);
     p->dfree(p->d_cnt, 16);
+    p->dfree(p->d_qd, sizeof(QueryDesc));
     for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : p->spare) cudaEventDestroy(e);
     p->marks.clear();
@@ -274,7 +246,6 @@ int mark_begin(plan_s* p, int kind) {
 void mark_end(plan_s* p, int idx) {
     if (idx >= 0) cudaEventRecord(p->marks[idx].b, p->stream);
 }
-unsigned long long* counter(plan_s* p, int kind) { return p->prof ? p->d_cnt + kind : nullptr; }
 
 }  // namespace
 
@@ -345,8 +316,9 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     p->d_seg = (plan_segment*)p->dalloc(sizeof(plan_segment) * kDevSegCap);
     p->d_status = (int*)p->dalloc(16);
     p->d_cnt = (unsigned long long*)p->dalloc(16);
+    p->d_qd = (QueryDesc*)p->dalloc(sizeof(QueryDesc));
     if (p->bits_bytes) p->d_bits = (uint32_t*)p->dalloc(p->bits_bytes);
-    if ((p->bits_bytes && !p->d_bits) || !p->d_cnt ||
+    if ((p->bits_bytes && !p->d_bits) || !p->d_cnt || !p->d_qd ||
         !p->d_blob || !p->d_img || !p->d_table || !p->d_V || !p->d_L || !p->d_B || !p->d_seg || !p->d_status) {
         release(p);
         delete p;
@@ -369,6 +341,26 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     g.bshear = (const int16_t*)(p->d_blob + o_bsh);
     g.run_off = (const int32_t*)(p->d_blob + o_roff);
     g.runs = (const Run*)(p->d_blob + o_runs);
+    QueryDesc& q = p->qd;
+    q.g = g;
+    q.v = Volumes{p->d_V, p->d_L, p->d_B, nullptr};
+    q.start = 0;
+    q.goal = 0;
+    q.n_cycles = 0;
+    q.pass = -1;
+    q.img = p->d_img;
+    q.bits = p->d_bits;
+    q.table = p->d_table;
+    q.seg = p->d_seg;
+    q.status = p->d_status;
+    q.seg_cap = kDevSegCap;
+    q.max_runs = std::max(1, p->max_runs);
+    rc = upload_desc(p);
+    if (rc != PLAN_OK) {
+        release(p);
+        delete p;
+        return rc;
+    }
     *out = p;
     return PLAN_OK;
 }
@@ -390,21 +382,9 @@ int plan_set_image(plan_t* p, const uint16_t* image) {
 int plan_render_cspace(plan_t* p) {
     if (!p) return PLAN_EINVAL;
     const int mk = mark_begin(p, K_RENDER);
-    const bool soft = p->img_max_soft > 256;
-    int rc = PLAN_OK;
-    if (soft || p->nx < 32) {
-        rc = cuda_rc(launch_sparse_table(p->d_img, p->d_table, p->lx, p->stream));
-        p->launches += p->lx + 1;
-    }
-    if (rc == PLAN_OK && p->nx >= 32) {
-        // bit-parallel hard test; soft maxima only for the non-hard poses
-        rc = cuda_rc(launch_render_bits(p->g, p->d_img, p->d_bits, p->d_B, soft, p->d_table,
-                                        std::max(1, p->max_runs), p->stream));
-        p->launches += p->lx + 2 + (soft ? 1 : 0);
-    } else if (rc == PLAN_OK) {
-        rc = cuda_rc(launch_render(p->g, p->d_table, p->d_B, std::max(1, p->max_runs), p->stream));
-        p->launches += 1;
-    }
+    int n = 0;
+    const int rc = cuda_rc(launch_render(p->group(), p->img_max_soft > 256, p->stream, &n));
+    p->launches += n;
     mark_end(p, mk);
     if (rc == PLAN_OK) p->rendered = true;
     return rc;
@@ -414,44 +394,28 @@ int plan_sweep(plan_t* p, plan_pose start, int n_cycles) {
     if (!p || n_cycles < 0 || n_cycles > 4096 || !pose_ok(p, start)) return PLAN_EINVAL;
     if (!p->rendered) return PLAN_ESTATE;
     if (pose_hard(p, start)) return PLAN_EINVAL;
-    // Every finite value is a sum over at most 6N segments of ct plus at most
-    // max(Nx, N_theta) - 1 edges; it must stay below the kernels' TH.
-    const double e_max = (double)(((uint64_t)p->w_max * p->img_max_soft) >> 8);
-    const double bound = 6.0 * n_cycles * ((double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max);
-    if (bound >= (double)TH) return PLAN_ERANGE;
-    Volumes vt{p->d_V, p->d_L, p->d_B, counter(p, K_TURN)};
-    Volumes vs{p->d_V, p->d_L, p->d_B, counter(p, K_STRAIGHT)};
-    const DevGrid& g = p->g;
+    if (range_check(p, n_cycles) != PLAN_OK) return PLAN_ERANGE;
+    p->qd.start = cell_index(p, start);
+    p->qd.n_cycles = n_cycles;
+    p->qd.v.improved = p->prof ? p->d_cnt : nullptr;
+    int rc = upload_desc(p);
+    if (rc != PLAN_OK) return rc;
+    const Group gr = p->group();
     cudaStream_t s = p->stream;
     int mk = mark_begin(p, K_INIT);
-    int rc = cuda_rc(launch_init(g, vt, cell_index(p, start), s));
+    rc = cuda_rc(launch_init(gr, s));
     mark_end(p, mk);
     p->launches++;
-    if (rc != PLAN_OK || n_cycles == 0) return rc;
-    auto turn = [&](int family, int asc, int mu1, int mu2) {
-        const int m = mark_begin(p, K_TURN);
-        const int r = cuda_rc(launch_turn(g, vt, family, asc, mu1, mu2, s));
+    // Passes 0 .. 4N of the cycle schedule (internal.h): the consecutive
+    // turns on one curve family, {RB, RF} and {LB of cycle c, LF of cycle
+    // c+1}, share a pass, so N cycles (6N maneuver layers) take 4N + 1.
+    const int np = pass_count(n_cycles);
+    for (int pass = 0; pass < np && rc == PLAN_OK; pass++) {
+        const bool turn = pass_is_turn(pass);
+        const int m = mark_begin(p, turn ? K_TURN : K_STRAIGHT);
+        rc = cuda_rc(turn ? launch_turn(gr, pass, -1, s) : launch_straight(gr, pass, 0, s));
         mark_end(p, m);
         p->launches++;
-        return r;
-    };
-    auto straight = [&](int mu) {
-        const int m = mark_begin(p, K_STRAIGHT);
-        const int r = cuda_rc(launch_straight(g, vs, mu, s));
-        mark_end(p, m);
-        p->launches++;
-        return r;
-    };
-    // Cycle order LF, SF, RB, RF, SB, LB (Section XVI.A).  Consecutive turns on
-    // the same curve family share one pass: {RB, RF} and {LB of cycle n, LF
-    // of cycle n+1}; a lone LF opens the run and a lone LB closes it, so N
-    // cycles take 4N + 1 passes over the volume instead of 6N.
-    rc = turn(0, 1, LF, -1);
-    for (int c = 0; c < n_cycles && rc == PLAN_OK; c++) {
-        rc = straight(SF);
-        if (rc == PLAN_OK) rc = turn(1, 1, RB, RF);
-        if (rc == PLAN_OK) rc = straight(SB);
-        if (rc == PLAN_OK) rc = turn(0, 0, LB, c + 1 < n_cycles ? LF : -1);
     }
     return rc;
 }
@@ -460,27 +424,26 @@ int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_o
     if (!p || !n_out || !cost || cap < 0 || (cap > 0 && !out) || !pose_ok(p, goal)) return PLAN_EINVAL;
     *n_out = 0;
     *cost = PLAN_INF;
-    Volumes v{p->d_V, p->d_L, p->d_B, nullptr};
-    int rc = cuda_rc(launch_extract(p->g, v, cell_index(p, goal), p->d_seg, kDevSegCap, p->d_status, p->stream));
+    p->qd.goal = cell_index(p, goal);
+    int rc = upload_desc(p);
+    if (rc == PLAN_OK) rc = cuda_rc(launch_extract(p->group(), p->stream));
     p->launches++;
     if (rc != PLAN_OK) return rc;
-    int status = 0;
-    uint32_t vg = PLAN_INF;
-    rc = cuda_rc(cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    if (rc == PLAN_OK)
-        rc = cuda_rc(cudaMemcpyAsync(&vg, p->d_V + cell_index(p, goal), 4, cudaMemcpyDeviceToHost, p->stream));
+    int32_t status[3] = {0, 0, 0};
+    rc = cuda_rc(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
     if (rc != PLAN_OK) return rc;
-    if (status == -1) return PLAN_EUNREACHABLE;
-    if (status < 0) return PLAN_EINTERNAL;
-    *cost = vg;
-    *n_out = status;
-    if (status > cap || status > kDevSegCap) return PLAN_ERANGE;
-    if (status > 0) {
-        rc = cuda_rc(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status, cudaMemcpyDeviceToHost, p->stream));
+    if (status[0] == -1) return PLAN_EUNREACHABLE;
+    if (status[0] < 0) return PLAN_EINTERNAL;
+    *cost = (uint32_t)(status[1] & 0xFFFF) | ((uint32_t)status[2] << 16);
+    *n_out = status[0];
+    if (status[0] > cap || status[0] > kDevSegCap) return PLAN_ERANGE;
+    if (status[0] > 0) {
+        rc = cuda_rc(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status[0], cudaMemcpyDeviceToHost,
+                                     p->stream));
         if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
         if (rc != PLAN_OK) return rc;
-        std::reverse(out, out + status);  // the walk runs goal -> start
+        std::reverse(out, out + status[0]);  // the walk runs goal -> start
     }
     return PLAN_OK;
 }

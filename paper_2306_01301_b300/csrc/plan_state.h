@@ -1,0 +1,75 @@
+// plan_state.h -- the plan object shared by the single-plan, batch and
+// server entry points (private).
+#pragma once
+#include <vector>
+
+#include "internal.h"
+
+using nhp::DevGrid;
+using nhp::PlaneInfo;
+using nhp::Run;
+
+struct plan_s {
+    int lx = 0, lt = 0, nx = 0, nt = 0;
+    int64_t nxy = 0, nr = 0;
+    double R = 0;
+    plan_costs costs{};
+    plan_footprint fp{};
+    cudaStream_t stream = nullptr;
+    plan_allocator alloc{};
+    // host copies
+    std::vector<int4> beta4;
+    std::vector<PlaneInfo> planes;
+    std::vector<int16_t> bshear;
+    std::vector<int32_t> run_off;
+    std::vector<Run> runs;
+    std::vector<int32_t> fp_dx, fp_dy;  // footprint cells of every heading, concatenated
+    std::vector<int32_t> fp_off;
+    std::vector<unsigned char> blob;    // staged table upload
+    std::vector<uint16_t> img;
+    int max_runs = 0;
+    uint32_t wA = 0, w_max = 0;
+    uint32_t img_max_soft = 256;
+    // device
+    unsigned char* d_blob = nullptr;
+    size_t blob_bytes = 0;
+    uint16_t* d_img = nullptr;
+    uint16_t* d_table = nullptr;
+    size_t table_bytes = 0;
+    uint32_t* d_bits = nullptr;  // bit-parallel hard table (Nx >= 32)
+    size_t bits_bytes = 0;
+    uint32_t* d_V = nullptr;
+    uint16_t* d_L = nullptr;
+    uint16_t* d_B = nullptr;
+    plan_segment* d_seg = nullptr;
+    int* d_status = nullptr;
+    bool rendered = false;
+    int64_t launches = 0;
+    DevGrid g{};
+    nhp::QueryDesc qd{};             // this plan as one query (host copy)
+    nhp::QueryDesc* d_qd = nullptr;  // ... and its device copy
+    nhp::Group group() const { return nhp::Group{d_qd, 1, lx, lt, max_runs > 0 ? max_runs : 1}; }
+    // profiling (plan_profile)
+    bool prof = false;
+    unsigned long long* d_cnt = nullptr;  // [0] turn, [1] straight improved cells
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> spare;
+    plan_profile_stats acc{};
+
+    void* dalloc(size_t bytes) { return alloc.alloc(bytes, (void*)stream, alloc.ctx); }
+    void dfree(void* p, size_t bytes) {
+        if (p) alloc.free(p, bytes, (void*)stream, alloc.ctx);
+    }
+};
+
+namespace nhp {
+int cuda_rc(cudaError_t e);
+bool pose_ok(const plan_s* p, plan_pose q);
+int64_t cell_index(const plan_s* p, plan_pose q);
+bool pose_hard(const plan_s* p, plan_pose q);
+// PLAN_ERANGE when finite costs of an N-cycle sweep could reach TH.
+int range_check(const plan_s* p, int n_cycles);
+// Copy the plan's QueryDesc to the device (async on the plan's stream).
+int upload_desc(plan_s* p);
+}  // namespace nhp

@@ -17,7 +17,11 @@ namespace nhp {
 namespace {
 
 // level 0: the image with the walls inserted
-__global__ void k_table_level0(const uint16_t* img, uint16_t* t0, int lx) {
+__global__ void k_table_level0(const QueryDesc* __restrict__ qd) {
+    const QueryDesc& Q = qd[blockIdx.y];
+    const uint16_t* img = Q.img;
+    uint16_t* t0 = Q.table;
+    const int lx = Q.g.lx;
     const int n = 1 << lx;
     const int64_t total = (int64_t)n * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -27,7 +31,12 @@ __global__ void k_table_level0(const uint16_t* img, uint16_t* t0, int lx) {
 }
 
 // level k from level k-1: window 2^k = two windows of 2^(k-1)
-__global__ void k_table_level(const uint16_t* prev, uint16_t* cur, int lx, int half) {
+__global__ void k_table_level(const QueryDesc* __restrict__ qd, int k) {
+    const QueryDesc& Q = qd[blockIdx.y];
+    const int lx = Q.g.lx, half = 1 << (k - 1);
+    const int64_t nxy = (int64_t)1 << (2 * lx);
+    const uint16_t* prev = Q.table + (k - 1) * nxy;
+    uint16_t* cur = Q.table + k * nxy;
     const int n = 1 << lx;
     const int64_t total = (int64_t)n * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -40,9 +49,12 @@ __global__ void k_table_level(const uint16_t* prev, uint16_t* cur, int lx, int h
 
 // One thread per pose cell of heading blockIdx.y; the heading's runs are
 // staged in shared memory.
-__global__ void __launch_bounds__(256) k_render(DevGrid g, const uint16_t* __restrict__ table,
-                                                uint16_t* __restrict__ B) {
+__global__ void __launch_bounds__(256) k_render(const QueryDesc* __restrict__ qd) {
     extern __shared__ Run runs[];
+    const QueryDesc& Q = qd[blockIdx.z];
+    const DevGrid g = Q.g;
+    const uint16_t* __restrict__ table = Q.table;
+    uint16_t* __restrict__ B = Q.v.B;
     const int T = blockIdx.y;
     const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
     for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
@@ -83,7 +95,11 @@ __device__ __forceinline__ uint32_t row_window(const uint32_t* row, int p, int n
     return __funnelshift_r(lo, hi, sh);
 }
 
-__global__ void k_bits_level0(const uint16_t* __restrict__ img, uint32_t* __restrict__ h0, int lx) {
+__global__ void k_bits_level0(const QueryDesc* __restrict__ qd) {
+    const QueryDesc& Q = qd[blockIdx.y];
+    const uint16_t* __restrict__ img = Q.img;
+    uint32_t* __restrict__ h0 = Q.bits;
+    const int lx = Q.g.lx;
     const int n = 1 << lx, nw = n >> 5;
     const int64_t total = (int64_t)n * nw;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -99,7 +115,12 @@ __global__ void k_bits_level0(const uint16_t* __restrict__ img, uint32_t* __rest
     }
 }
 
-__global__ void k_bits_level(const uint32_t* __restrict__ prev, uint32_t* __restrict__ cur, int lx, int half) {
+__global__ void k_bits_level(const QueryDesc* __restrict__ qd, int lvl) {
+    const QueryDesc& Q = qd[blockIdx.y];
+    const int lx = Q.g.lx, half = 1 << (lvl - 1);
+    const int64_t words = (int64_t)(1 << lx) * ((1 << lx) >> 5);
+    const uint32_t* __restrict__ prev = Q.bits + (lvl - 1) * words;
+    uint32_t* __restrict__ cur = Q.bits + lvl * words;
     const int n = 1 << lx, nw = n >> 5;
     const int64_t total = (int64_t)n * nw;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -112,9 +133,12 @@ __global__ void k_bits_level(const uint32_t* __restrict__ prev, uint32_t* __rest
 // One thread per (32-pose word, row j) of heading blockIdx.y.  Writes HARD
 // where the footprint meets a hard cell; elsewhere `free_value` (256 for a
 // hard-only image, 0 as a placeholder when a soft pass follows).
-__global__ void __launch_bounds__(256) k_render_bits(DevGrid g, const uint32_t* __restrict__ bits,
-                                                      uint16_t* __restrict__ B, uint16_t free_value) {
+__global__ void __launch_bounds__(256) k_render_bits(const QueryDesc* __restrict__ qd, uint16_t free_value) {
     extern __shared__ Run runs[];
+    const QueryDesc& Q = qd[blockIdx.z];
+    const DevGrid g = Q.g;
+    const uint32_t* __restrict__ bits = Q.bits;
+    uint16_t* __restrict__ B = Q.v.B;
     const int T = blockIdx.y;
     const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
     for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
@@ -147,9 +171,12 @@ __global__ void __launch_bounds__(256) k_render_bits(DevGrid g, const uint32_t* 
 }
 
 // Soft values for the poses the bit pass left non-hard.
-__global__ void __launch_bounds__(256) k_render_soft(DevGrid g, const uint16_t* __restrict__ table,
-                                                     uint16_t* __restrict__ B) {
+__global__ void __launch_bounds__(256) k_render_soft(const QueryDesc* __restrict__ qd) {
     extern __shared__ Run runs[];
+    const QueryDesc& Q = qd[blockIdx.z];
+    const DevGrid g = Q.g;
+    const uint16_t* __restrict__ table = Q.table;
+    uint16_t* __restrict__ B = Q.v.B;
     const int T = blockIdx.y;
     const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
     for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
@@ -172,39 +199,54 @@ __global__ void __launch_bounds__(256) k_render_soft(DevGrid g, const uint16_t* 
 
 }  // namespace
 
-cudaError_t launch_render_bits(const DevGrid& g, const uint16_t* img, uint32_t* bits, uint16_t* B, bool soft,
-                               const uint16_t* table, int max_runs, cudaStream_t s) {
-    const int64_t words = (int64_t)g.nx * (g.nx >> 5);
-    int64_t blocks = (words + 255) / 256;
-    if (blocks > 148 * 8) blocks = 148 * 8;
-    k_bits_level0<<<(unsigned)blocks, 256, 0, s>>>(img, bits, g.lx);
-    for (int k = 1; k <= g.lx; k++)
-        k_bits_level<<<(unsigned)blocks, 256, 0, s>>>(bits + (k - 1) * words, bits + k * words, g.lx, 1 << (k - 1));
-    dim3 grid((unsigned)((words + 255) / 256), (unsigned)g.nt);
-    k_render_bits<<<grid, 256, (size_t)max_runs * sizeof(Run), s>>>(g, bits, B, soft ? 0 : 256);
-    if (soft) {
-        const int64_t nxy = (int64_t)g.nx * g.nx;
-        dim3 g2((unsigned)((nxy + 255) / 256), (unsigned)g.nt);
-        k_render_soft<<<g2, 256, (size_t)max_runs * sizeof(Run), s>>>(g, table, B);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sparse_table(const uint16_t* img, uint16_t* table, int lx, cudaStream_t s) {
-    const int64_t nxy = (int64_t)1 << (2 * lx);
+cudaError_t launch_sparse_table(const Group& gr, cudaStream_t s) {
+    const int64_t nxy = (int64_t)1 << (2 * gr.lx);
     int64_t blocks = (nxy + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
-    k_table_level0<<<(unsigned)blocks, 256, 0, s>>>(img, table, lx);
-    for (int k = 1; k <= lx; k++)
-        k_table_level<<<(unsigned)blocks, 256, 0, s>>>(table + (k - 1) * nxy, table + k * nxy, lx, 1 << (k - 1));
+    const dim3 grid((unsigned)blocks, (unsigned)gr.nq);
+    k_table_level0<<<grid, 256, 0, s>>>(gr.d);
+    for (int k = 1; k <= gr.lx; k++) k_table_level<<<grid, 256, 0, s>>>(gr.d, k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_render(const DevGrid& g, const uint16_t* table, uint16_t* B, int max_runs, cudaStream_t s) {
-    const int64_t nxy = (int64_t)g.nx * g.nx;
-    dim3 grid((unsigned)((nxy + 255) / 256), (unsigned)g.nt);
-    k_render<<<grid, 256, (size_t)max_runs * sizeof(Run), s>>>(g, table, B);
+cudaError_t launch_render_table(const Group& gr, cudaStream_t s) {
+    const int64_t nxy = (int64_t)1 << (2 * gr.lx);
+    dim3 grid((unsigned)((nxy + 255) / 256), (unsigned)(1 << gr.lt), (unsigned)gr.nq);
+    k_render<<<grid, 256, (size_t)gr.max_runs * sizeof(Run), s>>>(gr.d);
     return cudaGetLastError();
+}
+
+cudaError_t launch_render(const Group& gr, bool soft, cudaStream_t s, int* launches) {
+    const int nx = 1 << gr.lx, nt = 1 << gr.lt;
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    if (soft || nx < 32) {
+        e = launch_sparse_table(gr, s);
+        n += gr.lx + 1;
+    }
+    if (e == cudaSuccess && nx >= 32) {
+        // bit-parallel hard test; soft maxima only for the non-hard poses
+        const int64_t words = (int64_t)nx * (nx >> 5);
+        int64_t blocks = (words + 255) / 256;
+        if (blocks > 148 * 8) blocks = 148 * 8;
+        const dim3 lg((unsigned)blocks, (unsigned)gr.nq);
+        k_bits_level0<<<lg, 256, 0, s>>>(gr.d);
+        for (int k = 1; k <= gr.lx; k++) k_bits_level<<<lg, 256, 0, s>>>(gr.d, k);
+        const dim3 grid((unsigned)((words + 255) / 256), (unsigned)nt, (unsigned)gr.nq);
+        k_render_bits<<<grid, 256, (size_t)gr.max_runs * sizeof(Run), s>>>(gr.d, soft ? 0 : 256);
+        n += gr.lx + 2;
+        if (soft) {
+            const dim3 g2((unsigned)(((int64_t)nx * nx + 255) / 256), (unsigned)nt, (unsigned)gr.nq);
+            k_render_soft<<<g2, 256, (size_t)gr.max_runs * sizeof(Run), s>>>(gr.d);
+            n += 1;
+        }
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
+        e = launch_render_table(gr, s);
+        n += 1;
+    }
+    if (launches) *launches = n;
+    return e;
 }
 
 }  // namespace nhp

@@ -32,7 +32,9 @@ constexpr int kMaxRuns = 1 << 16;       // footprint rows over all headings
 constexpr size_t kTableBytes = (size_t)(kMaxNxLog2 + 1) << (2 * kMaxNxLog2) << 1;  // 10 levels of 512^2 uint16
 constexpr size_t kRunBytes = sizeof(Run) * kMaxRuns;
 constexpr size_t kOffBytes = sizeof(int32_t) * ((1 << kMaxNtLog2) + 1);
-constexpr size_t kScratchBytes = kTableBytes + kRunBytes + ((kOffBytes + 255) & ~size_t(255));
+constexpr size_t kOffPad = (kOffBytes + 255) & ~size_t(255);
+constexpr size_t kDescBytes = 512;  // room for the kernel descriptor
+constexpr size_t kScratchBytes = kTableBytes + kRunBytes + kOffPad + kDescBytes;
 
 static __device__ __align__(256) unsigned char g_render_scratch[kScratchBytes];
 
@@ -40,10 +42,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 
-// Host staging for the run list (static, so the call allocates nothing;
-// cudaMemcpyAsync from pageable memory returns once the source may be reused).
+// Host staging for the run list and the kernel descriptor (static, so the
+// call allocates nothing; cudaMemcpyAsync from pageable memory returns once
+// the source may be reused).
 Run g_host_runs[kMaxRuns];
 int32_t g_host_off[(1 << kMaxNtLog2) + 1];
+QueryDesc g_host_desc;
+static_assert(sizeof(QueryDesc) <= kDescBytes, "descriptor slot too small");
 
 int scratch_for_current_device(unsigned char** out) {
     int dev = -1;
@@ -153,16 +158,24 @@ extern "C" int plan_render_cspace_static(const uint16_t* image_dev, int nx_log2,
             cudaSuccess ||
         cudaMemcpyAsync(off, g_host_off, sizeof(int32_t) * (nt + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return PLAN_ECUDA;
-    DevGrid g{};
-    g.lx = nx_log2;
-    g.lt = ntheta_log2;
-    g.nx = 1 << nx_log2;
-    g.nt = nt;
-    g.mx = g.nx - 1;
-    g.mt = nt - 1;
-    g.run_off = off;
-    g.runs = runs;
-    if (launch_sparse_table(image_dev, table, nx_log2, s) != cudaSuccess) return PLAN_ECUDA;
-    if (launch_render(g, table, B_dev, std::max(1, max_runs), s) != cudaSuccess) return PLAN_ECUDA;
+    QueryDesc* desc = (QueryDesc*)(scratch + kTableBytes + kRunBytes + kOffPad);
+    QueryDesc& q = g_host_desc;
+    q = QueryDesc{};
+    q.g.lx = nx_log2;
+    q.g.lt = ntheta_log2;
+    q.g.nx = 1 << nx_log2;
+    q.g.nt = nt;
+    q.g.mx = q.g.nx - 1;
+    q.g.mt = nt - 1;
+    q.g.run_off = off;
+    q.g.runs = runs;
+    q.v.B = B_dev;
+    q.img = image_dev;
+    q.table = table;
+    q.max_runs = std::max(1, max_runs);
+    if (cudaMemcpyAsync(desc, &q, sizeof(QueryDesc), cudaMemcpyHostToDevice, s) != cudaSuccess) return PLAN_ECUDA;
+    const Group gr{desc, 1, nx_log2, ntheta_log2, q.max_runs};
+    if (launch_sparse_table(gr, s) != cudaSuccess) return PLAN_ECUDA;
+    if (launch_render_table(gr, s) != cudaSuccess) return PLAN_ECUDA;
     return PLAN_OK;
 }

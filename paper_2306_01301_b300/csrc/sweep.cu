@@ -48,6 +48,23 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Decode pass p of a query with N cycles (the schedule in internal.h).
+struct PassInfo {
+    bool active, turn;
+    int family, asc, mu1, mu2;  // turns: curve family, first scan direction, maneuvers
+    int mu;                     // straights
+};
+__device__ __forceinline__ PassInfo decode_pass(int p, int N) {
+    PassInfo r{};
+    r.active = p >= 0 && N > 0 && p <= 4 * N;
+    r.turn = (p & 1) == 0;
+    if (p == 0) { r.family = 0; r.asc = 1; r.mu1 = LF; r.mu2 = -1; }
+    else if ((p & 3) == 2) { r.family = 1; r.asc = 1; r.mu1 = RB; r.mu2 = RF; }
+    else if ((p & 3) == 0) { r.family = 0; r.asc = 0; r.mu1 = LB; r.mu2 = (p >> 2) < N ? LF : -1; }
+    r.mu = (p & 3) == 1 ? SF : SB;
+    return r;
+}
+
 // Profiling only: add this warp's improved-cell count to the plan counter.
 __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t n) {
     if (!ctr) return;
@@ -252,12 +269,19 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
 
 template <int K, int SL, int CL>
 __global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : (1024 / (32 * SL) < 1 ? 1 : 1024 / (32 * SL)))
-k_turn(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
+k_turn(const QueryDesc* __restrict__ qd, int tiles_per_q, int pass_all) {
     constexpr int NTL = K * SL;  // headings held by this block
     __shared__ TurnSmem<K, SL, CL> sm;
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
     const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
-    const int tile = CL == 1 ? (int)blockIdx.x : (int)(blockIdx.x / CL);
+    const int bid = (int)(blockIdx.x / CL);
+    const int q = bid / tiles_per_q, tile = bid - q * tiles_per_q;
+    const QueryDesc& Q = qd[q];
+    const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
+    if (!ps.active || !ps.turn) return;  // uniform over the cluster: same query
+    const DevGrid g = Q.g;
+    const Volumes vol = Q.v;
+    const int family = ps.family, asc = ps.asc, mu1 = ps.mu1, mu2 = ps.mu2;
     const int T0 = rank * NTL;
     const int64_t nxy = (int64_t)g.nx * g.nx;
     const int64_t chain = (int64_t)tile * 32 + lane;
@@ -326,15 +350,16 @@ k_turn(DevGrid g, Volumes vol, int family, int asc, int mu1, int mu2) {
 }
 
 template <int K, int SL, int CL>
-cudaError_t launch_turn_t(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
-    const int64_t chains = (int64_t)g.nx * g.nx;
-    const unsigned tiles = (unsigned)((chains + 31) / 32);
+cudaError_t launch_turn_t(const Group& gr, int pass, cudaStream_t s) {
+    const int64_t chains = (int64_t)1 << (2 * gr.lx);
+    const int tiles = (int)((chains + 31) / 32);
+    const unsigned blocks = (unsigned)((int64_t)tiles * gr.nq);
     if (CL == 1) {
-        k_turn<K, SL, CL><<<tiles, 32 * SL, 0, s>>>(g, v, family, asc, mu1, mu2);
+        k_turn<K, SL, CL><<<blocks, 32 * SL, 0, s>>>(gr.d, tiles, pass);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(tiles * CL);
+    cfg.gridDim = dim3(blocks * CL);
     cfg.blockDim = dim3(32 * SL);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -345,7 +370,7 @@ cudaError_t launch_turn_t(const DevGrid& g, Volumes v, int family, int asc, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, g, v, family, asc, mu1, mu2);
+    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, gr.d, tiles, pass);
 }
 
 // ---------------------------------------------------------------- straights
@@ -439,10 +464,10 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
 }
 
 template <bool STEEP, bool FWD>
-__device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, int T, StraightStage* stage,
-                                              const PlaneInfo& pi) {
-    const int lines = blockDim.x;  // min(Nx, 256)
-    const int X0 = blockIdx.x * lines;
+__device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, int T, int lblock,
+                                              StraightStage* stage, const PlaneInfo& pi) {
+    const int lines = blockDim.x;  // min(Nx, 128 or 256)
+    const int X0 = lblock * lines;
     const int t = threadIdx.x;
     constexpr int dir = FWD ? 1 : -1;  // direction of y' along the sweep
     const int16_t* bs = g.bshear + (int64_t)T * g.nx;
@@ -531,27 +556,40 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
         cp_async_commit();
     }
     cp_async_wait0();
-    if (vol.improved) count_improved(vol.improved, nimp);
+    if (vol.improved) count_improved(vol.improved + 1, nimp);
 }
 
 __global__ void __launch_bounds__(kMaxLines, 3)
-k_straight(DevGrid g, Volumes vol, int mu) {
+k_straight(const QueryDesc* __restrict__ qd, int blocks_per_plane, int pass_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StraightStage* stage = reinterpret_cast<StraightStage*>(smem_raw);
+    const int q = blockIdx.x / blocks_per_plane, lblock = blockIdx.x - q * blocks_per_plane;
+    const QueryDesc& Q = qd[q];
+    const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
+    if (!ps.active || ps.turn) return;
+    const DevGrid g = Q.g;
+    const Volumes vol = Q.v;
+    const int mu = ps.mu;
     const int T = blockIdx.y;
     const PlaneInfo pi = g.plane[T];
     const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
     if (pi.iflag) {
-        if (fwd) straight_body<true, true>(g, vol, mu, T, stage, pi);
-        else straight_body<true, false>(g, vol, mu, T, stage, pi);
+        if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi);
+        else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi);
     } else {
-        if (fwd) straight_body<false, true>(g, vol, mu, T, stage, pi);
-        else straight_body<false, false>(g, vol, mu, T, stage, pi);
+        if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi);
+        else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi);
     }
 }
 
 // Grids narrower than one 16-step chunk: the plain per-thread loop.
-__global__ void k_straight_small(DevGrid g, Volumes vol, int mu) {
+__global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all) {
+    const QueryDesc& Q = qd[blockIdx.x];
+    const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
+    if (!ps.active || ps.turn) return;
+    const DevGrid g = Q.g;
+    const Volumes vol = Q.v;
+    const int mu = ps.mu;
     const int T = blockIdx.y;
     const int xq = threadIdx.x;
     const PlaneInfo pi = g.plane[T];
@@ -580,10 +618,13 @@ __global__ void k_straight_small(DevGrid g, Volumes vol, int mu) {
         if (tt < v) { v = tt; pv = q; }
         v += e;
     }
-    if (vol.improved) count_improved(vol.improved, nimp);
+    if (vol.improved) count_improved(vol.improved + 1, nimp);
 }
 
-__global__ void k_init(Volumes vol, int64_t n, int64_t start) {
+__global__ void k_init(const QueryDesc* __restrict__ qd) {
+    const QueryDesc& Q = qd[blockIdx.y];
+    const Volumes vol = Q.v;
+    const int64_t n = (int64_t)Q.g.nx * Q.g.nx * Q.g.nt, start = Q.start;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         vol.V[i] = i == start ? 0u : 0xFFFFFFFFu;
@@ -605,24 +646,42 @@ __global__ void k_init(Volumes vol, int64_t n, int64_t start) {
 #define TURN512_CL 1
 #endif
 
-cudaError_t launch_turn(const DevGrid& g, Volumes v, int family, int asc, int mu1, int mu2, cudaStream_t s) {
-    switch (g.nt) {
-        case 4: return launch_turn_t<1, 4, 1>(g, v, family, asc, mu1, mu2, s);
-        case 8: return launch_turn_t<2, 4, 1>(g, v, family, asc, mu1, mu2, s);
-        case 16: return launch_turn_t<4, 4, 1>(g, v, family, asc, mu1, mu2, s);
-        case 32: return launch_turn_t<8, 4, 1>(g, v, family, asc, mu1, mu2, s);
-        case 64: return launch_turn_t<8, 8, 1>(g, v, family, asc, mu1, mu2, s);
-        case 128: return launch_turn_t<16, 8, 1>(g, v, family, asc, mu1, mu2, s);
-        case 256: return launch_turn_t<16, 16, 1>(g, v, family, asc, mu1, mu2, s);
-        case 512: return launch_turn_t<TURN512_K, TURN512_SL, TURN512_CL>(g, v, family, asc, mu1, mu2, s);
-        case 1024: return launch_turn_t<16, 32, 2>(g, v, family, asc, mu1, mu2, s);
+int turn_variants(int nt) { return nt >= 128 && nt <= 1024 ? 3 : 1; }
+
+// Kernel shapes per N_theta (K headings per thread, SL warps, CL blocks per
+// cluster; K * SL * CL = N_theta).  Variant 0 is the default.
+cudaError_t launch_turn(const Group& gr, int pass, int variant, cudaStream_t s) {
+    const int v = variant < 0 ? 0 : variant;
+    switch (1 << gr.lt) {
+        case 4: return launch_turn_t<1, 4, 1>(gr, pass, s);
+        case 8: return launch_turn_t<2, 4, 1>(gr, pass, s);
+        case 16: return launch_turn_t<4, 4, 1>(gr, pass, s);
+        case 32: return launch_turn_t<8, 4, 1>(gr, pass, s);
+        case 64: return launch_turn_t<8, 8, 1>(gr, pass, s);
+        case 128:
+            return v == 1 ? launch_turn_t<8, 16, 1>(gr, pass, s)
+                 : v == 2 ? launch_turn_t<16, 4, 2>(gr, pass, s)
+                          : launch_turn_t<16, 8, 1>(gr, pass, s);
+        case 256:
+            return v == 1 ? launch_turn_t<16, 8, 2>(gr, pass, s)
+                 : v == 2 ? launch_turn_t<8, 32, 1>(gr, pass, s)
+                          : launch_turn_t<16, 16, 1>(gr, pass, s);
+        case 512:
+            return v == 1 ? launch_turn_t<16, 16, 2>(gr, pass, s)
+                 : v == 2 ? launch_turn_t<16, 8, 4>(gr, pass, s)
+                          : launch_turn_t<TURN512_K, TURN512_SL, TURN512_CL>(gr, pass, s);
+        case 1024:
+            return v == 1 ? launch_turn_t<16, 16, 4>(gr, pass, s)
+                 : v == 2 ? launch_turn_t<16, 8, 8>(gr, pass, s)
+                          : launch_turn_t<16, 32, 2>(gr, pass, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_straight(const DevGrid& g, Volumes v, int mu, cudaStream_t s) {
-    if (g.nx < kSteps) {
-        k_straight_small<<<dim3(1, (unsigned)g.nt), g.nx, 0, s>>>(g, v, mu);
+cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s) {
+    const int nx = 1 << gr.lx, nt = 1 << gr.lt;
+    if (nx < kSteps) {
+        k_straight_small<<<dim3((unsigned)gr.nq, (unsigned)nt), nx, 0, s>>>(gr.d, pass);
         return cudaGetLastError();
     }
     static bool attr_set[64] = {};
@@ -635,17 +694,19 @@ cudaError_t launch_straight(const DevGrid& g, Volumes v, int mu, cudaStream_t s)
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    const int tpb = g.nx < kMaxLines ? g.nx : kMaxLines;
-    dim3 grid((unsigned)(g.nx / tpb), (unsigned)g.nt);
-    k_straight<<<grid, tpb, smem, s>>>(g, v, mu);
+    int tpb = lines == 128 ? 128 : kMaxLines;
+    if (nx < tpb) tpb = nx;
+    const int bpp = nx / tpb;
+    k_straight<<<dim3((unsigned)(bpp * gr.nq), (unsigned)nt), tpb, smem, s>>>(gr.d, bpp, pass);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init(const DevGrid& g, Volumes v, int64_t start, cudaStream_t s) {
-    const int64_t n = (int64_t)g.nx * g.nx * g.nt;
+cudaError_t launch_init(const Group& gr, cudaStream_t s) {
+    const int64_t n = (int64_t)1 << (2 * gr.lx + gr.lt);
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    k_init<<<(unsigned)blocks, 256, 0, s>>>(v, n, start);
+    const int64_t cap = (148 * 16 + gr.nq - 1) / gr.nq;
+    if (blocks > cap) blocks = cap;
+    k_init<<<dim3((unsigned)blocks, (unsigned)gr.nq), 256, 0, s>>>(gr.d);
     return cudaGetLastError();
 }
 
