@@ -261,13 +261,77 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h, "plans_per_s": args.steps * world / e2e_s},
         "clocks": clk,
     }
+    p.close()
+    if world == 1 and not args.no_batched:
+        line["batched"] = run_batched(args, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, img)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    p.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(args, torch):
+    """64 uneven queries (sizes 128^2x128 .. 512^2x256, N in {4, 8, 16}) as
+    one batch: render + sweeps + label walks of all queries per step, one
+    graph replay, against the same queries planned one at a time through the
+    plain single-plan calls."""
+    from paper_2306_01301_b300 import binding, scenes
+    qs = scenes.batched_queries()
+    stream = torch.cuda.current_stream()
+    planners = [binding.Planner.from_scene(sc, stream=stream) for sc in qs]
+    queries = [(sc.start, sc.goal, sc.n_cycles) for sc in qs]
+    updates = sum(6 * sc.n_cycles * sc.cells for sc in qs)
+    b = binding.Batch(planners, stream=stream)
+    b.run(queries, render=True)  # tunes the lanes, captures the graph
+    b.sync()
+    for _ in range(max(3, args.warmup)):
+        b.run(queries, render=True)
+    b.sync()
+    steps = max(3, args.batch_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        b.run(queries, render=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res = b.results()
+    per_run, _ = b.kernel_launches()
+    lanes = b.lanes()
+    b.close()
+
+    def one_at_a_time():
+        out = []
+        for sc, p in zip(qs, planners):
+            p.render()
+            p.sweep(sc.start, sc.n_cycles)
+            out.append(p.extract(sc.goal))
+        return out
+
+    one_at_a_time()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        single = one_at_a_time()
+    torch.cuda.synchronize()
+    ms_single = 1e3 * (time.perf_counter() - t0) / steps
+    same = all((a is None and b_ is None) or (a is not None and b_ is not None and a.cost == b_.cost
+                                               and a.segments == b_.segments) for a, b_ in zip(res, single))
+    for p in planners:
+        p.close()
+    return {"workload": "batched_64_queries_128^2x128..512^2x256_N4-16", "queries": len(qs),
+            "ms_per_batch": ms, "plans_per_s": len(qs) / (ms / 1e3), "updates_per_s": updates / (ms / 1e3),
+            "gpu_launches_per_batch": per_run, "steps": steps,
+            "one_at_a_time": {"ms_per_batch": ms_single, "plans_per_s": len(qs) / (ms_single / 1e3),
+                              "updates_per_s": updates / (ms_single / 1e3), "timing": "host wall clock"},
+            "speedup_vs_one_at_a_time": ms_single / ms, "same_plans_as_one_at_a_time": same,
+            "lanes": [{k: l[k] for k in ("n_queries", "ntheta_log2", "nx_min", "nx_max", "turn_k",
+                                         "turn_sections", "turn_cluster", "turn_grid", "straight_lines",
+                                         "straight_grid", "n_candidates")} for l in lanes],
+            "l2": "inputs_larger_than_L2 (about 15 GB of volumes)"}
 
 
 def main():
@@ -277,6 +341,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

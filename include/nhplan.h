@@ -183,6 +183,11 @@ int plan_destroy(plan_t* plan);
 
 const char* plan_strerror(int code);
 
+/* Which CUDA call failed, and its error name, for the last PLAN_ECUDA
+ * returned on this host thread ("" if none).  The text stays valid until the
+ * next failure on the thread. */
+const char* plan_last_error(void);
+
 /* Obstacle rendering for callers that cannot allocate device memory -- for
  * example a runtime that owns all device memory through a fixed memory plan,
  * or a control loop that forbids allocation once it is running.  The paper
@@ -203,6 +208,76 @@ const char* plan_strerror(int code);
 int plan_render_cspace_static(const uint16_t* image_dev, int nx_log2, int ntheta_log2,
                               const plan_footprint* footprint, double turn_radius_cells, uint32_t flags,
                               uint16_t* B_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Batched planning.  Many independent queries -- each on its own plan, so
+ * grid size, vehicle, turn radius, costs and N may all differ -- run together:
+ * every sweep pass is one launch over all queries of a lane (same N_theta,
+ * compatible Nx), lanes run as parallel branches of one captured CUDA graph,
+ * and an autotuner picks each lane's kernel shapes on the first run.  Results
+ * are bit-identical to running each plan alone (plan_render_cspace,
+ * plan_sweep, plan_extract).
+ *
+ * The batch borrows the plans: they must outlive it, must not be used on
+ * their own while a batch run is in flight, and a plan may appear once.
+ * After a run, each plan's volumes (plan_copy_volumes) hold its query's
+ * result.  All batch work is ordered on the stream given at creation.
+ */
+typedef struct plan_batch_s plan_batch_t;
+
+#define PLAN_BATCH_NO_GRAPH 1u /* launch pass by pass instead of replaying a graph */
+#define PLAN_BATCH_NO_TUNE 2u  /* default kernel shapes, no timing runs */
+
+typedef struct {
+    plan_pose start, goal;
+    int32_t n_cycles; /* N >= 1 */
+} plan_query;
+
+typedef struct {
+    int32_t n_queries, ntheta_log2, nx_min, nx_max;
+    /* chosen shapes: turn kernel K headings per thread, warps per block and
+     * blocks per cluster (variant index among the shapes for N_theta), grid
+     * in work-item slots (0 = one block per item, else persistent); straight
+     * kernel lines per block and grid */
+    int32_t turn_variant, turn_k, turn_sections, turn_cluster, turn_grid;
+    int32_t straight_lines, straight_grid;
+    int32_t n_candidates; /* shapes timed (0 with PLAN_BATCH_NO_TUNE) */
+    float turn_ms, straight_ms; /* best timed pass of each kind */
+} plan_batch_lane_info;
+
+/* Create a batch over n distinct plans.  allocator (NULL = cudaMalloc) serves
+ * the batch's own small device buffers.  Synchronises the plans' streams
+ * once.  PLAN_EINVAL on NULL or repeated plans. */
+int plan_batch_create(plan_t* const* plans, int n, uint32_t flags, const plan_allocator* allocator,
+                      void* cuda_stream, plan_batch_t** out);
+
+/* Run query i on plan i for all i (queries: host array of n).  render != 0
+ * renders every plan's obstacle volume first (else each plan must have been
+ * rendered: PLAN_ESTATE).  Checks poses (PLAN_EINVAL: outside the grid, hard
+ * start, N < 1) and cost range (PLAN_ERANGE) before any work.  The first run
+ * tunes the kernel shapes (timing runs on the plans' volumes); a run whose
+ * N values differ from the previous run's captures a new graph, otherwise
+ * the graph is replayed with the new start and goal poses.  Async: returns
+ * once the work is enqueued. */
+int plan_batch_run(plan_batch_t* batch, const plan_query* queries, int render);
+
+/* Wait for the last run. */
+int plan_batch_sync(plan_batch_t* batch);
+
+/* Result of query i of the last run, as plan_extract reports it (segments in
+ * driving order, *n_out, *cost, PLAN_EUNREACHABLE, PLAN_ERANGE when cap is
+ * too small).  Synchronises. */
+int plan_batch_result(plan_batch_t* batch, int i, plan_segment* out, int cap, int* n_out, uint32_t* cost);
+
+/* Lanes and the shapes the autotuner chose for them (PLAN_ESTATE before the
+ * first run). */
+int plan_batch_lanes(plan_batch_t* batch, int* n_lanes);
+int plan_batch_lane(plan_batch_t* batch, int lane, plan_batch_lane_info* out);
+
+/* Kernel launches of one run (graph nodes) and since creation. */
+int plan_batch_kernel_launches(plan_batch_t* batch, int64_t* per_run, int64_t* total);
+
+int plan_batch_destroy(plan_batch_t* batch);
 
 /* Section VII, host helper: soft-obstacle image from a binary occupancy map
  * [nx][nx] (nonzero = obstacle).  Obstacle cells become 0xFFFF; a free cell at

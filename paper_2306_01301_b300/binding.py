@@ -30,7 +30,13 @@ MANEUVERS = ("LF", "SF", "RB", "RF", "SB", "LB")
 class PlanError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})")
+        detail = ""
+        if code == -3:
+            try:
+                detail = " [" + lib().plan_last_error().decode() + "]"
+            except Exception:
+                pass
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)}){detail}")
 
 
 class Pose(C.Structure):
@@ -107,6 +113,8 @@ def lib():
         L.plan_destroy.argtypes = [vp]
         L.plan_strerror.restype = C.c_char_p
         L.plan_strerror.argtypes = [C.c_int]
+        L.plan_last_error.restype = C.c_char_p
+        L.plan_last_error.argtypes = []
         L.plan_soft_image.restype = C.c_int
         L.plan_soft_image.argtypes = [C.c_int, vp, C.c_int, C.c_int, vp]
         _lib = L
@@ -266,3 +274,117 @@ class Planner:
         c = C.c_int64(0)
         _check(lib().plan_kernel_launches(self._h, C.byref(c)), "plan_kernel_launches")
         return int(c.value)
+
+
+# ---------------------------------------------------------------- batching
+class Query(C.Structure):
+    _fields_ = [("start", Pose), ("goal", Pose), ("n_cycles", C.c_int32)]
+
+
+class LaneInfo(C.Structure):
+    _fields_ = [("n_queries", C.c_int32), ("ntheta_log2", C.c_int32), ("nx_min", C.c_int32),
+                ("nx_max", C.c_int32), ("turn_variant", C.c_int32), ("turn_k", C.c_int32),
+                ("turn_sections", C.c_int32), ("turn_cluster", C.c_int32), ("turn_grid", C.c_int32),
+                ("straight_lines", C.c_int32), ("straight_grid", C.c_int32), ("n_candidates", C.c_int32),
+                ("turn_ms", C.c_float), ("straight_ms", C.c_float)]
+
+
+PLAN_BATCH_NO_GRAPH = 1
+PLAN_BATCH_NO_TUNE = 2
+
+
+def _batch_signatures(L):
+    vp = C.c_void_p
+    L.plan_batch_create.restype = C.c_int
+    L.plan_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.c_uint32, C.POINTER(Allocator), vp, C.POINTER(vp)]
+    L.plan_batch_run.restype = C.c_int
+    L.plan_batch_run.argtypes = [vp, C.POINTER(Query), C.c_int]
+    L.plan_batch_sync.restype = C.c_int
+    L.plan_batch_sync.argtypes = [vp]
+    L.plan_batch_result.restype = C.c_int
+    L.plan_batch_result.argtypes = [vp, C.c_int, C.POINTER(Segment), C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_uint32)]
+    L.plan_batch_lanes.restype = C.c_int
+    L.plan_batch_lanes.argtypes = [vp, C.POINTER(C.c_int)]
+    L.plan_batch_lane.restype = C.c_int
+    L.plan_batch_lane.argtypes = [vp, C.c_int, C.POINTER(LaneInfo)]
+    L.plan_batch_kernel_launches.restype = C.c_int
+    L.plan_batch_kernel_launches.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.plan_batch_destroy.restype = C.c_int
+    L.plan_batch_destroy.argtypes = [vp]
+
+
+def _segments(segs, n) -> List[dict]:
+    return [dict(mu=s.maneuver, entry=(s.entry.x, s.entry.y, s.entry.theta), exit=(s.exit.x, s.exit.y, s.exit.theta),
+                 steps=s.steps, cost=s.cost) for s in segs[:n]]
+
+
+class Batch:
+    """Many queries, one per Planner, run together (plan_batch_* in the C ABI)."""
+
+    def __init__(self, planners: List[Planner], graph: bool = True, tune: bool = True, stream=None):
+        import torch
+        L = lib()
+        if not hasattr(L, "_batch_sig"):
+            _batch_signatures(L)
+            L._batch_sig = True
+        self.planners = list(planners)
+        self.stream = stream or torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(torch, self.stream)
+        arr = (C.c_void_p * len(self.planners))(*[p._h.value for p in self.planners])
+        flags = (0 if graph else PLAN_BATCH_NO_GRAPH) | (0 if tune else PLAN_BATCH_NO_TUNE)
+        h = C.c_void_p()
+        _check(L.plan_batch_create(arr, len(self.planners), flags, C.byref(self._alloc.struct),
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)), "plan_batch_create")
+        self._h = h
+
+    def run(self, queries, render: bool = True):
+        """queries: [(start, goal, n_cycles)] (one per planner).  Async."""
+        n = len(self.planners)
+        assert len(queries) == n
+        arr = (Query * n)()
+        for i, (s, g, N) in enumerate(queries):
+            arr[i] = Query(Pose(*[int(v) for v in s]), Pose(*[int(v) for v in g]), int(N))
+        _check(lib().plan_batch_run(self._h, arr, 1 if render else 0), "plan_batch_run")
+
+    def sync(self):
+        _check(lib().plan_batch_sync(self._h), "plan_batch_sync")
+
+    def result(self, i: int, cap: int = 1024) -> Optional[PlanResult]:
+        segs = (Segment * cap)()
+        n = C.c_int(0)
+        cost = C.c_uint32(0)
+        rc = lib().plan_batch_result(self._h, int(i), segs, cap, C.byref(n), C.byref(cost))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_batch_result")
+        return PlanResult(int(cost.value), _segments(segs, n.value))
+
+    def results(self) -> List[Optional[PlanResult]]:
+        return [self.result(i) for i in range(len(self.planners))]
+
+    def lanes(self) -> List[dict]:
+        n = C.c_int(0)
+        _check(lib().plan_batch_lanes(self._h, C.byref(n)), "plan_batch_lanes")
+        out = []
+        for k in range(n.value):
+            li = LaneInfo()
+            _check(lib().plan_batch_lane(self._h, k, C.byref(li)), "plan_batch_lane")
+            out.append({f: getattr(li, f) for f, _ in LaneInfo._fields_})
+        return out
+
+    def kernel_launches(self) -> Tuple[int, int]:
+        a, b = C.c_int64(0), C.c_int64(0)
+        _check(lib().plan_batch_kernel_launches(self._h, C.byref(a), C.byref(b)), "plan_batch_kernel_launches")
+        return int(a.value), int(b.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().plan_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

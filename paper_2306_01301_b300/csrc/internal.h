@@ -71,12 +71,22 @@ struct QueryDesc {
     int32_t max_runs;         // footprint runs of the widest heading
 };
 
-// One launch group: nq descriptors of a single grid shape on the device.
+// One launch group: nq descriptors on the device.  Without `item_off` every
+// query has the shape (lx, lt) and a launch gives each work item its own
+// block.  A batched launch mixes grid sizes: item_off (device, nq + 1
+// entries) is the prefix sum of each query's work items (turn: 32-chain
+// tiles, all queries with N_theta = 2^lt; straight: heading planes times
+// line blocks, all queries with Nx >= the block's lines), `items` their
+// total, and `grid` > 0 caps the blocks, which then loop over the items
+// (a persistent launch).
 struct Group {
     const QueryDesc* d;
     int nq;
     int lx, lt;
     int max_runs;             // max over the group
+    const int32_t* item_off = nullptr;
+    int64_t items = 0;
+    int grid = 0;
 };
 
 // Cycle schedule (Section XVI.A) with the turn pairs fused: N cycles are the
@@ -101,6 +111,16 @@ cudaError_t launch_render(const Group& gr, bool soft, cudaStream_t s, int* launc
 // the group's N_theta, -1 = the measured default).
 cudaError_t launch_turn(const Group& gr, int pass, int variant, cudaStream_t s);
 int turn_variants(int nt);
+// Shape of a turn variant: K headings per thread, SL warps per block, CL
+// blocks per cluster (K * SL * CL = N_theta).
+void turn_shape(int lt, int variant, int* K, int* SL, int* CL);
+// Resident blocks of one SM for a turn variant / straight shape (persistent
+// grid sizing); 0 on error.
+int turn_blocks_per_sm(int lt, int variant);
+int straight_blocks_per_sm(int lines);
+// Work items of one query in a batched launch.
+inline int64_t turn_items(int lx) { return (((int64_t)1 << (2 * lx)) + 31) / 32; }
+inline int64_t straight_items(int lx, int lt, int lines) { return ((int64_t)1 << lt) * (((int64_t)1 << lx) / lines); }
 // Straight pass with `lines` (128 or 256, 0 = default) lines per block.
 cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s);
 // Label walk from each query's goal into its seg/status buffers.

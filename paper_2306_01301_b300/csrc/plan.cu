@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <new>
+#include <cstdio>
 #include <vector>
 
 #include "plan_state.h"
@@ -184,7 +185,18 @@ bool pose_hard(const plan_s* p, plan_pose q) {
     return false;
 }
 
-int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : PLAN_ECUDA; }
+namespace {
+thread_local char g_last_error[256];
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorName(e));
+    return PLAN_ECUDA;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : cuda_fail(e, "CUDA runtime call"); }
+
+const char* last_error_text() { return g_last_error; }
 
 int range_check(const plan_s* p, int n_cycles) {
     // Every finite value is a sum over at most 6N segments of ct plus at most
@@ -515,6 +527,8 @@ int plan_destroy(plan_t* p) {
     delete p;
     return PLAN_OK;
 }
+
+const char* plan_last_error(void) { return nhp::last_error_text(); }
 
 const char* plan_strerror(int code) {
     switch (code) {

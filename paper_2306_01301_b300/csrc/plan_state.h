@@ -65,6 +65,9 @@ struct plan_s {
 
 namespace nhp {
 int cuda_rc(cudaError_t e);
+// Record a failed CUDA call (plan_last_error) and return PLAN_ECUDA.
+int cuda_fail(cudaError_t e, const char* where);
+const char* last_error_text();
 bool pose_ok(const plan_s* p, plan_pose q);
 int64_t cell_index(const plan_s* p, plan_pose q);
 bool pose_hard(const plan_s* p, plan_pose q);
@@ -73,3 +76,10 @@ int range_check(const plan_s* p, int n_cycles);
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
 }  // namespace nhp
+
+// Return PLAN_ECUDA (recording the call) when a CUDA call fails.
+#define NHP_CK(call)                                              \
+    do {                                                          \
+        const cudaError_t nhp_e_ = (call);                        \
+        if (nhp_e_ != cudaSuccess) return nhp::cuda_fail(nhp_e_, #call); \
+    } while (0)

@@ -267,24 +267,29 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
     __syncthreads();  // the section arrays are reused by the next scan
 }
 
+// Largest q with off[q] <= item (off[0] = 0, strictly increasing).
+__device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq, int64_t item) {
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)__ldg(off + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One 32-chain tile of one query: load, scan (one or two maneuvers), store.
 template <int K, int SL, int CL>
-__global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : (1024 / (32 * SL) < 1 ? 1 : 1024 / (32 * SL)))
-k_turn(const QueryDesc* __restrict__ qd, int tiles_per_q, int pass_all) {
+__device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int64_t tile, int rank,
+                                          TurnSmem<K, SL, CL>& sm) {
     constexpr int NTL = K * SL;  // headings held by this block
-    __shared__ TurnSmem<K, SL, CL> sm;
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
-    const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
-    const int bid = (int)(blockIdx.x / CL);
-    const int q = bid / tiles_per_q, tile = bid - q * tiles_per_q;
-    const QueryDesc& Q = qd[q];
-    const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
-    if (!ps.active || !ps.turn) return;  // uniform over the cluster: same query
     const DevGrid g = Q.g;
     const Volumes vol = Q.v;
     const int family = ps.family, asc = ps.asc, mu1 = ps.mu1, mu2 = ps.mu2;
     const int T0 = rank * NTL;
     const int64_t nxy = (int64_t)g.nx * g.nx;
-    const int64_t chain = (int64_t)tile * 32 + lane;
+    const int64_t chain = tile * 32 + lane;
     const bool valid = chain < nxy;
     const int xq = (int)(chain & g.mx), yq = (int)((chain >> g.lx) & g.mx);
     // With Nx >= 32 all 32 chains of the block share y', so each heading's
@@ -293,7 +298,7 @@ k_turn(const QueryDesc* __restrict__ qd, int tiles_per_q, int pass_all) {
     for (int t = tid; t < NTL; t += 32 * SL) {
         const int4 b = g.beta4[T0 + t];
         const int bx = family ? b.z : b.x, by = family ? b.w : b.y;
-        const int ybase = row_uniform ? (int)(((int64_t)tile * 32 >> g.lx) & g.mx) : 0;
+        const int ybase = row_uniform ? (int)((tile * 32 >> g.lx) & g.mx) : 0;
         // volumes hold at most 2^32 cells, so 32-bit offsets suffice
         if (row_uniform)
             sm.cell[t] = make_int2((int)(uint32_t)((((ybase + by) & g.mx) << g.lx) + (int64_t)(T0 + t) * nxy), bx);
@@ -345,21 +350,52 @@ k_turn(const QueryDesc* __restrict__ qd, int tiles_per_q, int pass_all) {
             }
         }
     }
-    // the partner block reads this block's shared memory: leave together
-    if (CL > 1) cooperative_groups::this_cluster().sync();
+}
+
+// Grid: CL blocks per work item.  Without item_off, item = query * tiles +
+// tile; with it, items of different queries (any Nx, this N_theta) follow
+// each other.  Blocks loop over items when the grid is smaller than the
+// work (persistent launch); every block of a cluster visits the same items.
+template <int K, int SL, int CL>
+__global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : (1024 / (32 * SL) < 1 ? 1 : 1024 / (32 * SL)))
+k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, int nq, int64_t items,
+       int tiles_per_q, int pass_all) {
+    __shared__ TurnSmem<K, SL, CL> sm;
+    const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
+    const int64_t stride = gridDim.x / CL;
+    for (int64_t it = blockIdx.x / CL; it < items; it += stride) {
+        int q;
+        int64_t tile;
+        if (item_off) {
+            q = find_item(item_off, nq, it);
+            tile = it - __ldg(item_off + q);
+        } else {
+            q = (int)(it / tiles_per_q);
+            tile = it - (int64_t)q * tiles_per_q;
+        }
+        const QueryDesc& Q = qd[q];
+        const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
+        if (!ps.active || !ps.turn) continue;  // uniform over the block and the cluster
+        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm);
+        // the partner blocks read this block's shared memory, and the next
+        // item rewrites it: leave the tile together
+        if (CL > 1) cooperative_groups::this_cluster().sync();
+        else if (it + stride < items) __syncthreads();
+    }
 }
 
 template <int K, int SL, int CL>
 cudaError_t launch_turn_t(const Group& gr, int pass, cudaStream_t s) {
-    const int64_t chains = (int64_t)1 << (2 * gr.lx);
-    const int tiles = (int)((chains + 31) / 32);
-    const unsigned blocks = (unsigned)((int64_t)tiles * gr.nq);
+    const int tiles = (int)turn_items(gr.lx);
+    const int64_t items = gr.item_off ? gr.items : (int64_t)tiles * gr.nq;
+    if (items <= 0) return cudaSuccess;
+    const int64_t blocks = gr.grid > 0 && gr.grid < items ? gr.grid : items;
     if (CL == 1) {
-        k_turn<K, SL, CL><<<blocks, 32 * SL, 0, s>>>(gr.d, tiles, pass);
+        k_turn<K, SL, CL><<<(unsigned)blocks, 32 * SL, 0, s>>>(gr.d, gr.item_off, gr.nq, items, tiles, pass);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(blocks * CL);
+    cfg.gridDim = dim3((unsigned)(blocks * CL));
     cfg.blockDim = dim3(32 * SL);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -370,7 +406,14 @@ cudaError_t launch_turn_t(const Group& gr, int pass, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, gr.d, tiles, pass);
+    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, gr.d, gr.item_off, gr.nq, items, tiles, pass);
+}
+
+template <int K, int SL, int CL>
+int turn_occupancy() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_turn<K, SL, CL>, 32 * SL, 0) != cudaSuccess) return 0;
+    return n;
 }
 
 // ---------------------------------------------------------------- straights
@@ -559,26 +602,44 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
     if (vol.improved) count_improved(vol.improved + 1, nimp);
 }
 
+// Grid: one block per (query, heading plane, line block) work item, the
+// items of a query ordered plane by plane.  Without item_off every query has
+// Nx = 2^lx; with it, queries of any Nx >= lines follow each other.  Blocks
+// loop over items when the grid is smaller than the work.
 __global__ void __launch_bounds__(kMaxLines, 3)
-k_straight(const QueryDesc* __restrict__ qd, int blocks_per_plane, int pass_all) {
+k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, int nq, int64_t items,
+           int items_per_q, int pass_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StraightStage* stage = reinterpret_cast<StraightStage*>(smem_raw);
-    const int q = blockIdx.x / blocks_per_plane, lblock = blockIdx.x - q * blocks_per_plane;
-    const QueryDesc& Q = qd[q];
-    const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
-    if (!ps.active || ps.turn) return;
-    const DevGrid g = Q.g;
-    const Volumes vol = Q.v;
-    const int mu = ps.mu;
-    const int T = blockIdx.y;
-    const PlaneInfo pi = g.plane[T];
-    const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
-    if (pi.iflag) {
-        if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi);
-        else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi);
-    } else {
-        if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi);
-        else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi);
+    const int lines = blockDim.x;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        int q;
+        int64_t rem;
+        if (item_off) {
+            q = find_item(item_off, nq, it);
+            rem = it - __ldg(item_off + q);
+        } else {
+            q = (int)(it / items_per_q);
+            rem = it - (int64_t)q * items_per_q;
+        }
+        const QueryDesc& Q = qd[q];
+        const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
+        if (!ps.active || ps.turn) continue;  // uniform over the block
+        const DevGrid g = Q.g;
+        const Volumes vol = Q.v;
+        const int mu = ps.mu;
+        const int bpp = g.nx / lines;  // line blocks per plane (powers of two)
+        const int T = (int)(rem / bpp), lblock = (int)(rem - (int64_t)T * bpp);
+        const PlaneInfo pi = g.plane[T];
+        const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
+        if (pi.iflag) {
+            if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi);
+            else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi);
+        } else {
+            if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi);
+            else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi);
+        }
+        if (it + gridDim.x < items) __syncthreads();  // the stages are refilled by the next item
     }
 }
 
@@ -648,6 +709,22 @@ __global__ void k_init(const QueryDesc* __restrict__ qd) {
 
 int turn_variants(int nt) { return nt >= 128 && nt <= 1024 ? 3 : 1; }
 
+void turn_shape(int lt, int variant, int* K, int* SL, int* CL) {
+    static const int shapes[11][3][3] = {
+        {{0, 0, 0}}, {{0, 0, 0}},
+        {{1, 4, 1}}, {{2, 4, 1}}, {{4, 4, 1}}, {{8, 4, 1}}, {{8, 8, 1}},
+        {{16, 8, 1}, {8, 16, 1}, {16, 4, 2}},
+        {{16, 16, 1}, {16, 8, 2}, {8, 32, 1}},
+        {{TURN512_K, TURN512_SL, TURN512_CL}, {16, 16, 2}, {16, 8, 4}},
+        {{16, 32, 2}, {16, 16, 4}, {16, 8, 8}},
+    };
+    const int v = lt >= 7 && lt <= 10 && variant > 0 && variant < 3 ? variant : 0;
+    const int* sh = (lt >= 2 && lt <= 10) ? shapes[lt][v] : shapes[0][0];
+    *K = sh[0];
+    *SL = sh[1];
+    *CL = sh[2];
+}
+
 // Kernel shapes per N_theta (K headings per thread, SL warps, CL blocks per
 // cluster; K * SL * CL = N_theta).  Variant 0 is the default.
 cudaError_t launch_turn(const Group& gr, int pass, int variant, cudaStream_t s) {
@@ -678,27 +755,71 @@ cudaError_t launch_turn(const Group& gr, int pass, int variant, cudaStream_t s) 
     }
 }
 
-cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s) {
-    const int nx = 1 << gr.lx, nt = 1 << gr.lt;
-    if (nx < kSteps) {
-        k_straight_small<<<dim3((unsigned)gr.nq, (unsigned)nt), nx, 0, s>>>(gr.d, pass);
-        return cudaGetLastError();
-    }
+namespace {
+cudaError_t straight_attr() {
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const size_t smem = 2 * sizeof(StraightStage);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_straight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_straight, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * sizeof(StraightStage)));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s) {
+    const int nx = 1 << gr.lx, nt = 1 << gr.lt;
+    if (!gr.item_off && nx < kSteps) {
+        k_straight_small<<<dim3((unsigned)gr.nq, (unsigned)nt), nx, 0, s>>>(gr.d, pass);
+        return cudaGetLastError();
+    }
+    cudaError_t e = straight_attr();
+    if (e != cudaSuccess) return e;
     int tpb = lines == 128 ? 128 : kMaxLines;
-    if (nx < tpb) tpb = nx;
-    const int bpp = nx / tpb;
-    k_straight<<<dim3((unsigned)(bpp * gr.nq), (unsigned)nt), tpb, smem, s>>>(gr.d, bpp, pass);
+    if (gr.item_off) {
+        if (lines != 128 && lines != kMaxLines) return cudaErrorInvalidValue;  // the caller sized the items
+    } else if (nx < tpb) {
+        tpb = nx;
+    }
+    const int ipq = (int)straight_items(gr.lx, gr.lt, tpb);
+    const int64_t items = gr.item_off ? gr.items : (int64_t)ipq * gr.nq;
+    if (items <= 0) return cudaSuccess;
+    const int64_t blocks = gr.grid > 0 && gr.grid < items ? gr.grid : items;
+    k_straight<<<(unsigned)blocks, tpb, 2 * sizeof(StraightStage), s>>>(gr.d, gr.item_off, gr.nq, items, ipq, pass);
     return cudaGetLastError();
+}
+
+int straight_blocks_per_sm(int lines) {
+    if (straight_attr() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_straight, lines, 2 * sizeof(StraightStage)) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+int turn_blocks_per_sm(int lt, int variant) {
+    const int v = variant < 0 ? 0 : variant;
+    switch (1 << lt) {
+        case 4: return turn_occupancy<1, 4, 1>();
+        case 8: return turn_occupancy<2, 4, 1>();
+        case 16: return turn_occupancy<4, 4, 1>();
+        case 32: return turn_occupancy<8, 4, 1>();
+        case 64: return turn_occupancy<8, 8, 1>();
+        case 128: return v == 1 ? turn_occupancy<8, 16, 1>() : v == 2 ? turn_occupancy<16, 4, 2>()
+                                                                      : turn_occupancy<16, 8, 1>();
+        case 256: return v == 1 ? turn_occupancy<16, 8, 2>() : v == 2 ? turn_occupancy<8, 32, 1>()
+                                                                      : turn_occupancy<16, 16, 1>();
+        case 512: return v == 1 ? turn_occupancy<16, 16, 2>() : v == 2 ? turn_occupancy<16, 8, 4>()
+                                                                       : turn_occupancy<TURN512_K, TURN512_SL, TURN512_CL>();
+        case 1024: return v == 1 ? turn_occupancy<16, 16, 4>() : v == 2 ? turn_occupancy<16, 8, 8>()
+                                                                        : turn_occupancy<16, 32, 2>();
+        default: return 0;
+    }
 }
 
 cudaError_t launch_init(const Group& gr, cudaStream_t s) {

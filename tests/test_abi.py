@@ -77,3 +77,19 @@ def test_entry_points_have_header_comments():
     for n in declared_entry_points():
         i = src.index(n + "(")
         assert "*/" in src[max(0, i - 1200):i] or n in ("plan_destroy", "plan_strerror"), n
+
+
+def test_batch_entry_points_reject_bad_arguments_on_host(lib):
+    binding._batch_signatures(lib)
+    h = C.c_void_p()
+    assert lib.plan_batch_create(None, 1, 0, None, None, C.byref(h)) == -1
+    arr = (C.c_void_p * 2)(None, None)
+    assert lib.plan_batch_create(arr, 2, 0, None, None, C.byref(h)) == -1  # NULL plans
+    assert lib.plan_batch_create(arr, 0, 0, None, None, C.byref(h)) == -1
+    assert lib.plan_batch_run(None, None, 1) == -1
+    assert lib.plan_batch_sync(None) == -1
+    n = C.c_int(0)
+    cost = C.c_uint32(0)
+    assert lib.plan_batch_result(None, 0, None, 0, C.byref(n), C.byref(cost)) == -1
+    assert lib.plan_batch_lanes(None, C.byref(n)) == -1
+    assert lib.plan_batch_destroy(None) == -1
