@@ -264,6 +264,8 @@ def run_ours(args):
     p.close()
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, torch)
+    if world == 1 and not args.no_served:
+        line["served"] = run_served(args, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, img)
     if rank == 0:
@@ -334,6 +336,77 @@ def run_batched(args, torch):
             "l2": "inputs_larger_than_L2 (about 15 GB of volumes)"}
 
 
+def _res_key(res):
+    return None if res is None else (res.cost, [(g["mu"], g["steps"], g["cost"]) for g in res.segments])
+
+
+def _pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def run_served(args, torch):
+    """The served stream: 16 persistent scenes (c-space rendered once, kept in
+    HBM), Poisson arrivals at --served-rate plans/s for --served-seconds (10 %
+    of requests at 512^3, the rest of the batched sizes; N = 8), admission by a
+    120 GB budget.  The same trace runs through the continuous-batching
+    server and through the one-at-a-time server (the single-plan launch
+    sequence per request, in arrival order).  Latency = result ready minus
+    submission, both taken on the host inside the library.  A burst of the
+    first 1000 requests submitted at once gives each mode's saturated
+    plans/s."""
+    from paper_2306_01301_b300 import binding, scenes
+    scs = scenes.served_scenes()
+    trace = scenes.served_trace(scs, rate=args.served_rate, seconds=args.served_seconds)
+    free = torch.cuda.mem_get_info()[0]
+    budget = min(120 << 30, int(free * 0.8))
+    out = {"workload": f"served_stream_poisson{args.served_rate:g}_per_s_{args.served_seconds:g}s_16_scenes_N8",
+           "requests": len(trace), "budget_bytes": budget, "scenes": len(scs),
+           "big_share": sum(1 for x in trace if scs[x[1]].nt_log2 == 9) / max(1, len(trace))}
+    keys = {}
+    for mode in ("continuous", "one_at_a_time"):
+        torch.cuda.empty_cache()
+        srv = binding.Server(budget_bytes=budget, one_at_a_time=(mode == "one_at_a_time"))
+        for sc in scs:
+            srv.add_scene(sc)
+        for k, sc in enumerate(scs):  # warm-up: one request per scene
+            srv.wait(srv.submit(k, sc.pose_candidates[0], sc.pose_candidates[1], 8))
+        clocks = ClockSampler(torch.cuda.current_device())
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, k, st, gl, N) in trace:
+            while True:
+                dt = t0 + ta - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 0.0015:
+                    time.sleep(dt - 0.001)
+            tickets.append(srv.submit(k, st, gl, N))
+        got = [srv.wait(t) for t in tickets]
+        clk = clocks.stop()
+        lat = [1e3 * (i["t_done"] - i["t_submit"]) for i, _ in got]
+        span = max(i["t_done"] for i, _ in got) - min(i["t_submit"] for i, _ in got)
+        stats = srv.stats()
+        keys[mode] = [_res_key(r) for _, r in got]
+        # saturated: the first 1000 requests at once
+        burst = trace[:1000]
+        tb = [srv.submit(k, st, gl, N) for (_, k, st, gl, N) in burst]
+        gb = [srv.wait(t) for t in tb]
+        bspan = max(i["t_done"] for i, _ in gb) - min(i["t_submit"] for i, _ in gb)
+        srv.close()
+        out[mode] = {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "mean_ms": sum(lat) / len(lat),
+                     "max_ms": max(lat), "plans_per_s": len(got) / span,
+                     "saturated_plans_per_s": len(gb) / bspan, "gpu_launches": stats["launches"],
+                     "steps": stats["steps"], "peak_inflight": stats["peak_inflight"],
+                     "peak_arena_bytes": stats["peak_bytes"], "scene_bytes": stats["scene_bytes"],
+                     "reachable": sum(1 for k in keys[mode] if k is not None), "clocks": clk}
+    out["same_plans_in_both_modes"] = keys["continuous"] == keys["one_at_a_time"]
+    c, o = out["continuous"], out["one_at_a_time"]
+    out["p99_ratio_one_at_a_time_over_continuous"] = o["p99_ms"] / c["p99_ms"]
+    out["saturated_speedup"] = c["saturated_plans_per_s"] / o["saturated_plans_per_s"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,6 +416,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=60.0)
+    ap.add_argument("--served-rate", type=float, default=200.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -279,6 +279,82 @@ int plan_batch_kernel_launches(plan_batch_t* batch, int64_t* per_run, int64_t* t
 
 int plan_batch_destroy(plan_batch_t* batch);
 
+/* ------------------------------------------------------------------------
+ * Serving.  A server keeps scenes (image + vehicle + costs, rendered once)
+ * resident on the device and plans requests against them.  All its device
+ * memory -- scenes, each in-flight request's value and label volumes (6 bytes
+ * per pose cell) and small descriptor buffers -- comes from one arena of
+ * budget_bytes allocated at creation; a request is admitted (in arrival
+ * order) when the arena has room for its volumes and a slot is free.
+ *
+ * PLAN_SERVE_CONTINUOUS: a native scheduler thread runs the GPU in steps;
+ * each step initialises the newly admitted requests, advances every other
+ * admitted request by one sweep pass (one launch per lane and pass kind, each
+ * request at its own pass) and walks the labels of the requests that ran
+ * their last pass, so requests that arrive while others run join them on the
+ * GPU.  PLAN_SERVE_ONE_AT_A_TIME: the same thread plans one request at a time
+ * with the single-plan launch sequence (the plain-sweep baseline).  In both
+ * modes a request's result equals plan_sweep + plan_extract on its scene.
+ */
+typedef struct plan_server_s plan_server_t;
+
+#define PLAN_SERVE_CONTINUOUS 0
+#define PLAN_SERVE_ONE_AT_A_TIME 1
+
+typedef struct {
+    size_t budget_bytes;  /* device memory of the server (>= 1 MiB) */
+    int32_t max_inflight; /* requests admitted at once; 0 = only memory limits */
+    int32_t mode;         /* PLAN_SERVE_* */
+} plan_server_config;
+
+typedef struct {
+    int32_t status;     /* PLAN_OK, PLAN_EUNREACHABLE, PLAN_ENOMEM (can never fit), PLAN_ECUDA ... */
+    uint32_t cost;      /* V(goal) */
+    int32_t n_segments;
+    int32_t scene;
+    double t_submit, t_admit, t_done; /* host steady clock, seconds */
+} plan_request_info;
+
+typedef struct {
+    int64_t scenes, submitted, admitted, completed, rejected;
+    int64_t steps;         /* scheduler steps (one-at-a-time: requests) */
+    int64_t launches;      /* kernels launched for requests */
+    int64_t peak_inflight; /* most requests admitted at once */
+    int64_t arena_bytes, peak_bytes, scene_bytes;
+} plan_server_stats;
+
+/* Create a server and start its scheduler thread.  allocator (NULL =
+ * cudaMalloc) provides the one arena block; cuda_stream's earlier work is
+ * waited for once.  The server uses the device current at creation. */
+int plan_server_create(const plan_server_config* cfg, const plan_allocator* allocator, void* cuda_stream,
+                       plan_server_t** out);
+
+/* Add a scene (arguments as plan_create) and render its obstacle volume into
+ * the arena now (synchronous).  *scene_id numbers scenes from 0.
+ * PLAN_ENOMEM when the arena cannot hold it. */
+int plan_server_add_scene(plan_server_t* server, const plan_grid* grid, const plan_footprint* footprint,
+                          double turn_radius_cells, const plan_costs* costs, int32_t* scene_id);
+
+/* Queue a request (thread-safe, does not wait for the GPU).  Checks the
+ * scene, the poses (PLAN_EINVAL: outside the grid, hard start, N < 1), the
+ * cost range (PLAN_ERANGE) and that the volumes can ever fit (PLAN_ENOMEM).
+ * *ticket identifies the request for plan_server_wait. */
+int plan_server_submit(plan_server_t* server, int32_t scene_id, plan_pose start, plan_pose goal,
+                       int32_t n_cycles, uint64_t* ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; PLAN_ETIMEOUT
+ * if it is not done.  On PLAN_OK fills *info and up to cap segments in
+ * driving order (*n_out = all segments; PLAN_ERANGE if cap is too small) and
+ * releases the ticket. */
+int plan_server_wait(plan_server_t* server, uint64_t ticket, double timeout_s, plan_request_info* info,
+                     plan_segment* out, int cap, int* n_out);
+
+/* Counters since creation. */
+int plan_server_stats_read(plan_server_t* server, plan_server_stats* out);
+
+/* Finish every submitted request, stop the thread, free everything. */
+int plan_server_destroy(plan_server_t* server);
+
 /* Section VII, host helper: soft-obstacle image from a binary occupancy map
  * [nx][nx] (nonzero = obstacle).  Obstacle cells become 0xFFFF; a free cell at
  * squared Euclidean distance d2 from the nearest obstacle gets

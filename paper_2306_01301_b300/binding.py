@@ -388,3 +388,112 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- serving
+PLAN_SERVE_CONTINUOUS = 0
+PLAN_SERVE_ONE_AT_A_TIME = 1
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_inflight", C.c_int32), ("mode", C.c_int32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cost", C.c_uint32), ("n_segments", C.c_int32), ("scene", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("scenes", "submitted", "admitted", "completed", "rejected", "steps",
+                                         "launches", "peak_inflight", "arena_bytes", "peak_bytes",
+                                         "scene_bytes")]
+
+
+def _server_signatures(L):
+    vp = C.c_void_p
+    L.plan_server_create.restype = C.c_int
+    L.plan_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(Allocator), vp, C.POINTER(vp)]
+    L.plan_server_add_scene.restype = C.c_int
+    L.plan_server_add_scene.argtypes = [vp, C.POINTER(Grid), C.POINTER(Footprint), C.c_double, C.POINTER(Costs),
+                                        C.POINTER(C.c_int32)]
+    L.plan_server_submit.restype = C.c_int
+    L.plan_server_submit.argtypes = [vp, C.c_int32, Pose, Pose, C.c_int32, C.POINTER(C.c_uint64)]
+    L.plan_server_wait.restype = C.c_int
+    L.plan_server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(RequestInfo), C.POINTER(Segment), C.c_int,
+                                   C.POINTER(C.c_int)]
+    L.plan_server_stats_read.restype = C.c_int
+    L.plan_server_stats_read.argtypes = [vp, C.POINTER(ServerStats)]
+    L.plan_server_destroy.restype = C.c_int
+    L.plan_server_destroy.argtypes = [vp]
+
+
+class Server:
+    """Planning server (plan_server_* in the C ABI): cached scenes, requests
+    admitted by an HBM budget, continuous batching or one at a time."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 0, one_at_a_time: bool = False, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("nhplan needs a CUDA device; there is no CPU fallback")
+        L = lib()
+        if not hasattr(L, "_server_sig"):
+            _server_signatures(L)
+            L._server_sig = True
+        self.stream = stream or torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(torch, self.stream)
+        cfg = ServerConfig(int(budget_bytes), int(max_inflight),
+                           PLAN_SERVE_ONE_AT_A_TIME if one_at_a_time else PLAN_SERVE_CONTINUOUS)
+        h = C.c_void_p()
+        _check(L.plan_server_create(C.byref(cfg), C.byref(self._alloc.struct), C.c_void_p(self.stream.cuda_stream),
+                                    C.byref(h)), "plan_server_create")
+        self._h = h
+
+    def add_scene(self, sc, image: Optional[np.ndarray] = None) -> int:
+        if image is None:
+            image = soft_image(sc.occupancy, sc.soft_radius, sc.soft_max) if sc.soft_radius else sc.hard_image()
+        img = np.ascontiguousarray(image, dtype=np.uint16)
+        grid = Grid(sc.nx_log2, sc.nt_log2, img.ctypes.data_as(C.c_void_p))
+        fp = Footprint(*[int(v) for v in sc.footprint])
+        costs = Costs(sc.step_straight, sc.step_scale, sc.transition, PLAN_FLAG_HALF_SHIFT if sc.half_shift else 0)
+        sid = C.c_int32(-1)
+        _check(lib().plan_server_add_scene(self._h, C.byref(grid), C.byref(fp), float(sc.turn_radius),
+                                           C.byref(costs), C.byref(sid)), "plan_server_add_scene")
+        return int(sid.value)
+
+    def submit(self, scene: int, start, goal, n_cycles: int) -> int:
+        t = C.c_uint64(0)
+        _check(lib().plan_server_submit(self._h, int(scene), Pose(*[int(v) for v in start]),
+                                        Pose(*[int(v) for v in goal]), int(n_cycles), C.byref(t)),
+               "plan_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout: float = -1.0, cap: int = 1024):
+        """Returns (info dict, PlanResult or None when unreachable)."""
+        info = RequestInfo()
+        segs = (Segment * cap)()
+        n = C.c_int(0)
+        _check(lib().plan_server_wait(self._h, int(ticket), float(timeout), C.byref(info), segs, cap, C.byref(n)),
+               "plan_server_wait")
+        d = {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+        if info.status == PLAN_EUNREACHABLE:
+            return d, None
+        if info.status != PLAN_OK:
+            raise PlanError(info.status, "served request")
+        return d, PlanResult(int(info.cost), _segments(segs, n.value))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().plan_server_stats_read(self._h, C.byref(st)), "plan_server_stats_read")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().plan_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -207,6 +207,11 @@ int range_check(const plan_s* p, int n_cycles) {
     return bound >= (double)TH ? PLAN_ERANGE : PLAN_OK;
 }
 
+int check_sweep(const plan_s* p, plan_pose start, int n_cycles) {
+    if (n_cycles < 1 || n_cycles > 4096 || !pose_ok(p, start) || pose_hard(p, start)) return PLAN_EINVAL;
+    return range_check(p, n_cycles);
+}
+
 int upload_desc(plan_s* p) {
     return cuda_rc(cudaMemcpyAsync(p->d_qd, &p->qd, sizeof(QueryDesc), cudaMemcpyHostToDevice, p->stream));
 }
@@ -261,10 +266,11 @@ void mark_end(plan_s* p, int idx) {
 
 }  // namespace
 
-extern "C" {
+namespace nhp {
 
-int plan_create(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
-                const plan_costs* costs, const plan_allocator* allocator, void* cuda_stream, plan_t** out) {
+int create_plan(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
+                const plan_costs* costs, const plan_allocator* allocator, void* cuda_stream, bool volumes,
+                plan_s** out) {
     if (!out) return PLAN_EINVAL;
     *out = nullptr;
     if (!grid || !footprint || !costs || !grid->image) return PLAN_EINVAL;
@@ -322,8 +328,11 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     p->d_blob = (unsigned char*)p->dalloc(p->blob_bytes);
     p->d_img = (uint16_t*)p->dalloc((size_t)p->nxy * 2);
     p->d_table = (uint16_t*)p->dalloc(p->table_bytes);
-    p->d_V = (uint32_t*)p->dalloc((size_t)p->nr * 4);
-    p->d_L = (uint16_t*)p->dalloc((size_t)p->nr * 2);
+    p->volumes = volumes;
+    if (volumes) {
+        p->d_V = (uint32_t*)p->dalloc((size_t)p->nr * 4);
+        p->d_L = (uint16_t*)p->dalloc((size_t)p->nr * 2);
+    }
     p->d_B = (uint16_t*)p->dalloc((size_t)p->nr * 2);
     p->d_seg = (plan_segment*)p->dalloc(sizeof(plan_segment) * kDevSegCap);
     p->d_status = (int*)p->dalloc(16);
@@ -331,7 +340,8 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     p->d_qd = (QueryDesc*)p->dalloc(sizeof(QueryDesc));
     if (p->bits_bytes) p->d_bits = (uint32_t*)p->dalloc(p->bits_bytes);
     if ((p->bits_bytes && !p->d_bits) || !p->d_cnt || !p->d_qd ||
-        !p->d_blob || !p->d_img || !p->d_table || !p->d_V || !p->d_L || !p->d_B || !p->d_seg || !p->d_status) {
+        !p->d_blob || !p->d_img || !p->d_table || (volumes && (!p->d_V || !p->d_L)) || !p->d_B || !p->d_seg ||
+        !p->d_status) {
         release(p);
         delete p;
         return PLAN_ENOMEM;
@@ -377,6 +387,15 @@ int plan_create(const plan_grid* grid, const plan_footprint* footprint, double t
     return PLAN_OK;
 }
 
+}  // namespace nhp
+
+extern "C" {
+
+int plan_create(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
+                const plan_costs* costs, const plan_allocator* allocator, void* cuda_stream, plan_t** out) {
+    return nhp::create_plan(grid, footprint, turn_radius_cells, costs, allocator, cuda_stream, true, out);
+}
+
 int plan_set_image(plan_t* p, const uint16_t* image) {
     if (!p || !image) return PLAN_EINVAL;
     uint32_t m;
@@ -404,6 +423,7 @@ int plan_render_cspace(plan_t* p) {
 
 int plan_sweep(plan_t* p, plan_pose start, int n_cycles) {
     if (!p || n_cycles < 0 || n_cycles > 4096 || !pose_ok(p, start)) return PLAN_EINVAL;
+    if (!p->volumes) return PLAN_ESTATE;
     if (!p->rendered) return PLAN_ESTATE;
     if (pose_hard(p, start)) return PLAN_EINVAL;
     if (range_check(p, n_cycles) != PLAN_OK) return PLAN_ERANGE;

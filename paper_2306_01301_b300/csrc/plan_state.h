@@ -44,6 +44,7 @@ struct plan_s {
     plan_segment* d_seg = nullptr;
     int* d_status = nullptr;
     bool rendered = false;
+    bool volumes = true;  // V and L allocated (scenes of a server hold only B)
     int64_t launches = 0;
     DevGrid g{};
     nhp::QueryDesc qd{};             // this plan as one query (host copy)
@@ -75,6 +76,12 @@ bool pose_hard(const plan_s* p, plan_pose q);
 int range_check(const plan_s* p, int n_cycles);
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
+// plan_create, optionally without the V and L volumes (a cached scene).
+int create_plan(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
+                const plan_costs* costs, const plan_allocator* allocator, void* cuda_stream, bool volumes,
+                plan_s** out);
+// Host-side validity of a (start, n_cycles) sweep request: PLAN_OK, EINVAL, ERANGE.
+int check_sweep(const plan_s* p, plan_pose start, int n_cycles);
 }  // namespace nhp
 
 // Return PLAN_ECUDA (recording the call) when a CUDA call fails.

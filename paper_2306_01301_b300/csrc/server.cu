@@ -1,0 +1,758 @@
+// server.cu -- a planning server: cached scenes, HBM-budget admission and
+// continuous batching of the sweep passes.
+//
+// Scenes (occupancy image + vehicle + costs) are rendered once into their
+// obstacle volumes and stay on the device.  A request names a scene, a start
+// and goal pose and N; it needs its own value and label volumes (6 bytes per
+// pose cell), carved from one device arena whose size is the server's memory
+// budget (the scenes are carved from it too).  A native scheduler thread runs
+// the GPU in steps: each step initialises newly admitted requests, advances
+// every other request by one sweep pass -- one launch per lane (same
+// N_theta, compatible Nx) and pass kind, each request at its own pass of the
+// cycle schedule -- and walks the labels of the requests whose last pass ran
+// in this step, writing their plans straight into mapped host memory.
+// Requests that arrive while others are on the GPU join at the next step as
+// soon as the arena has room for their volumes, so their work overlaps on
+// the device.  Every request runs exactly the kernels and passes it would run
+// alone, so its result does not depend on what else is in flight.
+//
+// For comparison the server also has a one-at-a-time mode: requests are
+// taken in arrival order and each is planned with the single-plan launch
+// sequence (init, 4N + 1 passes, label walk, synchronise) before the next
+// starts.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "plan_state.h"
+
+using namespace nhp;
+
+namespace {
+
+constexpr int kDepth = 2;            // steps queued on the GPU ahead of the host
+constexpr int kSlots = kDepth + 1;   // descriptor / result slots in rotation
+constexpr size_t kAlign = 256;
+constexpr int kMaxScenes = 4096;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// First-fit suballocator over one device block, with coalescing.
+class Arena {
+  public:
+    void init(unsigned char* base, size_t bytes) {
+        base_ = base;
+        size_ = bytes;
+        free_.clear();
+        if (bytes) free_[0] = bytes;
+    }
+    unsigned char* alloc(size_t bytes) {
+        std::lock_guard<std::mutex> lk(mu_);
+        bytes = align_up(std::max<size_t>(bytes, 1), kAlign);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, rest = it->second - bytes;
+            free_.erase(it);
+            if (rest) free_[off + bytes] = rest;
+            live_[off] = bytes;
+            used_ += bytes;
+            peak_ = std::max(peak_, used_);
+            return base_ + off;
+        }
+        return nullptr;
+    }
+    void release(void* p) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        const size_t off = (size_t)((unsigned char*)p - base_);
+        auto lv = live_.find(off);
+        if (lv == live_.end()) return;
+        size_t o = off, n = lv->second;
+        live_.erase(lv);
+        used_ -= n;
+        auto nx = free_.lower_bound(o);
+        if (nx != free_.end() && nx->first == o + n) {
+            n += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == o) {
+                o = pv->first;
+                n += pv->second;
+                free_.erase(pv);
+            }
+        }
+        free_[o] = n;
+    }
+    size_t used() {
+        std::lock_guard<std::mutex> lk(mu_);
+        return used_;
+    }
+    size_t peak() {
+        std::lock_guard<std::mutex> lk(mu_);
+        return peak_;
+    }
+    size_t size() const { return size_; }
+
+  private:
+    std::mutex mu_;
+    unsigned char* base_ = nullptr;
+    size_t size_ = 0, used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;
+    std::unordered_map<size_t, size_t> live_;
+};
+
+void* arena_alloc(size_t bytes, void*, void* ctx) { return ((Arena*)ctx)->alloc(bytes); }
+void arena_free(void* p, size_t, void*, void* ctx) { ((Arena*)ctx)->release(p); }
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    int scene = 0;
+    plan_pose start{}, goal{};
+    int n_cycles = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int pass = -1;            // next pass; -1 = not initialised yet
+    unsigned char* mem = nullptr;
+    size_t mem_bytes = 0;
+    bool finishing = false;   // its label walk is on the GPU
+    bool done = false;
+    int status = PLAN_OK;
+    uint32_t cost = PLAN_INF;
+    std::vector<plan_segment> segs;
+    int res_off = 0;          // offset of its result in the step's result area
+};
+using ReqPtr = std::shared_ptr<Request>;
+
+struct Slot {
+    unsigned char* h_desc = nullptr;  // pinned staging
+    unsigned char* d_desc = nullptr;  // device copy
+    size_t desc_cap = 0;
+    unsigned char* h_res = nullptr;   // mapped pinned: written by the label walk
+    unsigned char* d_res = nullptr;   // its device address
+    size_t res_cap = 0;
+};
+
+struct Step {
+    cudaEvent_t ev = nullptr;
+    int slot = 0;
+    std::vector<ReqPtr> finishing;
+};
+
+// One launch of a step: requests of one lane and pass kind.
+struct LaunchSet {
+    int lt = 0, nx_key = 0;
+    bool turn = false;
+    std::vector<ReqPtr> reqs;
+};
+
+}  // namespace
+
+struct plan_server_s {
+    plan_server_config cfg{};
+    plan_allocator alloc{};
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    unsigned char* arena_base = nullptr;
+    Arena arena;
+    std::mutex mu;                    // guards everything below
+    std::condition_variable cv_in, cv_done;
+    // scenes: slots are written once (under mu) before their index is handed
+    // out, so the scheduler reads them without locking
+    plan_s* scenes[kMaxScenes] = {};
+    int n_scenes = 0;
+    std::deque<ReqPtr> incoming;      // submitted, not yet seen by the scheduler
+    std::unordered_map<uint64_t, ReqPtr> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int fatal = PLAN_OK;
+    plan_server_stats stats{};
+    // scheduler-thread state
+    std::deque<ReqPtr> pending;       // arrival order, waiting for memory / a slot
+    std::vector<ReqPtr> active;       // admitted, not finished
+    std::deque<Step> steps;           // on the GPU
+    std::vector<cudaEvent_t> spare_events;
+    Slot slots[kSlots];
+    uint64_t step_count = 0;
+    std::thread worker;
+};
+
+namespace {
+
+size_t request_bytes(const plan_s* sc) { return align_up((size_t)sc->nr * 4, kAlign) + (size_t)sc->nr * 2; }
+
+int lane_nx_key(int nx) { return nx >= 256 ? 256 : nx; }
+
+QueryDesc request_desc(const plan_s* sc, const Request& r) {
+    QueryDesc d = sc->qd;
+    d.v.V = (uint32_t*)r.mem;
+    d.v.L = (uint16_t*)(r.mem + align_up((size_t)sc->nr * 4, kAlign));
+    d.v.improved = nullptr;
+    d.start = cell_index(sc, r.start);
+    d.goal = cell_index(sc, r.goal);
+    d.n_cycles = r.n_cycles;
+    d.pass = r.pass;
+    d.seg = nullptr;
+    d.status = nullptr;
+    d.seg_cap = 0;
+    return d;
+}
+
+size_t result_bytes(const Request& r) { return 16 + sizeof(plan_segment) * 6 * (size_t)r.n_cycles; }
+
+void free_slot(Slot& s, plan_server_s* v) {
+    if (s.h_desc) cudaFreeHost(s.h_desc);
+    if (s.h_res) cudaFreeHost(s.h_res);
+    v->arena.release(s.d_desc);
+    s = Slot{};
+}
+
+void retire(plan_server_s* v, Step& st);
+
+// Make every slot hold at least `desc` descriptor bytes and `res` result
+// bytes.  Growing waits for the steps in flight (they use the old buffers).
+int ensure_slots(plan_server_s* v, size_t desc, size_t res) {
+    bool grow = false;
+    for (auto& s : v->slots) grow = grow || s.desc_cap < desc || s.res_cap < res;
+    if (!grow) return PLAN_OK;
+    // the steps in flight read the old buffers: finish and retire them first
+    NHP_CK(cudaStreamSynchronize(v->stream));
+    while (!v->steps.empty()) {
+        retire(v, v->steps.front());
+        v->steps.pop_front();
+    }
+    desc = align_up(std::max(desc, (size_t)64 << 10), 4096);
+    res = align_up(std::max(res, (size_t)64 << 10), 4096);
+    for (auto& s : v->slots) {
+        const size_t dcap = std::max(desc, s.desc_cap), rcap = std::max(res, s.res_cap);
+        free_slot(s, v);
+        s.d_desc = v->arena.alloc(dcap);
+        if (!s.d_desc) return PLAN_ENOMEM;
+        s.desc_cap = dcap;
+        NHP_CK(cudaHostAlloc((void**)&s.h_desc, dcap, cudaHostAllocDefault));
+        NHP_CK(cudaHostAlloc((void**)&s.h_res, rcap, cudaHostAllocMapped));
+        NHP_CK(cudaHostGetDevicePointer((void**)&s.d_res, s.h_res, 0));
+        s.res_cap = rcap;
+    }
+    return PLAN_OK;
+}
+
+cudaEvent_t take_event(plan_server_s* v) {
+    if (!v->spare_events.empty()) {
+        cudaEvent_t e = v->spare_events.back();
+        v->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+}
+
+// Store the results of a finished step and free the requests' volumes.
+void retire(plan_server_s* v, Step& st) {
+    const double t = now_s();
+    Slot& sl = v->slots[st.slot];
+    std::lock_guard<std::mutex> lk(v->mu);
+    for (auto& r : st.finishing) {
+        const int32_t* h = (const int32_t*)(sl.h_res + r->res_off);
+        const plan_segment* seg = (const plan_segment*)(sl.h_res + r->res_off + 16);
+        if (h[0] == -1) {
+            r->status = PLAN_EUNREACHABLE;
+        } else if (h[0] < 0 || h[0] > 6 * r->n_cycles) {
+            r->status = PLAN_EINTERNAL;
+        } else {
+            r->status = PLAN_OK;
+            r->cost = (uint32_t)(h[1] & 0xFFFF) | ((uint32_t)h[2] << 16);
+            r->segs.resize(h[0]);
+            for (int k = 0; k < h[0]; k++) r->segs[k] = seg[h[0] - 1 - k];  // walk runs goal -> start
+        }
+        v->arena.release(r->mem);
+        r->mem = nullptr;
+        r->t_done = t;
+        r->done = true;
+        v->stats.completed++;
+    }
+    v->spare_events.push_back(st.ev);
+    v->cv_done.notify_all();
+}
+
+void fail_all(plan_server_s* v, int code) {
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->fatal = code;
+    auto fin = [&](ReqPtr& r) {
+        if (r->done) return;
+        r->status = code;
+        r->done = true;
+        r->t_done = now_s();
+    };
+    for (auto& r : v->pending) fin(r);
+    for (auto& r : v->active) fin(r);
+    for (auto& r : v->incoming) fin(r);
+    for (auto& st : v->steps)
+        for (auto& r : st.finishing) fin(r);
+    v->cv_done.notify_all();
+}
+
+// Admit pending requests in arrival order while memory and slots allow.
+void admit(plan_server_s* v) {
+    while (!v->pending.empty()) {
+        if (v->cfg.max_inflight > 0 && (int)v->active.size() >= v->cfg.max_inflight) break;
+        ReqPtr r = v->pending.front();
+        const plan_s* sc = v->scenes[r->scene];
+        r->mem_bytes = request_bytes(sc);
+        r->mem = v->arena.alloc(r->mem_bytes);
+        if (!r->mem) break;  // first in, first served: wait for memory
+        r->t_admit = now_s();
+        r->pass = -1;
+        v->pending.pop_front();
+        v->active.push_back(r);
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stats.admitted++;
+        v->stats.peak_inflight = std::max<int64_t>(v->stats.peak_inflight, (int64_t)v->active.size());
+    }
+}
+
+// Build and enqueue one continuous-batching step.
+int launch_step(plan_server_s* v) {
+    std::vector<ReqPtr> init, fin;
+    std::vector<LaunchSet> sets;
+    for (auto& r : v->active) {
+        if (r->finishing) continue;
+        if (r->pass < 0) {
+            init.push_back(r);
+            r->pass = 0;
+        }
+        const plan_s* sc = v->scenes[r->scene];
+        const bool turn = pass_is_turn(r->pass);
+        const int key = lane_nx_key(sc->nx);
+        LaunchSet* ls = nullptr;
+        for (auto& s : sets)
+            if (s.lt == sc->lt && s.nx_key == key && s.turn == turn) ls = &s;
+        if (!ls) {
+            sets.emplace_back();
+            ls = &sets.back();
+            ls->lt = sc->lt;
+            ls->nx_key = key;
+            ls->turn = turn;
+        }
+        ls->reqs.push_back(r);
+        if (r->pass + 1 == pass_count(r->n_cycles)) fin.push_back(r);
+    }
+    if (init.empty() && sets.empty()) return PLAN_OK;
+    // descriptor layout
+    size_t off = 0;
+    const size_t o_init = off;
+    off = align_up(off + sizeof(QueryDesc) * init.size(), kAlign);
+    std::vector<size_t> o_set(sets.size()), o_items(sets.size());
+    for (size_t k = 0; k < sets.size(); k++) {
+        o_set[k] = off;
+        off = align_up(off + sizeof(QueryDesc) * sets[k].reqs.size(), kAlign);
+        o_items[k] = off;
+        off = align_up(off + sizeof(int32_t) * (sets[k].reqs.size() + 1), kAlign);
+    }
+    const size_t o_fin = off;
+    off = align_up(off + sizeof(QueryDesc) * fin.size(), kAlign);
+    size_t res = 0;
+    for (auto& r : fin) {
+        r->res_off = (int)res;
+        res = align_up(res + result_bytes(*r), 16);
+    }
+    int rc = ensure_slots(v, off, res);
+    if (rc != PLAN_OK) return rc;
+    const int si = (int)(v->step_count % kSlots);
+    Slot& sl = v->slots[si];
+    unsigned char* h = sl.h_desc;
+    cudaStream_t s = v->stream;
+    int64_t launches = 0;
+    // fill
+    for (size_t k = 0; k < init.size(); k++) {
+        QueryDesc d = request_desc(v->scenes[init[k]->scene], *init[k]);
+        memcpy(h + o_init + k * sizeof(QueryDesc), &d, sizeof d);
+    }
+    std::vector<int64_t> items(sets.size(), 0);
+    for (size_t k = 0; k < sets.size(); k++) {
+        int32_t* it = (int32_t*)(h + o_items[k]);
+        it[0] = 0;
+        for (size_t j = 0; j < sets[k].reqs.size(); j++) {
+            const Request& r = *sets[k].reqs[j];
+            const plan_s* sc = v->scenes[r.scene];
+            QueryDesc d = request_desc(sc, r);
+            memcpy(h + o_set[k] + j * sizeof(QueryDesc), &d, sizeof d);
+            const int64_t n = sets[k].turn ? turn_items(sc->lx)
+                                           : (sc->nx >= 256 ? straight_items(sc->lx, sc->lt, 256) : 0);
+            it[j + 1] = (int32_t)(it[j] + n);
+        }
+        items[k] = it[sets[k].reqs.size()];
+    }
+    for (size_t k = 0; k < fin.size(); k++) {
+        const Request& r = *fin[k];
+        QueryDesc d = request_desc(v->scenes[r.scene], r);
+        d.status = (int32_t*)(sl.d_res + r.res_off);
+        d.seg = (plan_segment*)(sl.d_res + r.res_off + 16);
+        d.seg_cap = 6 * r.n_cycles;
+        memcpy(h + o_fin + k * sizeof(QueryDesc), &d, sizeof d);
+    }
+    NHP_CK(cudaMemcpyAsync(sl.d_desc, h, off, cudaMemcpyHostToDevice, s));
+    if (!init.empty()) {
+        Group g{};
+        g.d = (const QueryDesc*)(sl.d_desc + o_init);
+        g.nq = (int)init.size();
+        for (auto& r : init) {
+            g.lx = std::max(g.lx, v->scenes[r->scene]->lx);
+            g.lt = std::max(g.lt, v->scenes[r->scene]->lt);
+        }
+        NHP_CK(launch_init(g, s));
+        launches++;
+    }
+    for (size_t k = 0; k < sets.size(); k++) {
+        const LaunchSet& ls = sets[k];
+        const plan_s* sc0 = v->scenes[ls.reqs[0]->scene];
+        bool uniform = true;
+        for (auto& r : ls.reqs) uniform = uniform && v->scenes[r->scene]->lx == sc0->lx;
+        Group g{};
+        g.d = (const QueryDesc*)(sl.d_desc + o_set[k]);
+        g.nq = (int)ls.reqs.size();
+        g.lx = sc0->lx;
+        g.lt = ls.lt;
+        g.max_runs = 1;
+        if (!uniform) {
+            g.item_off = (const int32_t*)(sl.d_desc + o_items[k]);
+            g.items = items[k];
+        }
+        // pass -1: every request at its own pass (QueryDesc::pass)
+        const int lines = ls.nx_key >= 256 ? 256 : (ls.nx_key >= 128 ? 128 : ls.nx_key);
+        NHP_CK(ls.turn ? launch_turn(g, -1, -1, s) : launch_straight(g, -1, lines, s));
+        launches++;
+    }
+    if (!fin.empty()) {
+        Group g{};
+        g.d = (const QueryDesc*)(sl.d_desc + o_fin);
+        g.nq = (int)fin.size();
+        NHP_CK(launch_extract(g, s));
+        launches++;
+    }
+    Step st;
+    st.ev = take_event(v);
+    st.slot = si;
+    st.finishing = fin;
+    if (!st.ev) return PLAN_ECUDA;
+    NHP_CK(cudaEventRecord(st.ev, s));
+    v->steps.push_back(std::move(st));
+    v->step_count++;
+    for (auto& r : v->active) {
+        if (r->finishing) continue;
+        r->pass++;
+        if (r->pass == pass_count(r->n_cycles)) r->finishing = true;
+    }
+    v->active.erase(std::remove_if(v->active.begin(), v->active.end(), [](const ReqPtr& r) { return r->finishing; }),
+                    v->active.end());
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->stats.steps++;
+    v->stats.launches += launches;
+    return PLAN_OK;
+}
+
+// One-at-a-time: the single-plan launch sequence for the oldest request.
+int run_one(plan_server_s* v) {
+    ReqPtr r = v->pending.front();
+    const plan_s* sc = v->scenes[r->scene];
+    r->mem_bytes = request_bytes(sc);
+    r->mem = v->arena.alloc(r->mem_bytes);
+    v->pending.pop_front();
+    if (!r->mem) {  // nothing else holds memory: the request can never fit
+        std::lock_guard<std::mutex> lk(v->mu);
+        r->status = PLAN_ENOMEM;
+        r->done = true;
+        r->t_done = now_s();
+        v->stats.rejected++;
+        v->cv_done.notify_all();
+        return PLAN_OK;
+    }
+    r->t_admit = now_s();
+    int rc = ensure_slots(v, sizeof(QueryDesc), result_bytes(*r));
+    if (rc != PLAN_OK) return rc;
+    Slot& sl = v->slots[0];
+    cudaStream_t s = v->stream;
+    QueryDesc d = request_desc(sc, *r);
+    d.pass = -1;
+    d.status = (int32_t*)sl.d_res;
+    d.seg = (plan_segment*)(sl.d_res + 16);
+    d.seg_cap = 6 * r->n_cycles;
+    memcpy(sl.h_desc, &d, sizeof d);
+    NHP_CK(cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof d, cudaMemcpyHostToDevice, s));
+    Group g{};
+    g.d = (const QueryDesc*)sl.d_desc;
+    g.nq = 1;
+    g.lx = sc->lx;
+    g.lt = sc->lt;
+    g.max_runs = 1;
+    int64_t launches = 0;
+    NHP_CK(launch_init(g, s));
+    launches++;
+    const int np = pass_count(r->n_cycles);
+    for (int p = 0; p < np; p++) {
+        NHP_CK(pass_is_turn(p) ? launch_turn(g, p, -1, s) : launch_straight(g, p, 0, s));
+        launches++;
+    }
+    NHP_CK(launch_extract(g, s));
+    launches++;
+    NHP_CK(cudaStreamSynchronize(s));
+    Step st;
+    st.slot = 0;
+    st.ev = take_event(v);
+    r->res_off = 0;
+    st.finishing.push_back(r);
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stats.admitted++;
+        v->stats.steps++;
+        v->stats.launches += launches;
+        v->stats.peak_inflight = std::max<int64_t>(v->stats.peak_inflight, 1);
+    }
+    retire(v, st);
+    return PLAN_OK;
+}
+
+void worker_main(plan_server_s* v) {
+    if (cudaSetDevice(v->device) != cudaSuccess) {
+        fail_all(v, cuda_fail(cudaGetLastError(), "server thread: cudaSetDevice"));
+        return;
+    }
+    const bool serial = v->cfg.mode == PLAN_SERVE_ONE_AT_A_TIME;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(v->mu);
+            while (!v->incoming.empty()) {
+                v->pending.push_back(v->incoming.front());
+                v->incoming.pop_front();
+            }
+            const bool idle = v->pending.empty() && v->active.empty() && v->steps.empty();
+            if (idle && v->stop) return;
+            if (idle) {
+                v->cv_in.wait(lk, [&] { return v->stop || !v->incoming.empty(); });
+                continue;
+            }
+        }
+        int rc = PLAN_OK;
+        if (serial) {
+            if (!v->pending.empty()) rc = run_one(v);
+        } else {
+            // retire what the GPU finished, admit, then keep kDepth steps queued
+            while (!v->steps.empty() && cudaEventQuery(v->steps.front().ev) == cudaSuccess) {
+                retire(v, v->steps.front());
+                v->steps.pop_front();
+            }
+            admit(v);
+            bool work = false;
+            for (auto& r : v->active) work = work || !r->finishing;
+            if (work && (int)v->steps.size() < kDepth) {
+                rc = launch_step(v);
+            } else if (!v->steps.empty()) {
+                const cudaError_t e = cudaEventSynchronize(v->steps.front().ev);
+                if (e != cudaSuccess) rc = cuda_fail(e, "server step");
+                else {
+                    retire(v, v->steps.front());
+                    v->steps.pop_front();
+                }
+            } else if (!v->pending.empty()) {
+                // nothing on the GPU and the head request still does not fit
+                ReqPtr r = v->pending.front();
+                v->pending.pop_front();
+                std::lock_guard<std::mutex> lk(v->mu);
+                r->status = PLAN_ENOMEM;
+                r->done = true;
+                r->t_done = now_s();
+                v->stats.rejected++;
+                v->cv_done.notify_all();
+            }
+        }
+        if (rc != PLAN_OK) {
+            fail_all(v, rc);
+            return;
+        }
+    }
+}
+
+void server_release(plan_server_s* v) {
+    if (v->stream) cudaStreamSynchronize(v->stream);
+    for (int i = 0; i < v->n_scenes; i++) plan_destroy(v->scenes[i]);  // arena blocks
+    v->n_scenes = 0;
+    for (auto& s : v->slots) free_slot(s, v);
+    for (auto e : v->spare_events) cudaEventDestroy(e);
+    for (auto& st : v->steps)
+        if (st.ev) cudaEventDestroy(st.ev);
+    if (v->arena_base) v->alloc.free(v->arena_base, v->arena.size(), (void*)v->stream, v->alloc.ctx);
+    if (v->stream) cudaStreamDestroy(v->stream);
+}
+
+void* server_default_alloc(size_t bytes, void*, void*) {
+    void* p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+void server_default_free(void* p, size_t, void*, void*) { cudaFree(p); }
+
+}  // namespace
+
+extern "C" {
+
+int plan_server_create(const plan_server_config* cfg, const plan_allocator* allocator, void* cuda_stream,
+                       plan_server_t** out) {
+    if (!out) return PLAN_EINVAL;
+    *out = nullptr;
+    if (!cfg || cfg->budget_bytes < ((size_t)1 << 20) || cfg->max_inflight < 0 ||
+        (cfg->mode != PLAN_SERVE_CONTINUOUS && cfg->mode != PLAN_SERVE_ONE_AT_A_TIME))
+        return PLAN_EINVAL;
+    if (allocator && (!allocator->alloc || !allocator->free)) return PLAN_EINVAL;
+    plan_server_s* v = new (std::nothrow) plan_server_s();
+    if (!v) return PLAN_ENOMEM;
+    v->cfg = *cfg;
+    v->alloc = allocator ? *allocator : plan_allocator{server_default_alloc, server_default_free, nullptr};
+    v->user_stream = (cudaStream_t)cuda_stream;
+    int rc = PLAN_OK;
+    if (cudaGetDevice(&v->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "server stream");
+    if (rc == PLAN_OK) {
+        v->arena_base = (unsigned char*)v->alloc.alloc(cfg->budget_bytes, (void*)v->stream, v->alloc.ctx);
+        if (!v->arena_base) rc = PLAN_ENOMEM;
+        else v->arena.init(v->arena_base, cfg->budget_bytes);
+    }
+    if (rc == PLAN_OK && v->user_stream) {
+        // the arena may still be in use by the caller's stream's earlier work
+        if (cudaStreamSynchronize(v->user_stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "caller stream");
+    }
+    if (rc != PLAN_OK) {
+        server_release(v);
+        delete v;
+        return rc;
+    }
+    v->worker = std::thread(worker_main, v);
+    *out = v;
+    return PLAN_OK;
+}
+
+int plan_server_add_scene(plan_server_t* v, const plan_grid* grid, const plan_footprint* footprint,
+                          double turn_radius_cells, const plan_costs* costs, int32_t* scene_id) {
+    if (!v || !scene_id) return PLAN_EINVAL;
+    *scene_id = -1;
+    cudaStream_t s = nullptr;
+    NHP_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const plan_allocator al{arena_alloc, arena_free, &v->arena};
+    plan_s* p = nullptr;
+    int rc = create_plan(grid, footprint, turn_radius_cells, costs, &al, (void*)s, false, &p);
+    if (rc == PLAN_OK) {
+        p->stream = s;
+        rc = plan_render_cspace(p);
+        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+    }
+    if (p) p->stream = v->stream;  // nothing else runs on the scene's own stream
+    cudaStreamDestroy(s);
+    if (rc != PLAN_OK) {
+        if (p) plan_destroy(p);
+        return rc;
+    }
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (v->n_scenes >= kMaxScenes) {
+        plan_destroy(p);
+        return PLAN_ERANGE;
+    }
+    v->scenes[v->n_scenes] = p;
+    *scene_id = (int32_t)v->n_scenes++;
+    v->stats.scenes = v->n_scenes;
+    v->stats.scene_bytes = (int64_t)v->arena.used();
+    return PLAN_OK;
+}
+
+int plan_server_submit(plan_server_t* v, int32_t scene_id, plan_pose start, plan_pose goal, int32_t n_cycles,
+                       uint64_t* ticket) {
+    if (!v || !ticket) return PLAN_EINVAL;
+    *ticket = 0;
+    const double t = now_s();
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (v->fatal != PLAN_OK) return v->fatal;
+    if (v->stop) return PLAN_ESTATE;
+    if (scene_id < 0 || scene_id >= v->n_scenes) return PLAN_EINVAL;
+    const plan_s* sc = v->scenes[scene_id];
+    int rc = check_sweep(sc, start, n_cycles);
+    if (rc != PLAN_OK) return rc;
+    if (!pose_ok(sc, goal)) return PLAN_EINVAL;
+    // scenes stay for the server's lifetime: the rest is all a request can get
+    if (request_bytes(sc) > v->arena.size() - (size_t)v->stats.scene_bytes) return PLAN_ENOMEM;
+    auto r = std::make_shared<Request>();
+    r->ticket = v->next_ticket++;
+    r->scene = scene_id;
+    r->start = start;
+    r->goal = goal;
+    r->n_cycles = n_cycles;
+    r->t_submit = t;
+    v->tickets[r->ticket] = r;
+    v->incoming.push_back(r);
+    v->stats.submitted++;
+    *ticket = r->ticket;
+    v->cv_in.notify_one();
+    return PLAN_OK;
+}
+
+int plan_server_wait(plan_server_t* v, uint64_t ticket, double timeout_s, plan_request_info* info,
+                     plan_segment* out, int cap, int* n_out) {
+    if (!v || !info || cap < 0 || (cap > 0 && !out)) return PLAN_EINVAL;
+    std::unique_lock<std::mutex> lk(v->mu);
+    auto it = v->tickets.find(ticket);
+    if (it == v->tickets.end()) return PLAN_EINVAL;
+    ReqPtr r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_s < 0) v->cv_done.wait(lk, ready);
+    else if (!v->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) return PLAN_ETIMEOUT;
+    v->tickets.erase(it);
+    memset(info, 0, sizeof *info);
+    info->status = r->status;
+    info->cost = r->cost;
+    info->n_segments = (int32_t)r->segs.size();
+    info->scene = r->scene;
+    info->t_submit = r->t_submit;
+    info->t_admit = r->t_admit;
+    info->t_done = r->t_done;
+    if (n_out) *n_out = (int)r->segs.size();
+    const int n = std::min(cap, (int)r->segs.size());
+    for (int k = 0; k < n; k++) out[k] = r->segs[k];
+    return (int)r->segs.size() > cap && r->status == PLAN_OK ? PLAN_ERANGE : PLAN_OK;
+}
+
+int plan_server_stats_read(plan_server_t* v, plan_server_stats* out) {
+    if (!v || !out) return PLAN_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    *out = v->stats;
+    out->arena_bytes = (int64_t)v->arena.size();
+    out->peak_bytes = (int64_t)v->arena.peak();
+    return PLAN_OK;
+}
+
+int plan_server_destroy(plan_server_t* v) {
+    if (!v) return PLAN_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stop = true;
+        v->cv_in.notify_all();
+    }
+    if (v->worker.joinable()) v->worker.join();  // finishes every submitted request first
+    server_release(v);
+    delete v;
+    return PLAN_OK;
+}
+
+}  // extern "C"

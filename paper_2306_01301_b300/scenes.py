@@ -20,6 +20,9 @@ is a synthetic stand-in with the sizes and structure the paper describes
                        R = 24, soft penalty band of 6 cells, N = 32.
 * ``batched_queries``  independent queries of mixed sizes
                        {128^2x128, 256^2x128, 256^2x256, 512^2x256}.
+* ``served_scenes``    16 persistent scenes (2 at 512^3, the rest of the
+                       batched sizes) and ``served_trace`` a Poisson request
+                       stream over them (200 plans/s, 10 % at 512^3, N = 8).
 
 Occupancy is uint8 [y][x] (1 = obstacle).  Images are uint16 Q8 reciprocal
 velocity: 256 = free, 0xFFFF = hard.
@@ -220,31 +223,88 @@ def maze(seed: int = 2, nx_log2: int = 9, nt_log2: int = 9, n_cycles: int = 32,
 BATCH_SHAPES = [(7, 7), (8, 7), (8, 8), (9, 8)]  # (nx_log2, nt_log2)
 
 
+def _uneven_scene(rng, name, lx, lt, sites=2):
+    """One scene of the batched / served mixes: random rectangles to 5-20 %
+    fill, a vehicle between 8x4 and 96x38 and a turn radius between 10 and 110
+    cells (both scaled by Nx / 512, so that the vehicle keeps its share of the
+    map on the smaller grids), and `sites` keep-out discs where the vehicle
+    fits at any heading (start and goal positions)."""
+    nx = 1 << lx
+    fill = float(rng.uniform(0.05, 0.20))
+    t = float(rng.uniform(0.0, 1.0))
+    L = int(round(8 + t * (96 - 8)))
+    W = int(round(4 + t * (38 - 4)))
+    s = nx / 512.0
+    L, W = max(2, int(round(L * s))), max(2, int(round(W * s)))
+    fp = vehicle_rect(L, W)
+    R = max(2.0, float(rng.integers(10, 111)) * s)
+    reach = int(np.ceil(np.hypot(max(fp[0], fp[1]), fp[2]))) + 2
+    lo, hi = reach + 1, nx - reach - 1
+    pts = [(int(rng.integers(lo, hi)), int(rng.integers(lo, hi))) for _ in range(sites)]
+    occ = _place_rects(rng, nx, fill, 3, 10, keepout=[(x, y, reach) for x, y in pts])
+    return name, lx, lt, R, fp, occ, pts
+
+
 def batched_queries(seed: int = 3, count: int = 64, shapes=None, cycles=(4, 8, 16)) -> List[Scene]:
     """Many independent, uneven queries: grid size, fill, vehicle, turn radius
-    and cycle count drawn per query."""
+    and cycle count drawn per query (see _uneven_scene)."""
     rng = np.random.default_rng(seed)
     shapes = shapes or BATCH_SHAPES
     out = []
     for q in range(count):
         lx, lt = shapes[int(rng.integers(0, len(shapes)))]
-        nx, nt = 1 << lx, 1 << lt
-        fill = float(rng.uniform(0.05, 0.20))
-        t = float(rng.uniform(0.0, 1.0))
-        L = int(round(8 + t * (96 - 8)))
-        W = int(round(4 + t * (38 - 4)))
-        s = nx / 512.0
-        L, W = max(2, int(round(L * s))), max(2, int(round(W * s)))
-        fp = vehicle_rect(L, W)
-        R = max(2.0, float(rng.integers(10, 111)) * s)
         n = int(cycles[int(rng.integers(0, len(cycles)))])
-        reach = int(np.ceil(np.hypot(max(fp[0], fp[1]), fp[2]))) + 2
-        lo, hi = reach + 1, nx - reach - 1
-        sx, sy = int(rng.integers(lo, hi)), int(rng.integers(lo, hi))
-        gx, gy = int(rng.integers(lo, hi)), int(rng.integers(lo, hi))
-        occ = _place_rects(rng, nx, fill, 3, 10, keepout=[(sx, sy, reach), (gx, gy, reach)])
-        out.append(Scene(f"batch{q}", lx, lt, R, fp, occ, (sx, sy, int(rng.integers(0, nt))),
+        name, lx, lt, R, fp, occ, pts = _uneven_scene(rng, f"batch{q}", lx, lt, 2)
+        nt = 1 << lt
+        (sx, sy), (gx, gy) = pts
+        out.append(Scene(name, lx, lt, R, fp, occ, (sx, sy, int(rng.integers(0, nt))),
                          (gx, gy, int(rng.integers(0, nt))), n, 500))
+    return out
+
+
+def served_scenes(seed: int = 4, count: int = 16, big: int = 2, sites: int = 12) -> List[Scene]:
+    """Persistent scenes of the served stream: `big` at 512^3, the rest cycling
+    through the batched sizes.  Each scene carries `sites` start/goal
+    positions in pose_candidates (heading 0; requests draw the heading)."""
+    rng = np.random.default_rng(seed)
+    shapes = [(9, 9)] * big + [BATCH_SHAPES[k % len(BATCH_SHAPES)] for k in range(count - big)]
+    out = []
+    for k, (lx, lt) in enumerate(shapes):
+        name, lx, lt, R, fp, occ, pts = _uneven_scene(rng, f"served{k}", lx, lt, sites)
+        cands = [(x, y, 0) for x, y in pts]
+        out.append(Scene(name, lx, lt, R, fp, occ, cands[0], cands[1], 8, 500, pose_candidates=cands))
+    return out
+
+
+def served_trace(scenes_: List[Scene], rate: float = 200.0, seconds: float = 60.0, n_cycles: int = 8,
+                 big_share: float = 0.10, seed: int = 5):
+    """Poisson arrivals: [(t, scene index, start, goal, N)].  A request is at
+    512^3 with probability big_share, otherwise its size is drawn uniformly
+    from the batched sizes; the scene is then drawn uniformly among the scenes
+    of that size, and start and goal from two different sites of the scene
+    with uniform headings."""
+    rng = np.random.default_rng(seed)
+    big = [i for i, sc in enumerate(scenes_) if (sc.nx_log2, sc.nt_log2) == (9, 9)]
+    by_shape = {}
+    for i, sc in enumerate(scenes_):
+        if (sc.nx_log2, sc.nt_log2) != (9, 9):
+            by_shape.setdefault((sc.nx_log2, sc.nt_log2), []).append(i)
+    shapes = sorted(by_shape)
+    out, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= seconds:
+            break
+        if big and rng.random() < big_share:
+            k = big[int(rng.integers(0, len(big)))]
+        else:
+            grp = by_shape[shapes[int(rng.integers(0, len(shapes)))]]
+            k = grp[int(rng.integers(0, len(grp)))]
+        sc = scenes_[k]
+        a, b = rng.choice(len(sc.pose_candidates), size=2, replace=False)
+        s = sc.pose_candidates[int(a)][:2] + (int(rng.integers(0, sc.nt)),)
+        g = sc.pose_candidates[int(b)][:2] + (int(rng.integers(0, sc.nt)),)
+        out.append((t, k, s, g, n_cycles))
     return out
 
 

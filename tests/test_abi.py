@@ -93,3 +93,20 @@ def test_batch_entry_points_reject_bad_arguments_on_host(lib):
     assert lib.plan_batch_result(None, 0, None, 0, C.byref(n), C.byref(cost)) == -1
     assert lib.plan_batch_lanes(None, C.byref(n)) == -1
     assert lib.plan_batch_destroy(None) == -1
+
+
+def test_server_entry_points_reject_bad_arguments_on_host(lib):
+    binding._server_signatures(lib)
+    h = C.c_void_p()
+    assert lib.plan_server_create(None, None, None, C.byref(h)) == -1
+    cfg = binding.ServerConfig(1000, 0, 0)  # below 1 MiB
+    assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
+    cfg = binding.ServerConfig(1 << 30, 0, 7)  # unknown mode
+    assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
+    cfg = binding.ServerConfig(1 << 30, -1, 0)
+    assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
+    t = C.c_uint64(0)
+    assert lib.plan_server_submit(None, 0, binding.Pose(0, 0, 0), binding.Pose(0, 0, 0), 1, C.byref(t)) == -1
+    info = binding.RequestInfo()
+    assert lib.plan_server_wait(None, 1, 0.0, C.byref(info), None, 0, None) == -1
+    assert lib.plan_server_destroy(None) == -1

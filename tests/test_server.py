@@ -1,0 +1,171 @@
+"""Served planning (plan_server_*): cached scenes, admission by an HBM budget,
+continuous batching.
+
+Every served result must equal the oracle's plan for its scene, start, goal
+and N, and must be the same whether the request runs alone, in a mix of
+requests that overlap on the GPU, one at a time, or squeezed by a memory
+budget that admits only a few requests at once.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_01301_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+# lx, lt, R, footprint, fill: lanes (16, 32), (32, 64), (16, >=256) with
+# Nx 256 and 512 (mixed-size launches).
+SCENES = [
+    (5, 4, 3.5, (2, 1, 1), 0.05),
+    (6, 5, 6.0, (3, 1, 1), 0.04),
+    (8, 4, 20.0, (6, 2, 2), 0.004),
+    (9, 4, 24.0, (12, 4, 3), 0.002),
+]
+
+
+@pytest.fixture(scope="module")
+def world():
+    out = []
+    for k, (lx, lt, R, fp, fill) in enumerate(SCENES):
+        sc, img = scenes.tiny(900 + k, lx, lt, fill=fill, turn_radius=R, footprint=fp, soft=(k % 2 == 0),
+                              transition=450)
+        o = O.Oracle(lx, lt, R, transition=sc.transition)
+        B = o.render(img, fp) if lx <= 6 else o.render_rows(img, fp)
+        free = np.flatnonzero(B != O.HARD)
+        out.append(dict(sc=sc, img=img, o=o, B=B, free=free))
+    rng = np.random.default_rng(17)
+    reqs = []
+    for q in range(24):
+        k = int(rng.integers(0, len(out)))
+        w = out[k]
+        s, g = rng.choice(w["free"], size=2, replace=False)
+        reqs.append((k, w["o"].pose(int(s)), w["o"].pose(int(g)), int(rng.integers(1, 4))))
+    return out, reqs
+
+
+def _server(world_scenes, **kw):
+    from paper_2306_01301_b300 import binding
+    srv = binding.Server(**kw)
+    ids = [srv.add_scene(w["sc"], w["img"]) for w in world_scenes]
+    assert ids == list(range(len(world_scenes)))
+    return srv
+
+
+def _key(res):
+    return None if res is None else (res.cost, [(s["mu"], s["entry"], s["exit"], s["steps"], s["cost"])
+                                                for s in res.segments])
+
+
+def _oracle_key(w, start, goal, N):
+    o = w["o"]
+    V, L, _ = o.sweep(w["B"], o.cell(start), N, mode=1)
+    ref = o.extract(V, L, o.cell(goal))
+    if ref is None:
+        return None
+    return (int(V[o.cell(goal)]), [(s["mu"], o.pose(s["entry"]), o.pose(s["exit"]), s["steps"], s["cost"])
+                                   for s in ref])
+
+
+def _run(srv, reqs):
+    tickets = [srv.submit(k, s, g, N) for (k, s, g, N) in reqs]
+    out = []
+    for t in tickets:
+        info, res = srv.wait(t, timeout=120.0)
+        out.append((info, res))
+    return out
+
+
+@pytest.fixture(scope="module")
+def oracle_keys(world):
+    ws, reqs = world
+    return [_oracle_key(ws[k], s, g, N) for (k, s, g, N) in reqs]
+
+
+def test_served_mix_matches_oracle_and_alone(world, oracle_keys):
+    ws, reqs = world
+    srv = _server(ws, budget_bytes=2 << 30)
+    alone = {}
+    for i in (0, 5, 11, 17):
+        (info, res), = _run(srv, [reqs[i]])
+        alone[i] = _key(res)
+    mix = _run(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    assert st["peak_inflight"] > 1, "requests overlapped on the GPU"
+    assert st["completed"] == len(reqs) + 4 and st["rejected"] == 0
+    assert st["peak_bytes"] <= st["arena_bytes"]
+    for i, (info, res) in enumerate(mix):
+        assert _key(res) == oracle_keys[i], f"request {i}"
+        assert info["t_submit"] <= info["t_admit"] <= info["t_done"]
+        if i in alone:
+            assert _key(res) == alone[i]
+
+
+def test_one_at_a_time_and_budget_squeeze_give_the_same_plans(world, oracle_keys):
+    ws, reqs = world
+    serial = _server(ws, budget_bytes=2 << 30, one_at_a_time=True)
+    got = _run(serial, reqs)
+    st = serial.stats()
+    serial.close()
+    assert st["peak_inflight"] == 1 and st["completed"] == len(reqs)
+    assert [_key(r) for _, r in got] == oracle_keys
+
+    # a budget that holds the scenes and about two requests of the largest scene
+    probe = _server(ws, budget_bytes=2 << 30)
+    scene_bytes = probe.stats()["scene_bytes"]
+    probe.close()
+    big = max(w["sc"].cells for w in ws)
+    budget = scene_bytes + (4 << 20) + int(2.5 * 6 * big)
+    tight = _server(ws, budget_bytes=budget)
+    big_reqs = [r for r in reqs if ws[r[0]]["sc"].cells == big]
+    assert len(big_reqs) >= 3
+    got = _run(tight, big_reqs * 2)
+    st = tight.stats()
+    tight.close()
+    assert st["peak_bytes"] <= budget
+    assert 1 <= st["peak_inflight"] <= 2
+    want = [oracle_keys[reqs.index(r)] for r in big_reqs * 2]
+    assert [_key(r) for _, r in got] == want
+
+
+def test_max_inflight_limits_admission(world, oracle_keys):
+    ws, reqs = world
+    srv = _server(ws, budget_bytes=2 << 30, max_inflight=3)
+    got = _run(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    assert st["peak_inflight"] <= 3
+    assert [_key(r) for _, r in got] == oracle_keys
+
+
+def test_submit_rejects_bad_requests(world):
+    from paper_2306_01301_b300 import binding
+    ws, reqs = world
+    srv = _server(ws, budget_bytes=1 << 30)
+    k, s, g, N = reqs[0]
+    w = ws[k]
+    hard = np.flatnonzero(w["B"] == O.HARD)
+    cases = [(k, w["o"].pose(int(hard[0])), g, N), (k, (1 << 12, 0, 0), g, N), (k, s, g, 0), (99, s, g, N),
+             (k, s, (0, 0, 1 << 12), N)]
+    for c in cases:
+        with pytest.raises(binding.PlanError) as e:
+            srv.submit(*c)
+        assert e.value.code == -1, c
+    with pytest.raises(binding.PlanError) as e:
+        srv.wait(123456789)
+    assert e.value.code == -1
+    srv.close()
+    # a request whose volumes can never fit next to the scene: refused at
+    # submission or, once nothing else holds memory, by the scheduler
+    w3 = ws[3]
+    probe = _server([w3], budget_bytes=1 << 30)
+    scene_bytes = probe.stats()["scene_bytes"]
+    probe.close()
+    small = _server([w3], budget_bytes=scene_bytes + (2 << 20))
+    s3, g3 = w3["o"].pose(int(w3["free"][0])), w3["o"].pose(int(w3["free"][-1]))
+    assert 6 * w3["sc"].cells > (2 << 20)
+    with pytest.raises(binding.PlanError) as e:
+        small.wait(small.submit(0, s3, g3, 1), timeout=60.0)
+    assert e.value.code == -2
+    small.close()
