@@ -168,6 +168,7 @@ typedef struct {
     double turn_ms, straight_ms, render_ms, init_ms; /* summed event times */
     uint64_t turn_improved;   /* cells written by turn passes */
     uint64_t straight_improved;
+    uint64_t turn_tiles_improved; /* turn-kernel work items (32 chains) with any written cell */
 } plan_profile_stats;
 
 /* Turn profiling on (enable != 0) or off; either way the counters restart. */
@@ -305,6 +306,17 @@ typedef struct {
     size_t budget_bytes;  /* device memory of the server (>= 1 MiB) */
     int32_t max_inflight; /* requests admitted at once; 0 = only memory limits */
     int32_t mode;         /* PLAN_SERVE_* */
+    /* Continuous mode, size classes: requests of at least big_cells pose
+     * cells are big, of at least heavy_cells heavy, the rest light (0 = class
+     * unused).  At most max_heavy big and max_heavy heavy requests run at
+     * once (0 = no limit), each class taken in arrival order while requests
+     * of other classes may pass one that waits for its slot.  Each class
+     * steps on a stream of its own, light at the highest stream priority and
+     * big at the lowest, so small requests do not wait for large passes. */
+    int64_t heavy_cells;
+    int64_t big_cells;
+    int32_t max_heavy;
+    int32_t reserved;
 } plan_server_config;
 
 typedef struct {

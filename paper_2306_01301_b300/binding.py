@@ -60,7 +60,7 @@ class ProfileStats(C.Structure):
     _fields_ = [("turn_passes", C.c_int64), ("straight_passes", C.c_int64), ("render_passes", C.c_int64),
                 ("init_passes", C.c_int64), ("turn_ms", C.c_double), ("straight_ms", C.c_double),
                 ("render_ms", C.c_double), ("init_ms", C.c_double), ("turn_improved", C.c_uint64),
-                ("straight_improved", C.c_uint64)]
+                ("straight_improved", C.c_uint64), ("turn_tiles_improved", C.c_uint64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -396,7 +396,9 @@ PLAN_SERVE_ONE_AT_A_TIME = 1
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("budget_bytes", C.c_size_t), ("max_inflight", C.c_int32), ("mode", C.c_int32)]
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_inflight", C.c_int32), ("mode", C.c_int32),
+                ("heavy_cells", C.c_int64), ("big_cells", C.c_int64), ("max_heavy", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class RequestInfo(C.Structure):
@@ -432,7 +434,8 @@ class Server:
     """Planning server (plan_server_* in the C ABI): cached scenes, requests
     admitted by an HBM budget, continuous batching or one at a time."""
 
-    def __init__(self, budget_bytes: int, max_inflight: int = 0, one_at_a_time: bool = False, stream=None):
+    def __init__(self, budget_bytes: int, max_inflight: int = 0, one_at_a_time: bool = False,
+                 heavy_cells: int = 0, big_cells: int = 0, max_heavy: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("nhplan needs a CUDA device; there is no CPU fallback")
@@ -443,7 +446,8 @@ class Server:
         self.stream = stream or torch.cuda.current_stream()
         self._alloc = _TorchAllocator(torch, self.stream)
         cfg = ServerConfig(int(budget_bytes), int(max_inflight),
-                           PLAN_SERVE_ONE_AT_A_TIME if one_at_a_time else PLAN_SERVE_CONTINUOUS)
+                           PLAN_SERVE_ONE_AT_A_TIME if one_at_a_time else PLAN_SERVE_CONTINUOUS,
+                           int(heavy_cells), int(big_cells), int(max_heavy), 0)
         h = C.c_void_p()
         _check(L.plan_server_create(C.byref(cfg), C.byref(self._alloc.struct), C.c_void_p(self.stream.cuda_stream),
                                     C.byref(h)), "plan_server_create")

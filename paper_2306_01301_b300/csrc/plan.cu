@@ -230,7 +230,7 @@ void release(plan_s* p) {
     p->dfree(p->d_B, (size_t)p->nr * 2);
     p->dfree(p->d_seg, sizeof(plan_segment) * kDevSegCap);
     p->dfree(p->d_status, 16);
-    p->dfree(p->d_cnt, 16);
+    p->dfree(p->d_cnt, 32);
     p->dfree(p->d_qd, sizeof(QueryDesc));
     for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : p->spare) cudaEventDestroy(e);
@@ -336,7 +336,7 @@ int create_plan(const plan_grid* grid, const plan_footprint* footprint, double t
     p->d_B = (uint16_t*)p->dalloc((size_t)p->nr * 2);
     p->d_seg = (plan_segment*)p->dalloc(sizeof(plan_segment) * kDevSegCap);
     p->d_status = (int*)p->dalloc(16);
-    p->d_cnt = (unsigned long long*)p->dalloc(16);
+    p->d_cnt = (unsigned long long*)p->dalloc(32);
     p->d_qd = (QueryDesc*)p->dalloc(sizeof(QueryDesc));
     if (p->bits_bytes) p->d_bits = (uint32_t*)p->dalloc(p->bits_bytes);
     if ((p->bits_bytes && !p->d_bits) || !p->d_cnt || !p->d_qd ||
@@ -506,13 +506,13 @@ int plan_profile(plan_t* p, int enable) {
     p->marks.clear();
     p->acc = plan_profile_stats{};
     p->prof = enable != 0;
-    return cuda_rc(cudaMemsetAsync(p->d_cnt, 0, 16, p->stream));
+    return cuda_rc(cudaMemsetAsync(p->d_cnt, 0, 32, p->stream));
 }
 
 int plan_profile_read(plan_t* p, plan_profile_stats* out) {
     if (!p || !out) return PLAN_EINVAL;
-    unsigned long long cnt[2] = {0, 0};
-    int rc = cuda_rc(cudaMemcpyAsync(cnt, p->d_cnt, 16, cudaMemcpyDeviceToHost, p->stream));
+    unsigned long long cnt[4] = {0, 0, 0, 0};
+    int rc = cuda_rc(cudaMemcpyAsync(cnt, p->d_cnt, 32, cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
     if (rc != PLAN_OK) return rc;
     for (auto& m : p->marks) {
@@ -530,6 +530,7 @@ int plan_profile_read(plan_t* p, plan_profile_stats* out) {
     p->marks.clear();
     p->acc.turn_improved = cnt[0];
     p->acc.straight_improved = cnt[1];
+    p->acc.turn_tiles_improved = cnt[2];
     *out = p->acc;
     return PLAN_OK;
 }

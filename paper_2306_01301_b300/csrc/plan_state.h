@@ -52,7 +52,7 @@ struct plan_s {
     nhp::Group group() const { return nhp::Group{d_qd, 1, lx, lt, max_runs > 0 ? max_runs : 1}; }
     // profiling (plan_profile)
     bool prof = false;
-    unsigned long long* d_cnt = nullptr;  // [0] turn, [1] straight improved cells
+    unsigned long long* d_cnt = nullptr;  // improved cells [0] turn, [1] straight; [2] turn tiles with any
     struct Mark { int kind; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> spare;

@@ -43,6 +43,8 @@ constexpr int kDepth = 2;            // steps queued on the GPU ahead of the hos
 constexpr int kSlots = kDepth + 1;   // descriptor / result slots in rotation
 constexpr size_t kAlign = 256;
 constexpr int kMaxScenes = 4096;
+constexpr int kTracks = 3;           // 0: big, 1: heavy, 2: light requests
+constexpr int kLight = kTracks - 1;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -135,6 +137,7 @@ struct Request {
     uint32_t cost = PLAN_INF;
     std::vector<plan_segment> segs;
     int res_off = 0;          // offset of its result in the step's result area
+    int track = kLight;
 };
 using ReqPtr = std::shared_ptr<Request>;
 
@@ -151,6 +154,26 @@ struct Step {
     cudaEvent_t ev = nullptr;
     int slot = 0;
     std::vector<ReqPtr> finishing;
+};
+
+// A sequence of steps on its own stream.  Requests are classed by size:
+// big (at least big_cells pose cells, track 0), heavy (at least heavy_cells,
+// track 1) and light (track 2).  Within the big and the heavy class at most
+// max_heavy requests run at once, in arrival order; light requests are not
+// limited.  Each track advances at its own pace on a stream of its own, light
+// kernels at the highest stream priority and big ones at the lowest, so a
+// request is slowed only by the work of its own and of smaller classes.
+struct Track {
+    cudaStream_t stream = nullptr;
+    std::vector<ReqPtr> active;  // admitted, not finished
+    std::deque<Step> steps;      // on the GPU
+    Slot slots[kSlots];
+    uint64_t step_count = 0;
+    bool has_work() const {
+        for (auto& r : active)
+            if (!r->finishing) return true;
+        return false;
+    }
 };
 
 // One launch of a step: requests of one lane and pass kind.
@@ -184,12 +207,20 @@ struct plan_server_s {
     plan_server_stats stats{};
     // scheduler-thread state
     std::deque<ReqPtr> pending;       // arrival order, waiting for memory / a slot
-    std::vector<ReqPtr> active;       // admitted, not finished
-    std::deque<Step> steps;           // on the GPU
+    Track tracks[kTracks];
     std::vector<cudaEvent_t> spare_events;
-    Slot slots[kSlots];
-    uint64_t step_count = 0;
     std::thread worker;
+
+    int inflight() const {
+        int n = 0;
+        for (auto& t : tracks) n += (int)t.active.size();
+        return n;
+    }
+    bool busy() const {
+        for (auto& t : tracks)
+            if (!t.active.empty() || !t.steps.empty()) return true;
+        return false;
+    }
 };
 
 namespace {
@@ -222,23 +253,23 @@ void free_slot(Slot& s, plan_server_s* v) {
     s = Slot{};
 }
 
-void retire(plan_server_s* v, Step& st);
+void retire(plan_server_s* v, Track& tr, Step& st);
 
-// Make every slot hold at least `desc` descriptor bytes and `res` result
-// bytes.  Growing waits for the steps in flight (they use the old buffers).
-int ensure_slots(plan_server_s* v, size_t desc, size_t res) {
+// Make every slot of the track hold at least `desc` descriptor bytes and
+// `res` result bytes.  Growing waits for the track's steps in flight (they
+// use the old buffers).
+int ensure_slots(plan_server_s* v, Track& tr, size_t desc, size_t res) {
     bool grow = false;
-    for (auto& s : v->slots) grow = grow || s.desc_cap < desc || s.res_cap < res;
+    for (auto& s : tr.slots) grow = grow || s.desc_cap < desc || s.res_cap < res;
     if (!grow) return PLAN_OK;
-    // the steps in flight read the old buffers: finish and retire them first
-    NHP_CK(cudaStreamSynchronize(v->stream));
-    while (!v->steps.empty()) {
-        retire(v, v->steps.front());
-        v->steps.pop_front();
+    NHP_CK(cudaStreamSynchronize(tr.stream));
+    while (!tr.steps.empty()) {
+        retire(v, tr, tr.steps.front());
+        tr.steps.pop_front();
     }
     desc = align_up(std::max(desc, (size_t)64 << 10), 4096);
     res = align_up(std::max(res, (size_t)64 << 10), 4096);
-    for (auto& s : v->slots) {
+    for (auto& s : tr.slots) {
         const size_t dcap = std::max(desc, s.desc_cap), rcap = std::max(res, s.res_cap);
         free_slot(s, v);
         s.d_desc = v->arena.alloc(dcap);
@@ -264,9 +295,9 @@ cudaEvent_t take_event(plan_server_s* v) {
 }
 
 // Store the results of a finished step and free the requests' volumes.
-void retire(plan_server_s* v, Step& st) {
+void retire(plan_server_s* v, Track& tr, Step& st) {
     const double t = now_s();
-    Slot& sl = v->slots[st.slot];
+    Slot& sl = tr.slots[st.slot];
     std::lock_guard<std::mutex> lk(v->mu);
     for (auto& r : st.finishing) {
         const int32_t* h = (const int32_t*)(sl.h_res + r->res_off);
@@ -301,37 +332,58 @@ void fail_all(plan_server_s* v, int code) {
         r->t_done = now_s();
     };
     for (auto& r : v->pending) fin(r);
-    for (auto& r : v->active) fin(r);
     for (auto& r : v->incoming) fin(r);
-    for (auto& st : v->steps)
-        for (auto& r : st.finishing) fin(r);
+    for (auto& tr : v->tracks) {
+        for (auto& r : tr.active) fin(r);
+        for (auto& st : tr.steps)
+            for (auto& r : st.finishing) fin(r);
+    }
     v->cv_done.notify_all();
 }
 
-// Admit pending requests in arrival order while memory and slots allow.
+// Track of a request: 0 big, 1 heavy, kLight light.
+int track_of(const plan_server_s* v, const plan_s* sc) {
+    if (v->cfg.big_cells > 0 && sc->nr >= v->cfg.big_cells) return 0;
+    if (v->cfg.heavy_cells > 0 && sc->nr >= v->cfg.heavy_cells) return 1;
+    return kLight;
+}
+
+// Admit pending requests in arrival order while memory and slots allow.  A
+// big or heavy request waiting for a slot of its class lets later requests
+// of other classes pass; a request waiting for memory stops admission (no
+// overtaking for memory, so large requests cannot starve).
 void admit(plan_server_s* v) {
-    while (!v->pending.empty()) {
-        if (v->cfg.max_inflight > 0 && (int)v->active.size() >= v->cfg.max_inflight) break;
-        ReqPtr r = v->pending.front();
+    int running[kTracks];
+    for (int k = 0; k < kTracks; k++) running[k] = (int)v->tracks[k].active.size();
+    for (auto it = v->pending.begin(); it != v->pending.end();) {
+        if (v->cfg.max_inflight > 0 && v->inflight() >= v->cfg.max_inflight) break;
+        ReqPtr r = *it;
         const plan_s* sc = v->scenes[r->scene];
+        const int k = track_of(v, sc);
+        if (k != kLight && v->cfg.max_heavy > 0 && running[k] >= v->cfg.max_heavy) {
+            ++it;
+            continue;
+        }
         r->mem_bytes = request_bytes(sc);
         r->mem = v->arena.alloc(r->mem_bytes);
-        if (!r->mem) break;  // first in, first served: wait for memory
+        if (!r->mem) break;
         r->t_admit = now_s();
         r->pass = -1;
-        v->pending.pop_front();
-        v->active.push_back(r);
+        r->track = k;
+        running[k]++;
+        it = v->pending.erase(it);
+        v->tracks[k].active.push_back(r);
         std::lock_guard<std::mutex> lk(v->mu);
         v->stats.admitted++;
-        v->stats.peak_inflight = std::max<int64_t>(v->stats.peak_inflight, (int64_t)v->active.size());
+        v->stats.peak_inflight = std::max<int64_t>(v->stats.peak_inflight, (int64_t)v->inflight());
     }
 }
 
-// Build and enqueue one continuous-batching step.
-int launch_step(plan_server_s* v) {
+// Build and enqueue one continuous-batching step of a track.
+int launch_step(plan_server_s* v, Track& tr) {
     std::vector<ReqPtr> init, fin;
     std::vector<LaunchSet> sets;
-    for (auto& r : v->active) {
+    for (auto& r : tr.active) {
         if (r->finishing) continue;
         if (r->pass < 0) {
             init.push_back(r);
@@ -372,12 +424,12 @@ int launch_step(plan_server_s* v) {
         r->res_off = (int)res;
         res = align_up(res + result_bytes(*r), 16);
     }
-    int rc = ensure_slots(v, off, res);
+    int rc = ensure_slots(v, tr, off, res);
     if (rc != PLAN_OK) return rc;
-    const int si = (int)(v->step_count % kSlots);
-    Slot& sl = v->slots[si];
+    const int si = (int)(tr.step_count % kSlots);
+    Slot& sl = tr.slots[si];
     unsigned char* h = sl.h_desc;
-    cudaStream_t s = v->stream;
+    cudaStream_t s = tr.stream;
     int64_t launches = 0;
     // fill
     for (size_t k = 0; k < init.size(); k++) {
@@ -452,15 +504,15 @@ int launch_step(plan_server_s* v) {
     st.finishing = fin;
     if (!st.ev) return PLAN_ECUDA;
     NHP_CK(cudaEventRecord(st.ev, s));
-    v->steps.push_back(std::move(st));
-    v->step_count++;
-    for (auto& r : v->active) {
+    tr.steps.push_back(std::move(st));
+    tr.step_count++;
+    for (auto& r : tr.active) {
         if (r->finishing) continue;
         r->pass++;
         if (r->pass == pass_count(r->n_cycles)) r->finishing = true;
     }
-    v->active.erase(std::remove_if(v->active.begin(), v->active.end(), [](const ReqPtr& r) { return r->finishing; }),
-                    v->active.end());
+    tr.active.erase(std::remove_if(tr.active.begin(), tr.active.end(), [](const ReqPtr& r) { return r->finishing; }),
+                    tr.active.end());
     std::lock_guard<std::mutex> lk(v->mu);
     v->stats.steps++;
     v->stats.launches += launches;
@@ -484,10 +536,11 @@ int run_one(plan_server_s* v) {
         return PLAN_OK;
     }
     r->t_admit = now_s();
-    int rc = ensure_slots(v, sizeof(QueryDesc), result_bytes(*r));
+    Track& tr = v->tracks[kLight];
+    int rc = ensure_slots(v, tr, sizeof(QueryDesc), result_bytes(*r));
     if (rc != PLAN_OK) return rc;
-    Slot& sl = v->slots[0];
-    cudaStream_t s = v->stream;
+    Slot& sl = tr.slots[0];
+    cudaStream_t s = tr.stream;
     QueryDesc d = request_desc(sc, *r);
     d.pass = -1;
     d.status = (int32_t*)sl.d_res;
@@ -524,8 +577,20 @@ int run_one(plan_server_s* v) {
         v->stats.launches += launches;
         v->stats.peak_inflight = std::max<int64_t>(v->stats.peak_inflight, 1);
     }
-    retire(v, st);
+    retire(v, tr, st);
     return PLAN_OK;
+}
+
+// Retire the finished steps at the front of every track; true if any.
+bool retire_done(plan_server_s* v) {
+    bool any = false;
+    for (auto& tr : v->tracks)
+        while (!tr.steps.empty() && cudaEventQuery(tr.steps.front().ev) == cudaSuccess) {
+            retire(v, tr, tr.steps.front());
+            tr.steps.pop_front();
+            any = true;
+        }
+    return any;
 }
 
 void worker_main(plan_server_s* v) {
@@ -541,7 +606,7 @@ void worker_main(plan_server_s* v) {
                 v->pending.push_back(v->incoming.front());
                 v->incoming.pop_front();
             }
-            const bool idle = v->pending.empty() && v->active.empty() && v->steps.empty();
+            const bool idle = v->pending.empty() && !v->busy();
             if (idle && v->stop) return;
             if (idle) {
                 v->cv_in.wait(lk, [&] { return v->stop || !v->incoming.empty(); });
@@ -552,24 +617,24 @@ void worker_main(plan_server_s* v) {
         if (serial) {
             if (!v->pending.empty()) rc = run_one(v);
         } else {
-            // retire what the GPU finished, admit, then keep kDepth steps queued
-            while (!v->steps.empty() && cudaEventQuery(v->steps.front().ev) == cudaSuccess) {
-                retire(v, v->steps.front());
-                v->steps.pop_front();
-            }
+            // retire what the GPU finished, admit, then keep each track
+            // kDepth steps ahead
+            retire_done(v);
             admit(v);
-            bool work = false;
-            for (auto& r : v->active) work = work || !r->finishing;
-            if (work && (int)v->steps.size() < kDepth) {
-                rc = launch_step(v);
-            } else if (!v->steps.empty()) {
-                const cudaError_t e = cudaEventSynchronize(v->steps.front().ev);
-                if (e != cudaSuccess) rc = cuda_fail(e, "server step");
-                else {
-                    retire(v, v->steps.front());
-                    v->steps.pop_front();
+            bool launched = false;
+            for (auto& tr : v->tracks) {
+                if (rc == PLAN_OK && tr.has_work() && (int)tr.steps.size() < kDepth) {
+                    rc = launch_step(v, tr);
+                    launched = true;
                 }
-            } else if (!v->pending.empty()) {
+            }
+            bool on_gpu = false;
+            for (auto& tr : v->tracks) on_gpu = on_gpu || !tr.steps.empty();
+            if (rc == PLAN_OK && !launched && on_gpu) {
+                // poll (a step takes microseconds to milliseconds); new
+                // requests are picked up between polls
+                if (!retire_done(v)) std::this_thread::yield();
+            } else if (rc == PLAN_OK && !launched && !on_gpu && !v->pending.empty() && !v->busy()) {
                 // nothing on the GPU and the head request still does not fit
                 ReqPtr r = v->pending.front();
                 v->pending.pop_front();
@@ -590,12 +655,18 @@ void worker_main(plan_server_s* v) {
 
 void server_release(plan_server_s* v) {
     if (v->stream) cudaStreamSynchronize(v->stream);
+    for (auto& tr : v->tracks)
+        if (tr.stream) cudaStreamSynchronize(tr.stream);
     for (int i = 0; i < v->n_scenes; i++) plan_destroy(v->scenes[i]);  // arena blocks
     v->n_scenes = 0;
-    for (auto& s : v->slots) free_slot(s, v);
+    for (auto& tr : v->tracks) {
+        for (auto& s : tr.slots) free_slot(s, v);
+        for (auto& st : tr.steps)
+            if (st.ev) cudaEventDestroy(st.ev);
+        if (tr.stream) cudaStreamDestroy(tr.stream);
+        tr.stream = nullptr;
+    }
     for (auto e : v->spare_events) cudaEventDestroy(e);
-    for (auto& st : v->steps)
-        if (st.ev) cudaEventDestroy(st.ev);
     if (v->arena_base) v->alloc.free(v->arena_base, v->arena.size(), (void*)v->stream, v->alloc.ctx);
     if (v->stream) cudaStreamDestroy(v->stream);
 }
@@ -614,7 +685,8 @@ int plan_server_create(const plan_server_config* cfg, const plan_allocator* allo
                        plan_server_t** out) {
     if (!out) return PLAN_EINVAL;
     *out = nullptr;
-    if (!cfg || cfg->budget_bytes < ((size_t)1 << 20) || cfg->max_inflight < 0 ||
+    if (!cfg || cfg->budget_bytes < ((size_t)1 << 20) || cfg->max_inflight < 0 || cfg->max_heavy < 0 ||
+        cfg->heavy_cells < 0 || cfg->big_cells < 0 ||
         (cfg->mode != PLAN_SERVE_CONTINUOUS && cfg->mode != PLAN_SERVE_ONE_AT_A_TIME))
         return PLAN_EINVAL;
     if (allocator && (!allocator->alloc || !allocator->free)) return PLAN_EINVAL;
@@ -627,6 +699,17 @@ int plan_server_create(const plan_server_config* cfg, const plan_allocator* allo
     if (cudaGetDevice(&v->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = cuda_fail(cudaGetLastError(), "server stream");
+    // light requests' kernels take precedence: the block scheduler then
+    // starts their blocks ahead of a heavy pass's waiting blocks
+    int prio_low = 0, prio_high = 0;
+    if (rc == PLAN_OK && cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "stream priorities");
+    for (int k = 0; k < kTracks && rc == PLAN_OK; k++) {
+        // priorities: numerically lower is higher; spread big .. light over the range
+        const int prio = prio_low + (prio_high - prio_low) * k / (kTracks - 1);
+        if (cudaStreamCreateWithPriority(&v->tracks[k].stream, cudaStreamNonBlocking, prio) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "server track stream");
+    }
     if (rc == PLAN_OK) {
         v->arena_base = (unsigned char*)v->alloc.alloc(cfg->budget_bytes, (void*)v->stream, v->alloc.ctx);
         if (!v->arena_base) rc = PLAN_ENOMEM;

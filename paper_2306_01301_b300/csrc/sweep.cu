@@ -339,7 +339,10 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm.sh);
         else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm.sh);
     }
-    if (vol.improved) count_improved(vol.improved, __popc(chg));
+    if (vol.improved) {
+        count_improved(vol.improved, __popc(chg));
+        if (__syncthreads_or(chg != 0) && threadIdx.x == 0) atomicAdd(vol.improved + 2, 1ull);
+    }
     if (valid && chg) {
 #pragma unroll
         for (int k = 0; k < K; k++) {

@@ -99,12 +99,14 @@ def test_server_entry_points_reject_bad_arguments_on_host(lib):
     binding._server_signatures(lib)
     h = C.c_void_p()
     assert lib.plan_server_create(None, None, None, C.byref(h)) == -1
-    cfg = binding.ServerConfig(1000, 0, 0)  # below 1 MiB
+    cfg = binding.ServerConfig(1000, 0, 0, 0, 0, 0, 0)  # below 1 MiB
     assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
-    cfg = binding.ServerConfig(1 << 30, 0, 7)  # unknown mode
+    cfg = binding.ServerConfig(1 << 30, 0, 7, 0, 0, 0, 0)  # unknown mode
     assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
-    cfg = binding.ServerConfig(1 << 30, -1, 0)
-    assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
+    for bad in ((1 << 30, -1, 0, 0, 0, 0, 0), (1 << 30, 0, 0, -5, 0, 1, 0), (1 << 30, 0, 0, 100, 0, -1, 0),
+                (1 << 30, 0, 0, 0, -3, 1, 0)):
+        cfg = binding.ServerConfig(*bad)
+        assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
     t = C.c_uint64(0)
     assert lib.plan_server_submit(None, 0, binding.Pose(0, 0, 0), binding.Pose(0, 0, 0), 1, C.byref(t)) == -1
     info = binding.RequestInfo()

@@ -129,6 +129,19 @@ def test_one_at_a_time_and_budget_squeeze_give_the_same_plans(world, oracle_keys
     assert [_key(r) for _, r in got] == want
 
 
+def test_heavy_track_gives_the_same_plans(world, oracle_keys):
+    """Big requests (the largest scene) and heavy ones (the next two) each
+    one at a time on streams of their own, light ones batched beside them."""
+    ws, reqs = world
+    cells = sorted(w["sc"].cells for w in ws)
+    srv = _server(ws, budget_bytes=2 << 30, heavy_cells=cells[-3], big_cells=cells[-1], max_heavy=1)
+    got = _run(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["peak_inflight"] > 1
+    assert [_key(r) for _, r in got] == oracle_keys
+
+
 def test_max_inflight_limits_admission(world, oracle_keys):
     ws, reqs = world
     srv = _server(ws, budget_bytes=2 << 30, max_inflight=3)
