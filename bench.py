@@ -173,6 +173,8 @@ def run_ours(args):
     updates = 6 * N * sc.cells
     stream = torch.cuda.current_stream()
     p = binding.Planner.from_scene(sc, img, stream=stream)
+    p.render()
+    tuning = p.autotune(sc.start)  # kernel shapes for this plan, outside the timed region
 
     def step():
         p.render()
@@ -250,6 +252,8 @@ def run_ours(args):
         "plans_per_s": args.steps * world / sec,
         "plan_cost": res.cost if res else None, "plan_maneuvers": len(res.segments) if res else 0,
         "gpu_launches": launches,
+        "autotuned": {k: min((e for e in tuning if e["kernel"] == k), key=lambda e: e["ms"])
+                      for k in ("turn", "straight")},
         "roofline": {"bound": "hbm", "kernel": "k_turn (fused turn-pair sweep)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(), "bytes_per_launch": turn_bytes, "launch_ms": turn_launch_ms},

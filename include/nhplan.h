@@ -148,6 +148,24 @@ int plan_sweep(plan_t* plan, plan_pose start, int n_cycles);
 int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out,
                  uint32_t* cost);
 
+/* One timed kernel shape of plan_autotune. */
+typedef struct {
+    int32_t kind;  /* 0 turn kernel, 1 straight kernel */
+    int32_t shape; /* turn: variant index (plan_batch_lane_info); straight: lines per block */
+    int32_t grid;  /* 0 = one block per work item, else persistent blocks */
+    float ms;      /* best of three timed passes */
+} plan_tune_entry;
+
+/* Pick the kernel shapes plan_sweep uses for this plan: time every turn
+ * shape on a turn pass and every straight shape on a straight pass of a
+ * sweep from `start`, on the plan's own volumes, and keep the fastest of
+ * each (all shapes give the same bits).  Requires a rendered plan.  Writes
+ * up to cap entries to out (host) and their count to *n_out (NULL allowed),
+ * PLAN_ERANGE if cap was too small (the choice is still made).  Leaves V and
+ * L in an intermediate state; the next plan_sweep starts over.
+ * Synchronises. */
+int plan_autotune(plan_t* plan, plan_pose start, plan_tune_entry* out, int cap, int* n_out);
+
 /* Copy the device volumes to host buffers (any may be NULL): V (uint32),
  * L (uint16), B (uint16), Nx*Nx*N_theta entries each.  Synchronises. */
 int plan_copy_volumes(plan_t* plan, uint32_t* V, uint16_t* L, uint16_t* B);

@@ -71,6 +71,10 @@ class Allocator(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("shape", C.c_int32), ("grid", C.c_int32), ("ms", C.c_float)]
+
+
 class Segment(C.Structure):
     _fields_ = [("maneuver", C.c_int32), ("entry", Pose), ("exit", Pose), ("steps", C.c_int32),
                 ("cost", C.c_uint32)]
@@ -115,6 +119,8 @@ def lib():
         L.plan_strerror.argtypes = [C.c_int]
         L.plan_last_error.restype = C.c_char_p
         L.plan_last_error.argtypes = []
+        L.plan_autotune.restype = C.c_int
+        L.plan_autotune.argtypes = [vp, Pose, vp, C.c_int, C.POINTER(C.c_int)]
         L.plan_soft_image.restype = C.c_int
         L.plan_soft_image.argtypes = [C.c_int, vp, C.c_int, C.c_int, vp]
         _lib = L
@@ -247,6 +253,17 @@ class Planner:
         self.render()
         self.sweep(start, n_cycles)
         return self.extract(goal)
+
+    def autotune(self, start) -> List[dict]:
+        """Time the kernel shapes on this plan and keep the fastest for its
+        sweeps (plan_autotune).  Returns every timed shape."""
+        cap = 64
+        arr = (TuneEntry * cap)()
+        n = C.c_int(0)
+        _check(lib().plan_autotune(self._h, Pose(*[int(v) for v in start]), C.cast(arr, C.c_void_p), cap,
+                                   C.byref(n)), "plan_autotune")
+        return [{"kernel": "turn" if e.kind == 0 else "straight", "shape": e.shape, "grid": e.grid, "ms": e.ms}
+                for e in arr[:n.value]]
 
     # ------------------------------------------------------------ inspection
     def volumes(self, V=True, L=True, B=True):

@@ -445,7 +445,9 @@ int plan_sweep(plan_t* p, plan_pose start, int n_cycles) {
     for (int pass = 0; pass < np && rc == PLAN_OK; pass++) {
         const bool turn = pass_is_turn(pass);
         const int m = mark_begin(p, turn ? K_TURN : K_STRAIGHT);
-        rc = cuda_rc(turn ? launch_turn(gr, pass, -1, s) : launch_straight(gr, pass, 0, s));
+        Group g2 = gr;
+        g2.grid = turn ? p->turn_grid : p->straight_grid;
+        rc = cuda_rc(turn ? launch_turn(g2, pass, p->turn_variant, s) : launch_straight(g2, pass, p->straight_lines, s));
         mark_end(p, m);
         p->launches++;
     }
@@ -478,6 +480,90 @@ int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_o
         std::reverse(out, out + status[0]);  // the walk runs goal -> start
     }
     return PLAN_OK;
+}
+
+int plan_autotune(plan_t* p, plan_pose start, plan_tune_entry* out, int cap, int* n_out) {
+    if (!p || cap < 0 || (cap > 0 && !out) || !pose_ok(p, start)) return PLAN_EINVAL;
+    if (!p->volumes) return PLAN_ESTATE;
+    if (!p->rendered) return PLAN_ESTATE;
+    if (pose_hard(p, start)) return PLAN_EINVAL;
+    if (n_out) *n_out = 0;
+    // Start the sweeps (init, passes 0 and 1), then time every turn shape on
+    // pass 2 (RB, RF) and every straight shape on pass 3 (SB).  Repeating a
+    // pass changes the values; the next plan_sweep initialises again.
+    p->qd.start = cell_index(p, start);
+    p->qd.n_cycles = 1;
+    p->qd.v.improved = nullptr;
+    int rc = upload_desc(p);
+    if (rc != PLAN_OK) return rc;
+    const Group gr = p->group();
+    cudaStream_t s = p->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NHP_CK(cudaEventCreate(&e0));
+    if (const cudaError_t ee = cudaEventCreate(&e1); ee != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ee, "cudaEventCreate");
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t err = launch_init(gr, s);
+    if (err == cudaSuccess) err = launch_turn(gr, 0, -1, s);
+    if (err == cudaSuccess) err = launch_straight(gr, 1, 0, s);
+    int n = 0;
+    float best_t = 1e30f, best_s = 1e30f;
+    auto timed = [&](auto launch) -> float {
+        if (launch() != cudaSuccess) return -1.f;  // warm-up
+        float best = 1e30f;
+        for (int r = 0; r < 3; r++) {
+            cudaEventRecord(e0, s);
+            if (launch() != cudaSuccess) return -1.f;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    const int nv = turn_variants(p->nt);
+    for (int v = 0; v < nv && err == cudaSuccess; v++) {
+        int K, SL, CL;
+        turn_shape(p->lt, v, &K, &SL, &CL);
+        for (int pers = 0; pers < 2 && err == cudaSuccess; pers++) {
+            const int occ = pers ? turn_blocks_per_sm(p->lt, v) : 0;
+            const int grid = pers ? std::max(1, occ * sms / CL) : 0;
+            if (pers && occ == 0) continue;
+            Group g2 = gr;
+            g2.grid = grid;
+            const float ms = timed([&] { return launch_turn(g2, 2, v, s); });
+            if (ms < 0) { err = cudaGetLastError(); break; }
+            if (n < cap) out[n] = plan_tune_entry{0, v, grid, ms};
+            n++;
+            if (ms < best_t) { best_t = ms; p->turn_variant = v; p->turn_grid = grid; }
+        }
+    }
+    const int widths[2] = {128, 256};
+    for (int wi = 0; wi < 2 && err == cudaSuccess; wi++) {
+        const int w = widths[wi];
+        if (p->nx < w && !(wi == 0 && p->nx < 128)) continue;
+        for (int pers = 0; pers < 2 && err == cudaSuccess; pers++) {
+            const int occ = pers ? straight_blocks_per_sm(w) : 0;
+            if (pers && (occ == 0 || p->nx < 16)) continue;
+            Group g2 = gr;
+            g2.grid = pers ? occ * sms : 0;
+            const float ms = timed([&] { return launch_straight(g2, 3, w, s); });
+            if (ms < 0) { err = cudaGetLastError(); break; }
+            if (n < cap) out[n] = plan_tune_entry{1, w, g2.grid, ms};
+            n++;
+            if (ms < best_s) { best_s = ms; p->straight_lines = w; p->straight_grid = g2.grid; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "plan_autotune");
+    if (n_out) *n_out = n;
+    return n > cap ? PLAN_ERANGE : PLAN_OK;
 }
 
 int plan_copy_volumes(plan_t* p, uint32_t* V, uint16_t* L, uint16_t* B) {

@@ -45,6 +45,8 @@ struct plan_s {
     int* d_status = nullptr;
     bool rendered = false;
     bool volumes = true;  // V and L allocated (scenes of a server hold only B)
+    // kernel shapes of plan_sweep (plan_autotune; defaults until then)
+    int turn_variant = -1, turn_grid = 0, straight_lines = 0, straight_grid = 0;
     int64_t launches = 0;
     DevGrid g{};
     nhp::QueryDesc qd{};             // this plan as one query (host copy)

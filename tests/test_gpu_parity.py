@@ -171,3 +171,25 @@ def test_maze_512cubed_full_size_soft_costs():
     img = binding.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max)
     assert np.array_equal(img, O.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max))
     _full_size(sc, img)
+
+
+@pytest.mark.parametrize("case", [SMALL[4], SMALL[7], SMALL[9]], ids=["nt32", "nt128", "nt512"])
+def test_autotuned_shapes_give_the_same_bits(case):
+    """plan_autotune times every kernel shape and keeps the fastest; sweeps
+    with the chosen shapes still equal the oracle."""
+    lx, lt, R, fp, soft, half, N = case
+    sc, img = scenes.tiny(300 + lx * 16 + lt, lx, lt, fill=0.08, turn_radius=R, footprint=fp, soft=soft,
+                          half_shift=half, transition=300)
+    o = O.Oracle(lx, lt, R, half_shift=half, transition=sc.transition)
+    Bo = o.render(img, fp)
+    start = first_free(o, Bo, sc.pose_candidates)
+    Vo, Lo, _ = o.sweep(Bo, o.cell(start), N, mode=1)
+    p = planner(sc, img)
+    p.render()
+    ents = p.autotune(start)
+    assert any(e["kernel"] == "turn" for e in ents) and any(e["kernel"] == "straight" for e in ents)
+    assert all(e["ms"] > 0 for e in ents)
+    p.sweep(start, N)
+    V, L, _ = p.volumes(B=False)
+    assert np.array_equal(V, Vo) and np.array_equal(L, Lo)
+    p.close()
