@@ -106,10 +106,8 @@ class ClockSampler:
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2306_01301_b300 import replicas
+    return replicas.rank_env()
 
 
 def cpu_baseline(sc, img):
@@ -186,9 +184,10 @@ def run_ours(args):
         res = step()
     torch.cuda.synchronize()
 
+    from paper_2306_01301_b300 import replicas
+
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier(world)
 
     # ---- device-resident timing (image already in HBM)
     clocks = ClockSampler(dev)
@@ -208,12 +207,8 @@ def run_ours(args):
     prof = p.profile_read()
     p.profile(False)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    sec = ms / 1e3
-    value = updates * args.steps * world / sec
+    # every rank plans its own replica: units of all ranks over the slowest rank's time
+    value, _, sec = replicas.job_rate(updates * args.steps, ms / 1e3, world, device="cuda")
 
     # ---- end to end through the C ABI: host image in, host plan out
     pinned = torch.from_numpy(img).pin_memory()
@@ -229,10 +224,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks(e2e_s, world, device="cuda")
     h2d = img.nbytes
     d2h = 8 + 36 * nseg
 
@@ -244,7 +236,7 @@ def run_ours(args):
     straight_bytes = sc.cells * 6 + 6 * prof["straight_improved"] / max(1, prof["straight_passes"])
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": "512x512x512", "n_cycles": N, "vehicle_cells": "96x38",
                    "turn_radius_cells": sc.turn_radius, "gear_cost": sc.transition,
@@ -268,6 +260,8 @@ def run_ours(args):
         "clocks": clk,
     }
     p.close()
+    if world == 1 and not args.no_maze:
+        line["maze"] = run_maze(args, torch)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, torch)
     if world == 1 and not args.no_served:
@@ -278,6 +272,35 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_maze(args, torch):
+    """The 512^3 maze (soft obstacle costs, N = 32): whole plans timed with
+    CUDA events, render included, after autotuning the kernel shapes."""
+    from paper_2306_01301_b300 import binding, scenes
+    sc = scenes.maze()
+    stream = torch.cuda.current_stream()
+    p = binding.Planner.from_scene(sc, stream=stream)
+    p.render()
+    p.autotune(sc.start)
+    for _ in range(max(3, args.warmup)):
+        p.plan(sc.start, sc.goal, sc.n_cycles)
+    steps = max(3, args.maze_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        p.render()
+        p.sweep(sc.start, sc.n_cycles)
+        res = p.extract(sc.goal)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    p.close()
+    updates = 6 * sc.n_cycles * sc.cells
+    return {"workload": "maze_512x512x512_N32_soft", "ms_per_plan": ms, "plans_per_s": 1e3 / ms,
+            "updates_per_s": updates / (ms / 1e3), "plan_cost": res.cost if res else None,
+            "plan_maneuvers": len(res.segments) if res else 0, "steps": steps}
 
 
 def run_batched(args, torch):
@@ -425,6 +448,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-maze", action="store_true")
+    ap.add_argument("--maze-steps", type=int, default=5)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=60.0)
