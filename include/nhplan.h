@@ -166,6 +166,14 @@ typedef struct {
  * Synchronises. */
 int plan_autotune(plan_t* plan, plan_pose start, plan_tune_entry* out, int cap, int* n_out);
 
+/* Fix the kernel shapes plan_sweep uses (as plan_autotune would): turn
+ * variant (-1 = default, else an index below the number of shapes for
+ * N_theta), turn grid in work-item slots (0 = one block per item), straight
+ * lines per block (0 = default, 128 or 256) and straight grid in blocks.  Every
+ * shape gives the same bits.  PLAN_EINVAL for values out of range. */
+int plan_set_kernel_shapes(plan_t* plan, int turn_variant, int turn_grid, int straight_lines,
+                           int straight_grid);
+
 /* Copy the device volumes to host buffers (any may be NULL): V (uint32),
  * L (uint16), B (uint16), Nx*Nx*N_theta entries each.  Synchronises. */
 int plan_copy_volumes(plan_t* plan, uint32_t* V, uint16_t* L, uint16_t* B);

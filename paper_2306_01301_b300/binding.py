@@ -119,6 +119,8 @@ def lib():
         L.plan_strerror.argtypes = [C.c_int]
         L.plan_last_error.restype = C.c_char_p
         L.plan_last_error.argtypes = []
+        L.plan_set_kernel_shapes.restype = C.c_int
+        L.plan_set_kernel_shapes.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.plan_autotune.restype = C.c_int
         L.plan_autotune.argtypes = [vp, Pose, vp, C.c_int, C.POINTER(C.c_int)]
         L.plan_soft_image.restype = C.c_int
@@ -253,6 +255,11 @@ class Planner:
         self.render()
         self.sweep(start, n_cycles)
         return self.extract(goal)
+
+    def set_kernel_shapes(self, turn_variant: int = -1, turn_grid: int = 0, straight_lines: int = 0,
+                          straight_grid: int = 0):
+        _check(lib().plan_set_kernel_shapes(self._h, int(turn_variant), int(turn_grid), int(straight_lines),
+                                            int(straight_grid)), "plan_set_kernel_shapes")
 
     def autotune(self, start) -> List[dict]:
         """Time the kernel shapes on this plan and keep the fastest for its

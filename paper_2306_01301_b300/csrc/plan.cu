@@ -482,6 +482,17 @@ int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_o
     return PLAN_OK;
 }
 
+int plan_set_kernel_shapes(plan_t* p, int turn_variant, int turn_grid, int straight_lines, int straight_grid) {
+    if (!p || turn_variant < -1 || turn_variant >= turn_variants(p->nt) || turn_grid < 0 || straight_grid < 0 ||
+        (straight_lines != 0 && straight_lines != 128 && straight_lines != 256))
+        return PLAN_EINVAL;
+    p->turn_variant = turn_variant;
+    p->turn_grid = turn_grid;
+    p->straight_lines = straight_lines;
+    p->straight_grid = straight_grid;
+    return PLAN_OK;
+}
+
 int plan_autotune(plan_t* p, plan_pose start, plan_tune_entry* out, int cap, int* n_out) {
     if (!p || cap < 0 || (cap > 0 && !out) || !pose_ok(p, start)) return PLAN_EINVAL;
     if (!p->volumes) return PLAN_ESTATE;

@@ -193,3 +193,28 @@ def test_autotuned_shapes_give_the_same_bits(case):
     V, L, _ = p.volumes(B=False)
     assert np.array_equal(V, Vo) and np.array_equal(L, Lo)
     p.close()
+
+
+SHAPES = [(v, g, sl, sg) for v in range(3) for g in (0, 37) for (sl, sg) in ((0, 0), (128, 29))]
+
+
+@pytest.mark.parametrize("lx,lt", [(6, 7), (7, 8), (6, 9)], ids=["64x128", "128x256", "64x512"])
+def test_every_kernel_shape_gives_the_same_bits(lx, lt):
+    """Every turn variant (K, warps, cluster), one block per item or a
+    persistent grid smaller than the work, and both straight widths:
+    identical V and L, equal to the oracle."""
+    R = 0.9 * (1 << lx) / 8
+    sc, img = scenes.tiny(40 + lx + lt, lx, lt, fill=0.03, turn_radius=R, footprint=(3, 1, 1), soft=True,
+                          transition=350)
+    o = O.Oracle(lx, lt, R, transition=sc.transition)
+    Bo = o.render(img, sc.footprint) if lx <= 6 else o.render_rows(img, sc.footprint)
+    start = first_free(o, Bo, sc.pose_candidates)
+    Vo, Lo, _ = o.sweep(Bo, o.cell(start), 2, mode=1)
+    p = planner(sc, img)
+    p.render()
+    for (v, g, sl, sg) in SHAPES:
+        p.set_kernel_shapes(v, g, sl, sg)
+        p.sweep(start, 2)
+        V, L, _ = p.volumes(B=False)
+        assert np.array_equal(V, Vo) and np.array_equal(L, Lo), (v, g, sl, sg)
+    p.close()
