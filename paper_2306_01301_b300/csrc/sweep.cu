@@ -92,9 +92,11 @@ __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t
 template <int K, int SL, int NSLOT>
 struct TurnShared {
     static constexpr int P = 32 + 32 / SL;  // pitch: the carry scan's reads hit 32 banks
-    uint32_t sa[SL][P];
-    uint32_t sb[SL][P];
-    int32_t sp[SL][P];
+    // two sets, used by alternate scans: a warp may start the next scan
+    // while a slower one still reads the previous scan's carries
+    uint32_t sa[2][SL][P];
+    uint32_t sb[2][SL][P];
+    int32_t sp[2][SL][P];
     uint32_t tot[NSLOT][3][32];             // per scan: this block's composite (A, B, P)
     uint16_t lab[K][32 * SL];               // labels of improved cells
 };
@@ -121,7 +123,7 @@ __device__ __forceinline__ void combine(uint32_t xa, uint32_t xb, int xp, uint32
 // results are the same cell for cell.
 template <int K, int SL, int CL, int NSLOT, bool ASC>
 __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t& chg, int mu,
-                                          uint32_t ct, int sec, int lane, int rank, int slot, uint32_t a,
+                                          uint32_t ct, int sec, int lane, int rank, int slot, int mb, uint32_t a,
                                           bool live, TurnShared<K, SL, NSLOT>& sm) {
     constexpr int S = SL * CL, NT = K * S;
     const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);  // this block's place in scan order
@@ -142,9 +144,9 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
             b += e[k];
         }
     }
-    sm.sa[sl][lane] = a;
-    sm.sb[sl][lane] = b;
-    sm.sp[sl][lane] = pb;
+    sm.sa[mb][sl][lane] = a;
+    sm.sb[mb][sl][lane] = b;
+    sm.sp[mb][sl][lane] = pb;
     __syncthreads();
     // 2) segmented warp scan over the SL local section maps of each chain
     //    (32/SL chains per warp), then the carry into each section of the
@@ -152,8 +154,8 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
     {
         const int c = sec * (32 / SL) + lane / SL;
         const int s = lane % SL;
-        uint32_t A = sm.sa[s][c], B = sm.sb[s][c];
-        int P = sm.sp[s][c];
+        uint32_t A = sm.sa[mb][s][c], B = sm.sb[mb][s][c];
+        int P = sm.sp[mb][s][c];
 #pragma unroll
         for (int off = 1; off < SL; off <<= 1) {
             const uint32_t xa = __shfl_up_sync(0xFFFFFFFFu, A, off, SL);
@@ -224,13 +226,13 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
             else { iv = eB; ip = eP + NT; }
         }
         __syncwarp();
-        sm.sb[s][c] = iv;
-        sm.sp[s][c] = ip;
+        sm.sb[mb][s][c] = iv;
+        sm.sp[mb][s][c] = ip;
     }
     __syncthreads();
     // 3) second loop: store where strictly better.
-    const uint32_t v0 = sm.sb[sl][lane];
-    const int p0 = sm.sp[sl][lane];
+    const uint32_t v0 = sm.sb[mb][sl][lane];
+    const int p0 = sm.sp[mb][sl][lane];
     // Lean pass: the carried value alone, and whether any cell improves.
     // Improvements are rare once the front has passed, so the pass that also
     // tracks entry positions and writes labels runs only in warps that need it.
@@ -264,7 +266,11 @@ __device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[
             v += e[k];
         }
     }
-    __syncthreads();  // the section arrays are reused by the next scan
+    // Without a cluster the next scan uses the other set of section maps,
+    // and every warp passes this scan's two barriers before any warp can
+    // reach the scan after next: no barrier here.  Cluster partners read
+    // the exchange slots remotely, so clusters keep one.
+    if (CL > 1) __syncthreads();
 }
 
 // Largest q with off[q] <= item (off[0] = 0, strictly increasing).
@@ -279,9 +285,10 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq
 }
 
 // One 32-chain tile of one query: load, scan (one or two maneuvers), store.
+// `scans` counts the block's scans so far (it picks the set of section maps).
 template <int K, int SL, int CL>
 __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int64_t tile, int rank,
-                                          TurnSmem<K, SL, CL>& sm) {
+                                          TurnSmem<K, SL, CL>& sm, int& scans) {
     constexpr int NTL = K * SL;  // headings held by this block
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
     const DevGrid g = Q.g;
@@ -294,8 +301,11 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
     const int xq = (int)(chain & g.mx), yq = (int)((chain >> g.lx) & g.mx);
     // With Nx >= 32 all 32 chains of the block share y', so each heading's
     // chain row has one offset: precompute (row offset, x shift) per heading.
+    // A warp reads only the entries of its own headings, so it writes them
+    // itself and no block barrier is needed.
     const bool row_uniform = g.nx >= 32;
-    for (int t = tid; t < NTL; t += 32 * SL) {
+    if (lane < K) {
+        const int t = sec * K + lane;
         const int4 b = g.beta4[T0 + t];
         const int bx = family ? b.z : b.x, by = family ? b.w : b.y;
         const int ybase = row_uniform ? (int)((tile * 32 >> g.lx) & g.mx) : 0;
@@ -305,7 +315,7 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         else
             sm.cell[t] = make_int2((int)(uint32_t)((int64_t)(T0 + t) * nxy), (bx & g.mx) | ((by & g.mx) << 16));
     }
-    __syncthreads();
+    __syncwarp();
     const uint32_t w = g.wA, ct = g.ct;
     auto cell_index = [&](int T) -> uint32_t {
         const int2 c = sm.cell[T];
@@ -332,12 +342,16 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         live |= ob != HARD && vv < TH;
     }
     uint32_t chg = 0;
-    if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm.sh);
-    else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct, sec, lane, rank, 0, a, live, sm.sh);
+    int mb = scans & 1;
+    if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct, sec, lane, rank, 0, mb, a, live, sm.sh);
+    else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct, sec, lane, rank, 0, mb, a, live, sm.sh);
+    scans++;
     if (mu2 >= 0) {
         live = live || chg != 0;
-        if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm.sh);
-        else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, a, live, sm.sh);
+        mb = scans & 1;
+        if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, mb, a, live, sm.sh);
+        else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, mb, a, live, sm.sh);
+        scans++;
     }
     if (vol.improved) {
         count_improved(vol.improved, __popc(chg));
@@ -366,6 +380,7 @@ k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, i
     __shared__ TurnSmem<K, SL, CL> sm;
     const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
     const int64_t stride = gridDim.x / CL;
+    int scans = 0;
     for (int64_t it = blockIdx.x / CL; it < items; it += stride) {
         int q;
         int64_t tile;
@@ -379,11 +394,12 @@ k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, i
         const QueryDesc& Q = qd[q];
         const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
         if (!ps.active || !ps.turn) continue;  // uniform over the block and the cluster
-        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm);
+        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm, scans);
         // the partner blocks read this block's shared memory, and the next
-        // item rewrites it: leave the tile together
+        // item rewrites it: a cluster leaves the tile together.  Without a
+        // cluster the next tile needs no barrier (own row entries, per-thread
+        // labels, alternating section maps).
         if (CL > 1) cooperative_groups::this_cluster().sync();
-        else if (it + stride < items) __syncthreads();
     }
 }
 
