@@ -172,7 +172,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     p = binding.Planner.from_scene(sc, img, stream=stream)
     p.render()
-    tuning = p.autotune(sc.start)  # kernel shapes for this plan, outside the timed region
+    if args.shapes:
+        # pinned kernel shapes (profiling runs: timing-based tuning under a profiler picks differently)
+        tv, tg, sl, sg = (int(x) for x in args.shapes.split(","))
+        p.set_kernel_shapes(tv, tg, sl, sg)
+        tuning = [{"kernel": "turn", "shape": tv, "grid": tg, "ms": 0.0, "pinned": True},
+                  {"kernel": "straight", "shape": sl, "grid": sg, "ms": 0.0, "pinned": True}]
+    else:
+        tuning = p.autotune(sc.start)  # kernel shapes for this plan, outside the timed region
 
     def step():
         p.render()
@@ -449,6 +456,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-maze", action="store_true")
+    ap.add_argument("--shapes", default="", help="pin turn variant,turn grid,straight lines,straight grid "
+                                                   "instead of autotuning (e.g. 0,148,256,0)")
     ap.add_argument("--maze-steps", type=int, default=5)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-served", action="store_true")
