@@ -17,6 +17,8 @@ computes:
   maneuvers with cost c (100 per cell of length plus a sufficient transition
   cost per maneuver), some graph vertex within 7 + pi d / N_theta cells in x
   and y and 4 headings of its end has value at most c after enough cycles.
+  The same holds for the shortest paths themselves, the Reeds-Shepp and
+  Dubins closed forms (Theorems 2-3) written in tests/curves.py.
 """
 import math
 
@@ -197,3 +199,76 @@ def test_sufficient_transition_cost_criterion():
         p = drive(p, LB, a)
         p = drive(p, RB, a)
         assert abs(p[2]) < 1e-12 and abs(p[1] - 4 * R * (1 - math.cos(a))) < 1e-9
+
+
+def _matched_by_graph(Vg, half, x, y, th, c):
+    """Theorem 7's box: some vertex within 7 + pi d / N_theta cells in x and
+    y and 4 headings of (x, y, th) with value <= c (d = c / 100 cells)."""
+    bound = 7 + math.pi * (c / 100) / NT
+    T = th * NT / (2 * math.pi)
+    for dT in range(-4, 5):
+        Tc = int(round(T)) + dT
+        if abs(Tc - T) > 4:
+            continue
+        Tm = Tc % NT
+        for j in range(max(1, math.ceil(y - bound - 0.5)), min(NX - 1, math.floor(y + bound)) + 1):
+            for i in range(max(1, math.ceil(x - bound - 0.5)), min(NX - 1, math.floor(x + bound)) + 1):
+                vx, vy, _ = vertex_pose((i, j, Tm), half)
+                if abs(vx - x) <= bound and abs(vy - y) <= bound and Vg[Tm, j, i] <= c:
+                    return True
+    return False
+
+
+@pytest.fixture(scope="module")
+def five_cycles(free_world):
+    """Five cycles cover any order of up to five maneuvers (Reeds-Shepp words)."""
+    o, half = free_world["o"], free_world["half"]
+    V, _, _ = o.sweep(free_world["B"], o.cell(free_world["start"]), 5, mode=1)
+    return V.reshape(NT, NX, NX), half
+
+
+@pytest.mark.parametrize("family", ["reeds_shepp", "dubins"])
+def test_shortest_continuum_paths_are_matched_by_the_graph(free_world, five_cycles, family):
+    """Theorem 7 on the shortest paths themselves: the Reeds-Shepp (Theorem 3)
+    and Dubins (Theorem 2) closed-form paths to random goals, with one
+    transition cost per maneuver, are matched by the graph within the bound."""
+    from tests import curves
+    Vg, half = five_cycles
+    q0 = vertex_pose(free_world["start"], half)
+    rng = np.random.default_rng(23 if family == "reeds_shepp" else 29)
+    checked = 0
+    for _ in range(150 if family == "reeds_shepp" else 400):
+        q1 = (float(rng.uniform(10, NX - 10)), float(rng.uniform(10, NX - 10)), float(rng.uniform(0, 2 * math.pi)))
+        path = curves.reeds_shepp_path(q0, q1, R) if family == "reeds_shepp" else curves.dubins_path(q0, q1, R)
+        end = curves.drive(q0, path, R)
+        assert abs(end[0] - q1[0]) < 1e-6 and abs(end[1] - q1[1]) < 1e-6
+        c = 100 * curves.length(path) + CT * max(1, curves.maneuvers(path))
+        if c > 100 * 60:
+            continue  # long detours leave the grid
+        assert _matched_by_graph(Vg, half, q1[0], q1[1], q1[2] % (2 * math.pi), c), (family, q1, path, c)
+        checked += 1
+    assert checked > 60  # forward-only paths often turn around: more samples for Dubins
+
+
+def test_closed_forms_are_shortest():
+    """The Reeds-Shepp construction used above: every candidate word reaches
+    its goal, no random path of up to five segments is shorter, it is
+    symmetric, and it is never longer than the forward-only Dubins path."""
+    from tests import curves
+    rng = np.random.default_rng(3)
+    for _ in range(3000):
+        m = int(rng.integers(1, 6))
+        path = []
+        for _k in range(m):
+            kind = "LRS"[int(rng.integers(0, 3))]
+            path.append((kind, float(rng.uniform(-3, 3) if kind == "S" else rng.uniform(-math.pi, math.pi))))
+        end = curves.drive((0.0, 0.0, 0.0), path, 1.0)
+        rs = curves.reeds_shepp_path((0.0, 0.0, 0.0), end, 1.0)
+        e2 = curves.drive((0.0, 0.0, 0.0), rs, 1.0)
+        assert abs(e2[0] - end[0]) < 1e-6 and abs(e2[1] - end[1]) < 1e-6
+        assert abs(curves.mod2pi(e2[2] - end[2])) < 1e-6
+        assert curves.length(rs) <= curves.length(path) + 1e-7
+        back = curves.reeds_shepp_path(end, (0.0, 0.0, 0.0), 1.0)
+        assert abs(curves.length(back) - curves.length(rs)) < 1e-7
+        db = curves.dubins_path((0.0, 0.0, 0.0), end, 1.0)
+        assert curves.length(rs) <= curves.length(db) + 1e-7
