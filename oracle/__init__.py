@@ -80,6 +80,10 @@ def lib():
         L.orc_extract.restype = C.c_int
         L.orc_extract.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         L.orc_soft_image.argtypes = [C.c_int, p, C.c_int, C.c_int, p]
+        L.orc_reach.restype = C.c_int
+        L.orc_reach.argtypes = [p, p, C.c_int64, C.c_int, p]
+        L.orc_reach_extract.restype = C.c_int
+        L.orc_reach_extract.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         _lib = L
     return _lib
 
@@ -215,6 +219,26 @@ class Oracle:
             raise ValueError(f"extract failed ({n})")
         return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3]),
                      cost=int(r[4]) | (int(r[5]) << 16)) for r in seg[:n]]
+
+
+    # ------------------------------------------- Appendix C reachability
+    def reach(self, B: np.ndarray, start: int, n_cycles: int) -> np.ndarray:
+        """Fewest maneuvers to every pose (255 beyond n_cycles)."""
+        count = np.zeros(self.nr, np.uint8)
+        if lib().orc_reach(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start), int(n_cycles),
+                           _ptr(count)) != 0:
+            raise ValueError("reach failed")
+        return count
+
+    def reach_extract(self, B: np.ndarray, count: np.ndarray, goal: int, cap: int = 256):
+        seg = np.zeros((cap, 4), np.int64)
+        n = lib().orc_reach_extract(self._c, _ptr(np.ascontiguousarray(B, np.uint16)),
+                                    _ptr(np.ascontiguousarray(count, np.uint8)), int(goal), _ptr(seg), cap)
+        if n == -1:
+            return None
+        if n < 0:
+            raise ValueError(f"reach_extract failed ({n})")
+        return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3])) for r in seg[:n]]
 
 
 def soft_image(occupancy: np.ndarray, radius: int, soft_max: int) -> np.ndarray:

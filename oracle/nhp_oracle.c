@@ -767,3 +767,87 @@ void orc_soft_image(int nx, const uint8_t* occ, int radius, int soft_max, uint16
             img[(size_t)y * nx + x] = (uint16_t)(256 + pen);
         }
 }
+
+/* ------------------------------------------------------------------------
+ * Maneuver-count reachability (Appendix C, Insert 2): hard obstacles only,
+ * every maneuver edge free, every transition one maneuver.  reach_m is the
+ * set of poses reachable from the start with at most m maneuvers; a cycle
+ * takes every maneuver from reach_m at once (each of the six maneuver
+ * kernels reads the previous cycle's reachability and the results are
+ * combined), so reach_{m+1} = reach_m united with, for every maneuver,
+ * the cells that follow a cell of reach_m along that maneuver's curve
+ * without meeting a hard cell.  A curve is followed for at most one period
+ * (N_theta steps for turns, Nx for straights, which meet the wall earlier).
+ * count[x] = the smallest m with x in reach_m, 255 if none up to N.
+ */
+int orc_reach(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint8_t* count) {
+    if (!c || !B || !count || start < 0 || start >= c->nr || n_cycles < 0 || n_cycles > 254) return -1;
+    if (B[start] == ORC_HARD) return -1;
+    for (int64_t x = 0; x < c->nr; x++) count[x] = 255;
+    count[start] = 0;
+    for (int m = 0; m < n_cycles; m++) {
+        for (int mu = 0; mu < 6; mu++) {
+            const int period = is_turn(mu) ? c->nt : c->nx;
+            for (int64_t x = 0; x < c->nr; x++) {
+                if (count[x] > m || B[x] == ORC_HARD) continue; /* entries: reach_m */
+                int64_t y = x;
+                for (int k = 1; k < period; k++) {
+                    y = orc_succ(c, mu, y);
+                    if (B[y] == ORC_HARD) break;
+                    /* a cell of reach_m starts its own walk; everything beyond
+                     * it is covered there (it is an entry of the same curve) */
+                    if (count[y] <= m) break;
+                    if (count[y] > m + 1) count[y] = (uint8_t)(m + 1);
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* Back-track a minimal maneuver sequence to `goal` (the paper does this on
+ * the host from the kept reachability volumes).  Canonical choice, also used
+ * by the library: at each level, the first maneuver in cycle order (LF, SF,
+ * RB, RF, SB, LB) whose curve, walked upstream from the current cell without
+ * meeting a hard cell, reaches a cell of the previous level; the nearest such
+ * cell is the segment's entry.  Writes seg[k*4 + {mu, entry, exit, steps}] in
+ * driving order.  Returns the number of segments, -1 if the goal is not
+ * reachable within the counts, -2 if cap is too small, -3 if the counts are
+ * inconsistent. */
+int orc_reach_extract(const orc_ctx* c, const uint16_t* B, const uint8_t* count, int64_t goal,
+                      int64_t* seg, int cap) {
+    if (!c || !B || !count || goal < 0 || goal >= c->nr) return -3;
+    if (count[goal] == 255) return -1;
+    int n = 0;
+    int64_t x = goal;
+    for (int m = count[goal]; m > 0; m--) {
+        int found = 0;
+        for (int mu = 0; mu < 6 && !found; mu++) {
+            const int period = is_turn(mu) ? c->nt : c->nx;
+            int64_t y = x;
+            for (int d = 1; d < period; d++) {
+                y = orc_succ(c, 5 - mu, y); /* the reverse maneuver walks the curve upstream */
+                if (B[y] == ORC_HARD) break;
+                if (count[y] <= m - 1) {
+                    if (n < cap) {
+                        int64_t* r = seg + 4 * (size_t)n;
+                        r[0] = mu; r[1] = y; r[2] = x; r[3] = d;
+                    }
+                    n++;
+                    x = y;
+                    found = 1;
+                    break;
+                }
+            }
+        }
+        if (!found) return -3;
+    }
+    if (n > cap) return -2;
+    for (int a = 0, b = n - 1; a < b; a++, b--)
+        for (int k = 0; k < 4; k++) {
+            int64_t t = seg[4 * a + k];
+            seg[4 * a + k] = seg[4 * b + k];
+            seg[4 * b + k] = t;
+        }
+    return n;
+}

@@ -86,6 +86,18 @@ int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cyc
 int orc_extract(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal,
                 int64_t* seg, int cap);
 
+/* Maneuver-count reachability (Appendix C, Insert 2): count[x] = fewest
+ * maneuvers from start to x over hard obstacles only, every maneuver of a
+ * cycle taken from the previous cycle's reachable set; 255 if more than
+ * n_cycles.  Returns 0, or -1 for bad arguments / a hard start. */
+int orc_reach(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint8_t* count);
+
+/* Canonical back-track of a fewest-maneuver sequence to goal (driving
+ * order, seg[k*4 + {mu, entry, exit, steps}]).  Returns the segment count,
+ * -1 unreachable, -2 cap too small, -3 inconsistent counts. */
+int orc_reach_extract(const orc_ctx* c, const uint16_t* B, const uint8_t* count, int64_t goal,
+                      int64_t* seg, int cap);
+
 /* Soft-obstacle image (Section VII): HARD where occ != 0, else 256 + pen with
  * pen = soft_max*(r2-d2)/r2 for squared Euclidean distance d2 < r2 to the
  * nearest occupied cell, else 256. */
