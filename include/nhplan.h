@@ -174,6 +174,29 @@ int plan_autotune(plan_t* plan, plan_pose start, plan_tune_entry* out, int cap, 
 int plan_set_kernel_shapes(plan_t* plan, int turn_variant, int turn_grid, int straight_lines,
                            int straight_grid);
 
+/* Appendix C: fewest maneuvers with hard obstacles only, one bit per pose.
+ * Requires a rendered plan (the hard poses of its obstacle volume are the
+ * obstacles; soft costs are ignored), 64 <= Nx <= 512 and 32 <= N_theta <= 512,
+ * a non-hard start (PLAN_EINVAL) and 0 <= n_cycles <= 254.  Cycle m + 1
+ * takes every maneuver from the poses reachable within m maneuvers (every
+ * maneuver edge free, every transition one maneuver), so after n_cycles the
+ * plan holds, per pose, whether it is reachable within m maneuvers for m = 0
+ * .. n_cycles (n_cycles + 1 bits per pose, plus 4 scratch bits per pose).
+ * Does not touch V or L.  Async. */
+int plan_reach_sweep(plan_t* plan, plan_pose start, int n_cycles);
+
+/* Back-track a fewest-maneuver plan to goal after plan_reach_sweep: at each
+ * level the first maneuver in cycle order (LF, SF, RB, RF, SB, LB) whose
+ * curve reaches back, without a hard pose, to a pose of the previous level,
+ * from its nearest such pose.  Segments in driving order (cost = maneuvers
+ * up to the segment's exit), *maneuvers = the fewest maneuvers.
+ * PLAN_EUNREACHABLE if the goal needs more than n_cycles.  Synchronises. */
+int plan_reach_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out, int* maneuvers);
+
+/* Fewest maneuvers of every pose after plan_reach_sweep (host, Nx*Nx*N_theta
+ * bytes; 255 where more than n_cycles).  Synchronises. */
+int plan_reach_counts(plan_t* plan, uint8_t* counts);
+
 /* Copy the device volumes to host buffers (any may be NULL): V (uint32),
  * L (uint16), B (uint16), Nx*Nx*N_theta entries each.  Synchronises. */
 int plan_copy_volumes(plan_t* plan, uint32_t* V, uint16_t* L, uint16_t* B);

@@ -119,6 +119,13 @@ def lib():
         L.plan_strerror.argtypes = [C.c_int]
         L.plan_last_error.restype = C.c_char_p
         L.plan_last_error.argtypes = []
+        L.plan_reach_sweep.restype = C.c_int
+        L.plan_reach_sweep.argtypes = [vp, Pose, C.c_int]
+        L.plan_reach_extract.restype = C.c_int
+        L.plan_reach_extract.argtypes = [vp, Pose, C.POINTER(Segment), C.c_int, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int)]
+        L.plan_reach_counts.restype = C.c_int
+        L.plan_reach_counts.argtypes = [vp, vp]
         L.plan_set_kernel_shapes.restype = C.c_int
         L.plan_set_kernel_shapes.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.plan_autotune.restype = C.c_int
@@ -255,6 +262,27 @@ class Planner:
         self.render()
         self.sweep(start, n_cycles)
         return self.extract(goal)
+
+    # ------------------------------------------------ Appendix C reachability
+    def reach_sweep(self, start, n_cycles: int):
+        """Fewest-maneuver reachability over hard obstacles (bit vectors)."""
+        _check(lib().plan_reach_sweep(self._h, Pose(*[int(v) for v in start]), int(n_cycles)), "plan_reach_sweep")
+
+    def reach_extract(self, goal, cap: int = 256):
+        """(fewest maneuvers, segments in driving order), or None if the goal
+        needs more maneuvers than were swept."""
+        segs = (Segment * cap)()
+        n, m = C.c_int(0), C.c_int(0)
+        rc = lib().plan_reach_extract(self._h, Pose(*[int(v) for v in goal]), segs, cap, C.byref(n), C.byref(m))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_reach_extract")
+        return int(m.value), _segments(segs, n.value)
+
+    def reach_counts(self) -> np.ndarray:
+        out = np.empty(self.cells, np.uint8)
+        _check(lib().plan_reach_counts(self._h, _ptr(out)), "plan_reach_counts")
+        return out
 
     def set_kernel_shapes(self, turn_variant: int = -1, turn_grid: int = 0, straight_lines: int = 0,
                           straight_grid: int = 0):

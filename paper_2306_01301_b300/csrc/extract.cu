@@ -86,7 +86,96 @@ __global__ void k_extract(const QueryDesc* __restrict__ qd) {
     status[0] = vol.V[x] == 0 ? n : -3;
 }
 
+// Back-track of the bit-vector reachability (Appendix C): the fewest
+// maneuvers m* to the goal is the first volume R_m whose goal bit is 0; then,
+// level by level, the first maneuver in cycle order whose curve, walked
+// upstream from the current cell without meeting a hard cell, reaches a cell
+// of R_{m-1}, at its nearest such cell.  Warp mu scans maneuver mu 32 steps
+// at a time (ballots find the first hard and the first reachable cell).
+__device__ __forceinline__ bool bit_of(const uint32_t* v, int64_t c) { return (v[c >> 5] >> (c & 31)) & 1u; }
+
+__global__ void k_reach_extract(const DevGrid g, const uint32_t* __restrict__ R, int n, int64_t words,
+                                const uint32_t* __restrict__ H, int64_t goal, plan_segment* __restrict__ seg,
+                                int cap, int32_t* __restrict__ status) {
+    __shared__ int found_d[6];
+    __shared__ int64_t found_e[6];
+    __shared__ int64_t cur;
+    __shared__ int mstar;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mstar = -1;
+        for (int m = 0; m <= n; m++)
+            if (!bit_of(R + (int64_t)m * words, goal)) { mstar = m; break; }
+        cur = goal;
+        status[1] = mstar;
+    }
+    __syncthreads();
+    if (mstar < 0) {
+        if (threadIdx.x == 0) status[0] = -1;
+        return;
+    }
+    int nseg = 0;
+    for (int m = mstar; m > 0; m--) {
+        const int mu = warp;  // six warps, one per maneuver
+        const int period = (mu == SF || mu == SB) ? g.nx : g.nt;
+        const uint32_t* prev = R + (int64_t)(m - 1) * words;
+        int d_found = 0;
+        int64_t e_found = -1;
+        for (int base = 0; base < period - 1; base += 32) {
+            const int d = base + lane + 1;
+            const bool ok = d < period;
+            const int64_t e = ok ? entry_cell(g, cur, mu, d) : 0;
+            const uint32_t hard = __ballot_sync(0xFFFFFFFFu, ok && bit_of(H, e));
+            const uint32_t reach = __ballot_sync(0xFFFFFFFFu, ok && !bit_of(prev, e));
+            const uint32_t before_hard = hard ? ((1u << (__ffs(hard) - 1)) - 1u) : 0xFFFFFFFFu;
+            const uint32_t cand = reach & before_hard;
+            if (cand) {
+                const int t = __ffs(cand) - 1;
+                d_found = base + t + 1;
+                e_found = __shfl_sync(0xFFFFFFFFu, e, t);
+                break;
+            }
+            if (hard) break;
+        }
+        if (lane == 0) {
+            found_d[mu] = d_found;
+            found_e[mu] = e_found;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int pick = -1;
+            for (int k = 0; k < 6 && pick < 0; k++)
+                if (found_d[k] > 0) pick = k;
+            if (pick < 0) {
+                status[0] = -3;
+                cur = -1;
+            } else {
+                if (nseg < cap) {
+                    plan_segment sgm;
+                    sgm.maneuver = pick;
+                    sgm.entry = pose_of(g, found_e[pick]);
+                    sgm.exit = pose_of(g, cur);
+                    sgm.steps = found_d[pick];
+                    sgm.cost = (uint32_t)m;  // maneuvers up to the exit
+                    seg[nseg] = sgm;
+                }
+                cur = found_e[pick];
+            }
+        }
+        nseg++;
+        __syncthreads();
+        if (cur < 0) return;
+    }
+    if (threadIdx.x == 0) status[0] = nseg;
+}
+
 }  // namespace
+
+cudaError_t launch_reach_extract(const DevGrid& g, const uint32_t* R, int n, int64_t words, const uint32_t* H,
+                                 int64_t goal, plan_segment* seg, int cap, int32_t* status, cudaStream_t s) {
+    k_reach_extract<<<1, 192, 0, s>>>(g, R, n, words, H, goal, seg, cap, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_extract(const Group& gr, cudaStream_t s) {
     k_extract<<<(unsigned)gr.nq, 32, 0, s>>>(gr.d);

@@ -126,6 +126,19 @@ cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s
 // Label walk from each query's goal into its seg/status buffers.
 cudaError_t launch_extract(const Group& gr, cudaStream_t s);
 
+// Maneuver-count reachability with bit vectors (reach.cu, extract.cu).
+cudaError_t launch_hard_bits(const uint16_t* B, uint32_t* H, int64_t nr, cudaStream_t s);
+cudaError_t launch_reach_init(uint32_t* R, int64_t nr, int64_t start, cudaStream_t s);
+cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32_t* planes, int nplanes, int lx,
+                                 bool and_into, cudaStream_t s);
+cudaError_t launch_reach_turn(const DevGrid& g, const uint32_t* Rm, uint32_t* Rn, const uint32_t* H, int family,
+                              cudaStream_t s);
+cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const uint32_t* H, const uint32_t* RmT,
+                                  const uint32_t* HT, uint32_t* Rn, uint32_t* OT, cudaStream_t s);
+cudaError_t launch_reach_counts(const uint32_t* R, int n, int64_t nr, uint8_t* count, cudaStream_t s);
+cudaError_t launch_reach_extract(const DevGrid& g, const uint32_t* R, int n, int64_t words, const uint32_t* H,
+                                 int64_t goal, plan_segment* seg, int cap, int32_t* status, cudaStream_t s);
+
 // Rendering pieces used by the allocation-free entry point.
 cudaError_t launch_sparse_table(const Group& gr, cudaStream_t s);
 cudaError_t launch_render_table(const Group& gr, cudaStream_t s);

@@ -15,7 +15,6 @@ using namespace nhp;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kDevSegCap = 4096;
 
 void* default_alloc(size_t bytes, void*, void*) {
     void* p = nullptr;
@@ -232,6 +231,13 @@ void release(plan_s* p) {
     p->dfree(p->d_status, 16);
     p->dfree(p->d_cnt, 32);
     p->dfree(p->d_qd, sizeof(QueryDesc));
+    const size_t bits = (size_t)(p->nr / 8);
+    p->dfree(p->d_hb, bits);
+    p->dfree(p->d_hbt, bits);
+    p->dfree(p->d_rt, bits);
+    p->dfree(p->d_ot, bits);
+    p->dfree(p->d_shallow, sizeof(int32_t) * (size_t)p->nt);
+    p->dfree(p->d_reach, bits * (size_t)p->reach_cap);
     for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : p->spare) cudaEventDestroy(e);
     p->marks.clear();

@@ -45,6 +45,18 @@ struct plan_s {
     int* d_status = nullptr;
     bool rendered = false;
     bool volumes = true;  // V and L allocated (scenes of a server hold only B)
+    // maneuver-count reachability (Appendix C): hard bits, their transposed
+    // shallow planes, scratch for transposed reachability and output, the
+    // reachability volumes R_0 .. R_N and the list of shallow planes
+    uint32_t* d_hb = nullptr;
+    uint32_t* d_hbt = nullptr;
+    uint32_t* d_rt = nullptr;
+    uint32_t* d_ot = nullptr;
+    uint32_t* d_reach = nullptr;
+    int32_t* d_shallow = nullptr;
+    std::vector<int32_t> shallow;
+    int n_shallow = 0, reach_cap = 0, reach_n = 0;
+    bool reach_ready = false;
     // kernel shapes of plan_sweep (plan_autotune; defaults until then)
     int turn_variant = -1, turn_grid = 0, straight_lines = 0, straight_grid = 0;
     int64_t launches = 0;
@@ -67,6 +79,8 @@ struct plan_s {
 };
 
 namespace nhp {
+// Segments the device label walk can hold for one plan.
+constexpr int kDevSegCap = 4096;
 int cuda_rc(cudaError_t e);
 // Record a failed CUDA call (plan_last_error) and return PLAN_ECUDA.
 int cuda_fail(cudaError_t e, const char* where);

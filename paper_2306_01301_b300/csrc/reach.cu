@@ -1,0 +1,451 @@
+// reach.cu -- maneuver-count reachability with bit vectors (Appendix C).
+//
+// With hard obstacles only and every maneuver edge free, the value of a pose
+// is the fewest maneuvers that reach it, and one bit per pose says whether
+// it is reachable within m maneuvers.  Bits are packed 32 poses per word
+// along x (the volumes' own order), 0 = reachable as in Insert 2.  A cycle
+// takes every maneuver from the previous cycle's reachability R_m: along a
+// maneuver curve, v = (v & R_m) | H turns reachability on at reachable poses
+// and off at hard ones (H = hard bit), and every pose the curve reaches is
+// combined by AND into R_{m+1} (which starts as R_m).
+//
+// A 32-bit word carries 32 neighbouring curves (chains x' .. x'+31 of one
+// row): the curves of a word meet the volume at a bit offset that changes
+// with the heading (turns, eq. 18) or the step (straights, eq. 23), so a
+// warp holds whole rows of words and realigns them with shuffles and funnel
+// shifts -- every load and store is an aligned word, and no word is written
+// by two threads.  Each curve is cut into sections (Appendix D, Inserts
+// 6-8): a section's effect on what enters it is v -> (v | D) & S with D the
+// OR of its hard bits and S what leaves it when nothing enters, these maps
+// are rippled across the sections in shared memory (twice around for the
+// cyclic turns, once for the straights, which start at the wall), and the
+// sections are then swept with the rippled value coming in.  Straight lines
+// of shallow planes (|tan theta| <= 1, eq. 19) run along x with one pose per
+// row, so those planes are swept through bit-transposed copies, where they
+// look like steep ones.
+#include <algorithm>
+
+#include "plan_state.h"
+
+namespace nhp {
+namespace {
+
+__device__ __forceinline__ uint32_t rd(const uint32_t* p) { return __ldg(p); }
+
+// Bits of the word of chains [32l, 32l+32) of a row whose cells start at bit
+// offset s of the volume row held (one aligned word per lane) in `w`; the W
+// lanes of a row form one shuffle group.
+__device__ __forceinline__ uint32_t gather_bits(uint32_t w, int l, int s, int W) {
+    const int q = s >> 5, r = s & 31;
+    const uint32_t a = __shfl_sync(0xFFFFFFFFu, w, (l + q) & (W - 1), W);
+    const uint32_t b = __shfl_sync(0xFFFFFFFFu, w, (l + q + 1) & (W - 1), W);
+    return __funnelshift_r(a, b, r);
+}
+
+// The inverse: the aligned volume word l of the row, from the chain words
+// (one per lane) whose cells start at bit offset s.
+__device__ __forceinline__ uint32_t scatter_bits(uint32_t c, int l, int s, int W) {
+    const int q = s >> 5, r = s & 31;
+    const uint32_t c1 = __shfl_sync(0xFFFFFFFFu, c, (l - q) & (W - 1), W);
+    const uint32_t c0 = __shfl_sync(0xFFFFFFFFu, c, (l - q - 1) & (W - 1), W);
+    return __funnelshift_l(c0, c1, r);
+}
+
+__global__ void k_hard_bits(const uint16_t* __restrict__ B, uint32_t* __restrict__ H, int64_t words) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < words;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const uint4* p = reinterpret_cast<const uint4*>(B + g * 32);
+        uint32_t bits = 0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint4 v = __ldg(p + c);
+            const uint32_t h[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int b = c * 8 + k * 2;
+                bits |= (uint32_t)((h[k] & 0xFFFFu) == HARD) << b;
+                bits |= (uint32_t)((h[k] >> 16) == HARD) << (b + 1);
+            }
+        }
+        H[g] = bits;
+    }
+}
+
+__global__ void k_reach_init(uint32_t* __restrict__ R, int64_t words, int64_t start) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < words;
+         g += (int64_t)gridDim.x * blockDim.x)
+        R[g] = g == (start >> 5) ? ~(1u << (start & 31)) : 0xFFFFFFFFu;
+}
+
+// Transpose the 32 x 32 bit tiles of the listed planes: bit (row j, column i)
+// of a plane goes to (row i, column j).  One warp per tile.  With `and_into`
+// the result is ANDed into dst, else stored.
+__global__ void k_bit_transpose(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                const int32_t* __restrict__ planes, int nplanes, int lx, int and_into) {
+    const int W = 1 << (lx - 5);
+    const int tiles = W * W;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int pi = (int)(warp / tiles), t = (int)(warp - (int64_t)pi * tiles);
+    if (pi >= nplanes) return;  // whole warps only: the ballots below need every lane
+    const int T = __ldg(planes + pi);
+    const int tj = t / W, ti = t - tj * W;  // tile row block (j / 32), column word (i / 32)
+    const int64_t plane = (int64_t)T << (2 * lx - 5);
+    const uint32_t w = src[plane + (int64_t)(tj * 32 + lane) * W + ti];
+    uint32_t out = 0;
+#pragma unroll
+    for (int b = 0; b < 32; b++) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, (w >> b) & 1u);
+        if (lane == b) out = m;
+    }
+    uint32_t* d = dst + plane + (int64_t)(ti * 32 + lane) * W + tj;
+    if (and_into) *d &= out;
+    else *d = out;
+}
+
+// One turn family (LEFT: LF up, LB down; RIGHT: RB up, RF down).  Block: SEC
+// warps = sections of K headings; a warp's lanes are G = 32 / W chain rows
+// of W words.  Both maneuvers read R_m and are ANDed into R_{m+1}.
+template <int K, int SEC>
+__global__ void __launch_bounds__(32 * SEC, 1)
+k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restrict__ Rn,
+             const uint32_t* __restrict__ H, int family) {
+    __shared__ uint32_t sD[SEC][32], sS[SEC][32], sC[SEC][32];
+    const int W = 1 << (g.lx - 5), G = 32 / W;
+    const int lane = threadIdx.x & 31, sec = threadIdx.x >> 5;
+    const int r = lane / W, l = lane & (W - 1);
+    const int yq = blockIdx.x * G + r;  // chain row y'
+    const int64_t nrow = (int64_t)W;     // words per row
+    const int64_t nplane = (int64_t)W << g.lx;
+    // row word of this lane and bit offset of the chain cells, heading T
+    auto where = [&](int T, int& off) -> int64_t {
+        const int4 b = __ldg(&g.beta4[T]);
+        const int bx = family ? b.z : b.x, by = family ? b.w : b.y;
+        off = bx & g.mx;
+        return (int64_t)T * nplane + (int64_t)((yq + by) & g.mx) * nrow + l;
+    };
+    uint32_t vi[K], hb[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        int off;
+        const int64_t ix = where(sec * K + k, off);
+        vi[k] = gather_bits(rd(Rm + ix), l, off, W);
+        hb[k] = gather_bits(rd(H + ix), l, off, W);
+    }
+    uint32_t o[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) o[k] = 0u;
+#pragma unroll
+    for (int dir = 0; dir < 2; dir++) {  // 0: heading up, 1: heading down
+        // pass 1: the section's map
+        uint32_t v = 0xFFFFFFFFu, D = 0u;
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = dir == 0 ? kk : K - 1 - kk;
+            v = (v & vi[k]) | hb[k];
+            D |= hb[k];
+        }
+        sD[sec][lane] = D;
+        sS[sec][lane] = v;
+        __syncthreads();
+        // pass 2: ripple around the cycle twice; the second round records
+        // what enters each section
+        if (sec == 0) {
+            uint32_t c = 0xFFFFFFFFu;
+            for (int round = 0; round < 2; round++)
+                for (int i = 0; i < SEC; i++) {
+                    const int s = dir == 0 ? i : SEC - 1 - i;
+                    if (round) sC[s][lane] = c;
+                    c = (c | sD[s][lane]) & sS[s][lane];
+                }
+        }
+        __syncthreads();
+        // pass 3: sweep the section with what enters it
+        v = sC[sec][lane];
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = dir == 0 ? kk : K - 1 - kk;
+            v = (v & vi[k]) | hb[k];
+            o[k] |= ~v;  // reachable (0 bits) collected as 1s
+        }
+        __syncthreads();  // the maps are rewritten by the next direction
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        int off;
+        const int64_t ix = where(sec * K + k, off);
+        Rn[ix] &= scatter_bits(~o[k], l, off, W);
+    }
+}
+
+// Straight lines of one plane per block (steep planes in place, shallow
+// planes through their transposed copies): lines x' packed 32 per word,
+// steps y' along the view's rows, row y' shifted by Bs(y') (eq. 23).  A
+// warp's lanes are 32 / W sections of W words; SEC sections of K steps.
+template <int K>
+__global__ void __launch_bounds__(512, 1) k_reach_straight(const DevGrid g, const uint32_t* __restrict__ Rm,
+                                 const uint32_t* __restrict__ H, const uint32_t* __restrict__ RmT,
+                                 const uint32_t* __restrict__ HT, uint32_t* __restrict__ Rn,
+                                 uint32_t* __restrict__ OT) {
+    extern __shared__ uint32_t smem[];
+    const int T = blockIdx.x;
+    const PlaneInfo pi = g.plane[T];
+    const bool steep = pi.iflag != 0;
+    const int W = 1 << (g.lx - 5), SPW = 32 / W;  // sections per warp
+    const int SEC = g.nx / K;
+    uint32_t* sD = smem;
+    uint32_t* sS = sD + SEC * W;
+    uint32_t* sC = sS + SEC * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sec = warp * SPW + lane / W, l = lane & (W - 1);
+    const int64_t nplane = (int64_t)W << g.lx;
+    const uint32_t* src = steep ? Rm : RmT;
+    const uint32_t* hsrc = steep ? H : HT;
+    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
+    uint32_t vi[K], hb[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int y = sec * K + k;  // step y' = row of the view
+        const int off = bs[y] & g.mx;
+        const int64_t ix = (int64_t)T * nplane + (int64_t)y * W + l;
+        vi[k] = gather_bits(rd(src + ix), l, off, W);
+        hb[k] = gather_bits(rd(hsrc + ix), l, off, W);
+    }
+    uint32_t o[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) o[k] = 0u;
+    const int up_first = pi.jsign > 0;  // SF walks y' up when J > 0 (eq. 24); SB the other way
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const int up = d == 0 ? up_first : !up_first;
+        uint32_t v = 0xFFFFFFFFu, D = 0u;
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = up ? kk : K - 1 - kk;
+            v = (v & vi[k]) | hb[k];
+            D |= hb[k];
+        }
+        sD[sec * W + l] = D;
+        sS[sec * W + l] = v;
+        __syncthreads();
+        // one ripple: a line starts at the wall, so nothing enters the first section
+        if (threadIdx.x < W) {
+            uint32_t c = 0xFFFFFFFFu;
+            for (int i = 0; i < SEC; i++) {
+                const int s = up ? i : SEC - 1 - i;
+                sC[s * W + threadIdx.x] = c;
+                c = (c | sD[s * W + threadIdx.x]) & sS[s * W + threadIdx.x];
+            }
+        }
+        __syncthreads();
+        v = sC[sec * W + l];
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const int k = up ? kk : K - 1 - kk;
+            v = (v & vi[k]) | hb[k];
+            o[k] |= ~v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int y = sec * K + k;
+        const int64_t ix = (int64_t)T * nplane + (int64_t)y * W + l;
+        const uint32_t word = scatter_bits(~o[k], l, bs[y] & g.mx, W);
+        if (steep) Rn[ix] &= word;
+        else OT[ix] = word;
+    }
+}
+
+// Fewest maneuvers per pose from R_0 .. R_N (255 beyond N).
+__global__ void k_reach_counts(const uint32_t* __restrict__ R, int n, int64_t words, uint8_t* __restrict__ count) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < words;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) c[i] = 0xFFFFFFFFu;
+        uint32_t seen = 0;
+        for (int m = 0; m <= n; m++) {
+            const uint32_t fresh = ~R[(int64_t)m * words + g] & ~seen;
+            seen |= fresh;
+            for (uint32_t f = fresh; f; f &= f - 1) {
+                const int b = __ffs(f) - 1;
+                c[b >> 2] = (c[b >> 2] & ~(0xFFu << (8 * (b & 3)))) | ((uint32_t)m << (8 * (b & 3)));
+            }
+        }
+        uint4* dst = reinterpret_cast<uint4*>(count + g * 32);
+        dst[0] = make_uint4(c[0], c[1], c[2], c[3]);
+        dst[1] = make_uint4(c[4], c[5], c[6], c[7]);
+    }
+}
+
+}  // namespace
+
+
+cudaError_t launch_hard_bits(const uint16_t* B, uint32_t* H, int64_t nr, cudaStream_t s) {
+    const int64_t words = nr / 32;
+    const int64_t blocks = std::min<int64_t>((words + 255) / 256, 148 * 16);
+    k_hard_bits<<<(unsigned)blocks, 256, 0, s>>>(B, H, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reach_init(uint32_t* R, int64_t nr, int64_t start, cudaStream_t s) {
+    const int64_t words = nr / 32;
+    const int64_t blocks = std::min<int64_t>((words + 255) / 256, 148 * 16);
+    k_reach_init<<<(unsigned)blocks, 256, 0, s>>>(R, words, start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32_t* planes, int nplanes, int lx,
+                                 bool and_into, cudaStream_t s) {
+    if (nplanes == 0) return cudaSuccess;
+    const int W = 1 << (lx - 5);
+    const int64_t warps = (int64_t)nplanes * W * W;
+    const int64_t blocks = (warps * 32 + 255) / 256;
+    k_bit_transpose<<<(unsigned)blocks, 256, 0, s>>>(src, dst, planes, nplanes, lx, and_into ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reach_turn(const DevGrid& g, const uint32_t* Rm, uint32_t* Rn, const uint32_t* H, int family,
+                              cudaStream_t s) {
+    const int W = 1 << (g.lx - 5), G = 32 / W;
+    const unsigned blocks = (unsigned)(g.nx / G);
+    switch (g.lt) {  // K = 16 headings per section
+        case 5: k_reach_turn<16, 2><<<blocks, 32 * 2, 0, s>>>(g, Rm, Rn, H, family); break;
+        case 6: k_reach_turn<16, 4><<<blocks, 32 * 4, 0, s>>>(g, Rm, Rn, H, family); break;
+        case 7: k_reach_turn<16, 8><<<blocks, 32 * 8, 0, s>>>(g, Rm, Rn, H, family); break;
+        case 8: k_reach_turn<16, 16><<<blocks, 32 * 16, 0, s>>>(g, Rm, Rn, H, family); break;
+        case 9: k_reach_turn<16, 32><<<blocks, 32 * 32, 0, s>>>(g, Rm, Rn, H, family); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const uint32_t* H, const uint32_t* RmT,
+                                  const uint32_t* HT, uint32_t* Rn, uint32_t* OT, cudaStream_t s) {
+    // K steps per section such that the (section, word) lanes fill whole
+    // warps and one block: Nx = 64 -> 4, 128 .. 512 -> 16, 1024 -> 32
+    const int K = g.nx == 64 ? 4 : 16;
+    const int W = 1 << (g.lx - 5);
+    const int SEC = g.nx / K;
+    const int threads = SEC * W;
+    if (g.nx < 64 || g.nx > 512 || threads % 32 != 0 || threads > 512) return cudaErrorInvalidValue;
+    const size_t smem = 3 * (size_t)SEC * W * sizeof(uint32_t);
+    if (K == 4) k_reach_straight<4><<<(unsigned)g.nt, threads, smem, s>>>(g, Rm, H, RmT, HT, Rn, OT);
+    else k_reach_straight<16><<<(unsigned)g.nt, threads, smem, s>>>(g, Rm, H, RmT, HT, Rn, OT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reach_counts(const uint32_t* R, int n, int64_t nr, uint8_t* count, cudaStream_t s) {
+    const int64_t words = nr / 32;
+    const int64_t blocks = std::min<int64_t>((words + 255) / 256, 148 * 16);
+    k_reach_counts<<<(unsigned)blocks, 256, 0, s>>>(R, n, words, count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ host
+namespace {
+
+int reach_alloc(plan_s* p, int n_cycles) {
+    const size_t vol = (size_t)(p->nr / 8);
+    if (!p->d_hb) {
+        p->d_hb = (uint32_t*)p->dalloc(vol);
+        p->d_hbt = (uint32_t*)p->dalloc(vol);
+        p->d_rt = (uint32_t*)p->dalloc(vol);
+        p->d_ot = (uint32_t*)p->dalloc(vol);
+        p->d_shallow = (int32_t*)p->dalloc(sizeof(int32_t) * (size_t)p->nt);
+        if (!p->d_hb || !p->d_hbt || !p->d_rt || !p->d_ot || !p->d_shallow) return PLAN_ENOMEM;
+        std::vector<int32_t> sh;
+        for (int T = 0; T < p->nt; T++)
+            if (p->planes[T].iflag == 0) sh.push_back(T);
+        p->n_shallow = (int)sh.size();
+        p->shallow = sh;
+        if (!sh.empty())
+            NHP_CK(cudaMemcpyAsync(p->d_shallow, p->shallow.data(), sizeof(int32_t) * sh.size(),
+                                   cudaMemcpyHostToDevice, p->stream));
+    }
+    if (n_cycles + 1 > p->reach_cap) {
+        p->dfree(p->d_reach, vol * (size_t)p->reach_cap);
+        p->d_reach = (uint32_t*)p->dalloc(vol * (size_t)(n_cycles + 1));
+        p->reach_cap = p->d_reach ? n_cycles + 1 : 0;
+        if (!p->d_reach) return PLAN_ENOMEM;
+    }
+    return PLAN_OK;
+}
+
+}  // namespace
+}  // namespace nhp
+
+using namespace nhp;
+
+extern "C" {
+
+int plan_reach_sweep(plan_t* p, plan_pose start, int n_cycles) {
+    if (!p || n_cycles < 0 || n_cycles > 254 || !pose_ok(p, start)) return PLAN_EINVAL;
+    if (p->nx < 64 || p->nx > 512 || p->nt < 32 || p->nt > 512) return PLAN_EINVAL;
+    if (!p->rendered) return PLAN_ESTATE;
+    if (pose_hard(p, start)) return PLAN_EINVAL;
+    int rc = reach_alloc(p, n_cycles);
+    if (rc != PLAN_OK) return rc;
+    cudaStream_t s = p->stream;
+    const DevGrid& g = p->g;
+    const int64_t words = p->nr / 32;
+    NHP_CK(launch_hard_bits(p->d_B, p->d_hb, p->nr, s));
+    NHP_CK(launch_bit_transpose(p->d_hb, p->d_hbt, p->d_shallow, p->n_shallow, p->lx, false, s));
+    NHP_CK(launch_reach_init(p->d_reach, p->nr, cell_index(p, start), s));
+    p->launches += 3;
+    for (int m = 0; m < n_cycles; m++) {
+        const uint32_t* Rm = p->d_reach + (size_t)m * words;
+        uint32_t* Rn = p->d_reach + (size_t)(m + 1) * words;
+        NHP_CK(cudaMemcpyAsync(Rn, Rm, (size_t)words * 4, cudaMemcpyDeviceToDevice, s));
+        NHP_CK(launch_bit_transpose(Rm, p->d_rt, p->d_shallow, p->n_shallow, p->lx, false, s));
+        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 0, s));
+        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 1, s));
+        NHP_CK(launch_reach_straight(g, Rm, p->d_hb, p->d_rt, p->d_hbt, Rn, p->d_ot, s));
+        NHP_CK(launch_bit_transpose(p->d_ot, Rn, p->d_shallow, p->n_shallow, p->lx, true, s));
+        p->launches += 5;
+    }
+    p->reach_n = n_cycles;
+    p->reach_ready = true;
+    return PLAN_OK;
+}
+
+int plan_reach_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_out, int* maneuvers) {
+    if (!p || !n_out || !maneuvers || cap < 0 || (cap > 0 && !out) || !pose_ok(p, goal)) return PLAN_EINVAL;
+    *n_out = 0;
+    *maneuvers = -1;
+    if (!p->reach_ready) return PLAN_ESTATE;
+    const int64_t words = p->nr / 32;
+    NHP_CK(launch_reach_extract(p->g, p->d_reach, p->reach_n, words, p->d_hb, cell_index(p, goal), p->d_seg,
+                                kDevSegCap, p->d_status, p->stream));
+    p->launches++;
+    int32_t status[2] = {0, 0};
+    NHP_CK(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
+    NHP_CK(cudaStreamSynchronize(p->stream));
+    if (status[0] == -1) return PLAN_EUNREACHABLE;
+    if (status[0] < 0) return PLAN_EINTERNAL;
+    *maneuvers = status[1];
+    *n_out = status[0];
+    if (status[0] > cap || status[0] > kDevSegCap) return PLAN_ERANGE;
+    if (status[0] > 0) {
+        NHP_CK(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status[0], cudaMemcpyDeviceToHost, p->stream));
+        NHP_CK(cudaStreamSynchronize(p->stream));
+        std::reverse(out, out + status[0]);  // the back-track runs goal -> start
+    }
+    return PLAN_OK;
+}
+
+int plan_reach_counts(plan_t* p, uint8_t* counts) {
+    if (!p || !counts) return PLAN_EINVAL;
+    if (!p->reach_ready) return PLAN_ESTATE;
+    uint8_t* d = (uint8_t*)p->dalloc((size_t)p->nr);
+    if (!d) return PLAN_ENOMEM;
+    int rc = cuda_rc(launch_reach_counts(p->d_reach, p->reach_n, p->nr, d, p->stream));
+    p->launches++;
+    if (rc == PLAN_OK) rc = cuda_rc(cudaMemcpyAsync(counts, d, (size_t)p->nr, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    p->dfree(d, (size_t)p->nr);
+    return rc;
+}
+
+}  // extern "C"
