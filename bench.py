@@ -269,6 +269,8 @@ def run_ours(args):
     p.close()
     if world == 1 and not args.no_maze:
         line["maze"] = run_maze(args, torch)
+    if world == 1 and not args.no_reach:
+        line["reach_bitvector"] = run_reach(args, torch)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, torch)
     if world == 1 and not args.no_served:
@@ -308,6 +310,44 @@ def run_maze(args, torch):
     return {"workload": "maze_512x512x512_N32_soft", "ms_per_plan": ms, "plans_per_s": 1e3 / ms,
             "updates_per_s": updates / (ms / 1e3), "plan_cost": res.cost if res else None,
             "plan_maneuvers": len(res.segments) if res else 0, "steps": steps}
+
+
+def run_reach(args, torch):
+    """Appendix C's bit-vector planner (fewest maneuvers over hard obstacles):
+    render + 8 reachability cycles + back-track, at the paper's Table 9
+    resolution (128^2 x 512) and on the 512^3 parking scene."""
+    from paper_2306_01301_b300 import binding, scenes
+    out = {}
+    t9, _ = scenes.tiny(17, 7, 9, fill=0.01, turn_radius=14.0, footprint=(3, 1, 1))
+    for name, sc, start, goal in (("table9_128x128x512_N8", t9, t9.pose_candidates[0], t9.pose_candidates[5]),
+                                  ("parking_512x512x512_N8", scenes.parallel_parking(), None, None)):
+        sc_start = start or sc.start
+        sc_goal = goal or sc.goal
+        stream = torch.cuda.current_stream()
+        p = binding.Planner.from_scene(sc, sc.hard_image(), stream=stream)
+
+        def step():
+            p.render()
+            p.reach_sweep(sc_start, 8)
+            return p.reach_extract(sc_goal)
+
+        for _ in range(max(3, args.warmup)):
+            res = step()
+        steps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_plan": ms, "plans_per_s": 1e3 / ms,
+                     "pose_cycles_per_s": 8 * 6 * sc.cells / (ms / 1e3),
+                     "maneuvers_to_goal": res[0] if res else None}
+        p.close()
+    out["paper_context"] = "Table 9: 2 ms for render + 8 cycles + back-track at 128^2 x 512 on its larger GPU"
+    return out
 
 
 def run_batched(args, torch):
@@ -456,6 +496,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-maze", action="store_true")
+    ap.add_argument("--no-reach", action="store_true")
     ap.add_argument("--shapes", default="", help="pin turn variant,turn grid,straight lines,straight grid "
                                                    "instead of autotuning (e.g. 0,148,256,0)")
     ap.add_argument("--maze-steps", type=int, default=5)

@@ -77,30 +77,68 @@ __global__ void k_reach_init(uint32_t* __restrict__ R, int64_t words, int64_t st
         R[g] = g == (start >> 5) ? ~(1u << (start & 31)) : 0xFFFFFFFFu;
 }
 
-// Transpose the 32 x 32 bit tiles of the listed planes: bit (row j, column i)
-// of a plane goes to (row i, column j).  One warp per tile.  With `and_into`
-// the result is ANDed into dst, else stored.
-__global__ void k_bit_transpose(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
-                                const int32_t* __restrict__ planes, int nplanes, int lx, int and_into) {
-    const int W = 1 << (lx - 5);
-    const int tiles = W * W;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int pi = (int)(warp / tiles), t = (int)(warp - (int64_t)pi * tiles);
-    if (pi >= nplanes) return;  // whole warps only: the ballots below need every lane
-    const int T = __ldg(planes + pi);
-    const int tj = t / W, ti = t - tj * W;  // tile row block (j / 32), column word (i / 32)
-    const int64_t plane = (int64_t)T << (2 * lx - 5);
-    const uint32_t w = src[plane + (int64_t)(tj * 32 + lane) * W + ti];
-    uint32_t out = 0;
+// 32 x 32 bit matrix held one row per lane (bit c of lane r = entry (r, c)),
+// transposed in place: five rounds, each swapping the two off-diagonal j x j
+// blocks of every 2j x 2j block (j = 16, 8, 4, 2, 1) between lanes r and r ^ j.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 #pragma unroll
-    for (int b = 0; b < 32; b++) {
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, (w >> b) & 1u);
-        if (lane == b) out = m;
+    for (int i = 0; i < 5; i++) {
+        const int j = 16 >> i;
+        // columns c with (c & j) == 0
+        const uint32_t m = i == 0 ? 0x0000FFFFu : i == 1 ? 0x00FF00FFu : i == 2 ? 0x0F0F0F0Fu : i == 3 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
     }
-    uint32_t* d = dst + plane + (int64_t)(ti * 32 + lane) * W + tj;
-    if (and_into) *d &= out;
-    else *d = out;
+    return x;
+}
+
+template <int G> struct WordVec;
+template <> struct WordVec<2> { using T = uint2; };
+template <> struct WordVec<4> { using T = uint4; };
+
+__device__ __forceinline__ void unpack(const uint2& w, uint32_t* v) { v[0] = w.x; v[1] = w.y; }
+__device__ __forceinline__ void unpack(const uint4& w, uint32_t* v) { v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w; }
+__device__ __forceinline__ void pack(uint2& w, const uint32_t* v) { w.x = v[0]; w.y = v[1]; }
+__device__ __forceinline__ void pack(uint4& w, const uint32_t* v) { w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3]; }
+
+// Transpose the 32 x 32 bit tiles of the listed planes: bit (row j, column
+// i) goes to (row i, column j), ANDed into dst with `and_into`.  Each warp
+// takes a G x G group of tiles (row blocks bj G.., words bi G..): every lane
+// reads G consecutive words of each of its G source rows in one vector load
+// and writes G consecutive words of each of its G destination rows in one
+// vector store, so the plane moves in 16-byte (G = 4) pieces.
+template <int G>
+__global__ void __launch_bounds__(256) k_bit_transpose(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                       const int32_t* __restrict__ planes, int64_t ngroups, int lx,
+                                                       int and_into) {
+    using V = typename WordVec<G>::T;
+    constexpr int LG = G == 4 ? 2 : 1;
+    const int lane = threadIdx.x & 31, lw = lx - 5, W = 1 << lw, lb = lw - LG;
+    const int64_t gi = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (gi >= ngroups) return;  // warp-uniform
+    const int pi = (int)(gi >> (2 * lb));
+    const int r = (int)(gi & ((1 << (2 * lb)) - 1)), bj = r >> lb, bi = r & ((1 << lb) - 1);
+    const int64_t plane = (int64_t)__ldg(planes + pi) << (2 * lx - 5);
+    uint32_t v[G][G];  // v[a][k]: source row block bj G + a, word bi G + k
+#pragma unroll
+    for (int a = 0; a < G; a++)
+        unpack(*reinterpret_cast<const V*>(src + plane + (int64_t)((bj * G + a) * 32 + lane) * W + bi * G), v[a]);
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        uint32_t o[G];  // destination row block bi G + k, words bj G + a
+#pragma unroll
+        for (int a = 0; a < G; a++) o[a] = transpose32(v[a][k], lane);
+        V* at = reinterpret_cast<V*>(dst + plane + (int64_t)((bi * G + k) * 32 + lane) * W + bj * G);
+        if (and_into) {
+            uint32_t d[G];
+            unpack(*at, d);
+#pragma unroll
+            for (int a = 0; a < G; a++) o[a] &= d[a];
+        }
+        V w;
+        pack(w, o);
+        *at = w;
+    }
 }
 
 // One turn family (LEFT: LF up, LB down; RIGHT: RB up, RF down).  Block: SEC
@@ -300,9 +338,11 @@ cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32
                                  bool and_into, cudaStream_t s) {
     if (nplanes == 0) return cudaSuccess;
     const int W = 1 << (lx - 5);
-    const int64_t warps = (int64_t)nplanes * W * W;
-    const int64_t blocks = (warps * 32 + 255) / 256;
-    k_bit_transpose<<<(unsigned)blocks, 256, 0, s>>>(src, dst, planes, nplanes, lx, and_into ? 1 : 0);
+    const int G = W >= 4 ? 4 : 2;  // W is a power of two, at least 2
+    const int64_t ngroups = (int64_t)nplanes * (W / G) * (W / G);
+    const unsigned blocks = (unsigned)((ngroups + 7) / 8);
+    if (G == 4) k_bit_transpose<4><<<blocks, 256, 0, s>>>(src, dst, planes, ngroups, lx, and_into ? 1 : 0);
+    else k_bit_transpose<2><<<blocks, 256, 0, s>>>(src, dst, planes, ngroups, lx, and_into ? 1 : 0);
     return cudaGetLastError();
 }
 
