@@ -132,7 +132,7 @@ cudaError_t launch_reach_init(uint32_t* R, int64_t nr, int64_t start, cudaStream
 cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32_t* planes, int nplanes, int lx,
                                  bool and_into, cudaStream_t s);
 cudaError_t launch_reach_turn(const DevGrid& g, const uint32_t* Rm, uint32_t* Rn, const uint32_t* H, int family,
-                              cudaStream_t s);
+                              bool assign, cudaStream_t s);
 cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const uint32_t* H, const uint32_t* RmT,
                                   const uint32_t* HT, uint32_t* Rn, uint32_t* OT, cudaStream_t s);
 cudaError_t launch_reach_counts(const uint32_t* R, int n, int64_t nr, uint8_t* count, cudaStream_t s);

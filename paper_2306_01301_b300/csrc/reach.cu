@@ -141,14 +141,43 @@ __global__ void __launch_bounds__(256) k_bit_transpose(const uint32_t* __restric
     }
 }
 
+// The sections of one curve in ripple order, one per lane of an n-lane
+// segment (p = the lane's position): section p maps what enters it to
+// (v & A) | C.  Returns what enters section p when the ripple starts from
+// all ones (unreachable) at section 0 -- for a cyclic curve after one full
+// turn around the cycle, i.e. from F(all ones) with F all sections composed.
+// The prefix compositions are a shuffle scan: the map of sections a..b
+// followed by that of b+1..c is (v & A1 & A2) | (C1 & A2) | C2.
+template <int N>
+__device__ __forceinline__ uint32_t ripple(uint32_t A, uint32_t C, int p, int n, bool cyclic) {
+#pragma unroll
+    for (int o = 1; o < (N ? N : 32); o <<= 1) {
+        if (!N && o >= n) break;
+        const uint32_t A2 = __shfl_up_sync(0xFFFFFFFFu, A, o, N ? N : n);
+        const uint32_t C2 = __shfl_up_sync(0xFFFFFFFFu, C, o, N ? N : n);
+        if (p >= o) {
+            C = (C2 & A) | C;
+            A &= A2;
+        }
+    }
+    const int w = N ? N : n;
+    const uint32_t c0 = cyclic ? __shfl_sync(0xFFFFFFFFu, A | C, w - 1, w) : 0xFFFFFFFFu;
+    const uint32_t Ap = __shfl_up_sync(0xFFFFFFFFu, A, 1, w), Cp = __shfl_up_sync(0xFFFFFFFFu, C, 1, w);
+    return p == 0 ? c0 : ((c0 & Ap) | Cp);
+}
+
 // One turn family (LEFT: LF up, LB down; RIGHT: RB up, RF down).  Block: SEC
 // warps = sections of K headings; a warp's lanes are G = 32 / W chain rows
-// of W words.  Both maneuvers read R_m and are ANDed into R_{m+1}.
+// of W words.  Both maneuvers read R_m; what they reach is ANDed into
+// R_{m+1}, or with `assign` stored as R_m AND it (the first writer of a
+// cycle, so that R_{m+1} needs no copy of R_m first).
 template <int K, int SEC>
 __global__ void __launch_bounds__(32 * SEC, 1)
 k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restrict__ Rn,
-             const uint32_t* __restrict__ H, int family) {
-    __shared__ uint32_t sD[SEC][32], sS[SEC][32], sC[SEC][32];
+             const uint32_t* __restrict__ H, int family, int assign) {
+    // [direction][chain word][section]: the section maps, then what enters
+    // each section; the odd pitch keeps both access patterns conflict-free
+    __shared__ uint32_t sA[2][32][SEC + 1], sC[2][32][SEC + 1];
     const int W = 1 << (g.lx - 5), G = 32 / W;
     const int lane = threadIdx.x & 31, sec = threadIdx.x >> 5;
     const int r = lane / W, l = lane & (W - 1);
@@ -170,56 +199,60 @@ k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restr
         vi[k] = gather_bits(rd(Rm + ix), l, off, W);
         hb[k] = gather_bits(rd(H + ix), l, off, W);
     }
-    uint32_t o[K];
+    // pass 1: the section's map in both directions, v -> (v | D) & S
+    {
+        uint32_t up = 0xFFFFFFFFu, down = 0xFFFFFFFFu, D = 0u;
 #pragma unroll
-    for (int k = 0; k < K; k++) o[k] = 0u;
-#pragma unroll
-    for (int dir = 0; dir < 2; dir++) {  // 0: heading up, 1: heading down
-        // pass 1: the section's map
-        uint32_t v = 0xFFFFFFFFu, D = 0u;
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = dir == 0 ? kk : K - 1 - kk;
-            v = (v & vi[k]) | hb[k];
+        for (int k = 0; k < K; k++) {
+            up = (up & vi[k]) | hb[k];
+            down = (down & vi[K - 1 - k]) | hb[K - 1 - k];
             D |= hb[k];
         }
-        sD[sec][lane] = D;
-        sS[sec][lane] = v;
-        __syncthreads();
-        // pass 2: ripple around the cycle twice; the second round records
-        // what enters each section
-        if (sec == 0) {
-            uint32_t c = 0xFFFFFFFFu;
-            for (int round = 0; round < 2; round++)
-                for (int i = 0; i < SEC; i++) {
-                    const int s = dir == 0 ? i : SEC - 1 - i;
-                    if (round) sC[s][lane] = c;
-                    c = (c | sD[s][lane]) & sS[s][lane];
-                }
+        sA[0][lane][sec] = up;
+        sC[0][lane][sec] = D & up;
+        sA[1][lane][sec] = down;
+        sC[1][lane][sec] = D & down;
+    }
+    __syncthreads();
+    // pass 2: thread t ripples chain word t / SEC at position t % SEC
+    {
+        const int w = threadIdx.x / SEC, p = threadIdx.x % SEC;
+#pragma unroll 1  // both scans unrolled together need more than the 64 registers a thread has
+        for (int dir = 0; dir < 2; dir++) {
+            const int s = dir == 0 ? p : SEC - 1 - p;
+            sA[dir][w][s] = ripple<SEC>(sA[dir][w][s], sC[dir][w][s], p, SEC, true);
         }
-        __syncthreads();
-        // pass 3: sweep the section with what enters it
-        v = sC[sec][lane];
+    }
+    __syncthreads();
+    // pass 3: sweep the section with what enters it, both directions
+    uint32_t o[K];
+    uint32_t v = sA[0][lane][sec];
 #pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = dir == 0 ? kk : K - 1 - kk;
-            v = (v & vi[k]) | hb[k];
-            o[k] |= ~v;  // reachable (0 bits) collected as 1s
-        }
-        __syncthreads();  // the maps are rewritten by the next direction
+    for (int k = 0; k < K; k++) {
+        v = (v & vi[k]) | hb[k];
+        o[k] = ~v;  // reachable (0 bits) collected as 1s
+    }
+    v = sA[1][lane][sec];
+#pragma unroll
+    for (int k = K - 1; k >= 0; k--) {
+        v = (v & vi[k]) | hb[k];
+        o[k] |= ~v;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int off;
         const int64_t ix = where(sec * K + k, off);
-        Rn[ix] &= scatter_bits(~o[k], l, off, W);
+        const uint32_t word = scatter_bits(~o[k], l, off, W);
+        if (assign) Rn[ix] = rd(Rm + ix) & word;
+        else Rn[ix] &= word;
     }
 }
 
 // Straight lines of one plane per block (steep planes in place, shallow
 // planes through their transposed copies): lines x' packed 32 per word,
 // steps y' along the view's rows, row y' shifted by Bs(y') (eq. 23).  A
-// warp's lanes are 32 / W sections of W words; SEC sections of K steps.
+// warp's lanes are 32 / W sections of W words; SEC sections of K steps.  SF
+// and SB walk the line in opposite directions; what either reaches counts.
 template <int K>
 __global__ void __launch_bounds__(512, 1) k_reach_straight(const DevGrid g, const uint32_t* __restrict__ Rm,
                                  const uint32_t* __restrict__ H, const uint32_t* __restrict__ RmT,
@@ -230,10 +263,10 @@ __global__ void __launch_bounds__(512, 1) k_reach_straight(const DevGrid g, cons
     const PlaneInfo pi = g.plane[T];
     const bool steep = pi.iflag != 0;
     const int W = 1 << (g.lx - 5), SPW = 32 / W;  // sections per warp
-    const int SEC = g.nx / K;
-    uint32_t* sD = smem;
-    uint32_t* sS = sD + SEC * W;
-    uint32_t* sC = sS + SEC * W;
+    const int SEC = g.nx / K, P = SEC + 1;
+    // [direction][word][section] maps, then what enters each section
+    uint32_t* sA = smem;
+    uint32_t* sC = sA + 2 * W * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sec = warp * SPW + lane / W, l = lane & (W - 1);
     const int64_t nplane = (int64_t)W << g.lx;
@@ -249,41 +282,42 @@ __global__ void __launch_bounds__(512, 1) k_reach_straight(const DevGrid g, cons
         vi[k] = gather_bits(rd(src + ix), l, off, W);
         hb[k] = gather_bits(rd(hsrc + ix), l, off, W);
     }
-    uint32_t o[K];
+    {
+        uint32_t up = 0xFFFFFFFFu, down = 0xFFFFFFFFu, D = 0u;
 #pragma unroll
-    for (int k = 0; k < K; k++) o[k] = 0u;
-    const int up_first = pi.jsign > 0;  // SF walks y' up when J > 0 (eq. 24); SB the other way
-#pragma unroll
-    for (int d = 0; d < 2; d++) {
-        const int up = d == 0 ? up_first : !up_first;
-        uint32_t v = 0xFFFFFFFFu, D = 0u;
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = up ? kk : K - 1 - kk;
-            v = (v & vi[k]) | hb[k];
+        for (int k = 0; k < K; k++) {
+            up = (up & vi[k]) | hb[k];
+            down = (down & vi[K - 1 - k]) | hb[K - 1 - k];
             D |= hb[k];
         }
-        sD[sec * W + l] = D;
-        sS[sec * W + l] = v;
-        __syncthreads();
-        // one ripple: a line starts at the wall, so nothing enters the first section
-        if (threadIdx.x < W) {
-            uint32_t c = 0xFFFFFFFFu;
-            for (int i = 0; i < SEC; i++) {
-                const int s = up ? i : SEC - 1 - i;
-                sC[s * W + threadIdx.x] = c;
-                c = (c | sD[s * W + threadIdx.x]) & sS[s * W + threadIdx.x];
-            }
-        }
-        __syncthreads();
-        v = sC[sec * W + l];
+        sA[l * P + sec] = up;
+        sC[l * P + sec] = D & up;
+        sA[(W + l) * P + sec] = down;
+        sC[(W + l) * P + sec] = D & down;
+    }
+    __syncthreads();
+    // one ripple: a line starts at the wall, so nothing enters the first section
+    {
+        const int w = threadIdx.x / SEC, p = threadIdx.x % SEC;
 #pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = up ? kk : K - 1 - kk;
-            v = (v & vi[k]) | hb[k];
-            o[k] |= ~v;
+        for (int dir = 0; dir < 2; dir++) {
+            const int at = (dir * W + w) * P + (dir == 0 ? p : SEC - 1 - p);
+            sA[at] = ripple<0>(sA[at], sC[at], p, SEC, false);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    uint32_t o[K];
+    uint32_t v = sA[l * P + sec];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        v = (v & vi[k]) | hb[k];
+        o[k] = ~v;
+    }
+    v = sA[(W + l) * P + sec];
+#pragma unroll
+    for (int k = K - 1; k >= 0; k--) {
+        v = (v & vi[k]) | hb[k];
+        o[k] |= ~v;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -347,15 +381,15 @@ cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32
 }
 
 cudaError_t launch_reach_turn(const DevGrid& g, const uint32_t* Rm, uint32_t* Rn, const uint32_t* H, int family,
-                              cudaStream_t s) {
+                              bool assign, cudaStream_t s) {
     const int W = 1 << (g.lx - 5), G = 32 / W;
     const unsigned blocks = (unsigned)(g.nx / G);
     switch (g.lt) {  // K = 16 headings per section
-        case 5: k_reach_turn<16, 2><<<blocks, 32 * 2, 0, s>>>(g, Rm, Rn, H, family); break;
-        case 6: k_reach_turn<16, 4><<<blocks, 32 * 4, 0, s>>>(g, Rm, Rn, H, family); break;
-        case 7: k_reach_turn<16, 8><<<blocks, 32 * 8, 0, s>>>(g, Rm, Rn, H, family); break;
-        case 8: k_reach_turn<16, 16><<<blocks, 32 * 16, 0, s>>>(g, Rm, Rn, H, family); break;
-        case 9: k_reach_turn<16, 32><<<blocks, 32 * 32, 0, s>>>(g, Rm, Rn, H, family); break;
+        case 5: k_reach_turn<16, 2><<<blocks, 32 * 2, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
+        case 6: k_reach_turn<16, 4><<<blocks, 32 * 4, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
+        case 7: k_reach_turn<16, 8><<<blocks, 32 * 8, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
+        case 8: k_reach_turn<16, 16><<<blocks, 32 * 16, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
+        case 9: k_reach_turn<16, 32><<<blocks, 32 * 32, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -370,7 +404,7 @@ cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const ui
     const int SEC = g.nx / K;
     const int threads = SEC * W;
     if (g.nx < 64 || g.nx > 512 || threads % 32 != 0 || threads > 512) return cudaErrorInvalidValue;
-    const size_t smem = 3 * (size_t)SEC * W * sizeof(uint32_t);
+    const size_t smem = 4 * (size_t)(SEC + 1) * W * sizeof(uint32_t);
     if (K == 4) k_reach_straight<4><<<(unsigned)g.nt, threads, smem, s>>>(g, Rm, H, RmT, HT, Rn, OT);
     else k_reach_straight<16><<<(unsigned)g.nt, threads, smem, s>>>(g, Rm, H, RmT, HT, Rn, OT);
     return cudaGetLastError();
@@ -437,10 +471,9 @@ int plan_reach_sweep(plan_t* p, plan_pose start, int n_cycles) {
     for (int m = 0; m < n_cycles; m++) {
         const uint32_t* Rm = p->d_reach + (size_t)m * words;
         uint32_t* Rn = p->d_reach + (size_t)(m + 1) * words;
-        NHP_CK(cudaMemcpyAsync(Rn, Rm, (size_t)words * 4, cudaMemcpyDeviceToDevice, s));
         NHP_CK(launch_bit_transpose(Rm, p->d_rt, p->d_shallow, p->n_shallow, p->lx, false, s));
-        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 0, s));
-        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 1, s));
+        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 0, true, s));
+        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 1, false, s));
         NHP_CK(launch_reach_straight(g, Rm, p->d_hb, p->d_rt, p->d_hbt, Rn, p->d_ot, s));
         NHP_CK(launch_bit_transpose(p->d_ot, Rn, p->d_shallow, p->n_shallow, p->lx, true, s));
         p->launches += 5;
