@@ -80,6 +80,16 @@ def lib():
         L.orc_extract.restype = C.c_int
         L.orc_extract.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         L.orc_soft_image.argtypes = [C.c_int, p, C.c_int, C.c_int, p]
+        L.orc_seed.restype = C.c_int
+        L.orc_seed.argtypes = [p, p, C.c_int64, p, p, p]
+        L.orc_sweep_state.restype = C.c_int
+        L.orc_sweep_state.argtypes = [p, p, C.c_int64, p, C.c_int, C.c_int, p, p, p]
+        L.orc_dijkstra_state.restype = C.c_int
+        L.orc_dijkstra_state.argtypes = [p, p, C.c_int64, p, p]
+        L.orc_bruteforce_state.restype = C.c_int
+        L.orc_bruteforce_state.argtypes = [p, p, C.c_int64, p, C.c_int, p]
+        L.orc_goal_search.restype = C.c_int
+        L.orc_goal_search.argtypes = [p, p, p, C.c_int, p, p]
         L.orc_reach.restype = C.c_int
         L.orc_reach.argtypes = [p, p, C.c_int64, C.c_int, p]
         L.orc_reach_extract.restype = C.c_int
@@ -207,6 +217,65 @@ class Oracle:
                                 int(n_cycles), _ptr(V)) != 0:
             raise ValueError("bruteforce failed")
         return V
+
+    # ----------------------------------------------------------- Section XII
+    def _entry(self, entry) -> np.ndarray:
+        e = np.ascontiguousarray(entry, dtype=np.uint32)
+        if e.shape != (6,):
+            raise ValueError("entry needs one cost per maneuver (cycle-order ids)")
+        return e
+
+    def sweep_state(self, B: np.ndarray, start: int, entry, n_cycles: int, mode: int = 0):
+        """orc_sweep with the start layer: maneuvers with entry[mu] < ct first
+        followed from the start alone, entered at entry[mu]."""
+        B = np.ascontiguousarray(B, dtype=np.uint16)
+        V = np.zeros(self.nr, np.uint32)
+        L = np.zeros(self.nr, np.uint16)
+        imp = np.zeros(max(1, 6 * n_cycles), np.int64)
+        rc = lib().orc_sweep_state(self._c, _ptr(B), int(start), _ptr(self._entry(entry)), int(n_cycles), int(mode),
+                                   _ptr(V), _ptr(L), _ptr(imp))
+        if rc != 0:
+            raise ValueError(f"oracle sweep_state failed ({rc})")
+        return V, L, imp[:6 * n_cycles]
+
+    def seed(self, B: np.ndarray, start: int, entry, V: np.ndarray, L: np.ndarray):
+        """The start layer applied to copies of (V, L)."""
+        V = np.array(V, dtype=np.uint32, copy=True)
+        L = np.array(L, dtype=np.uint16, copy=True)
+        if lib().orc_seed(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start), _ptr(self._entry(entry)),
+                          _ptr(V), _ptr(L)) != 0:
+            raise ValueError("seed failed")
+        return V, L
+
+    def dijkstra_state(self, B: np.ndarray, start: int, entry) -> np.ndarray:
+        V = np.zeros(self.nr, np.uint32)
+        if lib().orc_dijkstra_state(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start),
+                                    _ptr(self._entry(entry)), _ptr(V)) != 0:
+            raise ValueError("dijkstra_state failed")
+        return V
+
+    def bruteforce_state(self, B: np.ndarray, start: int, entry, n_cycles: int) -> np.ndarray:
+        V = np.zeros(self.nr, np.uint32)
+        if lib().orc_bruteforce_state(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start),
+                                      _ptr(self._entry(entry)), int(n_cycles), _ptr(V)) != 0:
+            raise ValueError("bruteforce_state failed")
+        return V
+
+    # ----------------------------------------------------------- Section IX
+    def goal_search(self, V: np.ndarray, goals):
+        """Best pose of a goal set: goals are (x, y, theta, r_xy, r_theta,
+        w_xy, w_theta, bias) tuples.  Returns (cell, score) or None when no
+        pose of any box was reached."""
+        g = np.ascontiguousarray(np.array(goals, dtype=np.int64).reshape(-1, 8))
+        cell = np.zeros(1, np.int64)
+        score = np.zeros(1, np.uint64)
+        rc = lib().orc_goal_search(self._c, _ptr(np.ascontiguousarray(V, np.uint32)), _ptr(g), len(g), _ptr(cell),
+                                   _ptr(score))
+        if rc == -1:
+            return None
+        if rc != 0:
+            raise ValueError(f"goal_search failed ({rc})")
+        return int(cell[0]), int(score[0])
 
     # ----------------------------------------------------------- Section X
     def extract(self, V: np.ndarray, L: np.ndarray, goal: int, cap: int = 4096):

@@ -581,6 +581,53 @@ int orc_sweep(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, 
     return orc_layers(c, B, 0, 6 * n_cycles, mode, V, L, improved);
 }
 
+/* ------------------------------------------------ start state (Section XII)
+ * A vehicle already under way when the plan starts: entry[mu] is what
+ * entering maneuver mu at the start pose costs -- ct for a vehicle at rest in
+ * the transition state, 0 for the maneuver in progress (no transition cost
+ * for it), the rest of a transition in progress toward mu.  Reading of
+ * Section XII's "first maneuver kernel of that type without a transition
+ * cost": every maneuver with entry[mu] < ct is first followed from the start
+ * pose alone (the start layer, maneuvers in cycle order, strict
+ * improvement), then the N cycles run as from rest.  The start keeps V = 0,
+ * so entering at ct stays possible and entries above ct are refused. */
+static int entries_ok(const orc_ctx* c, const uint32_t* entry) {
+    for (int m = 0; m < 6; m++)
+        if (entry[m] > c->ct) return 0;
+    return 1;
+}
+
+int orc_seed(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry, uint32_t* V,
+             uint16_t* L) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD || !entries_ok(c, entry)) return -1;
+    for (int l = 0; l < 6; l++) {
+        int mu = cycle_order[l];
+        if (entry[mu] >= c->ct) continue;
+        int n = is_turn(mu) ? c->nt : c->nx; /* the curve closes after n steps */
+        uint32_t run = entry[mu];
+        int64_t y = start;
+        for (int d = 1; d < n; d++) {
+            run = sadd(run, orc_edge(c, B, mu, y));
+            y = orc_succ(c, mu, y);
+            if (run == ORC_INF) break; /* a hard cell was left */
+            if (B[y] != ORC_HARD && run < V[y]) {
+                V[y] = run;
+                L[y] = (uint16_t)((mu << 13) | d);
+            }
+        }
+    }
+    return 0;
+}
+
+int orc_sweep_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry, int n_cycles,
+                    int mode, uint32_t* V, uint16_t* L, int64_t* improved) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD || n_cycles < 0 || !entries_ok(c, entry)) return -1;
+    for (int64_t x = 0; x < c->nr; x++) { V[x] = ORC_INF; L[x] = ORC_NONE; }
+    V[start] = 0;
+    if (orc_seed(c, B, start, entry, V, L) != 0) return -1;
+    return orc_layers(c, B, 0, 6 * n_cycles, mode, V, L, improved);
+}
+
 /* ----------------------------------------------------- Dijkstra (Section VIII.A)
  * Indexed binary heap kept in two arrays, heap position of a vertex and the
  * vertex at a heap position, keyed by the value array itself. */
@@ -615,7 +662,10 @@ static void heap_down(iheap* h, int64_t k) {
     }
 }
 
-int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* Vinf) {
+/* entry (optional): the start's own transition edges T(start) -> M_mu(start)
+ * weigh entry[mu] instead of ct (the start state of Section XII). */
+static int dijkstra_from(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                         uint32_t* Vinf) {
     if (start < 0 || start >= c->nr || B[start] == ORC_HARD) return -1;
     star_graph g;
     if (graph_build(c, B, &g) != 0) return -1;
@@ -651,7 +701,8 @@ int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* V
         uint32_t du = h.key[u];
         if (du == ORC_INF) break;
         if (u < nr) {
-            for (int m = 0; m < 6; m++) RELAX((1 + m) * nr + u, g.w_tm[m][u]);
+            for (int m = 0; m < 6; m++)
+                RELAX((1 + m) * nr + u, (entry && u == start) ? entry[m] : g.w_tm[m][u]);
         } else {
             int m = (int)(u / nr) - 1;
             int64_t x = u % nr;
@@ -663,6 +714,16 @@ int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* V
     for (int64_t x = 0; x < nr; x++) Vinf[x] = B[x] == ORC_HARD ? ORC_INF : h.key[x];
     free(h.key); free(h.heap); free(h.pos); free(done); graph_free(&g);
     return 0;
+}
+
+int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* Vinf) {
+    return dijkstra_from(c, B, start, NULL, Vinf);
+}
+
+int orc_dijkstra_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                       uint32_t* Vinf) {
+    if (!entries_ok(c, entry)) return -1;
+    return dijkstra_from(c, B, start, entry, Vinf);
 }
 
 /* ------------------------------------------------------------ brute force
@@ -698,7 +759,10 @@ static void bf_explore(bf_state* s, int layer, int64_t x, uint32_t cost) {
     }
 }
 
-int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* Vbest) {
+/* With entry: before layer 0, at most one segment of any maneuver mu with
+ * entry[mu] < ct leaves the start, entered at entry[mu] (the start layer). */
+static int bruteforce_from(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                           int n_cycles, uint32_t* Vbest) {
     if (start < 0 || start >= c->nr || B[start] == ORC_HARD) return -1;
     bf_state s = {c, B, 6 * n_cycles, NULL, Vbest};
     s.seen = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(s.layers + 1) * c->nr);
@@ -706,8 +770,30 @@ int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cyc
     for (int64_t k = 0; k < (int64_t)(s.layers + 1) * c->nr; k++) s.seen[k] = ORC_INF;
     for (int64_t x = 0; x < c->nr; x++) Vbest[x] = ORC_INF;
     bf_explore(&s, 0, start, 0);
+    for (int mu = 0; entry && mu < 6; mu++) {
+        if (entry[mu] >= c->ct) continue;
+        int n = is_turn(mu) ? c->nt : c->nx;
+        uint32_t run = entry[mu];
+        int64_t y = start;
+        for (int d = 1; d < n; d++) {
+            run = sadd(run, orc_edge(c, B, mu, y));
+            y = orc_succ(c, mu, y);
+            if (run == ORC_INF) break;
+            if (B[y] != ORC_HARD) bf_explore(&s, 0, y, run);
+        }
+    }
     free(s.seen);
     return 0;
+}
+
+int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* Vbest) {
+    return bruteforce_from(c, B, start, NULL, n_cycles, Vbest);
+}
+
+int orc_bruteforce_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                         int n_cycles, uint32_t* Vbest) {
+    if (!entries_ok(c, entry)) return -1;
+    return bruteforce_from(c, B, start, entry, n_cycles, Vbest);
 }
 
 /* ------------------------------------------------------------ extraction
@@ -745,6 +831,51 @@ int orc_extract(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t 
             seg[6 * b + k] = t;
         }
     return n;
+}
+
+/* ------------------------------------------------------------ goal search
+ * Section IX: a goal set instead of one exact pose, each pose scored by a
+ * reward that falls with its distance from an ideal pose; the best pose
+ * maximises reward minus cost.  Reading (the form of the neighbourhood
+ * search in Appendix G): the score to minimise is
+ *     V(x) + bias_g + w_xy * (|dx| + |dy|) + w_theta * |dtheta|
+ * over every goal g and every reached pose x of its box |dx|, |dy| <= r_xy
+ * (inside the grid; the grid does not wrap) and |dtheta| <= r_theta (modulo
+ * N_theta, 2 r_theta < N_theta).  Ties go to the earlier goal, within a goal
+ * to the ideal pose itself, then to the box in raster order (dtheta, then
+ * dy, then dx increasing).  goals[g*8 + {x, y, theta, r_xy, r_theta, w_xy,
+ * w_theta, bias}].  Returns 0 with *cell and *score set, -1 if no pose of
+ * any box was reached, -2 for a malformed goal. */
+int orc_goal_search(const orc_ctx* c, const uint32_t* V, const int64_t* goals, int n, int64_t* cell,
+                    uint64_t* score) {
+    uint64_t best = UINT64_MAX;
+    int64_t at = -1;
+    for (int g = 0; g < n; g++) {
+        const int64_t* q = goals + 8 * (size_t)g;
+        int gx = (int)q[0], gy = (int)q[1], gt = (int)q[2], r = (int)q[3], rt = (int)q[4];
+        uint64_t wxy = (uint64_t)q[5], wt = (uint64_t)q[6], bias = (uint64_t)q[7];
+        if (gx < 0 || gx >= c->nx || gy < 0 || gy >= c->nx || gt < 0 || gt >= c->nt) return -2;
+        if (r < 0 || r > 255 || rt < 0 || rt > 255 || 2 * rt >= c->nt) return -2;
+        if (q[5] < 0 || q[5] > 0xFFFFFFFFll || q[6] < 0 || q[6] > 0xFFFFFFFFll || q[7] < 0 || q[7] > 0xFFFFFFFFll)
+            return -2;
+        for (int pass = 0; pass < 2; pass++) /* the ideal pose, then the box */
+            for (int dt = -rt; dt <= rt; dt++)
+                for (int dy = -r; dy <= r; dy++)
+                    for (int dx = -r; dx <= r; dx++) {
+                        if (pass == 0 && (dx || dy || dt)) continue;
+                        int x = gx + dx, y = gy + dy;
+                        if (x < 0 || x >= c->nx || y < 0 || y >= c->nx) continue;
+                        int64_t k = cell_of(c, x, y, gt + dt);
+                        if (V[k] == ORC_INF) continue;
+                        uint64_t sc = (uint64_t)V[k] + bias + wxy * (uint64_t)(abs(dx) + abs(dy)) +
+                                      wt * (uint64_t)abs(dt);
+                        if (sc < best) { best = sc; at = k; }
+                    }
+    }
+    if (at < 0) return -1;
+    *cell = at;
+    *score = best;
+    return 0;
 }
 
 /* ----------------------------------------------------------- soft obstacles

@@ -79,6 +79,25 @@ int orc_dijkstra(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* V
 int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles,
                    uint32_t* Vbest);
 
+/* Start state (Section XII): entry[mu] = cost of entering maneuver mu at the
+ * start (<= ct).  orc_seed applies the start layer -- each maneuver with
+ * entry[mu] < ct followed from the start alone -- to (V, L); orc_sweep_state
+ * is orc_sweep with the start layer before the N cycles.  Dijkstra and the
+ * exhaustive search with the start's transition edges weighted by entry. */
+int orc_seed(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+             uint32_t* V, uint16_t* L);
+int orc_sweep_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                    int n_cycles, int mode, uint32_t* V, uint16_t* L, int64_t* improved);
+int orc_dijkstra_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                       uint32_t* Vinf);
+int orc_bruteforce_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
+                         int n_cycles, uint32_t* Vbest);
+/* Goal search over a goal set (Section IX): the reached pose minimising
+ * V + bias + w_xy (|dx|+|dy|) + w_theta |dtheta| over every goal's box;
+ * goals[g*8 + {x, y, theta, r_xy, r_theta, w_xy, w_theta, bias}].  Returns 0
+ * (*cell, *score), -1 nothing reached, -2 malformed goal. */
+int orc_goal_search(const orc_ctx* c, const uint32_t* V, const int64_t* goals, int n,
+                    int64_t* cell, uint64_t* score);
 /* Label walk from goal (Section X, forward tracking).  Writes segments in
  * driving order: seg[k*6 + {mu, entry, exit, d, cost_lo16, cost_hi16}] as
  * int64.  Returns segment count, -1 unreachable, -2 cap too small, -3
