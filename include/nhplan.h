@@ -148,6 +148,48 @@ int plan_sweep(plan_t* plan, plan_pose start, int n_cycles);
 int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out,
                  uint32_t* cost);
 
+/* Section XII: plan_sweep for a vehicle already under way.  entry[mu] is the
+ * cost of entering maneuver mu (cycle-order ids) at the start pose: ct
+ * (costs.transition) for a vehicle at rest in the transition state, 0 to
+ * continue the maneuver in progress without a transition cost, the rest of
+ * a transition in progress toward mu otherwise.  Every maneuver with
+ * entry[mu] < ct is first followed from the start alone (the start layer;
+ * maneuvers in cycle order, a cell keeps the first strictly cheaper value,
+ * labelled with that maneuver), then the N cycles run as in plan_sweep; the
+ * start keeps V = 0, so entering at ct stays possible.  With every entry
+ * equal to ct this is plan_sweep.  PLAN_EINVAL if an entry exceeds ct,
+ * otherwise the errors of plan_sweep (the range check counts the start
+ * layer as one more layer).  Async on the plan's stream. */
+int plan_sweep_state(plan_t* plan, plan_pose start, const uint32_t entry[6], int n_cycles);
+
+/* One goal of a goal set (Section IX): the poses of its box score
+ *   V + bias + w_xy * (|dx| + |dy|) + w_theta * |dtheta|
+ * (a reward falling with the distance from the ideal pose, turned into a
+ * cost).  The box is |dx|, |dy| <= radius_xy, clipped to the grid (which does
+ * not wrap), and |dtheta| <= radius_theta modulo N_theta. */
+typedef struct {
+    plan_pose pose;       /* the ideal goal pose */
+    int32_t radius_xy;    /* 0 .. 255 cells */
+    int32_t radius_theta; /* 0 .. 255 headings, 2 * radius_theta < N_theta */
+    uint32_t w_xy;        /* score per cell of |dx| + |dy| */
+    uint32_t w_theta;     /* score per heading of |dtheta| */
+    uint32_t bias;        /* score of choosing this goal at all */
+} plan_goal;
+
+#define PLAN_MAX_GOALS 65536
+
+/* Sections IX-X: find the best pose of a goal set on the device -- the
+ * reached pose with the smallest score over every goal's box; ties go to the
+ * earlier goal, then to the goal's ideal pose, then to the box in raster
+ * order (dtheta, dy, dx increasing) -- and back-track from it as
+ * plan_extract does, without V leaving the device.  Sets *best, *score and,
+ * as plan_extract, *cost = V(best), *n_out and `out`.  PLAN_EUNREACHABLE (*n_out
+ * = 0, *cost = PLAN_INF, *score = UINT64_MAX) when no pose of any box was
+ * reached; PLAN_EINVAL for 0 or more than PLAN_MAX_GOALS goals or a goal out
+ * of range.  Synchronises. */
+int plan_extract_goal_set(plan_t* plan, const plan_goal* goals, int n_goals, plan_segment* out, int cap,
+                          int* n_out, uint32_t* cost, plan_pose* best, uint64_t* score);
+
 /* One timed kernel shape of plan_autotune. */
 typedef struct {
     int32_t kind;  /* 0 turn kernel, 1 straight kernel */

@@ -19,6 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libnhplan.so")
 
 PLAN_OK = 0
+PLAN_EINVAL = -1
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNREACHABLE", -6: "ERANGE",
           -7: "EINTERNAL", -8: "ESTATE"}
 PLAN_EUNREACHABLE = -5
@@ -80,6 +81,11 @@ class Segment(C.Structure):
                 ("cost", C.c_uint32)]
 
 
+class Goal(C.Structure):
+    _fields_ = [("pose", Pose), ("radius_xy", C.c_int32), ("radius_theta", C.c_int32), ("w_xy", C.c_uint32),
+                ("w_theta", C.c_uint32), ("bias", C.c_uint32)]
+
+
 _lib = None
 
 
@@ -120,6 +126,12 @@ def lib():
         L.plan_last_error.restype = C.c_char_p
         L.plan_last_error.argtypes = []
         L.plan_reach_sweep.restype = C.c_int
+        L.plan_sweep_state.restype = C.c_int
+        L.plan_sweep_state.argtypes = [vp, Pose, C.POINTER(C.c_uint32), C.c_int]
+        L.plan_extract_goal_set.restype = C.c_int
+        L.plan_extract_goal_set.argtypes = [vp, C.POINTER(Goal), C.c_int, C.POINTER(Segment), C.c_int,
+                                            C.POINTER(C.c_int), C.POINTER(C.c_uint32), C.POINTER(Pose),
+                                            C.POINTER(C.c_uint64)]
         L.plan_reach_sweep.argtypes = [vp, Pose, C.c_int]
         L.plan_reach_extract.restype = C.c_int
         L.plan_reach_extract.argtypes = [vp, Pose, C.POINTER(Segment), C.c_int, C.POINTER(C.c_int),
@@ -246,6 +258,20 @@ class Planner:
     def sweep(self, start, n_cycles: int):
         _check(lib().plan_sweep(self._h, Pose(*[int(v) for v in start]), int(n_cycles)), "plan_sweep")
 
+    def sweep_state(self, start, entry, n_cycles: int):
+        """plan_sweep_state: entry[mu] = cost of entering maneuver mu (cycle
+        order LF, SF, RB, RF, SB, LB) at the start, at most the transition cost."""
+        e = (C.c_uint32 * 6)(*[int(v) for v in entry])
+        if len(entry) != 6:
+            raise ValueError("entry needs one cost per maneuver")
+        _check(lib().plan_sweep_state(self._h, Pose(*[int(v) for v in start]), e, int(n_cycles)),
+               "plan_sweep_state")
+
+    @staticmethod
+    def _segments(segs, n):
+        return [dict(mu=s.maneuver, entry=(s.entry.x, s.entry.y, s.entry.theta),
+                     exit=(s.exit.x, s.exit.y, s.exit.theta), steps=s.steps, cost=s.cost) for s in segs[:n]]
+
     def extract(self, goal, cap: int = 1024) -> Optional[PlanResult]:
         segs = (Segment * cap)()
         n = C.c_int(0)
@@ -254,9 +280,25 @@ class Planner:
         if rc == PLAN_EUNREACHABLE:
             return None
         _check(rc, "plan_extract")
-        out = [dict(mu=s.maneuver, entry=(s.entry.x, s.entry.y, s.entry.theta),
-                    exit=(s.exit.x, s.exit.y, s.exit.theta), steps=s.steps, cost=s.cost) for s in segs[:n.value]]
-        return PlanResult(int(cost.value), out)
+        return PlanResult(int(cost.value), self._segments(segs, n.value))
+
+    def extract_goal_set(self, goals, cap: int = 1024):
+        """plan_extract_goal_set over (x, y, theta, r_xy, r_theta, w_xy,
+        w_theta, bias) tuples.  Returns (best pose, score, PlanResult) or None
+        when no pose of any box was reached."""
+        arr = (Goal * len(goals))(*[Goal(Pose(*[int(v) for v in g[:3]]), *[int(v) for v in g[3:8]]) for g in goals])
+        segs = (Segment * cap)()
+        n = C.c_int(0)
+        cost = C.c_uint32(0)
+        best = Pose()
+        score = C.c_uint64(0)
+        rc = lib().plan_extract_goal_set(self._h, arr, len(goals), segs, cap, C.byref(n), C.byref(cost),
+                                         C.byref(best), C.byref(score))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_extract_goal_set")
+        return (best.x, best.y, best.theta), int(score.value), PlanResult(int(cost.value),
+                                                                         self._segments(segs, n.value))
 
     def plan(self, start, goal, n_cycles: int) -> Optional[PlanResult]:
         self.render()

@@ -126,6 +126,22 @@ cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s
 // Label walk from each query's goal into its seg/status buffers.
 cudaError_t launch_extract(const Group& gr, cudaStream_t s);
 
+// Start state (Section XII): entry cost of each maneuver at the start pose.
+struct StartEntry {
+    uint32_t e[6];
+};
+// Best pose of one goal's box, or of the whole set: score, then rank (goal
+// index << 40 | position in the box, the ideal pose first), cell (-1: none).
+struct GoalBest {
+    uint64_t score, rank;
+    int64_t cell;
+};
+// The start layer on qd[0]'s volumes (after init, before pass 0).
+cudaError_t launch_seed(const QueryDesc* qd, const StartEntry& entry, cudaStream_t s);
+// Goal search over n goals (device array); writes qd[0].goal on the device.
+cudaError_t launch_goal_search(QueryDesc* qd, const plan_goal* goals, int n, GoalBest* per_goal, GoalBest* result,
+                               cudaStream_t s);
+
 // Maneuver-count reachability with bit vectors (reach.cu, extract.cu).
 cudaError_t launch_hard_bits(const uint16_t* B, uint32_t* H, int64_t nr, cudaStream_t s);
 cudaError_t launch_reach_init(uint32_t* R, int64_t nr, int64_t start, cudaStream_t s);

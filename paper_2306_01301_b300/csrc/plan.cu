@@ -197,14 +197,17 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : cuda_fail(e, "C
 
 const char* last_error_text() { return g_last_error; }
 
-int range_check(const plan_s* p, int n_cycles) {
-    // Every finite value is a sum over at most 6N segments of ct plus at most
-    // max(Nx, N_theta) - 1 edges; it must stay below the kernels' TH.
+int range_check_layers(const plan_s* p, int layers) {
+    // Every finite value is a sum over at most one segment per layer of ct
+    // plus at most max(Nx, N_theta) - 1 edges; it must stay below the
+    // kernels' TH.
     const double e_max = (double)(((uint64_t)p->w_max * p->img_max_soft) >> 8);
     const double bound =
-        6.0 * n_cycles * ((double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max);
+        (double)layers * ((double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max);
     return bound >= (double)TH ? PLAN_ERANGE : PLAN_OK;
 }
+
+int range_check(const plan_s* p, int n_cycles) { return range_check_layers(p, 6 * n_cycles); }
 
 int check_sweep(const plan_s* p, plan_pose start, int n_cycles) {
     if (n_cycles < 1 || n_cycles > 4096 || !pose_ok(p, start) || pose_hard(p, start)) return PLAN_EINVAL;
@@ -219,6 +222,9 @@ int upload_desc(plan_s* p) {
 
 namespace {
 
+// goals, then one GoalBest per goal, then the result
+size_t goal_buffer_bytes(int n) { return (size_t)n * (sizeof(plan_goal) + sizeof(GoalBest)) + sizeof(GoalBest); }
+
 void release(plan_s* p) {
     p->dfree(p->d_blob, p->blob_bytes);
     p->dfree(p->d_img, (size_t)p->nxy * 2);
@@ -229,6 +235,7 @@ void release(plan_s* p) {
     p->dfree(p->d_B, (size_t)p->nr * 2);
     p->dfree(p->d_seg, sizeof(plan_segment) * kDevSegCap);
     p->dfree(p->d_status, 16);
+    p->dfree(p->d_goals, goal_buffer_bytes(p->goal_cap));
     p->dfree(p->d_cnt, 32);
     p->dfree(p->d_qd, sizeof(QueryDesc));
     const size_t bits = (size_t)(p->nr / 8);
@@ -395,6 +402,78 @@ int create_plan(const plan_grid* grid, const plan_footprint* footprint, double t
 
 }  // namespace nhp
 
+namespace {
+
+int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) {
+    if (!p || n_cycles < 0 || n_cycles > 4096 || !pose_ok(p, start)) return PLAN_EINVAL;
+    if (!p->volumes) return PLAN_ESTATE;
+    if (!p->rendered) return PLAN_ESTATE;
+    if (pose_hard(p, start)) return PLAN_EINVAL;
+    bool seeded = false;
+    StartEntry se{};
+    if (entry) {
+        for (int m = 0; m < 6; m++) {
+            if (entry[m] > p->costs.transition) return PLAN_EINVAL;
+            se.e[m] = entry[m];
+            seeded |= entry[m] < p->costs.transition;
+        }
+    }
+    if (range_check_layers(p, 6 * n_cycles + (seeded ? 1 : 0)) != PLAN_OK) return PLAN_ERANGE;
+    p->qd.start = cell_index(p, start);
+    p->qd.n_cycles = n_cycles;
+    p->qd.v.improved = p->prof ? p->d_cnt : nullptr;
+    int rc = upload_desc(p);
+    if (rc != PLAN_OK) return rc;
+    const Group gr = p->group();
+    cudaStream_t s = p->stream;
+    int mk = mark_begin(p, K_INIT);
+    rc = cuda_rc(launch_init(gr, s));
+    p->launches++;
+    if (rc == PLAN_OK && seeded) {  // the start layer (Section XII)
+        rc = cuda_rc(launch_seed(p->d_qd, se, s));
+        p->launches++;
+    }
+    mark_end(p, mk);
+    // Passes 0 .. 4N of the cycle schedule (internal.h): the consecutive
+    // turns on one curve family, {RB, RF} and {LB of cycle c, LF of cycle
+    // c+1}, share a pass, so N cycles (6N maneuver layers) take 4N + 1.
+    const int np = pass_count(n_cycles);
+    for (int pass = 0; pass < np && rc == PLAN_OK; pass++) {
+        const bool turn = pass_is_turn(pass);
+        const int m = mark_begin(p, turn ? K_TURN : K_STRAIGHT);
+        Group g2 = gr;
+        g2.grid = turn ? p->turn_grid : p->straight_grid;
+        rc = cuda_rc(turn ? launch_turn(g2, pass, p->turn_variant, s) : launch_straight(g2, pass, p->straight_lines, s));
+        mark_end(p, m);
+        p->launches++;
+    }
+    return rc;
+}
+
+// Status of the label walk just launched: segment count, V(goal); copies the
+// segments in driving order.  Synchronises.
+int finish_extract(plan_s* p, plan_segment* out, int cap, int* n_out, uint32_t* cost) {
+    int32_t status[3] = {0, 0, 0};
+    int rc = cuda_rc(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc != PLAN_OK) return rc;
+    if (status[0] == -1) return PLAN_EUNREACHABLE;
+    if (status[0] < 0) return PLAN_EINTERNAL;
+    *cost = (uint32_t)(status[1] & 0xFFFF) | ((uint32_t)status[2] << 16);
+    *n_out = status[0];
+    if (status[0] > cap || status[0] > kDevSegCap) return PLAN_ERANGE;
+    if (status[0] > 0) {
+        rc = cuda_rc(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status[0], cudaMemcpyDeviceToHost,
+                                     p->stream));
+        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+        if (rc != PLAN_OK) return rc;
+        std::reverse(out, out + status[0]);  // the walk runs goal -> start
+    }
+    return PLAN_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int plan_create(const plan_grid* grid, const plan_footprint* footprint, double turn_radius_cells,
@@ -427,37 +506,11 @@ int plan_render_cspace(plan_t* p) {
     return rc;
 }
 
-int plan_sweep(plan_t* p, plan_pose start, int n_cycles) {
-    if (!p || n_cycles < 0 || n_cycles > 4096 || !pose_ok(p, start)) return PLAN_EINVAL;
-    if (!p->volumes) return PLAN_ESTATE;
-    if (!p->rendered) return PLAN_ESTATE;
-    if (pose_hard(p, start)) return PLAN_EINVAL;
-    if (range_check(p, n_cycles) != PLAN_OK) return PLAN_ERANGE;
-    p->qd.start = cell_index(p, start);
-    p->qd.n_cycles = n_cycles;
-    p->qd.v.improved = p->prof ? p->d_cnt : nullptr;
-    int rc = upload_desc(p);
-    if (rc != PLAN_OK) return rc;
-    const Group gr = p->group();
-    cudaStream_t s = p->stream;
-    int mk = mark_begin(p, K_INIT);
-    rc = cuda_rc(launch_init(gr, s));
-    mark_end(p, mk);
-    p->launches++;
-    // Passes 0 .. 4N of the cycle schedule (internal.h): the consecutive
-    // turns on one curve family, {RB, RF} and {LB of cycle c, LF of cycle
-    // c+1}, share a pass, so N cycles (6N maneuver layers) take 4N + 1.
-    const int np = pass_count(n_cycles);
-    for (int pass = 0; pass < np && rc == PLAN_OK; pass++) {
-        const bool turn = pass_is_turn(pass);
-        const int m = mark_begin(p, turn ? K_TURN : K_STRAIGHT);
-        Group g2 = gr;
-        g2.grid = turn ? p->turn_grid : p->straight_grid;
-        rc = cuda_rc(turn ? launch_turn(g2, pass, p->turn_variant, s) : launch_straight(g2, pass, p->straight_lines, s));
-        mark_end(p, m);
-        p->launches++;
-    }
-    return rc;
+int plan_sweep(plan_t* p, plan_pose start, int n_cycles) { return sweep_impl(p, start, n_cycles, nullptr); }
+
+int plan_sweep_state(plan_t* p, plan_pose start, const uint32_t entry[6], int n_cycles) {
+    if (!entry) return PLAN_EINVAL;
+    return sweep_impl(p, start, n_cycles, entry);
 }
 
 int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_out, uint32_t* cost) {
@@ -469,23 +522,50 @@ int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_o
     if (rc == PLAN_OK) rc = cuda_rc(launch_extract(p->group(), p->stream));
     p->launches++;
     if (rc != PLAN_OK) return rc;
-    int32_t status[3] = {0, 0, 0};
-    rc = cuda_rc(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
+    return finish_extract(p, out, cap, n_out, cost);
+}
+
+int plan_extract_goal_set(plan_t* p, const plan_goal* goals, int n_goals, plan_segment* out, int cap, int* n_out,
+                          uint32_t* cost, plan_pose* best, uint64_t* score) {
+    if (!p || !goals || n_goals < 1 || n_goals > PLAN_MAX_GOALS || !n_out || !cost || !best || !score || cap < 0 ||
+        (cap > 0 && !out))
+        return PLAN_EINVAL;
+    *n_out = 0;
+    *cost = PLAN_INF;
+    *score = ~0ull;
+    for (int i = 0; i < n_goals; i++) {
+        const plan_goal& q = goals[i];
+        if (!pose_ok(p, q.pose) || q.radius_xy < 0 || q.radius_xy > 255 || q.radius_theta < 0 ||
+            q.radius_theta > 255 || 2 * q.radius_theta >= p->nt)
+            return PLAN_EINVAL;
+    }
+    if (!p->volumes) return PLAN_ESTATE;
+    if (n_goals > p->goal_cap) {
+        p->dfree(p->d_goals, goal_buffer_bytes(p->goal_cap));
+        p->d_goals = (unsigned char*)p->dalloc(goal_buffer_bytes(n_goals));
+        p->goal_cap = p->d_goals ? n_goals : 0;
+        if (!p->d_goals) return PLAN_ENOMEM;
+    }
+    plan_goal* d_goal = reinterpret_cast<plan_goal*>(p->d_goals);
+    GoalBest* d_per = reinterpret_cast<GoalBest*>(p->d_goals + (size_t)p->goal_cap * sizeof(plan_goal));
+    GoalBest* d_res = d_per + p->goal_cap;
+    p->qd.goal = cell_index(p, goals[0].pose);  // replaced on the device by the chosen pose
+    int rc = upload_desc(p);
+    if (rc == PLAN_OK)
+        rc = cuda_rc(cudaMemcpyAsync(d_goal, goals, sizeof(plan_goal) * n_goals, cudaMemcpyHostToDevice, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(launch_goal_search(p->d_qd, d_goal, n_goals, d_per, d_res, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(launch_extract(p->group(), p->stream));
+    p->launches += 3;
+    GoalBest res{};
+    if (rc == PLAN_OK) rc = cuda_rc(cudaMemcpyAsync(&res, d_res, sizeof(res), cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
     if (rc != PLAN_OK) return rc;
-    if (status[0] == -1) return PLAN_EUNREACHABLE;
-    if (status[0] < 0) return PLAN_EINTERNAL;
-    *cost = (uint32_t)(status[1] & 0xFFFF) | ((uint32_t)status[2] << 16);
-    *n_out = status[0];
-    if (status[0] > cap || status[0] > kDevSegCap) return PLAN_ERANGE;
-    if (status[0] > 0) {
-        rc = cuda_rc(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status[0], cudaMemcpyDeviceToHost,
-                                     p->stream));
-        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
-        if (rc != PLAN_OK) return rc;
-        std::reverse(out, out + status[0]);  // the walk runs goal -> start
-    }
-    return PLAN_OK;
+    if (res.cell < 0) return PLAN_EUNREACHABLE;
+    best->x = (int32_t)(res.cell & (p->nx - 1));
+    best->y = (int32_t)((res.cell >> p->lx) & (p->nx - 1));
+    best->theta = (int32_t)(res.cell >> (2 * p->lx));
+    *score = res.score;
+    return finish_extract(p, out, cap, n_out, cost);
 }
 
 int plan_set_kernel_shapes(plan_t* p, int turn_variant, int turn_grid, int straight_lines, int straight_grid) {

@@ -43,6 +43,8 @@ struct plan_s {
     uint16_t* d_B = nullptr;
     plan_segment* d_seg = nullptr;
     int* d_status = nullptr;
+    unsigned char* d_goals = nullptr;  // goal-set search: goals, per-goal bests, result
+    int goal_cap = 0;
     bool rendered = false;
     bool volumes = true;  // V and L allocated (scenes of a server hold only B)
     // maneuver-count reachability (Appendix C): hard bits, their transposed
@@ -90,6 +92,7 @@ int64_t cell_index(const plan_s* p, plan_pose q);
 bool pose_hard(const plan_s* p, plan_pose q);
 // PLAN_ERANGE when finite costs of an N-cycle sweep could reach TH.
 int range_check(const plan_s* p, int n_cycles);
+int range_check_layers(const plan_s* p, int layers);
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
 // plan_create, optionally without the V and L volumes (a cached scene).
