@@ -80,6 +80,8 @@ def lib():
         L.orc_extract.restype = C.c_int
         L.orc_extract.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         L.orc_soft_image.argtypes = [C.c_int, p, C.c_int, C.c_int, p]
+        L.orc_set_transition.restype = C.c_int
+        L.orc_set_transition.argtypes = [p, p, p]
         L.orc_seed.restype = C.c_int
         L.orc_seed.argtypes = [p, p, C.c_int64, p, p, p]
         L.orc_sweep_state.restype = C.c_int
@@ -217,6 +219,15 @@ class Oracle:
                                 int(n_cycles), _ptr(V)) != 0:
             raise ValueError("bruteforce failed")
         return V
+
+    # ------------------------------------------------- Section V.A, Fig. 9
+    def set_transition(self, cost_in, cost_out):
+        """Per-maneuver Star transition edges: entering mu costs cost_in[mu],
+        returning to the transition state cost_out[mu] (cycle-order ids)."""
+        ci = np.ascontiguousarray(cost_in, dtype=np.uint32)
+        co = np.ascontiguousarray(cost_out, dtype=np.uint32)
+        if ci.shape != (6,) or co.shape != (6,) or lib().orc_set_transition(self._c, _ptr(ci), _ptr(co)) != 0:
+            raise ValueError("transition costs need 6 + 6 values with every sum below 2^28")
 
     # ----------------------------------------------------------- Section XII
     def _entry(self, entry) -> np.ndarray:

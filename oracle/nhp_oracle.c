@@ -35,6 +35,7 @@ struct orc_ctx {
     double R;
     int half;
     uint32_t step_s, step_a, ct;
+    uint32_t cin[6], cout[6]; /* Star transition edges T->M_mu and M_mu->T (Fig. 9) */
     int32_t* beta;  /* beta(T), eq. 13 context */
     uint8_t* psi2;  /* 2*Psi(T), eq. 13 */
     uint8_t* iflag; /* I(T), eq. 19 */
@@ -65,6 +66,7 @@ orc_ctx* orc_create(int nx_log2, int nt_log2, double R, int half_shift,
     c->nr = (int64_t)c->nx * c->nx * c->nt;
     c->R = R; c->half = half_shift ? 1 : 0;
     c->step_s = step_straight; c->step_a = step_scale; c->ct = ct;
+    for (int m = 0; m < 6; m++) { c->cin[m] = ct; c->cout[m] = 0; }
     int nt = c->nt, nx = c->nx;
     c->beta = (int32_t*)malloc(sizeof(int32_t) * nt);
     c->psi2 = (uint8_t*)malloc(nt);
@@ -116,6 +118,17 @@ orc_ctx* orc_create(int nx_log2, int nt_log2, double R, int half_shift,
     /* Section V.D: a turn edge spans 2 pi R / N_theta. */
     c->wA = (uint32_t)lround((double)step_scale * (2.0 * ORC_PI) * R / (double)nt);
     return c;
+}
+
+/* Star transition edges per maneuver (Section V.A, Fig. 9): entering
+ * maneuver mu from the transition state costs cin[mu], returning to it
+ * cout[mu] (changing gear or steering, speeding up, slowing down).  Each sum
+ * must stay below 2^28. */
+int orc_set_transition(orc_ctx* c, const uint32_t* cin, const uint32_t* cout) {
+    for (int m = 0; m < 6; m++)
+        if ((uint64_t)cin[m] + cout[m] >= (1u << 28)) return -1;
+    for (int m = 0; m < 6; m++) { c->cin[m] = cin[m]; c->cout[m] = cout[m]; }
+    return 0;
 }
 
 void orc_destroy(orc_ctx* c) {
@@ -360,7 +373,8 @@ uint32_t orc_edge(const orc_ctx* c, const uint16_t* B, int mu, int64_t cell) {
 
 /* ------------------------------------------------- explicit Star graph (Fig. 9)
  * Per cell X: vertex T(X) (transition state) and M_mu(X) for the six
- * maneuvers; edges T->M_mu (weight ct), M_mu->T (weight 0), and the maneuver
+ * maneuvers; edges T->M_mu (weight cin[mu], ct by default), M_mu->T (weight
+ * cout[mu], 0 by default), and the maneuver
  * edge M_mu(X) -> M_mu(succ_mu(X)) (weight orc_edge).  A hard cell has no
  * transition vertex: its T<->M edges are absent (weight INF). */
 typedef struct {
@@ -389,8 +403,8 @@ static int graph_build(const orc_ctx* c, const uint16_t* B, star_graph* g) {
             int hard = B[x] == ORC_HARD;
             g->succ[m][x] = (uint32_t)orc_succ(c, m, x);
             g->w_mm[m][x] = orc_edge(c, B, m, x);
-            g->w_tm[m][x] = hard ? ORC_INF : c->ct;
-            g->w_mt[m][x] = hard ? ORC_INF : 0u;
+            g->w_tm[m][x] = hard ? ORC_INF : c->cin[m];
+            g->w_mt[m][x] = hard ? ORC_INF : c->cout[m];
         }
     }
     return 0;
@@ -525,14 +539,14 @@ static int layer_lockstep(const orc_ctx* c, const uint16_t* B, int mu, layer_io*
                 int hard = B[x] == ORC_HARD;
                 uint32_t u = io->Vin[x];
                 if (q >= n) {
-                    uint32_t cand = hard ? ORC_INF : v[k];
+                    uint32_t cand = hard ? ORC_INF : sadd(v[k], c->cout[mu]);
                     if (cand < u) {
                         io->Vout[x] = cand;
                         io->L[x] = (uint16_t)((io->mu << 13) | (q - qe[k]));
                         io->improved++;
                     }
                 }
-                uint32_t t = hard ? ORC_INF : sadd(u, c->ct);
+                uint32_t t = hard ? ORC_INF : sadd(u, c->cin[mu]);
                 if (t < v[k]) { v[k] = t; qe[k] = q; }
                 v[k] = sadd(v[k], orc_edge(c, B, mu, x));
                 cur[k] = orc_succ(c, mu, x);
@@ -583,17 +597,18 @@ int orc_sweep(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, 
 
 /* ------------------------------------------------ start state (Section XII)
  * A vehicle already under way when the plan starts: entry[mu] is what
- * entering maneuver mu at the start pose costs -- ct for a vehicle at rest in
- * the transition state, 0 for the maneuver in progress (no transition cost
- * for it), the rest of a transition in progress toward mu.  Reading of
- * Section XII's "first maneuver kernel of that type without a transition
- * cost": every maneuver with entry[mu] < ct is first followed from the start
- * pose alone (the start layer, maneuvers in cycle order, strict
- * improvement), then the N cycles run as from rest.  The start keeps V = 0,
- * so entering at ct stays possible and entries above ct are refused. */
+ * entering maneuver mu at the start pose costs -- cin[mu] (ct) for a vehicle
+ * at rest in the transition state, 0 for the maneuver in progress (no
+ * transition cost for it), the rest of a transition in progress toward mu.
+ * Reading of Section XII's "first maneuver kernel of that type without a
+ * transition cost": every maneuver with entry[mu] < cin[mu] is first
+ * followed from the start pose alone (the start layer, maneuvers in cycle
+ * order, strict improvement; leaving the maneuver still costs cout[mu]),
+ * then the N cycles run as from rest.  The start keeps V = 0, so entering at
+ * cin[mu] stays possible and entries above it are refused. */
 static int entries_ok(const orc_ctx* c, const uint32_t* entry) {
     for (int m = 0; m < 6; m++)
-        if (entry[m] > c->ct) return 0;
+        if (entry[m] > c->cin[m]) return 0;
     return 1;
 }
 
@@ -602,7 +617,7 @@ int orc_seed(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t*
     if (start < 0 || start >= c->nr || B[start] == ORC_HARD || !entries_ok(c, entry)) return -1;
     for (int l = 0; l < 6; l++) {
         int mu = cycle_order[l];
-        if (entry[mu] >= c->ct) continue;
+        if (entry[mu] >= c->cin[mu]) continue;
         int n = is_turn(mu) ? c->nt : c->nx; /* the curve closes after n steps */
         uint32_t run = entry[mu];
         int64_t y = start;
@@ -610,8 +625,9 @@ int orc_seed(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t*
             run = sadd(run, orc_edge(c, B, mu, y));
             y = orc_succ(c, mu, y);
             if (run == ORC_INF) break; /* a hard cell was left */
-            if (B[y] != ORC_HARD && run < V[y]) {
-                V[y] = run;
+            uint32_t back = sadd(run, c->cout[mu]); /* back in the transition state */
+            if (B[y] != ORC_HARD && back < V[y]) {
+                V[y] = back;
                 L[y] = (uint16_t)((mu << 13) | d);
             }
         }
@@ -749,18 +765,18 @@ static void bf_explore(bf_state* s, int layer, int64_t x, uint32_t cost) {
     bf_explore(s, layer + 1, x, cost); /* no segment in this layer */
     int mu = cycle_order[layer % 6];
     int n = is_turn(mu) ? c->nt : c->nx;
-    uint32_t run = sadd(cost, c->ct);
+    uint32_t run = sadd(cost, c->cin[mu]);
     int64_t y = x;
     for (int d = 1; d < n; d++) {
         run = sadd(run, orc_edge(c, s->B, mu, y));
         y = orc_succ(c, mu, y);
         if (run == ORC_INF) break;
-        if (s->B[y] != ORC_HARD) bf_explore(s, layer + 1, y, run);
+        if (s->B[y] != ORC_HARD) bf_explore(s, layer + 1, y, sadd(run, c->cout[mu]));
     }
 }
 
 /* With entry: before layer 0, at most one segment of any maneuver mu with
- * entry[mu] < ct leaves the start, entered at entry[mu] (the start layer). */
+ * entry[mu] < cin[mu] leaves the start, entered at entry[mu] (the start layer). */
 static int bruteforce_from(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
                            int n_cycles, uint32_t* Vbest) {
     if (start < 0 || start >= c->nr || B[start] == ORC_HARD) return -1;
@@ -771,7 +787,7 @@ static int bruteforce_from(const orc_ctx* c, const uint16_t* B, int64_t start, c
     for (int64_t x = 0; x < c->nr; x++) Vbest[x] = ORC_INF;
     bf_explore(&s, 0, start, 0);
     for (int mu = 0; entry && mu < 6; mu++) {
-        if (entry[mu] >= c->ct) continue;
+        if (entry[mu] >= c->cin[mu]) continue;
         int n = is_turn(mu) ? c->nt : c->nx;
         uint32_t run = entry[mu];
         int64_t y = start;
@@ -779,7 +795,7 @@ static int bruteforce_from(const orc_ctx* c, const uint16_t* B, int64_t start, c
             run = sadd(run, orc_edge(c, B, mu, y));
             y = orc_succ(c, mu, y);
             if (run == ORC_INF) break;
-            if (B[y] != ORC_HARD) bf_explore(&s, 0, y, run);
+            if (B[y] != ORC_HARD) bf_explore(&s, 0, y, sadd(run, c->cout[mu]));
         }
     }
     free(s.seen);

@@ -30,6 +30,10 @@ typedef struct orc_ctx orc_ctx;
 orc_ctx* orc_create(int nx_log2, int nt_log2, double R, int half_shift,
                     uint32_t step_straight, uint32_t step_scale, uint32_t ct);
 void     orc_destroy(orc_ctx* c);
+/* Per-maneuver Star transition edges (Section V.A, Fig. 9): T -> M_mu costs
+ * cin[mu], M_mu -> T costs cout[mu]; by default cin = ct, cout = 0.  Every
+ * function below uses them.  Returns -1 if some cin + cout >= 2^28. */
+int      orc_set_transition(orc_ctx* c, const uint32_t* cin, const uint32_t* cout);
 
 /* Geometry tables (Section V.C, eqs. 11-24).  Arrays are caller-owned:
  * beta[nt], psi2[nt] (2*Psi), iflag[nt], jsign[nt], bshear[nt*nx] (B(y',T) at
@@ -80,7 +84,7 @@ int orc_bruteforce(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cyc
                    uint32_t* Vbest);
 
 /* Start state (Section XII): entry[mu] = cost of entering maneuver mu at the
- * start (<= ct).  orc_seed applies the start layer -- each maneuver with
+ * start (<= cin[mu]).  orc_seed applies the start layer -- each maneuver with
  * entry[mu] < ct followed from the start alone -- to (V, L); orc_sweep_state
  * is orc_sweep with the start layer before the N cycles.  Dijkstra and the
  * exhaustive search with the start's transition edges weighted by entry. */
