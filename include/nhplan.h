@@ -148,16 +148,28 @@ int plan_sweep(plan_t* plan, plan_pose start, int n_cycles);
 int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out,
                  uint32_t* cost);
 
+/* Section V.A, Fig. 9: per-maneuver transition edges of the Star graph.
+ * Entering maneuver mu (cycle-order ids) from the transition state costs
+ * cost_in[mu], returning to it cost_out[mu] -- the time of changing gear or
+ * steering and of speeding up or slowing down, e.g. a dearer entry into the
+ * backward maneuvers.  Until this is called every cost_in is
+ * costs.transition and every cost_out 0.  Applies to later sweeps of this
+ * plan (plan_sweep, plan_sweep_state, plan_autotune).  PLAN_EINVAL if some
+ * cost_in[mu] + cost_out[mu] >= 2^28. */
+int plan_set_transition_costs(plan_t* plan, const uint32_t cost_in[6], const uint32_t cost_out[6]);
+
 /* Section XII: plan_sweep for a vehicle already under way.  entry[mu] is the
- * cost of entering maneuver mu (cycle-order ids) at the start pose: ct
- * (costs.transition) for a vehicle at rest in the transition state, 0 to
- * continue the maneuver in progress without a transition cost, the rest of
- * a transition in progress toward mu otherwise.  Every maneuver with
- * entry[mu] < ct is first followed from the start alone (the start layer;
- * maneuvers in cycle order, a cell keeps the first strictly cheaper value,
- * labelled with that maneuver), then the N cycles run as in plan_sweep; the
- * start keeps V = 0, so entering at ct stays possible.  With every entry
- * equal to ct this is plan_sweep.  PLAN_EINVAL if an entry exceeds ct,
+ * cost of entering maneuver mu (cycle-order ids) at the start pose: its
+ * cost_in (ct = costs.transition by default) for a vehicle at rest in the
+ * transition state, 0 to continue the maneuver in progress without a
+ * transition cost, the rest of a transition in progress toward mu otherwise.
+ * Every maneuver with entry[mu] < cost_in[mu] is first followed from the
+ * start alone (the start layer; maneuvers in cycle order, a cell keeps the
+ * first strictly cheaper value, labelled with that maneuver; leaving still
+ * costs cost_out[mu]), then the N cycles run as in plan_sweep; the start
+ * keeps V = 0, so entering at cost_in stays possible.  With every entry
+ * equal to cost_in this is plan_sweep.  PLAN_EINVAL if an entry exceeds
+ * cost_in,
  * otherwise the errors of plan_sweep (the range check counts the start
  * layer as one more layer).  Async on the plan's stream. */
 int plan_sweep_state(plan_t* plan, plan_pose start, const uint32_t entry[6], int n_cycles);

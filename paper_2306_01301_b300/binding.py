@@ -126,6 +126,8 @@ def lib():
         L.plan_last_error.restype = C.c_char_p
         L.plan_last_error.argtypes = []
         L.plan_reach_sweep.restype = C.c_int
+        L.plan_set_transition_costs.restype = C.c_int
+        L.plan_set_transition_costs.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.plan_sweep_state.restype = C.c_int
         L.plan_sweep_state.argtypes = [vp, Pose, C.POINTER(C.c_uint32), C.c_int]
         L.plan_extract_goal_set.restype = C.c_int
@@ -257,6 +259,15 @@ class Planner:
 
     def sweep(self, start, n_cycles: int):
         _check(lib().plan_sweep(self._h, Pose(*[int(v) for v in start]), int(n_cycles)), "plan_sweep")
+
+    def set_transition_costs(self, cost_in, cost_out):
+        """plan_set_transition_costs: per-maneuver Star transition edges
+        (cycle order LF, SF, RB, RF, SB, LB)."""
+        if len(cost_in) != 6 or len(cost_out) != 6:
+            raise ValueError("six entering and six leaving costs")
+        ci = (C.c_uint32 * 6)(*[int(v) for v in cost_in])
+        co = (C.c_uint32 * 6)(*[int(v) for v in cost_out])
+        _check(lib().plan_set_transition_costs(self._h, ci, co), "plan_set_transition_costs")
 
     def sweep_state(self, start, entry, n_cycles: int):
         """plan_sweep_state: entry[mu] = cost of entering maneuver mu (cycle

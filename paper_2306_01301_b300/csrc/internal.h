@@ -37,7 +37,12 @@ struct Run {
 
 struct DevGrid {
     int lx, lt, nx, nt, mx, mt;
-    uint32_t wA, ct;
+    uint32_t wA;
+    // Star transition edges (Fig. 9): ctm[mu] = cost of entering plus
+    // leaving maneuver mu.  Every segment takes both edges, so charging the
+    // sum on entering stores the same values and labels; cout[mu] alone is
+    // what the start layer adds after an entry cost of its own.
+    uint32_t ctm[6], cout[6];
     const int4* beta4;       // per heading: (beta_0, beta_3, beta_2, beta_1), raw
     const PlaneInfo* plane;  // per heading
     const int16_t* bshear;   // [T*nx + y'] B(y', T), eq. 22

@@ -197,13 +197,28 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : cuda_fail(e, "C
 
 const char* last_error_text() { return g_last_error; }
 
+uint64_t max_transition(const plan_s* p) {
+    uint64_t m = 0;
+    for (int k = 0; k < 6; k++) m = std::max<uint64_t>(m, (uint64_t)p->cin[k] + p->cout[k]);
+    return m;
+}
+
+void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout) {
+    for (int k = 0; k < 6; k++) {
+        p->cin[k] = cin[k];
+        p->cout[k] = cout[k];
+        p->g.ctm[k] = p->qd.g.ctm[k] = cin[k] + cout[k];
+        p->g.cout[k] = p->qd.g.cout[k] = cout[k];
+    }
+}
+
 int range_check_layers(const plan_s* p, int layers) {
     // Every finite value is a sum over at most one segment per layer of ct
     // plus at most max(Nx, N_theta) - 1 edges; it must stay below the
     // kernels' TH.
     const double e_max = (double)(((uint64_t)p->w_max * p->img_max_soft) >> 8);
     const double bound =
-        (double)layers * ((double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max);
+        (double)layers * ((double)max_transition(p) + (double)(std::max(p->nx, p->nt) - 1) * e_max);
     return bound >= (double)TH ? PLAN_ERANGE : PLAN_OK;
 }
 
@@ -370,7 +385,10 @@ int create_plan(const plan_grid* grid, const plan_footprint* footprint, double t
     DevGrid& g = p->g;
     g.lx = p->lx; g.lt = p->lt; g.nx = p->nx; g.nt = p->nt; g.mx = p->nx - 1; g.mt = p->nt - 1;
     g.wA = p->wA;
-    g.ct = p->costs.transition;
+    for (int k = 0; k < 6; k++) {
+        p->cin[k] = g.ctm[k] = p->costs.transition;
+        p->cout[k] = g.cout[k] = 0;
+    }
     g.beta4 = (const int4*)(p->d_blob + o_beta);
     g.plane = (const PlaneInfo*)(p->d_blob + o_plane);
     g.bshear = (const int16_t*)(p->d_blob + o_bsh);
@@ -413,9 +431,9 @@ int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) 
     StartEntry se{};
     if (entry) {
         for (int m = 0; m < 6; m++) {
-            if (entry[m] > p->costs.transition) return PLAN_EINVAL;
+            if (entry[m] > p->cin[m]) return PLAN_EINVAL;
             se.e[m] = entry[m];
-            seeded |= entry[m] < p->costs.transition;
+            seeded |= entry[m] < p->cin[m];
         }
     }
     if (range_check_layers(p, 6 * n_cycles + (seeded ? 1 : 0)) != PLAN_OK) return PLAN_ERANGE;
@@ -507,6 +525,14 @@ int plan_render_cspace(plan_t* p) {
 }
 
 int plan_sweep(plan_t* p, plan_pose start, int n_cycles) { return sweep_impl(p, start, n_cycles, nullptr); }
+
+int plan_set_transition_costs(plan_t* p, const uint32_t cost_in[6], const uint32_t cost_out[6]) {
+    if (!p || !cost_in || !cost_out) return PLAN_EINVAL;
+    for (int k = 0; k < 6; k++)
+        if ((uint64_t)cost_in[k] + cost_out[k] >= (1u << 28)) return PLAN_EINVAL;
+    set_transition(p, cost_in, cost_out);
+    return PLAN_OK;
+}
 
 int plan_sweep_state(plan_t* p, plan_pose start, const uint32_t entry[6], int n_cycles) {
     if (!entry) return PLAN_EINVAL;

@@ -14,6 +14,7 @@ struct plan_s {
     int64_t nxy = 0, nr = 0;
     double R = 0;
     plan_costs costs{};
+    uint32_t cin[6] = {}, cout[6] = {};  // Star transition edges per maneuver
     plan_footprint fp{};
     cudaStream_t stream = nullptr;
     plan_allocator alloc{};
@@ -93,6 +94,7 @@ bool pose_hard(const plan_s* p, plan_pose q);
 // PLAN_ERANGE when finite costs of an N-cycle sweep could reach TH.
 int range_check(const plan_s* p, int n_cycles);
 int range_check_layers(const plan_s* p, int layers);
+void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout);
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
 // plan_create, optionally without the V and L volumes (a cached scene).

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(1024) k_seed(const QueryDesc* __restrict__ qd,
     const int64_t start = Q.start;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int mu = 0; mu < 6; mu++) {  // maneuver ids are the cycle order
-        if (entry.e[mu] >= g.ct) continue;
+        const uint32_t cin = g.ctm[mu] - g.cout[mu], cout = g.cout[mu];
+        if (entry.e[mu] >= cin) continue;
         const bool turn = mu != SF && mu != SB;
         const int n = turn ? g.nt : g.nx;  // the curve closes after n steps
         const uint32_t w = turn ? g.wA : g.plane[start >> (2 * g.lx)].wS;
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(1024) k_seed(const QueryDesc* __restrict__ qd,
                 if (lane < nw) wsum[lane] = t;
             }
             __syncthreads();
-            const uint64_t run = carry + x + (wid ? wsum[wid - 1] : 0);
+            // back in the transition state after the maneuver's leaving edge
+            const uint64_t run = carry + x + (wid ? wsum[wid - 1] : 0) + cout;
             // an edge left a hard cell (cost TH) or the value is not finite
             if (to >= 0 && run < TH && vol.B[to] != HARD && run < vol.V[to]) {
                 vol.V[to] = (uint32_t)run;

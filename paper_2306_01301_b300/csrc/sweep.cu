@@ -316,7 +316,7 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
             sm.cell[t] = make_int2((int)(uint32_t)((int64_t)(T0 + t) * nxy), (bx & g.mx) | ((by & g.mx) << 16));
     }
     __syncwarp();
-    const uint32_t w = g.wA, ct = g.ct;
+    const uint32_t w = g.wA;
     auto cell_index = [&](int T) -> uint32_t {
         const int2 c = sm.cell[T];
         if (row_uniform) return (uint32_t)c.x + (uint32_t)((xq + c.y) & g.mx);
@@ -343,14 +343,16 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
     }
     uint32_t chg = 0;
     int mb = scans & 1;
-    if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct, sec, lane, rank, 0, mb, a, live, sm.sh);
-    else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct, sec, lane, rank, 0, mb, a, live, sm.sh);
+    const uint32_t ct1 = g.ctm[mu1];
+    if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct1, sec, lane, rank, 0, mb, a, live, sm.sh);
+    else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct1, sec, lane, rank, 0, mb, a, live, sm.sh);
     scans++;
     if (mu2 >= 0) {
         live = live || chg != 0;
         mb = scans & 1;
-        if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct, sec, lane, rank, 1, mb, a, live, sm.sh);
-        else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct, sec, lane, rank, 1, mb, a, live, sm.sh);
+        const uint32_t ct2 = g.ctm[mu2];
+        if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct2, sec, lane, rank, 1, mb, a, live, sm.sh);
+        else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct2, sec, lane, rank, 1, mb, a, live, sm.sh);
         scans++;
     }
     if (vol.improved) {
@@ -537,7 +539,7 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
     uint32_t* Vp = vol.V + (int64_t)T * nxy;
     uint16_t* Lp = vol.L + (int64_t)T * nxy;
     const uint16_t* Bp = vol.B + (int64_t)T * nxy;
-    const uint32_t w = pi.wS, ct = g.ct;
+    const uint32_t w = pi.wS, ct = g.ctm[mu];
     const uint32_t mtag = (uint32_t)mu << 13;
     // Sweep order: dir > 0 visits y' = 0, 1, .., Nx-1 (q = y'); dir < 0
     // visits Nx-1, .., 1, 0 (q = Nx - y').  Starting at Nx-1 with nothing
@@ -694,7 +696,7 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
             Lp[id] = (uint16_t)(mtag | (uint32_t)(q - pv));
             nimp++;
         }
-        const uint32_t tt = u + g.ct;
+        const uint32_t tt = u + g.ctm[mu];
         if (tt < v) { v = tt; pv = q; }
         v += e;
     }
