@@ -67,6 +67,7 @@ extern "C" {
 #define PLAN_ESTATE (-8)       /* call out of order (e.g. sweep before render) */
 
 #define PLAN_INF 0xFFFFFFFFu
+#define PLAN_NO_DIRECTION 0xFFFFu /* no preferred heading (plan_set_direction_field) */
 #define PLAN_HARD 0xFFFFu
 #define PLAN_LABEL_NONE 0xFFFFu
 
@@ -147,6 +148,20 @@ int plan_sweep(plan_t* plan, plan_pose start, int n_cycles);
  * *n_out = 0, *cost = PLAN_INF) if the goal was not reached. */
 int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out,
                  uint32_t* cost);
+
+/* Section XVI, Fig. 19: direction penalties (stay in the right-hand lane,
+ * do not drive against a lane's direction).  heading: Nx*Nx host values
+ * (row y, column x, like the image), the preferred heading of poses whose
+ * reference cell that is, in [0, N_theta), or PLAN_NO_DIRECTION.  A pose
+ * whose heading differs from its cell's preferred heading by more than
+ * `tolerance` heading steps (circular distance) has its obstacle value
+ * scaled after rendering: B = min(B * penalty_q8 >> 8, 0xFFFE); hard poses
+ * stay hard.  Copied to the device; applies from the next
+ * plan_render_cspace (the plan must be rendered again).  NULL removes the
+ * field.  PLAN_EINVAL for a heading >= N_theta other than PLAN_NO_DIRECTION,
+ * tolerance outside [0, N_theta/2] or penalty_q8 outside [256, 65535].  The
+ * allocation-free plan_render_cspace_static does not apply it. */
+int plan_set_direction_field(plan_t* plan, const uint16_t* heading, int tolerance, uint32_t penalty_q8);
 
 /* Section V.A, Fig. 9: per-maneuver transition edges of the Star graph.
  * Entering maneuver mu (cycle-order ids) from the transition state costs

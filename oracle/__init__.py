@@ -82,6 +82,8 @@ def lib():
         L.orc_soft_image.argtypes = [C.c_int, p, C.c_int, C.c_int, p]
         L.orc_set_transition.restype = C.c_int
         L.orc_set_transition.argtypes = [p, p, p]
+        L.orc_direction.restype = C.c_int
+        L.orc_direction.argtypes = [p, p, p, C.c_int, C.c_uint32]
         L.orc_seed.restype = C.c_int
         L.orc_seed.argtypes = [p, p, C.c_int64, p, p, p]
         L.orc_sweep_state.restype = C.c_int
@@ -219,6 +221,16 @@ class Oracle:
                                 int(n_cycles), _ptr(V)) != 0:
             raise ValueError("bruteforce failed")
         return V
+
+    # ---------------------------------------------- Section XVI, Fig. 19
+    def direction(self, B: np.ndarray, heading: np.ndarray, tol: int, pen: int) -> np.ndarray:
+        """B with direction penalties applied (a copy): heading is Nx x Nx,
+        0xFFFF = no preferred heading."""
+        B = np.array(B, dtype=np.uint16, copy=True)
+        h = np.ascontiguousarray(heading, dtype=np.uint16)
+        if h.shape != (self.nx, self.nx) or lib().orc_direction(self._c, _ptr(B), _ptr(h), int(tol), int(pen)) != 0:
+            raise ValueError("bad direction field")
+        return B
 
     # ------------------------------------------------- Section V.A, Fig. 9
     def set_transition(self, cost_in, cost_out):

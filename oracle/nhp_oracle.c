@@ -894,6 +894,34 @@ int orc_goal_search(const orc_ctx* c, const uint32_t* V, const int64_t* goals, i
     return 0;
 }
 
+/* ------------------------------------------------------ direction penalties
+ * Section XVI, Fig. 19: costs that encode which side of the road to drive on
+ * and which way to move in an area.  Reading: a field gives each cell a
+ * preferred heading (0xFFFF: none); a pose whose own cell has one and whose
+ * heading differs from it by more than tol heading steps (circular distance)
+ * has its obstacle value scaled, B = min(floor(B * pen / 256), 0xFFFE), so
+ * every step there costs pen/256 times more; hard poses stay hard.  Applied
+ * to a rendered B.  Returns -1 for a heading >= N_theta other than 0xFFFF,
+ * tol outside [0, N_theta/2] or pen outside [256, 65535]. */
+int orc_direction(const orc_ctx* c, uint16_t* B, const uint16_t* heading, int tol, uint32_t pen) {
+    if (tol < 0 || tol > c->nt / 2 || pen < 256 || pen > 65535) return -1;
+    for (int64_t k = 0; k < (int64_t)c->nx * c->nx; k++)
+        if (heading[k] != 0xFFFF && heading[k] >= c->nt) return -1;
+    for (int T = 0; T < c->nt; T++)
+        for (int j = 0; j < c->nx; j++)
+            for (int i = 0; i < c->nx; i++) {
+                uint16_t h = heading[(size_t)j * c->nx + i];
+                int64_t k = cell_of(c, i, j, T);
+                if (h == 0xFFFF || B[k] == ORC_HARD) continue;
+                int d = abs(T - (int)h);
+                if (c->nt - d < d) d = c->nt - d;
+                if (d <= tol) continue;
+                uint32_t v = (uint32_t)B[k] * pen / 256u;
+                B[k] = (uint16_t)(v < 0xFFFEu ? v : 0xFFFEu);
+            }
+    return 0;
+}
+
 /* ----------------------------------------------------------- soft obstacles
  * Only distances below the radius matter, and any occupied cell at squared
  * distance < r^2 lies inside the (2r-1)^2 window, so the window search gives

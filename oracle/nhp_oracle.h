@@ -121,6 +121,11 @@ int orc_reach(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, 
 int orc_reach_extract(const orc_ctx* c, const uint16_t* B, const uint8_t* count, int64_t goal,
                       int64_t* seg, int cap);
 
+/* Direction penalties (Section XVI, Fig. 19) on a rendered B: poses whose
+ * heading is more than tol steps (circular) from their cell's preferred
+ * heading (heading[j*Nx + i], 0xFFFF none) get B = min(B*pen/256, 0xFFFE);
+ * hard stays hard.  Returns 0, -1 for bad arguments. */
+int orc_direction(const orc_ctx* c, uint16_t* B, const uint16_t* heading, int tol, uint32_t pen);
 /* Soft-obstacle image (Section VII): HARD where occ != 0, else 256 + pen with
  * pen = soft_max*(r2-d2)/r2 for squared Euclidean distance d2 < r2 to the
  * nearest occupied cell, else 256. */

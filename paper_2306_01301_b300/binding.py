@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libnhplan.so")
 
 PLAN_OK = 0
 PLAN_EINVAL = -1
+PLAN_NO_DIRECTION = 0xFFFF
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNREACHABLE", -6: "ERANGE",
           -7: "EINTERNAL", -8: "ESTATE"}
 PLAN_EUNREACHABLE = -5
@@ -126,6 +127,8 @@ def lib():
         L.plan_last_error.restype = C.c_char_p
         L.plan_last_error.argtypes = []
         L.plan_reach_sweep.restype = C.c_int
+        L.plan_set_direction_field.restype = C.c_int
+        L.plan_set_direction_field.argtypes = [vp, vp, C.c_int, C.c_uint32]
         L.plan_set_transition_costs.restype = C.c_int
         L.plan_set_transition_costs.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.plan_sweep_state.restype = C.c_int
@@ -259,6 +262,17 @@ class Planner:
 
     def sweep(self, start, n_cycles: int):
         _check(lib().plan_sweep(self._h, Pose(*[int(v) for v in start]), int(n_cycles)), "plan_sweep")
+
+    def set_direction_field(self, heading, tolerance: int = 0, penalty_q8: int = 256):
+        """plan_set_direction_field: preferred heading per cell (Nx x Nx,
+        PLAN_NO_DIRECTION = none), or None to remove the field."""
+        if heading is None:
+            _check(lib().plan_set_direction_field(self._h, None, 0, 256), "plan_set_direction_field")
+            return
+        h = np.ascontiguousarray(heading, dtype=np.uint16)
+        assert h.shape == (self.nx, self.nx)
+        _check(lib().plan_set_direction_field(self._h, _ptr(h), int(tolerance), int(penalty_q8)),
+               "plan_set_direction_field")
 
     def set_transition_costs(self, cost_in, cost_out):
         """plan_set_transition_costs: per-maneuver Star transition edges

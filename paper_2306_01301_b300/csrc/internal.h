@@ -15,6 +15,7 @@ namespace nhp {
 constexpr uint32_t TH = 0x40000000u;
 constexpr uint16_t HARD = 0xFFFFu;
 constexpr uint16_t NONE = 0xFFFFu;
+constexpr uint16_t NO_DIRECTION = PLAN_NO_DIRECTION;
 
 enum Maneuver { LF = 0, SF = 1, RB = 2, RF = 3, SB = 4, LB = 5 };
 
@@ -130,6 +131,10 @@ inline int64_t straight_items(int lx, int lt, int lines) { return ((int64_t)1 <<
 cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s);
 // Label walk from each query's goal into its seg/status buffers.
 cudaError_t launch_extract(const Group& gr, cudaStream_t s);
+
+// Direction penalties (Section XVI, Fig. 19) applied to a rendered B.
+cudaError_t launch_direction(uint16_t* B, const uint16_t* field, int lx, int lt, int tol, uint32_t pen,
+                             cudaStream_t s);
 
 // Start state (Section XII): entry cost of each maneuver at the start pose.
 struct StartEntry {

@@ -216,7 +216,9 @@ int range_check_layers(const plan_s* p, int layers) {
     // Every finite value is a sum over at most one segment per layer of ct
     // plus at most max(Nx, N_theta) - 1 edges; it must stay below the
     // kernels' TH.
-    const double e_max = (double)(((uint64_t)p->w_max * p->img_max_soft) >> 8);
+    const uint64_t b_max = p->d_dir ? std::min<uint64_t>((uint64_t)p->img_max_soft * p->dir_pen >> 8, HARD - 1u)
+                                    : p->img_max_soft;
+    const double e_max = (double)(((uint64_t)p->w_max * b_max) >> 8);
     const double bound =
         (double)layers * ((double)max_transition(p) + (double)(std::max(p->nx, p->nt) - 1) * e_max);
     return bound >= (double)TH ? PLAN_ERANGE : PLAN_OK;
@@ -251,6 +253,7 @@ void release(plan_s* p) {
     p->dfree(p->d_seg, sizeof(plan_segment) * kDevSegCap);
     p->dfree(p->d_status, 16);
     p->dfree(p->d_goals, goal_buffer_bytes(p->goal_cap));
+    p->dfree(p->d_dir, (size_t)p->nxy * 2);
     p->dfree(p->d_cnt, 32);
     p->dfree(p->d_qd, sizeof(QueryDesc));
     const size_t bits = (size_t)(p->nr / 8);
@@ -517,14 +520,41 @@ int plan_render_cspace(plan_t* p) {
     if (!p) return PLAN_EINVAL;
     const int mk = mark_begin(p, K_RENDER);
     int n = 0;
-    const int rc = cuda_rc(launch_render(p->group(), p->img_max_soft > 256, p->stream, &n));
+    int rc = cuda_rc(launch_render(p->group(), p->img_max_soft > 256, p->stream, &n));
     p->launches += n;
+    if (rc == PLAN_OK && p->d_dir) {
+        rc = cuda_rc(launch_direction(p->d_B, p->d_dir, p->lx, p->lt, p->dir_tol, p->dir_pen, p->stream));
+        p->launches++;
+    }
     mark_end(p, mk);
     if (rc == PLAN_OK) p->rendered = true;
     return rc;
 }
 
 int plan_sweep(plan_t* p, plan_pose start, int n_cycles) { return sweep_impl(p, start, n_cycles, nullptr); }
+
+int plan_set_direction_field(plan_t* p, const uint16_t* heading, int tolerance, uint32_t penalty_q8) {
+    if (!p) return PLAN_EINVAL;
+    if (!heading) {
+        p->dfree(p->d_dir, (size_t)p->nxy * 2);
+        p->d_dir = nullptr;
+        p->rendered = false;  // B still holds the penalties
+        return PLAN_OK;
+    }
+    if (tolerance < 0 || tolerance > p->nt / 2 || penalty_q8 < 256 || penalty_q8 > 65535) return PLAN_EINVAL;
+    for (int64_t i = 0; i < p->nxy; i++)
+        if (heading[i] != PLAN_NO_DIRECTION && heading[i] >= p->nt) return PLAN_EINVAL;
+    if (!p->d_dir) {
+        p->d_dir = (uint16_t*)p->dalloc((size_t)p->nxy * 2);
+        if (!p->d_dir) return PLAN_ENOMEM;
+    }
+    const int rc = cuda_rc(cudaMemcpyAsync(p->d_dir, heading, (size_t)p->nxy * 2, cudaMemcpyHostToDevice, p->stream));
+    if (rc != PLAN_OK) return rc;
+    p->dir_tol = tolerance;
+    p->dir_pen = penalty_q8;
+    p->rendered = false;  // B must be rendered again with the field
+    return PLAN_OK;
+}
 
 int plan_set_transition_costs(plan_t* p, const uint32_t cost_in[6], const uint32_t cost_out[6]) {
     if (!p || !cost_in || !cost_out) return PLAN_EINVAL;

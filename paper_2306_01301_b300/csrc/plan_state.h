@@ -15,6 +15,9 @@ struct plan_s {
     double R = 0;
     plan_costs costs{};
     uint32_t cin[6] = {}, cout[6] = {};  // Star transition edges per maneuver
+    uint16_t* d_dir = nullptr;            // direction field (Nx*Nx), or none
+    int dir_tol = 0;
+    uint32_t dir_pen = 256;
     plan_footprint fp{};
     cudaStream_t stream = nullptr;
     plan_allocator alloc{};
