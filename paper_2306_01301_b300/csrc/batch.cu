@@ -34,6 +34,7 @@ struct Lane {
     int nx_key = 0;        // the Nx shared by all queries (< 256), or 256: any Nx >= 256
     int lx_max = 0;
     bool uniform = true;   // one Nx: launches index queries directly
+    bool same_costs = true;  // every member has the same transition costs
     std::vector<int> members;  // query indices in launch order (N descending)
     std::vector<int> n_of;     // N of each member, same order
     plan_batch_lane_info info{};
@@ -133,6 +134,7 @@ Group lane_group(const plan_batch_s* b, const Lane& L, int nact) {
     g.lx = L.lx_max;
     g.lt = L.lt;
     g.max_runs = 1;
+    if (L.same_costs) g.ctm = b->plans[L.members[0]]->g.ctm;
     return g;
 }
 
@@ -501,8 +503,13 @@ int plan_batch_create(plan_t* const* plans, int n, uint32_t flags, const plan_al
         R->max_runs = std::max(R->max_runs, std::max(1, p->max_runs));
     }
     for (auto& L : b->lanes)
-        for (int m : L.members)
-            if (b->plans[m]->lx != b->plans[L.members[0]]->lx) L.uniform = false;
+        for (int m : L.members) {
+            const plan_s* a = b->plans[m];
+            const plan_s* z = b->plans[L.members[0]];
+            if (a->lx != z->lx) L.uniform = false;
+            for (int k = 0; k < 6; k++)
+                if (a->g.ctm[k] != z->g.ctm[k]) L.same_costs = false;
+        }
     const int rc = batch_init(b);
     if (rc != PLAN_OK) {
         release(b);

@@ -93,6 +93,11 @@ struct Group {
     const int32_t* item_off = nullptr;
     int64_t items = 0;
     int grid = 0;
+    // host copy of the transition costs (DevGrid::ctm) when every query of
+    // the launch has the same ones, else null: turn launches then pass the
+    // pass's two costs as kernel parameters instead of each tile reading
+    // them from its descriptor
+    const uint32_t* ctm = nullptr;
 };
 
 // Cycle schedule (Section XVI.A) with the turn pairs fused: N cycles are the
@@ -105,6 +110,15 @@ struct Group {
 //                               c = N-1)
 inline int pass_count(int n_cycles) { return n_cycles > 0 ? 4 * n_cycles + 1 : 0; }
 inline bool pass_is_turn(int p) { return (p & 1) == 0; }
+// Maneuvers of turn pass p, in scan order (the second is -1 for p = 0; the
+// last pass of a query may drop it, which needs no cost).
+inline void turn_pass_maneuvers(int p, int* mu1, int* mu2) {
+    if (p == 0) { *mu1 = LF; *mu2 = -1; }
+    else if ((p & 3) == 2) { *mu1 = RB; *mu2 = RF; }
+    else { *mu1 = LB; *mu2 = LF; }
+}
+// Kernel-parameter marker: read the cost from each query's descriptor.
+constexpr uint32_t kCostPerQuery = 0xFFFFFFFFu;
 
 // Launchers.  `pass` < 0 means "each query's own QueryDesc::pass"; queries
 // whose pass is outside 0 .. 4N do nothing.  Each returns cudaGetLastError().
@@ -131,6 +145,18 @@ inline int64_t straight_items(int lx, int lt, int lines) { return ((int64_t)1 <<
 cudaError_t launch_straight(const Group& gr, int pass, int lines, cudaStream_t s);
 // Label walk from each query's goal into its seg/status buffers.
 cudaError_t launch_extract(const Group& gr, cudaStream_t s);
+
+// Per-maneuver constants by a select chain: indexing the arrays with a
+// runtime maneuver would move the kernel's copy of DevGrid to local memory.
+__device__ __forceinline__ uint32_t pick6(const uint32_t (&a)[6], int mu) {
+    uint32_t r = a[0];
+    r = mu == 1 ? a[1] : r;
+    r = mu == 2 ? a[2] : r;
+    r = mu == 3 ? a[3] : r;
+    r = mu == 4 ? a[4] : r;
+    r = mu == 5 ? a[5] : r;
+    return r;
+}
 
 // Direction penalties (Section XVI, Fig. 19) applied to a rendered B.
 cudaError_t launch_direction(uint16_t* B, const uint16_t* field, int lx, int lt, int tol, uint32_t pen,

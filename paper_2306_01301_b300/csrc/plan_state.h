@@ -69,7 +69,11 @@ struct plan_s {
     DevGrid g{};
     nhp::QueryDesc qd{};             // this plan as one query (host copy)
     nhp::QueryDesc* d_qd = nullptr;  // ... and its device copy
-    nhp::Group group() const { return nhp::Group{d_qd, 1, lx, lt, max_runs > 0 ? max_runs : 1}; }
+    nhp::Group group() const {
+        nhp::Group r{d_qd, 1, lx, lt, max_runs > 0 ? max_runs : 1};
+        r.ctm = g.ctm;
+        return r;
+    }
     // profiling (plan_profile)
     bool prof = false;
     unsigned long long* d_cnt = nullptr;  // improved cells [0] turn, [1] straight; [2] turn tiles with any

@@ -554,6 +554,7 @@ int run_one(plan_server_s* v) {
     g.lx = sc->lx;
     g.lt = sc->lt;
     g.max_runs = 1;
+    g.ctm = sc->g.ctm;
     int64_t launches = 0;
     NHP_CK(launch_init(g, s));
     launches++;

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(1024) k_seed(const QueryDesc* __restrict__ qd,
     const int64_t start = Q.start;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int mu = 0; mu < 6; mu++) {  // maneuver ids are the cycle order
-        const uint32_t cin = g.ctm[mu] - g.cout[mu], cout = g.cout[mu];
+        const uint32_t cout = pick6(g.cout, mu), cin = pick6(g.ctm, mu) - cout;
         if (entry.e[mu] >= cin) continue;
         const bool turn = mu != SF && mu != SB;
         const int n = turn ? g.nt : g.nx;  // the curve closes after n steps

@@ -288,7 +288,7 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq
 // `scans` counts the block's scans so far (it picks the set of section maps).
 template <int K, int SL, int CL>
 __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int64_t tile, int rank,
-                                          TurnSmem<K, SL, CL>& sm, int& scans) {
+                                          TurnSmem<K, SL, CL>& sm, int& scans, uint32_t ct_a, uint32_t ct_b) {
     constexpr int NTL = K * SL;  // headings held by this block
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
     const DevGrid g = Q.g;
@@ -342,15 +342,16 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         live |= ob != HARD && vv < TH;
     }
     uint32_t chg = 0;
+    // the launch's costs (kernel parameters), else this query's own
+    const uint32_t ct1 = ct_a != kCostPerQuery ? ct_a : __ldg(Q.g.ctm + mu1);
     int mb = scans & 1;
-    const uint32_t ct1 = g.ctm[mu1];
     if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct1, sec, lane, rank, 0, mb, a, live, sm.sh);
     else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct1, sec, lane, rank, 0, mb, a, live, sm.sh);
     scans++;
     if (mu2 >= 0) {
         live = live || chg != 0;
         mb = scans & 1;
-        const uint32_t ct2 = g.ctm[mu2];
+        const uint32_t ct2 = ct_b != kCostPerQuery ? ct_b : __ldg(Q.g.ctm + mu2);
         if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct2, sec, lane, rank, 1, mb, a, live, sm.sh);
         else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct2, sec, lane, rank, 1, mb, a, live, sm.sh);
         scans++;
@@ -378,7 +379,7 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
 template <int K, int SL, int CL>
 __global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : (1024 / (32 * SL) < 1 ? 1 : 1024 / (32 * SL)))
 k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, int nq, int64_t items,
-       int tiles_per_q, int pass_all) {
+       int tiles_per_q, int pass_all, uint32_t ct_a, uint32_t ct_b) {
     __shared__ TurnSmem<K, SL, CL> sm;
     const int rank = CL == 1 ? 0 : (int)(blockIdx.x % CL);
     const int64_t stride = gridDim.x / CL;
@@ -396,7 +397,7 @@ k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, i
         const QueryDesc& Q = qd[q];
         const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
         if (!ps.active || !ps.turn) continue;  // uniform over the block and the cluster
-        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm, scans);
+        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm, scans, ct_a, ct_b);
         // the partner blocks read this block's shared memory, and the next
         // item rewrites it: a cluster leaves the tile together.  Without a
         // cluster the next tile needs no barrier (own row entries, per-thread
@@ -407,12 +408,20 @@ k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, i
 
 template <int K, int SL, int CL>
 cudaError_t launch_turn_t(const Group& gr, int pass, cudaStream_t s) {
+    // the pass's two transition costs when every query shares them
+    uint32_t ca = kCostPerQuery, cb = kCostPerQuery;
+    if (gr.ctm && pass >= 0 && pass_is_turn(pass)) {
+        int m1, m2;
+        turn_pass_maneuvers(pass, &m1, &m2);
+        ca = gr.ctm[m1];
+        cb = m2 >= 0 ? gr.ctm[m2] : 0u;
+    }
     const int tiles = (int)turn_items(gr.lx);
     const int64_t items = gr.item_off ? gr.items : (int64_t)tiles * gr.nq;
     if (items <= 0) return cudaSuccess;
     const int64_t blocks = gr.grid > 0 && gr.grid < items ? gr.grid : items;
     if (CL == 1) {
-        k_turn<K, SL, CL><<<(unsigned)blocks, 32 * SL, 0, s>>>(gr.d, gr.item_off, gr.nq, items, tiles, pass);
+        k_turn<K, SL, CL><<<(unsigned)blocks, 32 * SL, 0, s>>>(gr.d, gr.item_off, gr.nq, items, tiles, pass, ca, cb);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -427,7 +436,7 @@ cudaError_t launch_turn_t(const Group& gr, int pass, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, gr.d, gr.item_off, gr.nq, items, tiles, pass);
+    return cudaLaunchKernelEx(&cfg, k_turn<K, SL, CL>, gr.d, gr.item_off, gr.nq, items, tiles, pass, ca, cb);
 }
 
 template <int K, int SL, int CL>
@@ -539,7 +548,7 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
     uint32_t* Vp = vol.V + (int64_t)T * nxy;
     uint16_t* Lp = vol.L + (int64_t)T * nxy;
     const uint16_t* Bp = vol.B + (int64_t)T * nxy;
-    const uint32_t w = pi.wS, ct = g.ctm[mu];
+    const uint32_t w = pi.wS, ct = mu == SF ? g.ctm[SF] : g.ctm[SB];
     const uint32_t mtag = (uint32_t)mu << 13;
     // Sweep order: dir > 0 visits y' = 0, 1, .., Nx-1 (q = y'); dir < 0
     // visits Nx-1, .., 1, 0 (q = Nx - y').  Starting at Nx-1 with nothing
@@ -696,7 +705,7 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
             Lp[id] = (uint16_t)(mtag | (uint32_t)(q - pv));
             nimp++;
         }
-        const uint32_t tt = u + g.ctm[mu];
+        const uint32_t tt = u + (mu == SF ? g.ctm[SF] : g.ctm[SB]);
         if (tt < v) { v = tt; pv = q; }
         v += e;
     }
