@@ -271,6 +271,8 @@ def run_ours(args):
         line["maze"] = run_maze(args, torch)
     if world == 1 and not args.no_reach:
         line["reach_bitvector"] = run_reach(args, torch)
+    if world == 1 and not args.no_extensions:
+        line["extensions"] = run_extensions(args, torch)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, torch)
     if world == 1 and not args.no_served:
@@ -348,6 +350,57 @@ def run_reach(args, torch):
         p.close()
     out["paper_context"] = "Table 9: 2 ms for render + 8 cycles + back-track at 128^2 x 512 on its larger GPU"
     return out
+
+
+def run_extensions(args, torch):
+    """The calls beyond the plain sweep, on the 512^3 parking scene, timed with
+    CUDA events: the direction-penalty pass over B (Section XVI, Fig. 19; the
+    difference between rendering with and without a two-lane field), the
+    start layer of a vehicle under way (Section XII; init + start layer
+    against init alone), and a goal-set search with back-track (Section IX;
+    12 goals of 13 x 13 x 9 poses, against the single-goal walk)."""
+    import numpy as np
+    from paper_2306_01301_b300 import binding, scenes
+    sc = scenes.parallel_parking()
+    stream = torch.cuda.current_stream()
+    p = binding.Planner.from_scene(sc, sc.hard_image(), stream=stream)
+    nx, nt = p.nx, p.nt
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    render_plain = timed(p.render)
+    field = np.zeros((nx, nx), np.uint16)
+    field[nx // 2:, :] = nt // 2
+    p.set_direction_field(field, nt // 8, 512)
+    render_dir = timed(p.render)
+    p.set_direction_field(None)
+    p.render()
+    entry = [sc.transition] * 6
+    entry[1] = 0  # straight forward in progress
+    init_only = timed(lambda: p.sweep(sc.start, 0))
+    init_seed = timed(lambda: p.sweep_state(sc.start, entry, 0))
+    p.sweep(sc.start, sc.n_cycles)
+    gx, gy, gt = sc.goal
+    goals = [(max(0, gx - 40 + 8 * k), gy, (gt + k) % nt, 6, 4, 40, 60, 100 * k) for k in range(12)]
+    walk = timed(lambda: p.extract(sc.goal))
+    goal_set = timed(lambda: p.extract_goal_set(goals))
+    p.close()
+    dir_ms = max(render_dir - render_plain, 1e-6)
+    return {"direction_pass_ms": dir_ms, "direction_pass_gbs": 4 * sc.cells / (dir_ms * 1e6),
+            "render_ms_with_field": render_dir, "render_ms": render_plain,
+            "start_layer_ms": max(init_seed - init_only, 0.0),
+            "goal_set_extract_ms": goal_set, "single_goal_extract_ms": walk,
+            "note": "direction pass moves 4 B per pose (read and write B); the other two are latency-bound one-block kernels"}
 
 
 def run_batched(args, torch):
@@ -497,6 +550,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-maze", action="store_true")
     ap.add_argument("--no-reach", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true")
     ap.add_argument("--shapes", default="", help="pin turn variant,turn grid,straight lines,straight grid "
                                                    "instead of autotuning (e.g. 0,148,256,0)")
     ap.add_argument("--maze-steps", type=int, default=5)
