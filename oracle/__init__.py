@@ -84,6 +84,14 @@ def lib():
         L.orc_set_transition.argtypes = [p, p, p]
         L.orc_direction.restype = C.c_int
         L.orc_direction.argtypes = [p, p, p, C.c_int, C.c_uint32]
+        L.orc_sweep_gear.restype = C.c_int
+        L.orc_sweep_gear.argtypes = [p, p, C.c_int64, C.c_int, C.c_uint32, C.c_int, p, p]
+        L.orc_dijkstra_gear.restype = C.c_int
+        L.orc_dijkstra_gear.argtypes = [p, p, C.c_int64, C.c_int, C.c_uint32, p]
+        L.orc_bruteforce_gear.restype = C.c_int
+        L.orc_bruteforce_gear.argtypes = [p, p, C.c_int64, C.c_int, C.c_uint32, C.c_int, p]
+        L.orc_extract_gear.restype = C.c_int
+        L.orc_extract_gear.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         L.orc_seed.restype = C.c_int
         L.orc_seed.argtypes = [p, p, C.c_int64, p, p, p]
         L.orc_sweep_state.restype = C.c_int
@@ -240,6 +248,43 @@ class Oracle:
         co = np.ascontiguousarray(cost_out, dtype=np.uint32)
         if ci.shape != (6,) or co.shape != (6,) or lib().orc_set_transition(self._c, _ptr(ci), _ptr(co)) != 0:
             raise ValueError("transition costs need 6 + 6 values with every sum below 2^28")
+
+    # ------------------------------------------------------ gear states
+    def sweep_gear(self, B: np.ndarray, start: int, start_gear: int, pen: int, n_cycles: int):
+        """Two transition states (forward / reverse gear of the last maneuver):
+        returns V, L of 2 * nr entries, the forward state first."""
+        V = np.zeros(2 * self.nr, np.uint32)
+        L = np.zeros(2 * self.nr, np.uint16)
+        rc = lib().orc_sweep_gear(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start), int(start_gear),
+                                  int(pen), int(n_cycles), _ptr(V), _ptr(L))
+        if rc != 0:
+            raise ValueError(f"sweep_gear failed ({rc})")
+        return V, L
+
+    def dijkstra_gear(self, B: np.ndarray, start: int, start_gear: int, pen: int) -> np.ndarray:
+        V = np.zeros(2 * self.nr, np.uint32)
+        if lib().orc_dijkstra_gear(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start), int(start_gear),
+                                   int(pen), _ptr(V)) != 0:
+            raise ValueError("dijkstra_gear failed")
+        return V
+
+    def bruteforce_gear(self, B: np.ndarray, start: int, start_gear: int, pen: int, n_cycles: int) -> np.ndarray:
+        V = np.zeros(2 * self.nr, np.uint32)
+        if lib().orc_bruteforce_gear(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start),
+                                     int(start_gear), int(pen), int(n_cycles), _ptr(V)) != 0:
+            raise ValueError("bruteforce_gear failed")
+        return V
+
+    def extract_gear(self, V: np.ndarray, L: np.ndarray, goal: int, cap: int = 4096):
+        seg = np.zeros((cap, 7), np.int64)
+        n = lib().orc_extract_gear(self._c, _ptr(np.ascontiguousarray(V, np.uint32)),
+                                   _ptr(np.ascontiguousarray(L, np.uint16)), int(goal), _ptr(seg), cap)
+        if n == -1:
+            return None
+        if n < 0:
+            raise ValueError(f"extract_gear failed ({n})")
+        return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3]),
+                     cost=int(r[4]) | (int(r[5]) << 16), entry_gear=int(r[6])) for r in seg[:n]]
 
     # ----------------------------------------------------------- Section XII
     def _entry(self, entry) -> np.ndarray:

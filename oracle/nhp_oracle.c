@@ -849,6 +849,242 @@ int orc_extract(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t 
     return n;
 }
 
+/* --------------------------------------------------------------- gear states
+ * A gear penalty that depends on the pair of consecutive maneuvers needs the
+ * transition state to remember the gear: two transition vertices per cell,
+ * T_F (the last maneuver ran forward, LF SF RF) and T_R (reverse, LB SB RB).
+ * Entering maneuver mu costs cin[mu] from the state of its own gear and
+ * cin[mu] + pen from the other one; leaving mu costs cout[mu] and returns to
+ * the state of mu's gear (the Star of Fig. 9 with its centre split in two).
+ * Volumes: V[0 .. nr) is T_F, V[nr .. 2 nr) is T_R, L alike, a label being
+ * (mu << 13) | (other << 12) | d, other = 1 when the segment was entered
+ * from the other gear's state.  Kernel-style layers as in orc_layers (all
+ * values read at the start of the layer); at one entry cell the own gear's
+ * state wins a tie.  A segment may now run a whole cycle (d = n): going
+ * once around a turn circle from T_F(x) reaches T_R(x), which with one
+ * transition state could never pay off; so d <= n <= 4095 (grids up to
+ * 2048).  start_gear: 0 the vehicle stands in forward gear, 1 in reverse, 2
+ * at rest (both states 0 at the start). */
+static int gear_of(int mu) { return (mu == LB || mu == SB || mu == RB) ? 1 : 0; }
+
+static int layer_gear(const orc_ctx* c, const uint16_t* B, int mu, uint32_t pen, const uint32_t* Vin,
+                      uint32_t* V, uint16_t* L) {
+    int nx = c->nx, G = gear_of(mu);
+    int64_t nr = c->nr, nchains;
+    int n;
+    if (is_turn(mu)) { nchains = (int64_t)nx * nx; n = c->nt; }
+    else { nchains = nx; n = nx; }
+    int nplanes = is_turn(mu) ? 1 : c->nt;
+    const uint32_t* Vs = Vin + (G ? nr : 0); /* own gear */
+    const uint32_t* Vo = Vin + (G ? 0 : nr); /* other gear */
+    uint32_t* Vw = V + (G ? nr : 0);
+    uint16_t* Lw = L + (G ? nr : 0);
+    for (int plane = 0; plane < nplanes; plane++)
+        for (int64_t k = 0; k < nchains; k++) {
+            int64_t start;
+            if (is_turn(mu)) start = k;
+            else start = c->iflag[plane] == 0 ? cell_of(c, 0, (int)k, plane) : cell_of(c, (int)k, 0, plane);
+            int64_t x = start;
+            uint32_t v = ORC_INF;
+            int qe = 0, vo = 0;
+            for (int q = 0; q < 2 * n; q++) {
+                int hard = B[x] == ORC_HARD;
+                if (q >= n) {
+                    uint32_t cand = hard ? ORC_INF : sadd(v, c->cout[mu]);
+                    if (cand < Vs[x]) {
+                        Vw[x] = cand;
+                        Lw[x] = (uint16_t)((mu << 13) | (vo << 12) | (q - qe));
+                    }
+                }
+                uint32_t ts = hard ? ORC_INF : sadd(Vs[x], c->cin[mu]);
+                uint32_t to = hard ? ORC_INF : sadd(sadd(Vo[x], c->cin[mu]), pen);
+                int oth = to < ts;
+                uint32_t t = oth ? to : ts;
+                if (t < v) { v = t; qe = q; vo = oth; }
+                v = sadd(v, orc_edge(c, B, mu, x));
+                x = orc_succ(c, mu, x);
+            }
+            if (x != start) return -1;
+        }
+    return 0;
+}
+
+static int gear_args_ok(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear) {
+    return start >= 0 && start < c->nr && B[start] != ORC_HARD && start_gear >= 0 && start_gear <= 2 &&
+           c->nx <= 2048 && c->nt <= 2048;
+}
+
+int orc_sweep_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear, uint32_t pen,
+                   int n_cycles, uint32_t* V, uint16_t* L) {
+    if (!gear_args_ok(c, B, start, start_gear) || n_cycles < 0) return -1;
+    int64_t nr = c->nr;
+    for (int64_t x = 0; x < 2 * nr; x++) { V[x] = ORC_INF; L[x] = ORC_NONE; }
+    if (start_gear != 1) V[start] = 0;
+    if (start_gear != 0) V[nr + start] = 0;
+    uint32_t* Vin = (uint32_t*)malloc(sizeof(uint32_t) * 2 * nr);
+    if (!Vin) return -1;
+    int rc = 0;
+    for (int l = 0; l < 6 * n_cycles && rc == 0; l++) {
+        memcpy(Vin, V, sizeof(uint32_t) * 2 * nr);
+        rc = layer_gear(c, B, cycle_order[l % 6], pen, Vin, V, L);
+    }
+    free(Vin);
+    return rc;
+}
+
+/* Dijkstra on the explicit graph: vertices T_F(x), T_R(x), M_mu(x).  A
+ * segment moves at least one step (Insert 1 tests a cell for storing before
+ * entering there), so a transition vertex leads straight over the first
+ * maneuver edge: T_g(x) -> M_mu(succ(x)); otherwise T_F(x) -> M_mu(x) ->
+ * T_R(x) would change gear without moving, which the sweeps never do. */
+int orc_dijkstra_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear, uint32_t pen,
+                      uint32_t* Vinf) {
+    if (!gear_args_ok(c, B, start, start_gear)) return -1;
+    int64_t nr = c->nr, nv = 8 * nr; /* [0, nr) T_F, [nr, 2nr) T_R, (2+mu)*nr + x: M_mu(x) */
+    iheap h;
+    h.key = (uint32_t*)malloc(sizeof(uint32_t) * nv);
+    h.heap = (int64_t*)malloc(sizeof(int64_t) * nv);
+    h.pos = (int64_t*)malloc(sizeof(int64_t) * nv);
+    uint8_t* done = (uint8_t*)calloc((size_t)nv, 1);
+    if (!h.key || !h.heap || !h.pos || !done) { free(h.key); free(h.heap); free(h.pos); free(done); return -1; }
+    for (int64_t v = 0; v < nv; v++) { h.key[v] = ORC_INF; h.pos[v] = -1; }
+    h.n = 0;
+    for (int g = 0; g < 2; g++) {
+        if ((g == 0 && start_gear == 1) || (g == 1 && start_gear == 0)) continue;
+        int64_t v = g * nr + start;
+        h.key[v] = 0;
+        h.heap[h.n] = v; h.pos[v] = h.n; h.n++;
+    }
+#define GRELAX(dst, w)                                                  \
+    do {                                                                \
+        uint32_t nd_ = sadd(du, (w));                                   \
+        int64_t d_ = (dst);                                             \
+        if (nd_ < h.key[d_] && !done[d_]) {                             \
+            h.key[d_] = nd_;                                            \
+            if (h.pos[d_] < 0) { h.heap[h.n] = d_; h.pos[d_] = h.n; h.n++; } \
+            heap_up(&h, h.pos[d_]);                                     \
+        }                                                               \
+    } while (0)
+    while (h.n > 0) {
+        int64_t u = h.heap[0];
+        heap_swap(&h, 0, h.n - 1);
+        h.n--;
+        h.pos[u] = -1;
+        if (h.n > 0) heap_down(&h, 0);
+        done[u] = 1;
+        uint32_t du = h.key[u];
+        if (du == ORC_INF) break;
+        int64_t x = u % nr;
+        int kind = (int)(u / nr);
+        if (B[x] == ORC_HARD) continue;
+        if (kind < 2) {
+            for (int m = 0; m < 6; m++) {
+                int64_t y = orc_succ(c, m, x);
+                uint32_t w = sadd(gear_of(m) == kind ? c->cin[m] : sadd(c->cin[m], pen), orc_edge(c, B, m, x));
+                if (B[y] != ORC_HARD) GRELAX((2 + m) * nr + y, w);
+            }
+        } else {
+            int m = kind - 2;
+            GRELAX(gear_of(m) * nr + x, c->cout[m]);
+            int64_t y = orc_succ(c, m, x);
+            uint32_t w = orc_edge(c, B, m, x);
+            if (B[y] != ORC_HARD) GRELAX((2 + m) * nr + y, w);
+        }
+    }
+#undef GRELAX
+    for (int64_t x = 0; x < 2 * nr; x++) Vinf[x] = B[x % nr] == ORC_HARD ? ORC_INF : h.key[x];
+    free(h.key); free(h.heap); free(h.pos); free(done);
+    return 0;
+}
+
+/* Exhaustive search over layer-ordered segment sequences with the gear
+ * state: best[g*nr + x] over sequences ending in state g at x. */
+typedef struct {
+    const orc_ctx* c;
+    const uint16_t* B;
+    uint32_t pen;
+    int layers;
+    uint32_t* seen; /* [layer][gear][cell] */
+    uint32_t* best;
+} bfg_state;
+
+static void bfg_explore(bfg_state* s, int layer, int g, int64_t x, uint32_t cost) {
+    const orc_ctx* c = s->c;
+    int64_t nr = c->nr;
+    uint32_t* sl = s->seen + ((size_t)layer * 2 + g) * nr;
+    if (cost >= sl[x]) return;
+    sl[x] = cost;
+    if (cost < s->best[g * nr + x]) s->best[g * nr + x] = cost;
+    if (layer == s->layers) return;
+    bfg_explore(s, layer + 1, g, x, cost);
+    int mu = cycle_order[layer % 6], G = gear_of(mu);
+    int n = is_turn(mu) ? c->nt : c->nx;
+    uint32_t run = sadd(cost, G == g ? c->cin[mu] : sadd(c->cin[mu], s->pen));
+    int64_t y = x;
+    for (int d = 1; d <= n; d++) { /* a whole cycle may change the gear state */
+        run = sadd(run, orc_edge(c, s->B, mu, y));
+        y = orc_succ(c, mu, y);
+        if (run == ORC_INF) break;
+        if (s->B[y] != ORC_HARD) bfg_explore(s, layer + 1, G, y, sadd(run, c->cout[mu]));
+    }
+}
+
+int orc_bruteforce_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear, uint32_t pen,
+                        int n_cycles, uint32_t* Vbest) {
+    if (!gear_args_ok(c, B, start, start_gear) || n_cycles < 0) return -1;
+    int64_t nr = c->nr;
+    bfg_state s = {c, B, pen, 6 * n_cycles, NULL, Vbest};
+    s.seen = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(s.layers + 1) * 2 * nr);
+    if (!s.seen) return -1;
+    for (int64_t k = 0; k < (int64_t)(s.layers + 1) * 2 * nr; k++) s.seen[k] = ORC_INF;
+    for (int64_t x = 0; x < 2 * nr; x++) Vbest[x] = ORC_INF;
+    if (start_gear != 1) bfg_explore(&s, 0, 0, start, 0);
+    if (start_gear != 0) bfg_explore(&s, 0, 1, start, 0);
+    free(s.seen);
+    return 0;
+}
+
+/* Label walk with gear states: from the cheaper state at the goal (forward
+ * on a tie), each label names the maneuver, the steps back to its entry and
+ * whether it entered from the other gear's state.  seg[k*7 + {mu, entry,
+ * exit, d, cost_lo16, cost_hi16, entry_gear}] in driving order.  Returns the
+ * segment count, -1 unreachable, -2 cap too small, -3 malformed labels. */
+int orc_extract_gear(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal, int64_t* seg,
+                     int cap) {
+    if (goal < 0 || goal >= c->nr) return -3;
+    int64_t nr = c->nr;
+    int g = V[nr + goal] < V[goal] ? 1 : 0;
+    if (V[g * nr + goal] == ORC_INF) return -1;
+    int n = 0, guard = 0;
+    int64_t x = goal;
+    while (L[g * nr + x] != ORC_NONE) {
+        if (++guard > 1 << 20) return -3;
+        uint16_t lab = L[g * nr + x];
+        int mu = lab >> 13, oth = (lab >> 12) & 1, d = lab & 4095;
+        if (mu > 5 || d == 0 || gear_of(mu) != g) return -3;
+        int64_t e = x;
+        for (int k = 0; k < d; k++) e = orc_succ(c, 5 - mu, e);
+        int ge = oth ? 1 - g : g;
+        if (n < cap) {
+            int64_t* r = seg + 7 * (size_t)n;
+            uint32_t cost = V[g * nr + x];
+            r[0] = mu; r[1] = e; r[2] = x; r[3] = d; r[4] = cost & 0xFFFF; r[5] = cost >> 16; r[6] = ge;
+        }
+        n++;
+        x = e;
+        g = ge;
+    }
+    if (V[g * nr + x] != 0) return -3;
+    if (n > cap) return -2;
+    for (int a2 = 0, b2 = n - 1; a2 < b2; a2++, b2--)
+        for (int k = 0; k < 7; k++) {
+            int64_t t = seg[7 * a2 + k];
+            seg[7 * a2 + k] = seg[7 * b2 + k];
+            seg[7 * b2 + k] = t;
+        }
+    return n;
+}
+
 /* ------------------------------------------------------------ goal search
  * Section IX: a goal set instead of one exact pose, each pose scored by a
  * reward that falls with its distance from an ideal pose; the best pose

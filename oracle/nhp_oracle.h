@@ -96,6 +96,20 @@ int orc_dijkstra_state(const orc_ctx* c, const uint16_t* B, int64_t start, const
                        uint32_t* Vinf);
 int orc_bruteforce_state(const orc_ctx* c, const uint16_t* B, int64_t start, const uint32_t* entry,
                          int n_cycles, uint32_t* Vbest);
+/* Gear states: two transition vertices per cell (forward / reverse gear of
+ * the last maneuver); entering a maneuver of the other gear costs pen more.
+ * V, L hold 2 * nr entries (forward state first); labels (mu << 13) |
+ * (entered from the other state << 12) | d.  start_gear 0 forward, 1 reverse,
+ * 2 at rest.  Sweep, Dijkstra, exhaustive search and label walk
+ * (seg[k*7 + {mu, entry, exit, d, cost_lo16, cost_hi16, entry_gear}]). */
+int orc_sweep_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear, uint32_t pen,
+                   int n_cycles, uint32_t* V, uint16_t* L);
+int orc_dijkstra_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear, uint32_t pen,
+                      uint32_t* Vinf);
+int orc_bruteforce_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int start_gear, uint32_t pen,
+                        int n_cycles, uint32_t* Vbest);
+int orc_extract_gear(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal, int64_t* seg,
+                     int cap);
 /* Goal search over a goal set (Section IX): the reached pose minimising
  * V + bias + w_xy (|dx|+|dy|) + w_theta |dtheta| over every goal's box;
  * goals[g*8 + {x, y, theta, r_xy, r_theta, w_xy, w_theta, bias}].  Returns 0
