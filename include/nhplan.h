@@ -163,6 +163,42 @@ int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* 
  * allocation-free plan_render_cspace_static does not apply it. */
 int plan_set_direction_field(plan_t* plan, const uint16_t* heading, int tolerance, uint32_t penalty_q8);
 
+#define PLAN_GEAR_OFF 0xFFFFFFFFu
+#define PLAN_GEAR_FORWARD 0
+#define PLAN_GEAR_REVERSE 1
+#define PLAN_GEAR_AT_REST 2
+
+/* Two gear states: the transition vertex of Fig. 9 split into a forward and
+ * a reverse one (the gear of the last maneuver: LF SF RF forward, LB SB RB
+ * reverse), so that `penalty` is charged exactly when two consecutive
+ * maneuvers change gear -- entering maneuver mu costs cost_in[mu] from its own
+ * gear's state and cost_in[mu] + penalty from the other; leaving returns to
+ * its own gear's state at cost_out[mu].  Allocates the reverse state's V and
+ * L (6 B per pose) on first use; PLAN_GEAR_OFF releases them.  Only for grids
+ * up to 2048 (Nx and N_theta; labels need d <= n, a whole turn circle now
+ * being able to pay off by changing the gear state).  PLAN_EINVAL for a
+ * penalty >= 2^28 or a larger grid, PLAN_ESTATE for a plan without volumes. */
+int plan_set_gear_penalty(plan_t* plan, uint32_t penalty);
+
+/* The sweep of the two-state graph: init (start_gear PLAN_GEAR_FORWARD or
+ * _REVERSE: the vehicle stands in that gear; _AT_REST: both states 0) and
+ * 6N maneuver layers in the cycle order, each reading both states and
+ * writing its own gear's (one maneuver per launch, no fused pairs).  The
+ * forward state is the plan's V and L (plan_copy_volumes), the reverse one
+ * plan_copy_reverse_volumes; labels are (mu << 13) | (entered from the other
+ * state << 12) | d.  Saturating arithmetic, no range check needed.  Async.
+ * PLAN_ESTATE without plan_set_gear_penalty or before rendering. */
+int plan_sweep_gear(plan_t* plan, plan_pose start, int start_gear, int n_cycles);
+
+/* Back-track after plan_sweep_gear from the cheaper state at the goal
+ * (forward on a tie), as plan_extract; *end_gear is that state.
+ * Synchronises. */
+int plan_extract_gear(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out, uint32_t* cost,
+                      int* end_gear);
+
+/* The reverse gear state's V and L (either may be NULL).  Synchronises. */
+int plan_copy_reverse_volumes(plan_t* plan, uint32_t* V, uint16_t* L);
+
 /* Section V.A, Fig. 9: per-maneuver transition edges of the Star graph.
  * Entering maneuver mu (cycle-order ids) from the transition state costs
  * cost_in[mu], returning to it cost_out[mu] -- the time of changing gear or

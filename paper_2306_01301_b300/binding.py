@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libnhplan.so")
 PLAN_OK = 0
 PLAN_EINVAL = -1
 PLAN_NO_DIRECTION = 0xFFFF
+PLAN_GEAR_FORWARD, PLAN_GEAR_REVERSE, PLAN_GEAR_AT_REST = 0, 1, 2
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNREACHABLE", -6: "ERANGE",
           -7: "EINTERNAL", -8: "ESTATE"}
 PLAN_EUNREACHABLE = -5
@@ -129,6 +130,15 @@ def lib():
         L.plan_reach_sweep.restype = C.c_int
         L.plan_set_direction_field.restype = C.c_int
         L.plan_set_direction_field.argtypes = [vp, vp, C.c_int, C.c_uint32]
+        L.plan_set_gear_penalty.restype = C.c_int
+        L.plan_set_gear_penalty.argtypes = [vp, C.c_uint32]
+        L.plan_sweep_gear.restype = C.c_int
+        L.plan_sweep_gear.argtypes = [vp, Pose, C.c_int, C.c_int]
+        L.plan_extract_gear.restype = C.c_int
+        L.plan_extract_gear.argtypes = [vp, Pose, C.POINTER(Segment), C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_uint32), C.POINTER(C.c_int)]
+        L.plan_copy_reverse_volumes.restype = C.c_int
+        L.plan_copy_reverse_volumes.argtypes = [vp, vp, vp]
         L.plan_set_transition_costs.restype = C.c_int
         L.plan_set_transition_costs.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.plan_sweep_state.restype = C.c_int
@@ -273,6 +283,34 @@ class Planner:
         assert h.shape == (self.nx, self.nx)
         _check(lib().plan_set_direction_field(self._h, _ptr(h), int(tolerance), int(penalty_q8)),
                "plan_set_direction_field")
+
+    def set_gear_penalty(self, penalty):
+        """plan_set_gear_penalty (None: PLAN_GEAR_OFF)."""
+        _check(lib().plan_set_gear_penalty(self._h, 0xFFFFFFFF if penalty is None else int(penalty)),
+               "plan_set_gear_penalty")
+
+    def sweep_gear(self, start, start_gear: int, n_cycles: int):
+        _check(lib().plan_sweep_gear(self._h, Pose(*[int(v) for v in start]), int(start_gear), int(n_cycles)),
+               "plan_sweep_gear")
+
+    def extract_gear(self, goal, cap: int = 1024):
+        """Returns (PlanResult, end gear) or None when unreachable."""
+        segs = (Segment * cap)()
+        n = C.c_int(0)
+        cost = C.c_uint32(0)
+        gear = C.c_int(0)
+        rc = lib().plan_extract_gear(self._h, Pose(*[int(v) for v in goal]), segs, cap, C.byref(n), C.byref(cost),
+                                     C.byref(gear))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_extract_gear")
+        return PlanResult(int(cost.value), self._segments(segs, n.value)), int(gear.value)
+
+    def reverse_volumes(self):
+        v = np.empty(self.cells, np.uint32)
+        l_ = np.empty(self.cells, np.uint16)
+        _check(lib().plan_copy_reverse_volumes(self._h, _ptr(v), _ptr(l_)), "plan_copy_reverse_volumes")
+        return v, l_
 
     def set_transition_costs(self, cost_in, cost_out):
         """plan_set_transition_costs: per-maneuver Star transition edges

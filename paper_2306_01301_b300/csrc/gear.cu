@@ -1,0 +1,177 @@
+// gear.cu -- two gear states: forward / reverse transition vertices.
+//
+// The Star of Fig. 9 with its centre split in two remembers the gear of the
+// last maneuver (forward: LF SF RF; reverse: LB SB RB), so a penalty can be
+// charged exactly when consecutive maneuvers change gear: entering maneuver
+// mu costs cost_in[mu] from its own gear's state and cost_in[mu] + pen from
+// the other one; leaving costs cost_out[mu] and returns to mu's gear's
+// state.  Each maneuver layer reads both states and writes its own gear's.
+//
+// A layer walks every curve of the maneuver twice around its cycle (turn
+// chains: one thread per chain over N_theta headings; straight lines: one
+// thread per line over Nx steps from the wall cell), as the paper's two
+// sequential loops do: the first loop warms the carried value up, the
+// second stores.  A cell is read once per step before its possible store,
+// so the values used for entering are those before the layer (only this
+// thread writes the cell, and only in the second loop).  Arithmetic
+// saturates at PLAN_INF.  Labels are (mu << 13) | (other << 12) | d with
+// d <= n (a whole turn circle can now pay off: it changes the gear state),
+// so grids are limited to 2048.  A feature path, not a tuned one: it streams
+// both value volumes, B and the labels twice per layer.
+#include "curve.cuh"
+#include "internal.h"
+
+namespace nhp {
+namespace {
+
+constexpr uint32_t INF32 = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t sadd(uint32_t a, uint32_t b) {
+    const uint64_t s = (uint64_t)a + b;
+    return s >= INF32 ? INF32 : (uint32_t)s;
+}
+
+__device__ __forceinline__ int gear_of(int mu) { return (mu == LB || mu == SB || mu == RB) ? 1 : 0; }
+
+// One step of the two-loop walk at cell c, position q of 2n.
+struct Walk {
+    uint32_t v = INF32;  // carried value (entered and moved, not yet left)
+    int qe = 0, vo = 0;  // entry position, entered from the other gear's state
+};
+
+__device__ __forceinline__ void walk_step(Walk& s, int64_t c, int q, int n, int mu, uint32_t w,
+                                          const GearLayer& a) {
+    const int G = gear_of(mu);
+    uint32_t* Vs = G ? a.Vr : a.Vf;
+    uint16_t* Ls = G ? a.Lr : a.Lf;
+    const uint32_t* Vo = G ? a.Vf : a.Vr;
+    const uint16_t b = a.B[c];
+    const bool hard = b == HARD;
+    const uint32_t u = Vs[c];  // before this layer: only this thread writes c, below
+    if (q >= n) {
+        const uint32_t cand = hard ? INF32 : sadd(s.v, a.cout);
+        if (cand < u) {
+            Vs[c] = cand;
+            Ls[c] = (uint16_t)((mu << 13) | (s.vo << 12) | (q - s.qe));
+        }
+    }
+    const uint32_t ts = hard ? INF32 : sadd(u, a.cin);
+    const uint32_t to = hard ? INF32 : sadd(sadd(Vo[c], a.cin), a.pen);
+    const int oth = to < ts;
+    const uint32_t t = oth ? to : ts;
+    if (t < s.v) {
+        s.v = t;
+        s.qe = q;
+        s.vo = oth;
+    }
+    s.v = sadd(s.v, hard ? INF32 : (uint32_t)(((uint64_t)w * b) >> 8));
+}
+
+__global__ void __launch_bounds__(256) k_gear_turn(const GearLayer a, int mu) {
+    const DevGrid& g = a.g;
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int64_t chain = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (chain >= nxy) return;
+    const int xq = (int)(chain & g.mx), yq = (int)(chain >> g.lx);
+    const bool left = mu == LF || mu == LB;
+    const int step = (mu == LF || mu == RB) ? 1 : -1;  // heading step along the maneuver
+    const int n = g.nt;
+    Walk s;
+    for (int q = 0; q < 2 * n; q++) {
+        const int T = (step * q) & g.mt;
+        const int4 b = __ldg(&g.beta4[T]);
+        const int64_t c = cell_of(g, xq + (left ? b.x : b.z), yq + (left ? b.y : b.w), T);
+        walk_step(s, c, q, n, mu, g.wA, a);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gear_straight(const GearLayer a, int mu) {
+    const DevGrid& g = a.g;
+    const int xq = blockIdx.x * blockDim.x + threadIdx.x;  // line
+    if (xq >= g.nx) return;
+    const int T = blockIdx.y;
+    const PlaneInfo pi = g.plane[T];
+    const int dir = (mu == SF ? pi.jsign : -pi.jsign) > 0 ? 1 : -1;  // y' along the maneuver
+    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
+    const int n = g.nx;
+    Walk s;
+    for (int q = 0; q < 2 * n; q++) {
+        const int y = (dir * q) & g.mx;  // from the wall cell y' = 0
+        const int col = (xq + bs[y]) & g.mx;
+        const int64_t c = pi.iflag ? cell_of(g, col, y, T) : cell_of(g, y, col, T);
+        walk_step(s, c, q, n, mu, pi.wS, a);
+    }
+}
+
+__global__ void k_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
+                            int start_gear) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x) {
+        Vf[i] = (i == start && start_gear != 1) ? 0u : INF32;
+        Vr[i] = (i == start && start_gear != 0) ? 0u : INF32;
+        Lf[i] = NONE;
+        Lr[i] = NONE;
+    }
+}
+
+// Label walk from the cheaper state at the goal (forward on a tie).
+// status: [0] segments or -1 unreachable / -3 malformed, [1] cost, [2] gear
+// of the last segment's state.
+__global__ void k_gear_extract(const GearLayer a, int64_t goal, plan_segment* seg, int cap, int32_t* status) {
+    if (threadIdx.x != 0) return;
+    const DevGrid& g = a.g;
+    int st = a.Vr[goal] < a.Vf[goal] ? 1 : 0;
+    const uint32_t cost = st ? a.Vr[goal] : a.Vf[goal];
+    status[1] = (int32_t)cost;
+    status[2] = st;
+    if (cost == INF32) { status[0] = -1; return; }
+    int64_t x = goal;
+    int n = 0;
+    for (;;) {
+        const uint16_t lab = st ? a.Lr[x] : a.Lf[x];
+        if (lab == NONE) break;
+        if (n >= (1 << 20)) { status[0] = -3; return; }
+        const int mu = lab >> 13, oth = (lab >> 12) & 1, d = lab & 4095;
+        if (mu > 5 || d == 0 || gear_of(mu) != st) { status[0] = -3; return; }
+        const int64_t e = entry_cell(g, x, mu, d);
+        if (n < cap) {
+            plan_segment s;
+            s.maneuver = mu;
+            s.entry = pose_of(g, e);
+            s.exit = pose_of(g, x);
+            s.steps = d;
+            s.cost = st ? a.Vr[x] : a.Vf[x];
+            seg[n] = s;
+        }
+        n++;
+        x = e;
+        st = oth ? 1 - st : st;
+    }
+    status[0] = (st ? a.Vr[x] : a.Vf[x]) == 0 ? n : -3;
+}
+
+}  // namespace
+
+cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
+                             int start_gear, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>((nr + 255) / 256, 148 * 16);
+    k_gear_init<<<(unsigned)blocks, 256, 0, s>>>(Vf, Vr, Lf, Lr, nr, start, start_gear);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s) {
+    if (mu == SF || mu == SB) {
+        k_gear_straight<<<dim3((unsigned)((a.g.nx + 255) / 256), (unsigned)a.g.nt), 256, 0, s>>>(a, mu);
+    } else {
+        const int64_t chains = (int64_t)a.g.nx * a.g.nx;
+        k_gear_turn<<<(unsigned)((chains + 255) / 256), 256, 0, s>>>(a, mu);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gear_extract(const GearLayer& a, int64_t goal, plan_segment* seg, int cap, int32_t* status,
+                                cudaStream_t s) {
+    k_gear_extract<<<1, 32, 0, s>>>(a, goal, seg, cap, status);
+    return cudaGetLastError();
+}
+
+}  // namespace nhp

@@ -158,6 +158,22 @@ __device__ __forceinline__ uint32_t pick6(const uint32_t (&a)[6], int mu) {
     return r;
 }
 
+// Two gear states (forward / reverse transition vertices): one maneuver
+// layer's arguments.  Vf, Lf are the plan's own volumes, Vr, Lr the reverse
+// state's.
+struct GearLayer {
+    DevGrid g;
+    const uint16_t* B;
+    uint32_t *Vf, *Vr;
+    uint16_t *Lf, *Lr;
+    uint32_t pen, cin, cout;  // gear change; entering and leaving the layer's maneuver
+};
+cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
+                             int start_gear, cudaStream_t s);
+cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s);
+cudaError_t launch_gear_extract(const GearLayer& a, int64_t goal, plan_segment* seg, int cap, int32_t* status,
+                                cudaStream_t s);
+
 // Direction penalties (Section XVI, Fig. 19) applied to a rendered B.
 cudaError_t launch_direction(uint16_t* B, const uint16_t* field, int lx, int lt, int tol, uint32_t pen,
                              cudaStream_t s);

@@ -254,6 +254,8 @@ void release(plan_s* p) {
     p->dfree(p->d_status, 16);
     p->dfree(p->d_goals, goal_buffer_bytes(p->goal_cap));
     p->dfree(p->d_dir, (size_t)p->nxy * 2);
+    p->dfree(p->d_Vr, (size_t)p->nr * 4);
+    p->dfree(p->d_Lr, (size_t)p->nr * 2);
     p->dfree(p->d_cnt, 32);
     p->dfree(p->d_qd, sizeof(QueryDesc));
     const size_t bits = (size_t)(p->nr / 8);
@@ -532,6 +534,110 @@ int plan_render_cspace(plan_t* p) {
 }
 
 int plan_sweep(plan_t* p, plan_pose start, int n_cycles) { return sweep_impl(p, start, n_cycles, nullptr); }
+
+int plan_set_gear_penalty(plan_t* p, uint32_t penalty) {
+    if (!p) return PLAN_EINVAL;
+    if (penalty == PLAN_GEAR_OFF) {
+        p->dfree(p->d_Vr, (size_t)p->nr * 4);
+        p->dfree(p->d_Lr, (size_t)p->nr * 2);
+        p->d_Vr = nullptr;
+        p->d_Lr = nullptr;
+        p->gear_on = p->gear_ready = false;
+        return PLAN_OK;
+    }
+    if (penalty >= (1u << 28) || p->nx > 2048 || p->nt > 2048) return PLAN_EINVAL;
+    if (!p->volumes) return PLAN_ESTATE;
+    if (!p->d_Vr) {
+        p->d_Vr = (uint32_t*)p->dalloc((size_t)p->nr * 4);
+        p->d_Lr = (uint16_t*)p->dalloc((size_t)p->nr * 2);
+        if (!p->d_Vr || !p->d_Lr) {
+            p->dfree(p->d_Vr, (size_t)p->nr * 4);
+            p->dfree(p->d_Lr, (size_t)p->nr * 2);
+            p->d_Vr = nullptr;
+            p->d_Lr = nullptr;
+            return PLAN_ENOMEM;
+        }
+    }
+    p->gear_pen = penalty;
+    p->gear_on = true;
+    p->gear_ready = false;
+    return PLAN_OK;
+}
+
+int plan_sweep_gear(plan_t* p, plan_pose start, int start_gear, int n_cycles) {
+    if (!p || n_cycles < 0 || n_cycles > 4096 || start_gear < 0 || start_gear > 2 || !pose_ok(p, start))
+        return PLAN_EINVAL;
+    if (!p->gear_on || !p->rendered) return PLAN_ESTATE;
+    if (pose_hard(p, start)) return PLAN_EINVAL;
+    GearLayer a{};
+    a.g = p->g;
+    a.B = p->d_B;
+    a.Vf = p->d_V;
+    a.Vr = p->d_Vr;
+    a.Lf = p->d_L;
+    a.Lr = p->d_Lr;
+    a.pen = p->gear_pen;
+    cudaStream_t s = p->stream;
+    p->gear_ready = false;
+    int rc = cuda_rc(launch_gear_init(p->d_V, p->d_Vr, p->d_L, p->d_Lr, p->nr, cell_index(p, start), start_gear, s));
+    p->launches++;
+    for (int l = 0; l < 6 * n_cycles && rc == PLAN_OK; l++) {
+        const int mu = l % 6;  // maneuver ids are the cycle order
+        a.cin = p->cin[mu];
+        a.cout = p->cout[mu];
+        rc = cuda_rc(launch_gear_layer(a, mu, s));
+        p->launches++;
+    }
+    if (rc == PLAN_OK) p->gear_ready = true;
+    return rc;
+}
+
+int plan_extract_gear(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_out, uint32_t* cost,
+                      int* end_gear) {
+    if (!p || !n_out || !cost || !end_gear || cap < 0 || (cap > 0 && !out) || !pose_ok(p, goal)) return PLAN_EINVAL;
+    *n_out = 0;
+    *cost = PLAN_INF;
+    *end_gear = -1;
+    if (!p->gear_ready) return PLAN_ESTATE;
+    GearLayer a{};
+    a.g = p->g;
+    a.Vf = p->d_V;
+    a.Vr = p->d_Vr;
+    a.Lf = p->d_L;
+    a.Lr = p->d_Lr;
+    int rc = cuda_rc(launch_gear_extract(a, cell_index(p, goal), p->d_seg, kDevSegCap, p->d_status, p->stream));
+    p->launches++;
+    int32_t status[3] = {0, 0, 0};
+    if (rc == PLAN_OK)
+        rc = cuda_rc(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc != PLAN_OK) return rc;
+    if (status[0] == -1) return PLAN_EUNREACHABLE;
+    if (status[0] < 0) return PLAN_EINTERNAL;
+    *cost = (uint32_t)status[1];
+    *end_gear = status[2];
+    *n_out = status[0];
+    if (status[0] > cap || status[0] > kDevSegCap) return PLAN_ERANGE;
+    if (status[0] > 0) {
+        rc = cuda_rc(cudaMemcpyAsync(out, p->d_seg, sizeof(plan_segment) * status[0], cudaMemcpyDeviceToHost,
+                                     p->stream));
+        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+        if (rc != PLAN_OK) return rc;
+        std::reverse(out, out + status[0]);
+    }
+    return PLAN_OK;
+}
+
+int plan_copy_reverse_volumes(plan_t* p, uint32_t* V, uint16_t* L) {
+    if (!p) return PLAN_EINVAL;
+    if (!p->gear_on) return PLAN_ESTATE;
+    int rc = PLAN_OK;
+    if (V) rc = cuda_rc(cudaMemcpyAsync(V, p->d_Vr, (size_t)p->nr * 4, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK && L)
+        rc = cuda_rc(cudaMemcpyAsync(L, p->d_Lr, (size_t)p->nr * 2, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    return rc;
+}
 
 int plan_set_direction_field(plan_t* p, const uint16_t* heading, int tolerance, uint32_t penalty_q8) {
     if (!p) return PLAN_EINVAL;

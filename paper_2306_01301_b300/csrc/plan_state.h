@@ -16,6 +16,10 @@ struct plan_s {
     plan_costs costs{};
     uint32_t cin[6] = {}, cout[6] = {};  // Star transition edges per maneuver
     uint16_t* d_dir = nullptr;            // direction field (Nx*Nx), or none
+    uint32_t* d_Vr = nullptr;             // reverse gear state (plan_set_gear_penalty)
+    uint16_t* d_Lr = nullptr;
+    uint32_t gear_pen = 0;
+    bool gear_on = false, gear_ready = false;
     int dir_tol = 0;
     uint32_t dir_pen = 256;
     plan_footprint fp{};
