@@ -358,7 +358,9 @@ def run_extensions(args, torch):
     difference between rendering with and without a two-lane field), the
     start layer of a vehicle under way (Section XII; init + start layer
     against init alone), and a goal-set search with back-track (Section IX;
-    12 goals of 13 x 13 x 9 poses, against the single-goal walk)."""
+    12 goals of 13 x 13 x 9 poses, against the single-goal walk), and the
+    two-gear-state sweep (forward / reverse transition states, penalty 3000,
+    N = 8, one maneuver per launch)."""
     import numpy as np
     from paper_2306_01301_b300 import binding, scenes
     sc = scenes.parallel_parking()
@@ -394,12 +396,17 @@ def run_extensions(args, torch):
     goals = [(max(0, gx - 40 + 8 * k), gy, (gt + k) % nt, 6, 4, 40, 60, 100 * k) for k in range(12)]
     walk = timed(lambda: p.extract(sc.goal))
     goal_set = timed(lambda: p.extract_goal_set(goals))
+    p.set_gear_penalty(3000)
+    gear_plan = timed(lambda: p.sweep_gear(sc.start, 0, sc.n_cycles), reps=3)
+    gear_res = p.extract_gear(sc.goal)
     p.close()
     dir_ms = max(render_dir - render_plain, 1e-6)
     return {"direction_pass_ms": dir_ms, "direction_pass_gbs": 4 * sc.cells / (dir_ms * 1e6),
             "render_ms_with_field": render_dir, "render_ms": render_plain,
             "start_layer_ms": max(init_seed - init_only, 0.0),
             "goal_set_extract_ms": goal_set, "single_goal_extract_ms": walk,
+            "gear_states_sweep_ms": gear_plan, "gear_states_updates_per_s": 6 * sc.n_cycles * sc.cells / (gear_plan / 1e3),
+            "gear_states_plan_cost": gear_res[0].cost if gear_res else None,
             "note": "direction pass moves 4 B per pose (read and write B); the other two are latency-bound one-block kernels"}
 
 
