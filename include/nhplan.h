@@ -145,7 +145,9 @@ int plan_sweep(plan_t* plan, plan_pose start, int n_cycles);
  * the start.  Writes at most `cap` segments in driving order to `out` (host),
  * sets *n_out to the number of segments (also when cap is too small:
  * PLAN_ERANGE) and *cost to V(goal).  Synchronises.  PLAN_EUNREACHABLE (with
- * *n_out = 0, *cost = PLAN_INF) if the goal was not reached. */
+ * *n_out = 0, *cost = PLAN_INF) if the goal was not reached; PLAN_ESTATE
+ * unless the plan's volumes come from plan_sweep, plan_sweep_state or a
+ * batch run (not from plan_sweep_gear or plan_autotune). */
 int plan_extract(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out,
                  uint32_t* cost);
 
@@ -192,7 +194,7 @@ int plan_sweep_gear(plan_t* plan, plan_pose start, int start_gear, int n_cycles)
 
 /* Back-track after plan_sweep_gear from the cheaper state at the goal
  * (forward on a tie), as plan_extract; *end_gear is that state.
- * Synchronises. */
+ * Synchronises.  PLAN_ESTATE unless the volumes come from plan_sweep_gear. */
 int plan_extract_gear(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out, uint32_t* cost,
                       int* end_gear);
 

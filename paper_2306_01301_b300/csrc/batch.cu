@@ -290,6 +290,12 @@ int enqueue_render(plan_batch_s* b, cudaStream_t s, int64_t* launches) {
         NHP_CK(launch_render(g, soft, s, &n));
         *launches += n;
     }
+    // direction penalties of the plans that have a field, as plan_render_cspace applies them
+    for (const plan_s* p : b->plans)
+        if (p->d_dir) {
+            NHP_CK(launch_direction(p->d_B, p->d_dir, p->lx, p->lt, p->dir_tol, p->dir_pen, s));
+            (*launches)++;
+        }
     return PLAN_OK;
 }
 
@@ -547,6 +553,14 @@ int plan_batch_run(plan_batch_t* b, const plan_query* queries, int render) {
     key.reserve(n + 1);
     for (int i = 0; i < n; i++) key.push_back(queries[i].n_cycles);
     key.push_back(render ? 1 : 0);
+    // launch parameters a captured graph holds: transition costs, direction fields
+    for (const plan_s* p : b->plans) {
+        for (int k = 0; k < 6; k++) key.push_back((int)p->g.ctm[k]);
+        key.push_back(p->d_dir ? 1 : 0);
+        key.push_back(p->dir_tol);
+        key.push_back((int)p->dir_pen);
+        key.push_back((int)((uintptr_t)p->d_dir & 0x7FFFFFFF));
+    }
     const bool use_graph = !(b->flags & PLAN_BATCH_NO_GRAPH);
     int rc = PLAN_OK;
     if (key != b->key || !use_graph) {
@@ -596,6 +610,7 @@ int plan_batch_run(plan_batch_t* b, const plan_query* queries, int render) {
     }
     if (render)
         for (auto* p : b->plans) p->rendered = true;
+    for (auto* p : b->plans) p->vol_kind = VOL_PLAIN;
     NHP_CK(cudaEventRecord(b->done, b->stream));
     b->in_flight = true;
     // later work on the caller's and the plans' streams sees the results

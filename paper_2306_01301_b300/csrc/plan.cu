@@ -445,6 +445,7 @@ int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) 
     p->qd.start = cell_index(p, start);
     p->qd.n_cycles = n_cycles;
     p->qd.v.improved = p->prof ? p->d_cnt : nullptr;
+    p->vol_kind = VOL_NONE;
     int rc = upload_desc(p);
     if (rc != PLAN_OK) return rc;
     const Group gr = p->group();
@@ -470,6 +471,7 @@ int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) 
         mark_end(p, m);
         p->launches++;
     }
+    if (rc == PLAN_OK) p->vol_kind = VOL_PLAIN;
     return rc;
 }
 
@@ -542,7 +544,8 @@ int plan_set_gear_penalty(plan_t* p, uint32_t penalty) {
         p->dfree(p->d_Lr, (size_t)p->nr * 2);
         p->d_Vr = nullptr;
         p->d_Lr = nullptr;
-        p->gear_on = p->gear_ready = false;
+        p->gear_on = false;
+        if (p->vol_kind == VOL_GEAR) p->vol_kind = VOL_NONE;
         return PLAN_OK;
     }
     if (penalty >= (1u << 28) || p->nx > 2048 || p->nt > 2048) return PLAN_EINVAL;
@@ -560,7 +563,7 @@ int plan_set_gear_penalty(plan_t* p, uint32_t penalty) {
     }
     p->gear_pen = penalty;
     p->gear_on = true;
-    p->gear_ready = false;
+    if (p->vol_kind == VOL_GEAR) p->vol_kind = VOL_NONE;  // swept with another penalty
     return PLAN_OK;
 }
 
@@ -578,7 +581,7 @@ int plan_sweep_gear(plan_t* p, plan_pose start, int start_gear, int n_cycles) {
     a.Lr = p->d_Lr;
     a.pen = p->gear_pen;
     cudaStream_t s = p->stream;
-    p->gear_ready = false;
+    p->vol_kind = VOL_NONE;
     int rc = cuda_rc(launch_gear_init(p->d_V, p->d_Vr, p->d_L, p->d_Lr, p->nr, cell_index(p, start), start_gear, s));
     p->launches++;
     for (int l = 0; l < 6 * n_cycles && rc == PLAN_OK; l++) {
@@ -588,7 +591,7 @@ int plan_sweep_gear(plan_t* p, plan_pose start, int start_gear, int n_cycles) {
         rc = cuda_rc(launch_gear_layer(a, mu, s));
         p->launches++;
     }
-    if (rc == PLAN_OK) p->gear_ready = true;
+    if (rc == PLAN_OK) p->vol_kind = VOL_GEAR;
     return rc;
 }
 
@@ -598,7 +601,7 @@ int plan_extract_gear(plan_t* p, plan_pose goal, plan_segment* out, int cap, int
     *n_out = 0;
     *cost = PLAN_INF;
     *end_gear = -1;
-    if (!p->gear_ready) return PLAN_ESTATE;
+    if (p->vol_kind != VOL_GEAR) return PLAN_ESTATE;
     GearLayer a{};
     a.g = p->g;
     a.Vf = p->d_V;
@@ -679,6 +682,7 @@ int plan_extract(plan_t* p, plan_pose goal, plan_segment* out, int cap, int* n_o
     if (!p || !n_out || !cost || cap < 0 || (cap > 0 && !out) || !pose_ok(p, goal)) return PLAN_EINVAL;
     *n_out = 0;
     *cost = PLAN_INF;
+    if (p->vol_kind != VOL_PLAIN) return PLAN_ESTATE;
     p->qd.goal = cell_index(p, goal);
     int rc = upload_desc(p);
     if (rc == PLAN_OK) rc = cuda_rc(launch_extract(p->group(), p->stream));
@@ -701,7 +705,7 @@ int plan_extract_goal_set(plan_t* p, const plan_goal* goals, int n_goals, plan_s
             q.radius_theta > 255 || 2 * q.radius_theta >= p->nt)
             return PLAN_EINVAL;
     }
-    if (!p->volumes) return PLAN_ESTATE;
+    if (!p->volumes || p->vol_kind != VOL_PLAIN) return PLAN_ESTATE;
     if (n_goals > p->goal_cap) {
         p->dfree(p->d_goals, goal_buffer_bytes(p->goal_cap));
         p->d_goals = (unsigned char*)p->dalloc(goal_buffer_bytes(n_goals));
@@ -747,6 +751,7 @@ int plan_autotune(plan_t* p, plan_pose start, plan_tune_entry* out, int cap, int
     if (!p->rendered) return PLAN_ESTATE;
     if (pose_hard(p, start)) return PLAN_EINVAL;
     if (n_out) *n_out = 0;
+    p->vol_kind = VOL_NONE;  // the timed passes leave V and L in between
     // Start the sweeps (init, passes 0 and 1), then time every turn shape on
     // pass 2 (RB, RF) and every straight shape on pass 3 (SB).  Repeating a
     // pass changes the values; the next plan_sweep initialises again.

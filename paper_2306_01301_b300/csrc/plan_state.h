@@ -9,6 +9,8 @@ using nhp::DevGrid;
 using nhp::PlaneInfo;
 using nhp::Run;
 
+enum { VOL_NONE = 0, VOL_PLAIN = 1, VOL_GEAR = 2 };
+
 struct plan_s {
     int lx = 0, lt = 0, nx = 0, nt = 0;
     int64_t nxy = 0, nr = 0;
@@ -19,7 +21,10 @@ struct plan_s {
     uint32_t* d_Vr = nullptr;             // reverse gear state (plan_set_gear_penalty)
     uint16_t* d_Lr = nullptr;
     uint32_t gear_pen = 0;
-    bool gear_on = false, gear_ready = false;
+    bool gear_on = false;
+    // what V and L hold: nothing usable, a plain (one transition state)
+    // sweep, or a two-gear-state sweep; each back-track reads only its own
+    int vol_kind = VOL_NONE;
     int dir_tol = 0;
     uint32_t dir_pen = 256;
     plan_footprint fp{};

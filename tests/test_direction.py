@@ -64,6 +64,37 @@ def test_direction_penalties_bit_exact(grid):
     p.close()
 
 
+def test_batch_renders_the_direction_fields():
+    """A batch renders every member's B as plan_render_cspace would, its
+    direction field included, and replays its graph again when a field
+    changes."""
+    from paper_2306_01301_b300 import binding
+    lx, lt = 6, 6
+    sc, img = scenes.tiny(21, lx, lt, fill=0.05, turn_radius=8.0, footprint=(3, 1, 1), soft=True, transition=300)
+    o = O.Oracle(lx, lt, 8.0, transition=sc.transition)
+    B0 = o.render(img, sc.footprint)
+    starts = [c for c in sc.pose_candidates if B0[o.cell(c)] != O.HARD][:2]
+    rng = np.random.default_rng(4)
+    fields = [random_field(rng, o.nx, o.nt), None]
+    planners = [planner(sc, img) for _ in starts]
+    planners[0].set_direction_field(fields[0], 5, 900)
+    b = binding.Batch(planners)
+    for rep in range(2):
+        b.run([(s, sc.goal, 2) for s in starts], render=True)
+        b.sync()
+        for q, f, s in zip(planners, fields, starts):
+            _, _, B = q.volumes(V=False, L=False)
+            Bo = B0 if f is None else o.direction(B0, f, 5 if rep == 0 else 2, 900 if rep == 0 else 400)
+            assert np.array_equal(B, Bo)
+            V, L, _ = q.volumes(B=False)
+            Vo, Lo, _ = o.sweep(Bo, o.cell(s), 2, mode=1)
+            assert np.array_equal(V, Vo) and np.array_equal(L, Lo)
+        planners[0].set_direction_field(fields[0], 2, 400)  # a new tolerance and penalty: a new graph
+    b.close()
+    for q in planners:
+        q.close()
+
+
 def test_direction_field_is_checked():
     from paper_2306_01301_b300 import binding
     sc, img = scenes.tiny(6, 4, 4, fill=0.05)

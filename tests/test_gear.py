@@ -80,6 +80,16 @@ def test_gear_calls_are_checked():
     assert e.value.code == binding.PLAN_EINVAL
     with pytest.raises(binding.PlanError):
         p.extract_gear(sc.goal)  # nothing swept yet
+    # each back-track reads only volumes of its own kind of sweep
+    p.sweep_gear(sc.start, 0, 1)
+    with pytest.raises(binding.PlanError) as e:
+        p.extract(sc.goal)
+    assert e.value.code == -8
+    p.sweep(sc.start, 1)
+    with pytest.raises(binding.PlanError) as e:
+        p.extract_gear(sc.goal)
+    assert e.value.code == -8
+    p.extract(sc.goal)
     p.set_gear_penalty(None)
     with pytest.raises(binding.PlanError):
         p.sweep_gear(sc.start, 0, 1)
