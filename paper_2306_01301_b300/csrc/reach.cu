@@ -178,24 +178,32 @@ k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restr
     // [direction][chain word][section]: the section maps, then what enters
     // each section; the odd pitch keeps both access patterns conflict-free
     __shared__ uint32_t sA[2][32][SEC + 1], sC[2][32][SEC + 1];
+    // per heading: the volume row of the block's first chain row << 16 | the
+    // chains' bit offset; a warp fills and reads only its own K headings
+    __shared__ uint32_t srow[K * SEC];
     const int W = 1 << (g.lx - 5), G = 32 / W;
     const int lane = threadIdx.x & 31, sec = threadIdx.x >> 5;
     const int r = lane / W, l = lane & (W - 1);
-    const int yq = blockIdx.x * G + r;  // chain row y'
-    const int64_t nrow = (int64_t)W;     // words per row
-    const int64_t nplane = (int64_t)W << g.lx;
-    // row word of this lane and bit offset of the chain cells, heading T
-    auto where = [&](int T, int& off) -> int64_t {
+    if (lane < K) {
+        const int T = sec * K + lane;
         const int4 b = __ldg(&g.beta4[T]);
         const int bx = family ? b.z : b.x, by = family ? b.w : b.y;
-        off = bx & g.mx;
-        return (int64_t)T * nplane + (int64_t)((yq + by) & g.mx) * nrow + l;
+        srow[T] = ((uint32_t)((blockIdx.x * G + by) & g.mx) << 16) | (uint32_t)(bx & g.mx);
+    }
+    __syncwarp();
+    // word of this lane's chain row and bit offset of the chain cells, heading
+    // T (volumes here hold at most 2^22 words: 32-bit offsets)
+    auto where = [&](int T, int& off) -> uint32_t {
+        const uint32_t e = srow[T];
+        off = (int)(e & 0xFFFFu);
+        const uint32_t row = ((e >> 16) + (uint32_t)r) & (uint32_t)g.mx;
+        return ((uint32_t)T << (2 * g.lx - 5)) + (row << (g.lx - 5)) + (uint32_t)l;
     };
     uint32_t vi[K], hb[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int off;
-        const int64_t ix = where(sec * K + k, off);
+        const uint32_t ix = where(sec * K + k, off);
         vi[k] = gather_bits(rd(Rm + ix), l, off, W);
         hb[k] = gather_bits(rd(H + ix), l, off, W);
     }
@@ -241,7 +249,7 @@ k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restr
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int off;
-        const int64_t ix = where(sec * K + k, off);
+        const uint32_t ix = where(sec * K + k, off);
         const uint32_t word = scatter_bits(~o[k], l, off, W);
         if (assign) Rn[ix] = rd(Rm + ix) & word;
         else Rn[ix] &= word;
