@@ -29,6 +29,8 @@
 // u = 0 for hard cells (a hard cell is never stored because v < 0 is
 // impossible, and its entry is cancelled by its edge cost TH before it can
 // reach another cell).
+#include <atomic>
+
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -786,16 +788,18 @@ cudaError_t launch_turn(const Group& gr, int pass, int variant, cudaStream_t s) 
 }
 
 namespace {
+// The attribute is per device; setting it twice (two host threads racing
+// here) is harmless, the flags only save the call.
 cudaError_t straight_attr() {
-    static bool attr_set[64] = {};
+    static std::atomic<bool> attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(k_straight, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(2 * sizeof(StraightStage)));
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
     }
     return cudaSuccess;
 }
