@@ -241,6 +241,8 @@ def run_ours(args):
     achieved = turn_bytes / (turn_launch_ms / 1e3) / 1e9
     straight_launch_ms = prof["straight_ms"] / max(1, prof["straight_passes"])
     straight_bytes = sc.cells * 6 + 6 * prof["straight_improved"] / max(1, prof["straight_passes"])
+    render_ms = prof["render_ms"] / max(1, prof["render_passes"])
+    render_gbs = sc.cells * 2 / (render_ms / 1e3) / 1e9  # writes B; the image and bit tables come from L2
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -258,7 +260,12 @@ def run_ours(args):
                      "traffic": ncu_traffic(), "bytes_per_launch": turn_bytes, "launch_ms": turn_launch_ms},
         "kernels": {"turn_ms_per_launch": turn_launch_ms, "straight_ms_per_launch": straight_launch_ms,
                     "straight_GBps": straight_bytes / (straight_launch_ms / 1e3) / 1e9,
-                    "render_ms_per_step": prof["render_ms"] / max(1, prof["render_passes"]),
+                    "straight_frac": straight_bytes / (straight_launch_ms / 1e3) / 1e9 / peak,
+                    "render_ms_per_step": render_ms,
+                    "render": {"bound": "alu", "GBps": render_gbs, "frac_of_hbm": render_gbs / peak,
+                               "note": "2 B of B written per pose; per 32 poses one OR of two sparse-table windows "
+                                       "per footprint row run (96x38 vehicle: about 40 to 100 runs per heading), "
+                                       "so the footprint test, not HBM, bounds it"},
                     "init_ms_per_step": prof["init_ms"] / max(1, prof["init_passes"]),
                     "turn_tiles_improved_share": prof["turn_tiles_improved"] / max(1, prof["turn_passes"])
                     / ((sc.nx * sc.nx + 31) // 32)},
