@@ -130,30 +130,60 @@ __global__ void k_bits_level(const QueryDesc* __restrict__ qd, int lvl) {
     }
 }
 
+// A footprint row run decoded for one heading: the table level's word
+// offset, the row shift, and the word offset and bit shift of its two
+// windows (both starts taken modulo Nx).
+struct RunW {
+    int32_t base, dy, q1, s1, q2, s2;
+};
+
 // One thread per (32-pose word, row j) of heading blockIdx.y.  Writes HARD
 // where the footprint meets a hard cell; elsewhere `free_value` (256 for a
-// hard-only image, 0 as a placeholder when a soft pass follows).
+// hard-only image, 0 as a placeholder when a soft pass follows).  With at
+// most 32 words per row (Nx <= 1024) the words of a row are neighbouring
+// lanes: a window's two words are this lane's load and the next lane's
+// (a shuffle within the row's segment of lanes), and everything about a run
+// but the lane's own word index is the same for the whole warp.
 __global__ void __launch_bounds__(256) k_render_bits(const QueryDesc* __restrict__ qd, uint16_t free_value) {
-    extern __shared__ Run runs[];
+    extern __shared__ RunW rw[];
     const QueryDesc& Q = qd[blockIdx.z];
     const DevGrid g = Q.g;
     const uint32_t* __restrict__ bits = Q.bits;
     uint16_t* __restrict__ B = Q.v.B;
     const int T = blockIdx.y;
     const int r0 = g.run_off[T], nr = g.run_off[T + 1] - r0;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = g.runs[r0 + r];
-    __syncthreads();
     const int nw = g.nx >> 5;
+    const int64_t plane_words = (int64_t)g.nx * nw;  // words of one table level (<= 2^19)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        const Run ru = g.runs[r0 + r];
+        const int lo = ru.lo & g.mx, hi = ru.hi2 & g.mx;
+        rw[r] = RunW{(int32_t)(ru.lvl * plane_words), ru.dy, lo >> 5, lo & 31, hi >> 5, hi & 31};
+    }
+    __syncthreads();
     const int64_t words = (int64_t)g.nx * nw;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= words) return;
+    if (k >= words) return;  // whole warps: words is a multiple of 32
     const int j = (int)(k / nw), w = (int)(k % nw);
-    const int64_t plane_words = (int64_t)g.nx * nw;
     uint32_t hard = 0;
-    for (int r = 0; r < nr && hard != 0xFFFFFFFFu; r++) {
-        const Run ru = runs[r];
-        const uint32_t* row = bits + (int64_t)ru.lvl * plane_words + (int64_t)((j + ru.dy) & g.mx) * nw;
-        hard |= row_window(row, ((32 * w + ru.lo) & g.mx), nw - 1) | row_window(row, ((32 * w + ru.hi2) & g.mx), nw - 1);
+    if (nw <= 32) {
+        const int nm = nw - 1, next = (w + 1) & nm;
+        for (int r = 0; r < nr; r++) {
+            if ((r & 7) == 0 && __all_sync(0xFFFFFFFFu, hard == 0xFFFFFFFFu)) break;
+            const RunW ru = rw[r];
+            const uint32_t* row = bits + ru.base + ((j + ru.dy) & g.mx) * nw;
+            const uint32_t a1 = __ldg(row + ((w + ru.q1) & nm));
+            const uint32_t b1 = __shfl_sync(0xFFFFFFFFu, a1, next, nw);
+            const uint32_t a2 = __ldg(row + ((w + ru.q2) & nm));
+            const uint32_t b2 = __shfl_sync(0xFFFFFFFFu, a2, next, nw);
+            hard |= __funnelshift_r(a1, b1, ru.s1) | __funnelshift_r(a2, b2, ru.s2);
+        }
+    } else {
+        for (int r = 0; r < nr && hard != 0xFFFFFFFFu; r++) {
+            const RunW ru = rw[r];
+            const uint32_t* row = bits + ru.base + (int64_t)((j + ru.dy) & g.mx) * nw;
+            hard |= row_window(row, 32 * (w + ru.q1) + ru.s1, nw - 1) |
+                    row_window(row, 32 * (w + ru.q2) + ru.s2, nw - 1);
+        }
     }
     uint4* out = (uint4*)(B + (int64_t)T * g.nx * g.nx + (int64_t)j * g.nx + 32 * w);
 #pragma unroll
@@ -199,6 +229,20 @@ __global__ void __launch_bounds__(256) k_render_soft(const QueryDesc* __restrict
 
 }  // namespace
 
+// Footprints with many row runs need more than the default 48 KB of dynamic
+// shared memory for a heading's runs: raise the kernel's limit (up to what
+// the device allows) when a launch needs it.
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0, most = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&most, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)most) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t launch_sparse_table(const Group& gr, cudaStream_t s) {
     const int64_t nxy = (int64_t)1 << (2 * gr.lx);
     int64_t blocks = (nxy + 255) / 256;
@@ -212,7 +256,10 @@ cudaError_t launch_sparse_table(const Group& gr, cudaStream_t s) {
 cudaError_t launch_render_table(const Group& gr, cudaStream_t s) {
     const int64_t nxy = (int64_t)1 << (2 * gr.lx);
     dim3 grid((unsigned)((nxy + 255) / 256), (unsigned)(1 << gr.lt), (unsigned)gr.nq);
-    k_render<<<grid, 256, (size_t)gr.max_runs * sizeof(Run), s>>>(gr.d);
+    const size_t bytes = (size_t)gr.max_runs * sizeof(Run);
+    const cudaError_t e = allow_smem(k_render, bytes);
+    if (e != cudaSuccess) return e;
+    k_render<<<grid, 256, bytes, s>>>(gr.d);
     return cudaGetLastError();
 }
 
@@ -233,11 +280,15 @@ cudaError_t launch_render(const Group& gr, bool soft, cudaStream_t s, int* launc
         k_bits_level0<<<lg, 256, 0, s>>>(gr.d);
         for (int k = 1; k <= gr.lx; k++) k_bits_level<<<lg, 256, 0, s>>>(gr.d, k);
         const dim3 grid((unsigned)((words + 255) / 256), (unsigned)nt, (unsigned)gr.nq);
-        k_render_bits<<<grid, 256, (size_t)gr.max_runs * sizeof(Run), s>>>(gr.d, soft ? 0 : 256);
+        const size_t wbytes = (size_t)gr.max_runs * sizeof(RunW), rbytes = (size_t)gr.max_runs * sizeof(Run);
+        e = allow_smem(k_render_bits, wbytes);
+        if (e == cudaSuccess) e = soft ? allow_smem(k_render_soft, rbytes) : cudaSuccess;
+        if (e != cudaSuccess) return e;
+        k_render_bits<<<grid, 256, wbytes, s>>>(gr.d, soft ? 0 : 256);
         n += gr.lx + 2;
         if (soft) {
             const dim3 g2((unsigned)(((int64_t)nx * nx + 255) / 256), (unsigned)nt, (unsigned)gr.nq);
-            k_render_soft<<<g2, 256, (size_t)gr.max_runs * sizeof(Run), s>>>(gr.d);
+            k_render_soft<<<g2, 256, rbytes, s>>>(gr.d);
             n += 1;
         }
         e = cudaGetLastError();
