@@ -92,6 +92,20 @@ def lib():
         L.orc_bruteforce_gear.argtypes = [p, p, C.c_int64, C.c_int, C.c_uint32, C.c_int, p]
         L.orc_extract_gear.restype = C.c_int
         L.orc_extract_gear.argtypes = [p, p, p, C.c_int64, p, C.c_int]
+        L.orc4_create.restype = p
+        L.orc4_create.argtypes = [p, C.c_int, C.c_double, C.c_uint32]
+        L.orc4_destroy.argtypes = [p]
+        L.orc4_tables.argtypes = [p, p, p, p]
+        L.orc4_succ.restype = C.c_int64
+        L.orc4_succ.argtypes = [p, C.c_int, C.c_int64]
+        L.orc4_sweep.restype = C.c_int
+        L.orc4_sweep.argtypes = [p, p, C.c_int64, C.c_int, p, p]
+        L.orc4_dijkstra.restype = C.c_int
+        L.orc4_dijkstra.argtypes = [p, p, C.c_int64, p]
+        L.orc4_bruteforce.restype = C.c_int
+        L.orc4_bruteforce.argtypes = [p, p, C.c_int64, C.c_int, p]
+        L.orc4_extract.restype = C.c_int
+        L.orc4_extract.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         L.orc_seed.restype = C.c_int
         L.orc_seed.argtypes = [p, p, C.c_int64, p, p, p]
         L.orc_sweep_state.restype = C.c_int
@@ -376,6 +390,76 @@ class Oracle:
         if n < 0:
             raise ValueError(f"reach_extract failed ({n})")
         return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3])) for r in seg[:n]]
+
+
+class Oracle4:
+    """4D generalisation (App. F): 2M+1 curvature levels of an Oracle's 3D
+    volume, clothoid maneuvers between them (ids 6 C1F, 7 C1B, 8 C2F, 9 C2B)."""
+
+    C1F, C1B, C2F, C2B = 6, 7, 8, 9
+
+    def __init__(self, base: "Oracle", M: int, L: float, ct_clothoid: int):
+        self.base, self.M, self.nk, self.L = base, M, 2 * M + 1, L
+        self.nr = base.nr
+        self.n4 = base.nr * self.nk
+        self._c = lib().orc4_create(base._c, int(M), float(L), int(ct_clothoid))
+        if not self._c:
+            raise ValueError("bad 4D parameters")
+
+    def __del__(self):
+        if getattr(self, "_c", None):
+            lib().orc4_destroy(self._c)
+            self._c = None
+
+    def cell(self, pose, level: int) -> int:
+        """level = kappa in [-M, M]"""
+        return (level + self.M) * self.nr + self.base.cell(pose)
+
+    def pose(self, cell4: int):
+        return self.base.pose(cell4 % self.nr), cell4 // self.nr - self.M
+
+    def tables(self):
+        nt = self.base.nt
+        dx = np.zeros((2, self.nk, nt), np.int16)
+        dy = np.zeros((2, self.nk, nt), np.int16)
+        dth = np.zeros((2, self.nk), np.int32)
+        lib().orc4_tables(self._c, _ptr(dx), _ptr(dy), _ptr(dth))
+        return dx, dy, dth
+
+    def succ(self, mu: int, cell4: int) -> int:
+        return int(lib().orc4_succ(self._c, int(mu), int(cell4)))
+
+    def sweep(self, B: np.ndarray, start4: int, n_cycles: int):
+        V = np.zeros(self.n4, np.uint32)
+        L = np.zeros(self.n4, np.uint16)
+        if lib().orc4_sweep(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start4), int(n_cycles),
+                            _ptr(V), _ptr(L)) != 0:
+            raise ValueError("4D sweep failed")
+        return V, L
+
+    def dijkstra(self, B: np.ndarray, start4: int) -> np.ndarray:
+        V = np.zeros(self.n4, np.uint32)
+        if lib().orc4_dijkstra(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start4), _ptr(V)) != 0:
+            raise ValueError("4D dijkstra failed")
+        return V
+
+    def bruteforce(self, B: np.ndarray, start4: int, n_cycles: int) -> np.ndarray:
+        V = np.zeros(self.n4, np.uint32)
+        if lib().orc4_bruteforce(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start4), int(n_cycles),
+                                 _ptr(V)) != 0:
+            raise ValueError("4D bruteforce failed")
+        return V
+
+    def extract(self, V: np.ndarray, L: np.ndarray, goal4: int, cap: int = 4096):
+        seg = np.zeros((cap, 5), np.int64)
+        n = lib().orc4_extract(self._c, _ptr(np.ascontiguousarray(V, np.uint32)),
+                               _ptr(np.ascontiguousarray(L, np.uint16)), int(goal4), _ptr(seg), cap)
+        if n == -1:
+            return None
+        if n < 0:
+            raise ValueError(f"4D extract failed ({n})")
+        return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3]), cost=int(r[4]))
+                for r in seg[:n]]
 
 
 def soft_image(occupancy: np.ndarray, radius: int, soft_max: int) -> np.ndarray:

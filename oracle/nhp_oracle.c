@@ -1085,6 +1085,355 @@ int orc_extract_gear(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int
     return n;
 }
 
+/* ------------------------------------------------- 4D generalisation (App. F)
+ * Curvature as a fourth state dimension: 2M+1 levels kappa = -M .. M (index
+ * K = kappa + M) of the 3D volume, curvature k = kappa / (M R).  Readings of
+ * App. F where it is silent:
+ *   - extremal controls: the turns of the 3D model at the steering limits
+ *     (LF, LB at kappa = +M; RF, RB at -M), the straights at kappa = 0, and
+ *     clothoids that change the curvature one level per arc length L (cells)
+ *     at the other levels: family C1 with dk/ds = +1/(M R L), family C2 with
+ *     dk/ds = -1/(M R L), each driven forward and backward (time reversal:
+ *     C1F raises kappa, C1B lowers it, C2F lowers it, C2B raises it);
+ *   - a clothoid chain is named by its pose (x0, y0, theta0) at kappa = 0;
+ *     at level kappa it is at (x0 + round X, y0 + round Y, theta0 + round
+ *     Psi) with s = kappa L (C1) or -kappa L (C2), Psi = +-a s^2, a = 1 /
+ *     (2 M R L), X = int_0^s cos(theta0 +- a sigma^2) dsigma, Y the sine
+ *     (App. F's per-level map, a bijection per level), integrals by
+ *     composite Simpson with 64 |kappa| intervals, headings Psi * N_theta /
+ *     (2 pi), rounding half away from zero;
+ *   - a clothoid step costs round(step_scale * L) * B >> 8 of the cell left
+ *     (B does not depend on the curvature), entering a clothoid ctc, leaving
+ *     it nothing; the 3D maneuvers keep their Star costs;
+ *   - chains of a clothoid are open (kappa runs from one steering limit to
+ *     the other): one pass from their first level;
+ *   - cycle order: C1F, C2F, C1B, C2B, then the 3D order LF SF RB RF SB LB
+ *     (maneuver ids 6, 8, 7, 9, 0 .. 5);
+ *   - labels (mu << 12) | d.  The start and the goal name their level. */
+struct orc4 {
+    const orc_ctx* c;
+    int M, nk;
+    double L;
+    uint32_t wC, ctc;
+    int16_t* dx; /* [f][K][T0] */
+    int16_t* dy;
+    int32_t* dth; /* [f][K] */
+};
+
+static double clothoid_f(int f, int xy, double th0, double a, double sg) {
+    double ang = f == 0 ? th0 + a * sg * sg : th0 - a * sg * sg;
+    return xy == 0 ? cos(ang) : sin(ang);
+}
+
+/* int_0^s of cos or sin (xy) of theta0 +- a sigma^2, composite Simpson */
+static double clothoid_int(int f, int xy, double th0, double a, double s, int n) {
+    double h = s / n, acc = clothoid_f(f, xy, th0, a, 0.0) + clothoid_f(f, xy, th0, a, s);
+    for (int i = 1; i < n; i++) acc += (i & 1 ? 4.0 : 2.0) * clothoid_f(f, xy, th0, a, i * h);
+    return acc * h / 3.0;
+}
+
+orc4* orc4_create(const orc_ctx* c, int M, double L, uint32_t ctc) {
+    if (M < 1 || M > 1000 || !(L > 0.0) || L > 4.0 || ctc >= (1u << 28)) return NULL;
+    orc4* q = (orc4*)calloc(1, sizeof(orc4));
+    if (!q) return NULL;
+    q->c = c; q->M = M; q->nk = 2 * M + 1; q->L = L; q->ctc = ctc;
+    q->wC = (uint32_t)lround((double)c->step_a * L);
+    if (q->wC == 0) q->wC = 1;
+    size_t n = (size_t)2 * q->nk * c->nt;
+    q->dx = (int16_t*)malloc(sizeof(int16_t) * n);
+    q->dy = (int16_t*)malloc(sizeof(int16_t) * n);
+    q->dth = (int32_t*)malloc(sizeof(int32_t) * 2 * q->nk);
+    if (!q->dx || !q->dy || !q->dth) { orc4_destroy(q); return NULL; }
+    double a = 1.0 / (2.0 * M * c->R * L);
+    for (int f = 0; f < 2; f++)
+        for (int K = 0; K < q->nk; K++) {
+            int kap = K - M;
+            double s = f == 0 ? kap * L : -kap * L;
+            double psi = f == 0 ? a * s * s : -a * s * s;
+            q->dth[f * q->nk + K] = (int32_t)lround(psi * c->nt / (2.0 * ORC_PI));
+            int nint = 64 * (kap < 0 ? -kap : kap);
+            for (int T0 = 0; T0 < c->nt; T0++) {
+                size_t at = ((size_t)f * q->nk + K) * c->nt + T0;
+                if (kap == 0) { q->dx[at] = 0; q->dy[at] = 0; continue; }
+                double th0 = heading(T0, c->nt);
+                q->dx[at] = (int16_t)lround(clothoid_int(f, 0, th0, a, s, nint));
+                q->dy[at] = (int16_t)lround(clothoid_int(f, 1, th0, a, s, nint));
+            }
+        }
+    return q;
+}
+
+void orc4_destroy(orc4* q) {
+    if (!q) return;
+    free(q->dx); free(q->dy); free(q->dth); free(q);
+}
+
+void orc4_tables(const orc4* q, int16_t* dx, int16_t* dy, int32_t* dth) {
+    size_t n = (size_t)2 * q->nk * q->c->nt;
+    memcpy(dx, q->dx, sizeof(int16_t) * n);
+    memcpy(dy, q->dy, sizeof(int16_t) * n);
+    memcpy(dth, q->dth, sizeof(int32_t) * 2 * q->nk);
+}
+
+static int m4_level(const orc4* q, int mu) { /* level of a 3D maneuver */
+    if (mu == LF || mu == LB) return q->nk - 1;
+    if (mu == RF || mu == RB) return 0;
+    return q->M;
+}
+static int m4_family(int mu) { return (mu == 6 || mu == 7) ? 0 : 1; }
+static int m4_dir(int mu) { return (mu == 6 || mu == 9) ? 1 : -1; } /* kappa step */
+
+/* Cell (3D index) of clothoid family f's chain (i0, j0, T0) at level K. */
+static int64_t m4_chain_cell(const orc4* q, int f, int i0, int j0, int T0, int K) {
+    const orc_ctx* c = q->c;
+    size_t at = ((size_t)f * q->nk + K) * c->nt + T0;
+    return cell_of(c, i0 + q->dx[at], j0 + q->dy[at], T0 + q->dth[f * q->nk + K]);
+}
+
+/* Successor of 4D cell (3D cell x at level K) along maneuver mu; -1 none. */
+int64_t orc4_succ(const orc4* q, int mu, int64_t x4) {
+    const orc_ctx* c = q->c;
+    int64_t nr = c->nr;
+    int K = (int)(x4 / nr);
+    int64_t x = x4 % nr;
+    if (mu < 6) {
+        if (K != m4_level(q, mu)) return -1;
+        return (int64_t)K * nr + orc_succ(c, mu, x);
+    }
+    int f = m4_family(mu), K2 = K + m4_dir(mu);
+    if (K2 < 0 || K2 >= q->nk) return -1;
+    int i, j, T;
+    coords(c, x, &i, &j, &T);
+    int T0 = (T - q->dth[f * q->nk + K]) & c->mt;
+    size_t at = ((size_t)f * q->nk + K) * c->nt + T0;
+    return (int64_t)K2 * nr + m4_chain_cell(q, f, i - q->dx[at], j - q->dy[at], T0, K2);
+}
+
+static uint32_t m4_edge(const orc4* q, const uint16_t* B, int mu, int64_t x4) {
+    int64_t x = x4 % q->c->nr;
+    if (mu < 6) return orc_edge(q->c, B, mu, x);
+    if (B[x] == ORC_HARD) return ORC_INF;
+    return (uint32_t)(((uint64_t)q->wC * B[x]) >> 8);
+}
+static uint32_t m4_cin(const orc4* q, int mu) { return mu < 6 ? q->c->cin[mu] : q->ctc; }
+static uint32_t m4_cout(const orc4* q, int mu) { return mu < 6 ? q->c->cout[mu] : 0u; }
+
+static const int cycle4[10] = {6, 8, 7, 9, LF, SF, RB, RF, SB, LB};
+
+/* One maneuver layer on the 4D volumes (values read at the start of the
+ * layer).  Cyclic chains (turns, straights) take two loops as in
+ * layer_lockstep; clothoid chains are open and take one pass. */
+static int layer4(const orc4* q, const uint16_t* B, int mu, const uint32_t* Vin, uint32_t* V, uint16_t* L) {
+    const orc_ctx* c = q->c;
+    int64_t nr = c->nr;
+    int64_t* cyc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(c->nx > c->nt ? c->nx : c->nt) * 2 + 64 +
+                                    sizeof(int64_t) * q->nk);
+    if (!cyc) return -1;
+    int rc = 0;
+    if (mu < 6) {
+        int K = m4_level(q, mu), n;
+        int64_t nchains;
+        if (is_turn(mu)) { nchains = (int64_t)c->nx * c->nx; n = c->nt; }
+        else { nchains = c->nx; n = c->nx; }
+        int nplanes = is_turn(mu) ? 1 : c->nt;
+        for (int plane = 0; plane < nplanes && rc == 0; plane++)
+            for (int64_t k = 0; k < nchains && rc == 0; k++) {
+                int64_t x = is_turn(mu) ? k
+                            : (c->iflag[plane] == 0 ? cell_of(c, 0, (int)k, plane) : cell_of(c, (int)k, 0, plane));
+                for (int t = 0; t < n; t++) { cyc[t] = (int64_t)K * nr + x; x = orc_succ(c, mu, x); }
+                if ((int64_t)K * nr + x != cyc[0]) rc = -1;
+                uint32_t v = ORC_INF;
+                int qe = 0;
+                for (int qq = 0; qq < 2 * n; qq++) {
+                    int64_t y = cyc[qq % n];
+                    int hard = B[y % nr] == ORC_HARD;
+                    if (qq >= n) {
+                        uint32_t cand = hard ? ORC_INF : sadd(v, m4_cout(q, mu));
+                        if (cand < Vin[y] && cand < V[y]) {
+                            V[y] = cand;
+                            L[y] = (uint16_t)((mu << 12) | (qq - qe));
+                        }
+                    }
+                    uint32_t t = hard ? ORC_INF : sadd(Vin[y], m4_cin(q, mu));
+                    if (t < v) { v = t; qe = qq; }
+                    v = sadd(v, m4_edge(q, B, mu, y));
+                }
+            }
+    } else {
+        int f = m4_family(mu), dir = m4_dir(mu);
+        for (int T0 = 0; T0 < c->nt; T0++)
+            for (int j0 = 0; j0 < c->nx; j0++)
+                for (int i0 = 0; i0 < c->nx; i0++) {
+                    uint32_t v = ORC_INF;
+                    int qe = 0;
+                    for (int qq = 0; qq < q->nk; qq++) {
+                        int K = dir > 0 ? qq : q->nk - 1 - qq;
+                        int64_t y = (int64_t)K * nr + m4_chain_cell(q, f, i0, j0, T0, K);
+                        int hard = B[y % nr] == ORC_HARD;
+                        uint32_t cand = hard ? ORC_INF : sadd(v, m4_cout(q, mu));
+                        if (cand < Vin[y] && cand < V[y]) {
+                            V[y] = cand;
+                            L[y] = (uint16_t)((mu << 12) | (qq - qe));
+                        }
+                        uint32_t t = hard ? ORC_INF : sadd(Vin[y], m4_cin(q, mu));
+                        if (t < v) { v = t; qe = qq; }
+                        v = sadd(v, m4_edge(q, B, mu, y));
+                    }
+                }
+    }
+    free(cyc);
+    return rc;
+}
+
+int orc4_sweep(const orc4* q, const uint16_t* B, int64_t start4, int n_cycles, uint32_t* V, uint16_t* L) {
+    const orc_ctx* c = q->c;
+    int64_t n4 = c->nr * q->nk;
+    if (start4 < 0 || start4 >= n4 || B[start4 % c->nr] == ORC_HARD || n_cycles < 0) return -1;
+    if (c->nx > 2048 || c->nt > 2048) return -1;
+    for (int64_t x = 0; x < n4; x++) { V[x] = ORC_INF; L[x] = ORC_NONE; }
+    V[start4] = 0;
+    uint32_t* Vin = (uint32_t*)malloc(sizeof(uint32_t) * n4);
+    if (!Vin) return -1;
+    int rc = 0;
+    for (int l = 0; l < 10 * n_cycles && rc == 0; l++) {
+        memcpy(Vin, V, sizeof(uint32_t) * n4);
+        rc = layer4(q, B, cycle4[l % 10], Vin, V, L);
+    }
+    free(Vin);
+    return rc;
+}
+
+/* Dijkstra on the explicit 4D Star graph: T(x4) and M_mu(x4) for the
+ * maneuvers that exist at x4's level. */
+int orc4_dijkstra(const orc4* q, const uint16_t* B, int64_t start4, uint32_t* Vinf) {
+    const orc_ctx* c = q->c;
+    int64_t n4 = c->nr * q->nk, nv = 11 * n4; /* [0, n4) T, (1+mu)*n4 + x4: M_mu */
+    if (start4 < 0 || start4 >= n4 || B[start4 % c->nr] == ORC_HARD) return -1;
+    iheap h;
+    h.key = (uint32_t*)malloc(sizeof(uint32_t) * nv);
+    h.heap = (int64_t*)malloc(sizeof(int64_t) * nv);
+    h.pos = (int64_t*)malloc(sizeof(int64_t) * nv);
+    uint8_t* done = (uint8_t*)calloc((size_t)nv, 1);
+    if (!h.key || !h.heap || !h.pos || !done) { free(h.key); free(h.heap); free(h.pos); free(done); return -1; }
+    for (int64_t v = 0; v < nv; v++) { h.key[v] = ORC_INF; h.pos[v] = -1; }
+    h.key[start4] = 0; h.heap[0] = start4; h.pos[start4] = 0; h.n = 1;
+#define R4(dst, w)                                                      \
+    do {                                                                \
+        uint32_t nd_ = sadd(du, (w));                                   \
+        int64_t d_ = (dst);                                             \
+        if (nd_ < h.key[d_] && !done[d_]) {                             \
+            h.key[d_] = nd_;                                            \
+            if (h.pos[d_] < 0) { h.heap[h.n] = d_; h.pos[d_] = h.n; h.n++; } \
+            heap_up(&h, h.pos[d_]);                                     \
+        }                                                               \
+    } while (0)
+    while (h.n > 0) {
+        int64_t u = h.heap[0];
+        heap_swap(&h, 0, h.n - 1);
+        h.n--;
+        h.pos[u] = -1;
+        if (h.n > 0) heap_down(&h, 0);
+        done[u] = 1;
+        uint32_t du = h.key[u];
+        if (du == ORC_INF) break;
+        int64_t x4 = u % n4;
+        int kind = (int)(u / n4);
+        if (B[x4 % c->nr] == ORC_HARD) continue;
+        if (kind == 0) {
+            for (int m = 0; m < 10; m++) {
+                if (m < 6 && x4 / c->nr != m4_level(q, m)) continue;
+                R4((1 + m) * n4 + x4, m4_cin(q, m));
+            }
+        } else {
+            int m = kind - 1;
+            R4(x4, m4_cout(q, m));
+            int64_t y4 = orc4_succ(q, m, x4);
+            if (y4 >= 0 && B[y4 % c->nr] != ORC_HARD) R4((1 + m) * n4 + y4, m4_edge(q, B, m, x4));
+        }
+    }
+#undef R4
+    for (int64_t x = 0; x < n4; x++) Vinf[x] = B[x % c->nr] == ORC_HARD ? ORC_INF : h.key[x];
+    free(h.key); free(h.heap); free(h.pos); free(done);
+    return 0;
+}
+
+/* Exhaustive search over layer-ordered segment sequences (tiny grids). */
+typedef struct {
+    const orc4* q;
+    const uint16_t* B;
+    int layers;
+    uint32_t* seen;
+    uint32_t* best;
+} bf4_state;
+
+static void bf4_explore(bf4_state* s, int layer, int64_t x4, uint32_t cost) {
+    const orc4* q = s->q;
+    int64_t n4 = q->c->nr * q->nk;
+    uint32_t* sl = s->seen + (size_t)layer * n4;
+    if (cost >= sl[x4]) return;
+    sl[x4] = cost;
+    if (cost < s->best[x4]) s->best[x4] = cost;
+    if (layer == s->layers) return;
+    bf4_explore(s, layer + 1, x4, cost);
+    int mu = cycle4[layer % 10];
+    if (mu < 6 && x4 / q->c->nr != m4_level(q, mu)) return;
+    int n = mu < 6 ? (is_turn(mu) ? q->c->nt : q->c->nx) : q->nk;
+    uint32_t run = sadd(cost, m4_cin(q, mu));
+    int64_t y = x4;
+    for (int d = 1; d < n; d++) {
+        run = sadd(run, m4_edge(q, s->B, mu, y));
+        y = orc4_succ(q, mu, y);
+        if (y < 0 || run == ORC_INF) break;
+        if (s->B[y % q->c->nr] != ORC_HARD) bf4_explore(s, layer + 1, y, sadd(run, m4_cout(q, mu)));
+    }
+}
+
+int orc4_bruteforce(const orc4* q, const uint16_t* B, int64_t start4, int n_cycles, uint32_t* Vbest) {
+    int64_t n4 = q->c->nr * q->nk;
+    if (start4 < 0 || start4 >= n4 || B[start4 % q->c->nr] == ORC_HARD || n_cycles < 0) return -1;
+    bf4_state s = {q, B, 10 * n_cycles, NULL, Vbest};
+    s.seen = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(s.layers + 1) * n4);
+    if (!s.seen) return -1;
+    for (int64_t k = 0; k < (int64_t)(s.layers + 1) * n4; k++) s.seen[k] = ORC_INF;
+    for (int64_t x = 0; x < n4; x++) Vbest[x] = ORC_INF;
+    bf4_explore(&s, 0, start4, 0);
+    free(s.seen);
+    return 0;
+}
+
+/* Label walk in 4D: seg[k*5 + {mu, entry4, exit4, d, cost}], driving order. */
+int orc4_extract(const orc4* q, const uint32_t* V, const uint16_t* L, int64_t goal4, int64_t* seg, int cap) {
+    int64_t n4 = q->c->nr * q->nk;
+    if (goal4 < 0 || goal4 >= n4) return -3;
+    if (V[goal4] == ORC_INF) return -1;
+    static const int rev4[10] = {LB, SB, RF, RB, SF, LF, 7, 6, 9, 8};
+    int n = 0, guard = 0;
+    int64_t x = goal4;
+    while (L[x] != ORC_NONE) {
+        if (++guard > 1 << 20) return -3;
+        int mu = L[x] >> 12, d = L[x] & 4095;
+        if (mu > 9 || d == 0) return -3;
+        int64_t e = x;
+        for (int k = 0; k < d && e >= 0; k++) e = orc4_succ(q, rev4[mu], e);
+        if (e < 0) return -3;
+        if (n < cap) {
+            int64_t* r = seg + 5 * (size_t)n;
+            r[0] = mu; r[1] = e; r[2] = x; r[3] = d; r[4] = V[x];
+        }
+        n++;
+        x = e;
+    }
+    if (V[x] != 0) return -3;
+    if (n > cap) return -2;
+    for (int a2 = 0, b2 = n - 1; a2 < b2; a2++, b2--)
+        for (int k = 0; k < 5; k++) {
+            int64_t t = seg[5 * a2 + k];
+            seg[5 * a2 + k] = seg[5 * b2 + k];
+            seg[5 * b2 + k] = t;
+        }
+    return n;
+}
+
 /* ------------------------------------------------------------ goal search
  * Section IX: a goal set instead of one exact pose, each pose scored by a
  * reward that falls with its distance from an ideal pose; the best pose

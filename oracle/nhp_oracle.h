@@ -110,6 +110,21 @@ int orc_bruteforce_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int 
                         int n_cycles, uint32_t* Vbest);
 int orc_extract_gear(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal, int64_t* seg,
                      int cap);
+/* 4D generalisation (App. F): 2M+1 curvature levels of the 3D volume,
+ * clothoid maneuvers between them (ids 6 C1F, 7 C1B, 8 C2F, 9 C2B), the 3D
+ * turns at the steering limits and the straights at zero curvature.  4D
+ * cells are K * nr + 3D cell (K = kappa + M); labels (mu << 12) | d.
+ * orc4_tables: dx, dy [2][2M+1][N_theta], dth [2][2M+1].  Extract rows
+ * seg[k*5 + {mu, entry4, exit4, d, cost}]. */
+typedef struct orc4 orc4;
+orc4*   orc4_create(const orc_ctx* c, int M, double L, uint32_t ct_clothoid);
+void    orc4_destroy(orc4* q);
+void    orc4_tables(const orc4* q, int16_t* dx, int16_t* dy, int32_t* dth);
+int64_t orc4_succ(const orc4* q, int mu, int64_t cell4);
+int     orc4_sweep(const orc4* q, const uint16_t* B, int64_t start4, int n_cycles, uint32_t* V, uint16_t* L);
+int     orc4_dijkstra(const orc4* q, const uint16_t* B, int64_t start4, uint32_t* Vinf);
+int     orc4_bruteforce(const orc4* q, const uint16_t* B, int64_t start4, int n_cycles, uint32_t* Vbest);
+int     orc4_extract(const orc4* q, const uint32_t* V, const uint16_t* L, int64_t goal4, int64_t* seg, int cap);
 /* Goal search over a goal set (Section IX): the reached pose minimising
  * V + bias + w_xy (|dx|+|dy|) + w_theta |dtheta| over every goal's box;
  * goals[g*8 + {x, y, theta, r_xy, r_theta, w_xy, w_theta, bias}].  Returns 0
