@@ -201,6 +201,56 @@ int plan_extract_gear(plan_t* plan, plan_pose goal, plan_segment* out, int cap, 
 /* The reverse gear state's V and L (either may be NULL).  Synchronises. */
 int plan_copy_reverse_volumes(plan_t* plan, uint32_t* V, uint16_t* L);
 
+/* Appendix F, the 4D generalisation: curvature as a fourth state variable.
+ * levels_per_side = M gives 2M+1 levels kappa = -M .. M of the 3D volume,
+ * curvature kappa / (M R).  The 3D turns run at the steering limits (LF, LB
+ * at kappa = +M; RF, RB at -M), the straights at kappa = 0, and four clothoid
+ * maneuvers change the curvature one level per `arc_per_level` cells of
+ * travel: PLAN_C1F (curvature rising as the vehicle drives forward), its
+ * reverse-gear traversal PLAN_C1B, PLAN_C2F (falling forward) and PLAN_C2B.
+ * A clothoid chain through the pose (x0, y0, theta0) at kappa = 0 is at
+ * (x0 + round X, y0 + round Y, theta0 + round Psi) at level kappa, X and Y
+ * the clothoid's integrals over its arc length (Appendix F's per-level map,
+ * a bijection per level).  A clothoid step costs round(step_scale *
+ * arc_per_level) * B >> 8 of the cell it leaves; entering a clothoid costs
+ * clothoid_cost, the 3D maneuvers keep their costs.  A cycle is the layers
+ * C1F, C2F, C1B, C2B, LF, SF, RB, RF, SB, LB.  Allocates (2M+1) * 6 B per
+ * pose; M = 0 releases.  PLAN_EINVAL for M > 1000, arc_per_level outside
+ * (0, 4], clothoid_cost >= 2^28 or a grid above 2048; PLAN_ESTATE for a plan
+ * without volumes. */
+#define PLAN_C1F 6
+#define PLAN_C1B 7
+#define PLAN_C2F 8
+#define PLAN_C2B 9
+int plan_set_curvature_levels(plan_t* plan, int levels_per_side, double arc_per_level, uint32_t clothoid_cost);
+
+/* The sweep over the curvature levels: init (V = 0 at the start pose on
+ * start_level, a curvature in -M .. M) and N cycles of the ten layers.
+ * Labels are (maneuver << 12) | d.  Async.  PLAN_ESTATE without
+ * plan_set_curvature_levels or before rendering. */
+int plan_sweep4(plan_t* plan, plan_pose start, int start_level, int n_cycles);
+
+typedef struct {
+    int32_t maneuver;    /* 0 .. 5 as plan_segment, PLAN_C1F .. PLAN_C2B */
+    plan_pose entry;
+    int32_t entry_level; /* kappa at the entry */
+    plan_pose exit;
+    int32_t exit_level;
+    int32_t steps;
+    uint32_t cost;       /* V at the exit */
+} plan_segment4;
+
+/* Back-track after plan_sweep4 from the goal pose at goal_level, as
+ * plan_extract.  Synchronises. */
+int plan_extract4(plan_t* plan, plan_pose goal, int goal_level, plan_segment4* out, int cap, int* n_out,
+                  uint32_t* cost);
+
+/* The 4D V and L ((2M+1) * Nx^2 * N_theta entries each, level -M first) and
+ * the clothoid tables the library built (dx, dy: [2][2M+1][N_theta], dth:
+ * [2][2M+1]); any pointer may be NULL.  Synchronises. */
+int plan_copy_volumes4(plan_t* plan, uint32_t* V, uint16_t* L);
+int plan_clothoid_tables(plan_t* plan, int16_t* dx, int16_t* dy, int32_t* dth);
+
 /* Section V.A, Fig. 9: per-maneuver transition edges of the Star graph.
  * Entering maneuver mu (cycle-order ids) from the transition state costs
  * cost_in[mu], returning to it cost_out[mu] -- the time of changing gear or

@@ -83,6 +83,11 @@ class Segment(C.Structure):
                 ("cost", C.c_uint32)]
 
 
+class Segment4(C.Structure):
+    _fields_ = [("maneuver", C.c_int32), ("entry", Pose), ("entry_level", C.c_int32), ("exit", Pose),
+                ("exit_level", C.c_int32), ("steps", C.c_int32), ("cost", C.c_uint32)]
+
+
 class Goal(C.Structure):
     _fields_ = [("pose", Pose), ("radius_xy", C.c_int32), ("radius_theta", C.c_int32), ("w_xy", C.c_uint32),
                 ("w_theta", C.c_uint32), ("bias", C.c_uint32)]
@@ -130,6 +135,17 @@ def lib():
         L.plan_reach_sweep.restype = C.c_int
         L.plan_set_direction_field.restype = C.c_int
         L.plan_set_direction_field.argtypes = [vp, vp, C.c_int, C.c_uint32]
+        L.plan_set_curvature_levels.restype = C.c_int
+        L.plan_set_curvature_levels.argtypes = [vp, C.c_int, C.c_double, C.c_uint32]
+        L.plan_sweep4.restype = C.c_int
+        L.plan_sweep4.argtypes = [vp, Pose, C.c_int, C.c_int]
+        L.plan_extract4.restype = C.c_int
+        L.plan_extract4.argtypes = [vp, Pose, C.c_int, C.POINTER(Segment4), C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_uint32)]
+        L.plan_copy_volumes4.restype = C.c_int
+        L.plan_copy_volumes4.argtypes = [vp, vp, vp]
+        L.plan_clothoid_tables.restype = C.c_int
+        L.plan_clothoid_tables.argtypes = [vp, vp, vp, vp]
         L.plan_set_gear_penalty.restype = C.c_int
         L.plan_set_gear_penalty.argtypes = [vp, C.c_uint32]
         L.plan_sweep_gear.restype = C.c_int
@@ -283,6 +299,45 @@ class Planner:
         assert h.shape == (self.nx, self.nx)
         _check(lib().plan_set_direction_field(self._h, _ptr(h), int(tolerance), int(penalty_q8)),
                "plan_set_direction_field")
+
+    # ---------------------------------------- curvature levels (Appendix F)
+    def set_curvature_levels(self, levels_per_side: int, arc_per_level: float = 1.0, clothoid_cost: int = 0):
+        _check(lib().plan_set_curvature_levels(self._h, int(levels_per_side), float(arc_per_level),
+                                               int(clothoid_cost)), "plan_set_curvature_levels")
+        self.curv_M = int(levels_per_side)
+
+    def sweep4(self, start, start_level: int, n_cycles: int):
+        _check(lib().plan_sweep4(self._h, Pose(*[int(v) for v in start]), int(start_level), int(n_cycles)),
+               "plan_sweep4")
+
+    def extract4(self, goal, goal_level: int, cap: int = 1024):
+        segs = (Segment4 * cap)()
+        n = C.c_int(0)
+        cost = C.c_uint32(0)
+        rc = lib().plan_extract4(self._h, Pose(*[int(v) for v in goal]), int(goal_level), segs, cap, C.byref(n),
+                                 C.byref(cost))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_extract4")
+        out = [dict(mu=x.maneuver, entry=(x.entry.x, x.entry.y, x.entry.theta), entry_level=x.entry_level,
+                    exit=(x.exit.x, x.exit.y, x.exit.theta), exit_level=x.exit_level, steps=x.steps, cost=x.cost)
+               for x in segs[:n.value]]
+        return PlanResult(int(cost.value), out)
+
+    def volumes4(self):
+        n4 = self.cells * (2 * self.curv_M + 1)
+        v = np.empty(n4, np.uint32)
+        l_ = np.empty(n4, np.uint16)
+        _check(lib().plan_copy_volumes4(self._h, _ptr(v), _ptr(l_)), "plan_copy_volumes4")
+        return v, l_
+
+    def clothoid_tables(self):
+        nk = 2 * self.curv_M + 1
+        dx = np.zeros((2, nk, self.nt), np.int16)
+        dy = np.zeros((2, nk, self.nt), np.int16)
+        dth = np.zeros((2, nk), np.int32)
+        _check(lib().plan_clothoid_tables(self._h, _ptr(dx), _ptr(dy), _ptr(dth)), "plan_clothoid_tables")
+        return dx, dy, dth
 
     def set_gear_penalty(self, penalty):
         """plan_set_gear_penalty (None: PLAN_GEAR_OFF)."""

@@ -174,6 +174,25 @@ cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s);
 cudaError_t launch_gear_extract(const GearLayer& a, int64_t goal, plan_segment* seg, int cap, int32_t* status,
                                 cudaStream_t s);
 
+// 4D generalisation (Appendix F): one maneuver layer over 2M+1 curvature
+// levels of the 3D volume (V, L hold nk * nr entries, level K = kappa + M
+// first), with the clothoid tables dx, dy [2][nk][N_theta] and dth [2][nk].
+struct Layer4 {
+    DevGrid g;
+    const uint16_t* B;
+    uint32_t* V;
+    uint16_t* L;
+    int64_t nr;
+    int nk;
+    const int16_t *dx, *dy;
+    const int32_t* dth;
+    uint32_t w, cin, cout;  // step weight of the layer's maneuver; entering, leaving
+};
+cudaError_t launch4_init(uint32_t* V, uint16_t* L, int64_t n4, int64_t start4, cudaStream_t s);
+cudaError_t launch4_layer(const Layer4& a, int mu, int level, cudaStream_t s);
+cudaError_t launch4_extract(const Layer4& a, int64_t goal4, plan_segment4* seg, int cap, int32_t* status,
+                            cudaStream_t s);
+
 // Direction penalties (Section XVI, Fig. 19) applied to a rendered B.
 cudaError_t launch_direction(uint16_t* B, const uint16_t* field, int lx, int lt, int tol, uint32_t pen,
                              cudaStream_t s);

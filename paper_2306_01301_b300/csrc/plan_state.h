@@ -10,6 +10,7 @@ using nhp::PlaneInfo;
 using nhp::Run;
 
 enum { VOL_NONE = 0, VOL_PLAIN = 1, VOL_GEAR = 2 };
+enum { VOL4_NONE = 0, VOL4_SWEPT = 1 };
 
 struct plan_s {
     int lx = 0, lt = 0, nx = 0, nt = 0;
@@ -21,10 +22,21 @@ struct plan_s {
     uint32_t* d_Vr = nullptr;             // reverse gear state (plan_set_gear_penalty)
     uint16_t* d_Lr = nullptr;
     uint32_t gear_pen = 0;
+    // curvature levels (plan_set_curvature_levels)
+    int curv_M = 0, curv_nk = 0;
+    double curv_L = 0.0;
+    uint32_t curv_w = 0, curv_ct = 0;
+    uint32_t* d_V4 = nullptr;
+    uint16_t* d_L4 = nullptr;
+    int16_t *d_cdx = nullptr, *d_cdy = nullptr;
+    int32_t* d_cdth = nullptr;
+    std::vector<int16_t> cdx, cdy;
+    std::vector<int32_t> cdth;
     bool gear_on = false;
     // what V and L hold: nothing usable, a plain (one transition state)
     // sweep, or a two-gear-state sweep; each back-track reads only its own
     int vol_kind = VOL_NONE;
+    int vol4_kind = VOL4_NONE;
     int dir_tol = 0;
     uint32_t dir_pen = 256;
     plan_footprint fp{};
@@ -111,6 +123,7 @@ bool pose_hard(const plan_s* p, plan_pose q);
 int range_check(const plan_s* p, int n_cycles);
 int range_check_layers(const plan_s* p, int layers);
 void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout);
+void curv4_release(plan_s* p);  // the curvature levels' buffers
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
 // plan_create, optionally without the V and L volumes (a cached scene).
