@@ -310,10 +310,16 @@ int plan_set_curvature_levels(plan_t* p, int levels_per_side, double arc_per_lev
         curv4_release(p);
         return PLAN_ENOMEM;
     }
-    NHP_CK(cudaMemcpyAsync(p->d_cdx, p->cdx.data(), p->cdx.size() * 2, cudaMemcpyHostToDevice, p->stream));
-    NHP_CK(cudaMemcpyAsync(p->d_cdy, p->cdy.data(), p->cdy.size() * 2, cudaMemcpyHostToDevice, p->stream));
-    NHP_CK(cudaMemcpyAsync(p->d_cdth, p->cdth.data(), p->cdth.size() * 4, cudaMemcpyHostToDevice, p->stream));
-    NHP_CK(cudaStreamSynchronize(p->stream));  // the host tables may change with the next call
+    cudaError_t e = cudaMemcpyAsync(p->d_cdx, p->cdx.data(), p->cdx.size() * 2, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_cdy, p->cdy.data(), p->cdy.size() * 2, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_cdth, p->cdth.data(), p->cdth.size() * 4, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // the host tables may change with the next call
+    if (e != cudaSuccess) {
+        curv4_release(p);  // no half-built levels
+        return cuda_fail(e, "plan_set_curvature_levels");
+    }
     return PLAN_OK;
 }
 
