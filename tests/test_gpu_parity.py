@@ -165,6 +165,34 @@ def test_parallel_parking_512cubed_full_size():
     _full_size(sc, sc.hard_image())
 
 
+def test_parallel_parking_512cubed_all_cycles_bit_exact():
+    """The benchmark's workload end to end, every cycle: 512^3, N = 8, the
+    kernel shapes the autotuner picks for it (as bench.py times them), the
+    whole V and L against the oracle's full 8-cycle sweep (about four
+    minutes of oracle time), and the plan to the goal."""
+    sc = scenes.parallel_parking()
+    img = sc.hard_image()
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    Bo = o.render_rows(img, sc.footprint)
+    Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
+    p = planner(sc, img)
+    p.render()
+    p.autotune(sc.start)
+    p.sweep(sc.start, sc.n_cycles)
+    V, L, _ = p.volumes(B=False)
+    assert np.array_equal(V, Vo), f"values differ at {np.flatnonzero(V != Vo)[:5]}"
+    assert np.array_equal(L, Lo), f"labels differ at {np.flatnonzero(L != Lo)[:5]}"
+    del V, L
+    res = p.extract(sc.goal)
+    ref = o.extract(Vo, Lo, o.cell(sc.goal))
+    assert (res is None) == (ref is None)
+    if res is not None:
+        assert res.cost == Vo[o.cell(sc.goal)]
+        assert [(s["mu"], s["entry"], s["exit"], s["steps"], s["cost"]) for s in res.segments] == \
+               [(s["mu"], o.pose(s["entry"]), o.pose(s["exit"]), s["steps"], s["cost"]) for s in ref]
+    p.close()
+
+
 def test_maze_512cubed_full_size_soft_costs():
     from paper_2306_01301_b300 import binding
     sc = scenes.maze()
