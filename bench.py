@@ -41,10 +41,20 @@ def load_peaks():
 
 
 def source_hash():
+    """Hash of what the turn kernel is built from: the turn section of
+    sweep.cu (kernel and launcher) and the structures it reads."""
+    csrc = os.path.join(ROOT, "paper_2306_01301_b300", "csrc")
+    with open(os.path.join(csrc, "sweep.cu")) as f:
+        sweep = f.read()
+    with open(os.path.join(csrc, "internal.h")) as f:
+        internal = f.read()
+    a = sweep.index("// ------------------------------------------------------------------- turns")
+    b = sweep.index("// ---------------------------------------------------------------- straights", a)
     h = hashlib.sha256()
-    for name in ("sweep.cu", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2306_01301_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+    h.update(sweep[a:b].encode())
+    for name in ("PlaneInfo", "DevGrid", "Volumes", "QueryDesc"):
+        i = internal.index("struct " + name + " {")
+        h.update(internal[i:internal.index("\n};", i) + 3].encode())
     return h.hexdigest()[:16]
 
 
