@@ -158,6 +158,46 @@ def test_batch_modes_give_the_same_bits(mixed, graph, tune):
     b.close()
 
 
+def test_batch_with_per_plan_transition_costs():
+    """Plans of one lane with different per-maneuver transition costs (the
+    turn launches then read each query's own costs) and a change of costs
+    after the graph was captured (a new graph), bit for bit as the oracle."""
+    from paper_2306_01301_b300 import binding
+    costs = [([300, 100, 900, 300, 700, 900], [0, 0, 50, 0, 50, 50]),
+             ([400] * 6, [0] * 6),
+             ([100, 50, 400, 120, 450, 380], [150, 60, 300, 170, 250, 320])]
+    cases, planners, queries = [], [], []
+    for k, (cin, cout) in enumerate(costs):
+        sc, img = scenes.tiny(760 + k, 6, 7, fill=0.06, turn_radius=9.0, footprint=(3, 1, 1), soft=True,
+                              transition=400)
+        o = O.Oracle(6, 7, 9.0, transition=sc.transition)
+        o.set_transition(cin, cout)
+        Bo = _oracle_render(o, img, (3, 1, 1), 64)
+        p = _planner(sc, img)
+        p.set_transition_costs(cin, cout)
+        cases.append(dict(sc=sc, img=img, o=o, B=Bo, N=2))
+        planners.append(p)
+        s, g = _free(Bo, o, sc.pose_candidates)
+        queries.append((s, g, 2))
+    b = binding.Batch(planners)
+    b.run(queries, render=True)
+    b.sync()
+    assert len(b.lanes()) == 1
+    _check_against_oracle(cases, planners, b, queries)
+    launches = b.kernel_launches()[1]
+    # the same costs for every plan: the launch may pass them as parameters, in a new graph
+    for c, p in zip(cases, planners):
+        c["o"].set_transition([500] * 6, [0] * 6)
+        p.set_transition_costs([500] * 6, [0] * 6)
+    b.run(queries, render=False)
+    b.sync()
+    _check_against_oracle(cases, planners, b, queries)
+    assert b.kernel_launches()[1] > launches
+    b.close()
+    for p in planners:
+        p.close()
+
+
 def test_batch_rejects_bad_queries(mixed):
     from paper_2306_01301_b300 import binding
     cases, planners = mixed
