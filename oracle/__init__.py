@@ -92,6 +92,14 @@ def lib():
         L.orc_bruteforce_gear.argtypes = [p, p, C.c_int64, C.c_int, C.c_uint32, C.c_int, p]
         L.orc_extract_gear.restype = C.c_int
         L.orc_extract_gear.argtypes = [p, p, p, C.c_int64, p, C.c_int]
+        L.orc_sweep_compact.restype = C.c_int
+        L.orc_sweep_compact.argtypes = [p, p, C.c_int64, C.c_int, p, p]
+        L.orc_dijkstra_compact.restype = C.c_int
+        L.orc_dijkstra_compact.argtypes = [p, p, C.c_int64, p]
+        L.orc_bruteforce_compact.restype = C.c_int
+        L.orc_bruteforce_compact.argtypes = [p, p, C.c_int64, C.c_int, p]
+        L.orc_extract_compact.restype = C.c_int
+        L.orc_extract_compact.argtypes = [p, p, p, C.c_int64, p, C.c_int]
         L.orc4_create.restype = p
         L.orc4_create.argtypes = [p, C.c_int, C.c_double, C.c_uint32]
         L.orc4_destroy.argtypes = [p]
@@ -262,6 +270,40 @@ class Oracle:
         co = np.ascontiguousarray(cost_out, dtype=np.uint32)
         if ci.shape != (6,) or co.shape != (6,) or lib().orc_set_transition(self._c, _ptr(ci), _ptr(co)) != 0:
             raise ValueError("transition costs need 6 + 6 values with every sum below 2^28")
+
+    # ------------------------------------------------ Compact graph (Fig. 12)
+    def sweep_compact(self, B: np.ndarray, start: int, n_cycles: int):
+        """V, L of 3 * nr entries: vertex types S, L, R."""
+        V = np.zeros(3 * self.nr, np.uint32)
+        L = np.zeros(3 * self.nr, np.uint16)
+        if lib().orc_sweep_compact(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start), int(n_cycles),
+                                   _ptr(V), _ptr(L)) != 0:
+            raise ValueError("sweep_compact failed")
+        return V, L
+
+    def dijkstra_compact(self, B: np.ndarray, start: int) -> np.ndarray:
+        V = np.zeros(3 * self.nr, np.uint32)
+        if lib().orc_dijkstra_compact(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start), _ptr(V)) != 0:
+            raise ValueError("dijkstra_compact failed")
+        return V
+
+    def bruteforce_compact(self, B: np.ndarray, start: int, n_cycles: int) -> np.ndarray:
+        V = np.zeros(3 * self.nr, np.uint32)
+        if lib().orc_bruteforce_compact(self._c, _ptr(np.ascontiguousarray(B, np.uint16)), int(start),
+                                        int(n_cycles), _ptr(V)) != 0:
+            raise ValueError("bruteforce_compact failed")
+        return V
+
+    def extract_compact(self, V: np.ndarray, L: np.ndarray, goal: int, cap: int = 4096):
+        seg = np.zeros((cap, 6), np.int64)
+        n = lib().orc_extract_compact(self._c, _ptr(np.ascontiguousarray(V, np.uint32)),
+                                      _ptr(np.ascontiguousarray(L, np.uint16)), int(goal), _ptr(seg), cap)
+        if n == -1:
+            return None
+        if n < 0:
+            raise ValueError(f"extract_compact failed ({n})")
+        return [dict(mu=int(r[0]), entry=int(r[1]), exit=int(r[2]), steps=int(r[3]), cost=int(r[4]),
+                     from_s=int(r[5])) for r in seg[:n]]
 
     # ------------------------------------------------------ gear states
     def sweep_gear(self, B: np.ndarray, start: int, start_gear: int, pen: int, n_cycles: int):

@@ -1085,6 +1085,219 @@ int orc_extract_gear(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int
     return n;
 }
 
+/* ------------------------------------------------------- Compact graph
+ * Section V.A, Fig. 12: three vertices per cell -- S (the straight maneuver
+ * type, which is also the transition state), L (left turns, forward and
+ * backward) and R (right turns) -- and ten edges: S -> L and S -> R (the
+ * transition cost ct of plan creation), L -> S and R -> S (free), and the six
+ * maneuver edges, straights within S, LF/LB within L, RF/RB within R.  So a
+ * turn costs ct to start, a straight nothing, and a gear change within one
+ * turn direction nothing (the flexibility the Compact graph gives up).
+ * Readings for its kernel-style processing: the cycle order of Section
+ * XVI.A; a turn layer enters its chain from the cell's own turn state free
+ * or from S at ct (own state on a tie) and stores into its turn state and,
+ * over the free edge back, into S; a straight layer moves within S; a
+ * segment moves at least one step, and a whole turn circle from S back to
+ * the same cell counts (it reaches the turn state; d <= n <= 2048).
+ * Volumes: V[0, nr) S, [nr, 2nr) L, [2nr, 3nr) R; labels (mu << 13) |
+ * (entered from S << 12) | d. */
+static int compact_type(int mu) { return (mu == LF || mu == LB) ? 1 : (mu == RF || mu == RB) ? 2 : 0; }
+
+static int layer_compact(const orc_ctx* c, const uint16_t* B, int mu, const uint32_t* Vin, uint32_t* V,
+                         uint16_t* L) {
+    int64_t nr = c->nr;
+    int ty = compact_type(mu), n;
+    int64_t nchains;
+    if (is_turn(mu)) { nchains = (int64_t)c->nx * c->nx; n = c->nt; }
+    else { nchains = c->nx; n = c->nx; }
+    int nplanes = is_turn(mu) ? 1 : c->nt;
+    for (int plane = 0; plane < nplanes; plane++)
+        for (int64_t k = 0; k < nchains; k++) {
+            int64_t start;
+            if (is_turn(mu)) start = k;
+            else start = c->iflag[plane] == 0 ? cell_of(c, 0, (int)k, plane) : cell_of(c, (int)k, 0, plane);
+            int64_t x = start;
+            uint32_t v = ORC_INF;
+            int qe = 0, vs = 0;
+            for (int q = 0; q < 2 * n; q++) {
+                int hard = B[x] == ORC_HARD;
+                uint32_t uT = Vin[ty * nr + x], uS = Vin[x];
+                if (q >= n && !hard) {
+                    uint16_t lab = (uint16_t)((mu << 13) | (vs << 12) | (q - qe));
+                    if (v < uT && v < V[ty * nr + x]) { V[ty * nr + x] = v; L[ty * nr + x] = lab; }
+                    if (ty != 0 && v < uS && v < V[x]) { V[x] = v; L[x] = lab; } /* back to S, free */
+                }
+                uint32_t tT = hard ? ORC_INF : uT;
+                uint32_t tS = (hard || ty == 0) ? ORC_INF : sadd(uS, c->ct);
+                int fromS = tS < tT;
+                uint32_t t = fromS ? tS : tT;
+                if (t < v) { v = t; qe = q; vs = fromS; }
+                v = sadd(v, orc_edge(c, B, mu, x));
+                x = orc_succ(c, mu, x);
+            }
+            if (x != start) return -1;
+        }
+    return 0;
+}
+
+int orc_sweep_compact(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* V,
+                      uint16_t* L) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD || n_cycles < 0 || c->nx > 2048 || c->nt > 2048)
+        return -1;
+    int64_t n3 = 3 * c->nr;
+    for (int64_t x = 0; x < n3; x++) { V[x] = ORC_INF; L[x] = ORC_NONE; }
+    V[start] = 0; /* the vehicle starts in S */
+    uint32_t* Vin = (uint32_t*)malloc(sizeof(uint32_t) * n3);
+    if (!Vin) return -1;
+    int rc = 0;
+    for (int l = 0; l < 6 * n_cycles && rc == 0; l++) {
+        memcpy(Vin, V, sizeof(uint32_t) * n3);
+        rc = layer_compact(c, B, cycle_order[l % 6], Vin, V, L);
+    }
+    free(Vin);
+    return rc;
+}
+
+/* Dijkstra on the explicit Compact graph; a transition into a turn leads over
+ * the turn's first edge (a segment moves at least one step). */
+int orc_dijkstra_compact(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* Vinf) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD) return -1;
+    int64_t nr = c->nr, nv = 3 * nr;
+    iheap h;
+    h.key = (uint32_t*)malloc(sizeof(uint32_t) * nv);
+    h.heap = (int64_t*)malloc(sizeof(int64_t) * nv);
+    h.pos = (int64_t*)malloc(sizeof(int64_t) * nv);
+    uint8_t* done = (uint8_t*)calloc((size_t)nv, 1);
+    if (!h.key || !h.heap || !h.pos || !done) { free(h.key); free(h.heap); free(h.pos); free(done); return -1; }
+    for (int64_t v = 0; v < nv; v++) { h.key[v] = ORC_INF; h.pos[v] = -1; }
+    h.key[start] = 0; h.heap[0] = start; h.pos[start] = 0; h.n = 1;
+#define RC(dst, w)                                                      \
+    do {                                                                \
+        uint32_t nd_ = sadd(du, (w));                                   \
+        int64_t d_ = (dst);                                             \
+        if (nd_ < h.key[d_] && !done[d_]) {                             \
+            h.key[d_] = nd_;                                            \
+            if (h.pos[d_] < 0) { h.heap[h.n] = d_; h.pos[d_] = h.n; h.n++; } \
+            heap_up(&h, h.pos[d_]);                                     \
+        }                                                               \
+    } while (0)
+    static const int of_type[3][2] = {{SF, SB}, {LF, LB}, {RF, RB}};
+    while (h.n > 0) {
+        int64_t u = h.heap[0];
+        heap_swap(&h, 0, h.n - 1);
+        h.n--;
+        h.pos[u] = -1;
+        if (h.n > 0) heap_down(&h, 0);
+        done[u] = 1;
+        uint32_t du = h.key[u];
+        if (du == ORC_INF) break;
+        int ty = (int)(u / nr);
+        int64_t x = u % nr;
+        if (B[x] == ORC_HARD) continue;
+        for (int k = 0; k < 2; k++) { /* maneuver edges within the vertex type */
+            int mu = of_type[ty][k];
+            int64_t y = orc_succ(c, mu, x);
+            if (B[y] != ORC_HARD) RC(ty * nr + y, orc_edge(c, B, mu, x));
+        }
+        if (ty == 0) { /* S -> L, S -> R over the turn's first edge */
+            for (int t2 = 1; t2 < 3; t2++)
+                for (int k = 0; k < 2; k++) {
+                    int mu = of_type[t2][k];
+                    int64_t y = orc_succ(c, mu, x);
+                    if (B[y] != ORC_HARD) RC(t2 * nr + y, sadd(c->ct, orc_edge(c, B, mu, x)));
+                }
+        } else {
+            RC(x, 0u); /* back to S */
+        }
+    }
+#undef RC
+    for (int64_t x = 0; x < nv; x++) Vinf[x] = B[x % nr] == ORC_HARD ? ORC_INF : h.key[x];
+    free(h.key); free(h.heap); free(h.pos); free(done);
+    return 0;
+}
+
+/* Exhaustive search over layer-ordered segment sequences (tiny grids):
+ * best[ty * nr + x] over sequences ending in vertex type ty at x. */
+typedef struct {
+    const orc_ctx* c;
+    const uint16_t* B;
+    int layers;
+    uint32_t* seen; /* [layer][type][cell] */
+    uint32_t* best;
+} bfc_state;
+
+static void bfc_explore(bfc_state* s, int layer, int ty, int64_t x, uint32_t cost) {
+    const orc_ctx* c = s->c;
+    int64_t nr = c->nr;
+    uint32_t* sl = s->seen + ((size_t)layer * 3 + ty) * nr;
+    if (cost >= sl[x]) return;
+    sl[x] = cost;
+    if (cost < s->best[ty * nr + x]) s->best[ty * nr + x] = cost;
+    if (ty != 0) bfc_explore(s, layer, 0, x, cost); /* back to S, free */
+    if (layer == s->layers) return;
+    bfc_explore(s, layer + 1, ty, x, cost);
+    int mu = cycle_order[layer % 6], T = compact_type(mu);
+    if (T != ty && ty != 0) return;          /* a turn state enters only its own turns */
+    if (T == 0 && ty != 0) return;
+    uint32_t run = (T != 0 && ty == 0) ? sadd(cost, c->ct) : cost;
+    int n = is_turn(mu) ? c->nt : c->nx;
+    int64_t y = x;
+    for (int d = 1; d <= n; d++) { /* a whole turn circle from S changes the vertex type */
+        run = sadd(run, orc_edge(c, s->B, mu, y));
+        y = orc_succ(c, mu, y);
+        if (run == ORC_INF) break;
+        if (s->B[y] != ORC_HARD) bfc_explore(s, layer + 1, T, y, run);
+    }
+}
+
+int orc_bruteforce_compact(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* Vbest) {
+    if (start < 0 || start >= c->nr || B[start] == ORC_HARD || n_cycles < 0) return -1;
+    int64_t nr = c->nr;
+    bfc_state s = {c, B, 6 * n_cycles, NULL, Vbest};
+    s.seen = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(s.layers + 1) * 3 * nr);
+    if (!s.seen) return -1;
+    for (int64_t k = 0; k < (int64_t)(s.layers + 1) * 3 * nr; k++) s.seen[k] = ORC_INF;
+    for (int64_t x = 0; x < 3 * nr; x++) Vbest[x] = ORC_INF;
+    bfc_explore(&s, 0, 0, start, 0);
+    free(s.seen);
+    return 0;
+}
+
+/* Label walk from S(goal): seg[k*6 + {mu, entry, exit, d, cost, entered_from_S}]. */
+int orc_extract_compact(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal, int64_t* seg,
+                        int cap) {
+    if (goal < 0 || goal >= c->nr) return -3;
+    int64_t nr = c->nr;
+    if (V[goal] == ORC_INF) return -1;
+    int ty = 0, n = 0, guard = 0;
+    int64_t x = goal;
+    while (L[ty * nr + x] != ORC_NONE) {
+        if (++guard > 1 << 20) return -3;
+        uint16_t lab = L[ty * nr + x];
+        int mu = lab >> 13, fs = (lab >> 12) & 1, d = lab & 4095;
+        int T = compact_type(mu);
+        if (mu > 5 || d == 0 || (ty != 0 && T != ty)) return -3;
+        int64_t e = x;
+        for (int k = 0; k < d; k++) e = orc_succ(c, 5 - mu, e);
+        if (n < cap) {
+            int64_t* r = seg + 6 * (size_t)n;
+            r[0] = mu; r[1] = e; r[2] = x; r[3] = d; r[4] = V[ty * nr + x]; r[5] = fs;
+        }
+        n++;
+        x = e;
+        ty = fs ? 0 : T;
+    }
+    if (V[ty * nr + x] != 0) return -3;
+    if (n > cap) return -2;
+    for (int a2 = 0, b2 = n - 1; a2 < b2; a2++, b2--)
+        for (int k = 0; k < 6; k++) {
+            int64_t t = seg[6 * a2 + k];
+            seg[6 * a2 + k] = seg[6 * b2 + k];
+            seg[6 * b2 + k] = t;
+        }
+    return n;
+}
+
 /* ------------------------------------------------- 4D generalisation (App. F)
  * Curvature as a fourth state dimension: 2M+1 levels kappa = -M .. M (index
  * K = kappa + M) of the 3D volume, curvature k = kappa / (M R).  Readings of

@@ -110,6 +110,17 @@ int orc_bruteforce_gear(const orc_ctx* c, const uint16_t* B, int64_t start, int 
                         int n_cycles, uint32_t* Vbest);
 int orc_extract_gear(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal, int64_t* seg,
                      int cap);
+/* Compact graph (Section V.A, Fig. 12): vertices S (straight = transition
+ * state), L, R per cell; V, L hold 3 * nr entries (S, L, R); labels (mu <<
+ * 13) | (entered from S << 12) | d.  Sweep (kernel-style layers), Dijkstra,
+ * exhaustive search and the label walk from S(goal) (seg[k*6 + {mu, entry,
+ * exit, d, cost, entered_from_S}]). */
+int orc_sweep_compact(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* V,
+                      uint16_t* L);
+int orc_dijkstra_compact(const orc_ctx* c, const uint16_t* B, int64_t start, uint32_t* Vinf);
+int orc_bruteforce_compact(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles, uint32_t* Vbest);
+int orc_extract_compact(const orc_ctx* c, const uint32_t* V, const uint16_t* L, int64_t goal, int64_t* seg,
+                        int cap);
 /* 4D generalisation (App. F): 2M+1 curvature levels of the 3D volume,
  * clothoid maneuvers between them (ids 6 C1F, 7 C1B, 8 C2F, 9 C2B), the 3D
  * turns at the steering limits and the straights at zero curvature.  4D
