@@ -201,6 +201,36 @@ int plan_extract_gear(plan_t* plan, plan_pose goal, plan_segment* out, int cap, 
 /* The reverse gear state's V and L (either may be NULL).  Synchronises. */
 int plan_copy_reverse_volumes(plan_t* plan, uint32_t* V, uint16_t* L);
 
+/* Section V.A, Fig. 12: the Compact graph -- three vertices per cell, S (the
+ * straight maneuver type, which is also the transition state), L (left
+ * turns, forward and backward) and R (right turns), and ten edges: S -> L and
+ * S -> R at costs.transition, L -> S and R -> S free, and the six maneuver
+ * edges inside their types.  A turn costs ct to start, a straight nothing, a
+ * change of gear within one turn direction nothing.  enable = 1 allocates the
+ * L and R values and labels (12 B per pose; S is the plan's own V and L),
+ * 0 releases them.  PLAN_EINVAL for a grid above 2048, PLAN_ESTATE for a plan
+ * without volumes. */
+int plan_set_compact_graph(plan_t* plan, int enable);
+
+/* Kernel-style processing of the Compact graph: the cycle order of Section
+ * XVI.A, one maneuver per launch; a turn layer enters its chain from the
+ * cell's turn state free or from S at ct (the turn state on a tie) and stores
+ * into its turn state and into S; a straight layer moves within S.  The
+ * vehicle starts in S.  Labels (maneuver << 13) | (entered from S << 12) | d.
+ * Async.  PLAN_ESTATE without plan_set_compact_graph or before rendering. */
+int plan_sweep_compact(plan_t* plan, plan_pose start, int n_cycles);
+
+/* Back-track from S(goal) (never above L(goal) or R(goal)) as plan_extract;
+ * *cost = V_S(goal).  A walk may cost less than *cost when a later layer
+ * lowered an entry's value after its segment was labelled (forward
+ * tracking), never more.  Synchronises.  PLAN_ESTATE unless the volumes come
+ * from plan_sweep_compact. */
+int plan_extract_compact(plan_t* plan, plan_pose goal, plan_segment* out, int cap, int* n_out, uint32_t* cost);
+
+/* The L and R vertex values and labels (S: plan_copy_volumes); any pointer
+ * may be NULL.  Synchronises. */
+int plan_copy_compact_volumes(plan_t* plan, uint32_t* VL, uint16_t* LL, uint32_t* VR, uint16_t* LR);
+
 /* Appendix F, the 4D generalisation: curvature as a fourth state variable.
  * levels_per_side = M gives 2M+1 levels kappa = -M .. M of the 3D volume,
  * curvature kappa / (M R).  The 3D turns run at the steering limits (LF, LB

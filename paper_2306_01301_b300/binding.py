@@ -135,6 +135,15 @@ def lib():
         L.plan_reach_sweep.restype = C.c_int
         L.plan_set_direction_field.restype = C.c_int
         L.plan_set_direction_field.argtypes = [vp, vp, C.c_int, C.c_uint32]
+        L.plan_set_compact_graph.restype = C.c_int
+        L.plan_set_compact_graph.argtypes = [vp, C.c_int]
+        L.plan_sweep_compact.restype = C.c_int
+        L.plan_sweep_compact.argtypes = [vp, Pose, C.c_int]
+        L.plan_extract_compact.restype = C.c_int
+        L.plan_extract_compact.argtypes = [vp, Pose, C.POINTER(Segment), C.c_int, C.POINTER(C.c_int),
+                                           C.POINTER(C.c_uint32)]
+        L.plan_copy_compact_volumes.restype = C.c_int
+        L.plan_copy_compact_volumes.argtypes = [vp, vp, vp, vp, vp]
         L.plan_set_curvature_levels.restype = C.c_int
         L.plan_set_curvature_levels.argtypes = [vp, C.c_int, C.c_double, C.c_uint32]
         L.plan_sweep4.restype = C.c_int
@@ -299,6 +308,32 @@ class Planner:
         assert h.shape == (self.nx, self.nx)
         _check(lib().plan_set_direction_field(self._h, _ptr(h), int(tolerance), int(penalty_q8)),
                "plan_set_direction_field")
+
+    # ------------------------------------------- Compact graph (Fig. 12)
+    def set_compact_graph(self, enable: bool = True):
+        _check(lib().plan_set_compact_graph(self._h, 1 if enable else 0), "plan_set_compact_graph")
+
+    def sweep_compact(self, start, n_cycles: int):
+        _check(lib().plan_sweep_compact(self._h, Pose(*[int(v) for v in start]), int(n_cycles)),
+               "plan_sweep_compact")
+
+    def extract_compact(self, goal, cap: int = 1024) -> Optional[PlanResult]:
+        segs = (Segment * cap)()
+        n = C.c_int(0)
+        cost = C.c_uint32(0)
+        rc = lib().plan_extract_compact(self._h, Pose(*[int(v) for v in goal]), segs, cap, C.byref(n),
+                                        C.byref(cost))
+        if rc == PLAN_EUNREACHABLE:
+            return None
+        _check(rc, "plan_extract_compact")
+        return PlanResult(int(cost.value), self._segments(segs, n.value))
+
+    def compact_volumes(self):
+        """(V_S, L_S, V_L, L_L, V_R, L_R)"""
+        vs, ls, _ = self.volumes(B=False)
+        arrs = [np.empty(self.cells, t) for t in (np.uint32, np.uint16, np.uint32, np.uint16)]
+        _check(lib().plan_copy_compact_volumes(self._h, *[_ptr(a) for a in arrs]), "plan_copy_compact_volumes")
+        return (vs, ls, *arrs)
 
     # ---------------------------------------- curvature levels (Appendix F)
     def set_curvature_levels(self, levels_per_side: int, arc_per_level: float = 1.0, clothoid_cost: int = 0):

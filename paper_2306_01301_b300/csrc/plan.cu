@@ -257,6 +257,7 @@ void release(plan_s* p) {
     p->dfree(p->d_Vr, (size_t)p->nr * 4);
     p->dfree(p->d_Lr, (size_t)p->nr * 2);
     curv4_release(p);
+    compact_release(p);
     p->dfree(p->d_cnt, 32);
     p->dfree(p->d_qd, sizeof(QueryDesc));
     const size_t bits = (size_t)(p->nr / 8);

@@ -9,7 +9,7 @@ using nhp::DevGrid;
 using nhp::PlaneInfo;
 using nhp::Run;
 
-enum { VOL_NONE = 0, VOL_PLAIN = 1, VOL_GEAR = 2 };
+enum { VOL_NONE = 0, VOL_PLAIN = 1, VOL_GEAR = 2, VOL_COMPACT = 3 };
 enum { VOL4_NONE = 0, VOL4_SWEPT = 1 };
 
 struct plan_s {
@@ -19,6 +19,8 @@ struct plan_s {
     plan_costs costs{};
     uint32_t cin[6] = {}, cout[6] = {};  // Star transition edges per maneuver
     uint16_t* d_dir = nullptr;            // direction field (Nx*Nx), or none
+    uint32_t *d_Vcl = nullptr, *d_Vcr = nullptr;  // Compact graph: L and R vertex values and labels
+    uint16_t *d_Lcl = nullptr, *d_Lcr = nullptr;
     uint32_t* d_Vr = nullptr;             // reverse gear state (plan_set_gear_penalty)
     uint16_t* d_Lr = nullptr;
     uint32_t gear_pen = 0;
@@ -124,6 +126,7 @@ int range_check(const plan_s* p, int n_cycles);
 int range_check_layers(const plan_s* p, int layers);
 void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout);
 void curv4_release(plan_s* p);  // the curvature levels' buffers
+void compact_release(plan_s* p);  // the Compact graph's L and R volumes
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
 // plan_create, optionally without the V and L volumes (a cached scene).
