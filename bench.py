@@ -377,8 +377,9 @@ def run_extensions(args, torch):
     against init alone), and a goal-set search with back-track (Section IX;
     12 goals of 13 x 13 x 9 poses, against the single-goal walk), and the
     two-gear-state sweep (forward / reverse transition states, penalty 3000,
-    N = 8, one maneuver per launch) and the 4D sweep over 9 curvature levels
-    (Appendix F; clothoids of one level per cell, N = 8)."""
+    N = 8, one maneuver per launch), the 4D sweep over 9 curvature levels
+    (Appendix F; clothoids of one level per cell, N = 8) and the Compact
+    graph's sweep (Fig. 12; three vertex types, N = 8)."""
     import numpy as np
     from paper_2306_01301_b300 import binding, scenes
     sc = scenes.parallel_parking()
@@ -425,6 +426,10 @@ def run_extensions(args, torch):
     nk = 2 * M4 + 1
     curv_updates = sc.n_cycles * (4 * nk + 6) * sc.cells  # 4 clothoid layers over every level, 6 3D layers on one
     p.set_curvature_levels(0)
+    p.set_compact_graph(True)
+    compact_plan = timed(lambda: p.sweep_compact(sc.start, sc.n_cycles), reps=3)
+    compact_res = p.extract_compact(sc.goal)
+    p.set_compact_graph(False)
     p.close()
     dir_ms = max(render_dir - render_plain, 1e-6)
     return {"direction_pass_ms": dir_ms, "direction_pass_gbs": 4 * sc.cells / (dir_ms * 1e6),
@@ -433,6 +438,9 @@ def run_extensions(args, torch):
             "goal_set_extract_ms": goal_set, "single_goal_extract_ms": walk,
             "gear_states_sweep_ms": gear_plan, "gear_states_updates_per_s": 6 * sc.n_cycles * sc.cells / (gear_plan / 1e3),
             "gear_states_plan_cost": gear_res[0].cost if gear_res else None,
+            "compact_graph": {"sweep_ms": compact_plan, "updates_per_s": 6 * sc.n_cycles * sc.cells / (compact_plan / 1e3),
+                              "plan_cost": compact_res.cost if compact_res else None,
+                              "plan_maneuvers": len(compact_res.segments) if compact_res else None},
             "curvature_levels": {"levels": nk, "sweep_ms": curv_plan, "updates_per_s": curv_updates / (curv_plan / 1e3),
                                  "plan_cost": curv_res.cost if curv_res else None,
                                  "plan_maneuvers": len(curv_res.segments) if curv_res else None},
