@@ -79,15 +79,9 @@ __global__ void __launch_bounds__(256) kc_turn(const CompactLayer a, int mu) {
     const int64_t chain = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (chain >= nxy) return;
     const int xq = (int)(chain & g.mx), yq = (int)(chain >> g.lx);
-    const bool left = mu == LF || mu == LB;
-    const int step = (mu == LF || mu == RB) ? 1 : -1;
     const int n = g.nt;
     CWalk s;
-    for (int q = 0; q < 2 * n; q++) {
-        const int T = (step * q) & g.mt;
-        const int4 b = __ldg(&g.beta4[T]);
-        cstep(s, cell_of(g, xq + (left ? b.x : b.z), yq + (left ? b.y : b.w), T), q, n, mu, g.wA, a);
-    }
+    for (int q = 0; q < 2 * n; q++) cstep(s, turn_chain_cell(g, mu, xq, yq, q), q, n, mu, g.wA, a);
 }
 
 __global__ void __launch_bounds__(256) kc_straight(const CompactLayer a, int mu) {
@@ -96,15 +90,9 @@ __global__ void __launch_bounds__(256) kc_straight(const CompactLayer a, int mu)
     if (xq >= g.nx) return;
     const int T = blockIdx.y;
     const PlaneInfo pi = g.plane[T];
-    const int dir = (mu == SF ? pi.jsign : -pi.jsign) > 0 ? 1 : -1;
-    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
     const int n = g.nx;
     CWalk s;
-    for (int q = 0; q < 2 * n; q++) {
-        const int y = (dir * q) & g.mx;
-        const int col = (xq + bs[y]) & g.mx;
-        cstep(s, pi.iflag ? cell_of(g, col, y, T) : cell_of(g, y, col, T), q, n, mu, pi.wS, a);
-    }
+    for (int q = 0; q < 2 * n; q++) cstep(s, line_cell(g, pi, mu, T, xq, q), q, n, mu, pi.wS, a);
 }
 
 __global__ void kc_init(CompactLayer a, int64_t nr, int64_t start) {

@@ -63,15 +63,11 @@ __global__ void __launch_bounds__(256) k4_turn(const Layer4 a, int mu, int level
     const int64_t chain = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (chain >= nxy) return;
     const int xq = (int)(chain & g.mx), yq = (int)(chain >> g.lx);
-    const bool left = mu == LF || mu == LB;
-    const int step = (mu == LF || mu == RB) ? 1 : -1;
     const int n = g.nt;
     const int64_t base = (int64_t)level * a.nr;
     Carry s;
     for (int q = 0; q < 2 * n; q++) {
-        const int T = (step * q) & g.mt;
-        const int4 b = __ldg(&g.beta4[T]);
-        const int64_t c = cell_of(g, xq + (left ? b.x : b.z), yq + (left ? b.y : b.w), T);
+        const int64_t c = turn_chain_cell(g, mu, xq, yq, q);
         step4(s, base + c, c, q, q >= n, mu, a.w, a);
     }
 }
@@ -82,15 +78,11 @@ __global__ void __launch_bounds__(256) k4_straight(const Layer4 a, int mu, int l
     if (xq >= g.nx) return;
     const int T = blockIdx.y;
     const PlaneInfo pi = g.plane[T];
-    const int dir = (mu == SF ? pi.jsign : -pi.jsign) > 0 ? 1 : -1;
-    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
     const int n = g.nx;
     const int64_t base = (int64_t)level * a.nr;
     Carry s;
     for (int q = 0; q < 2 * n; q++) {
-        const int y = (dir * q) & g.mx;
-        const int col = (xq + bs[y]) & g.mx;
-        const int64_t c = pi.iflag ? cell_of(g, col, y, T) : cell_of(g, y, col, T);
+        const int64_t c = line_cell(g, pi, mu, T, xq, q);
         step4(s, base + c, c, q, q >= n, mu, pi.wS, a);
     }
 }

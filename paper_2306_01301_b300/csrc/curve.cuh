@@ -49,4 +49,23 @@ __device__ __forceinline__ int64_t entry_cell(const DevGrid& g, int64_t c, int m
     return cell_of(g, xq + (left ? be.x : be.z), yq + (left ? be.y : be.w), Te);
 }
 
+// Cell of turn chain (xq, yq) of maneuver mu at step q of a walk that starts
+// at heading 0: LF and RB step the heading up, LB and RF down (eq. 18).
+__device__ __forceinline__ int64_t turn_chain_cell(const DevGrid& g, int mu, int xq, int yq, int q) {
+    const bool left = mu == LF || mu == LB;
+    const int step = (mu == LF || mu == RB) ? 1 : -1;
+    const int T = (step * q) & g.mt;
+    const int4 b = __ldg(&g.beta4[T]);
+    return cell_of(g, xq + (left ? b.x : b.z), yq + (left ? b.y : b.w), T);
+}
+
+// Cell of straight line xq of heading T at step q of a walk from its wall
+// cell y' = 0 in the maneuver's direction (eqs. 23-24).
+__device__ __forceinline__ int64_t line_cell(const DevGrid& g, const PlaneInfo& pi, int mu, int T, int xq, int q) {
+    const int dir = (mu == SF ? pi.jsign : -pi.jsign) > 0 ? 1 : -1;
+    const int y = (dir * q) & g.mx;
+    const int col = (xq + g.bshear[(int64_t)T * g.nx + y]) & g.mx;
+    return pi.iflag ? cell_of(g, col, y, T) : cell_of(g, y, col, T);
+}
+
 }  // namespace nhp

@@ -73,16 +73,9 @@ __global__ void __launch_bounds__(256) k_gear_turn(const GearLayer a, int mu) {
     const int64_t chain = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (chain >= nxy) return;
     const int xq = (int)(chain & g.mx), yq = (int)(chain >> g.lx);
-    const bool left = mu == LF || mu == LB;
-    const int step = (mu == LF || mu == RB) ? 1 : -1;  // heading step along the maneuver
     const int n = g.nt;
     Walk s;
-    for (int q = 0; q < 2 * n; q++) {
-        const int T = (step * q) & g.mt;
-        const int4 b = __ldg(&g.beta4[T]);
-        const int64_t c = cell_of(g, xq + (left ? b.x : b.z), yq + (left ? b.y : b.w), T);
-        walk_step(s, c, q, n, mu, g.wA, a);
-    }
+    for (int q = 0; q < 2 * n; q++) walk_step(s, turn_chain_cell(g, mu, xq, yq, q), q, n, mu, g.wA, a);
 }
 
 __global__ void __launch_bounds__(256) k_gear_straight(const GearLayer a, int mu) {
@@ -91,16 +84,9 @@ __global__ void __launch_bounds__(256) k_gear_straight(const GearLayer a, int mu
     if (xq >= g.nx) return;
     const int T = blockIdx.y;
     const PlaneInfo pi = g.plane[T];
-    const int dir = (mu == SF ? pi.jsign : -pi.jsign) > 0 ? 1 : -1;  // y' along the maneuver
-    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
     const int n = g.nx;
     Walk s;
-    for (int q = 0; q < 2 * n; q++) {
-        const int y = (dir * q) & g.mx;  // from the wall cell y' = 0
-        const int col = (xq + bs[y]) & g.mx;
-        const int64_t c = pi.iflag ? cell_of(g, col, y, T) : cell_of(g, y, col, T);
-        walk_step(s, c, q, n, mu, pi.wS, a);
-    }
+    for (int q = 0; q < 2 * n; q++) walk_step(s, line_cell(g, pi, mu, T, xq, q), q, n, mu, pi.wS, a);
 }
 
 __global__ void k_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
