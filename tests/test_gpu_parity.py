@@ -223,14 +223,16 @@ def test_autotuned_shapes_give_the_same_bits(case):
     p.close()
 
 
-SHAPES = [(v, g, sl, sg) for v in range(3) for g in (0, 37) for (sl, sg) in ((0, 0), (128, 29))]
+SHAPES = [(v, g, sl, sg) for v in range(3) for g in (0, 5, 37) for (sl, sg) in ((0, 0), (128, 29))]
 
 
-@pytest.mark.parametrize("lx,lt", [(6, 7), (7, 8), (6, 9)], ids=["64x128", "128x256", "64x512"])
+@pytest.mark.parametrize("lx,lt", [(6, 7), (7, 8), (6, 9), (5, 9)], ids=["64x128", "128x256", "64x512", "32x512"])
 def test_every_kernel_shape_gives_the_same_bits(lx, lt):
     """Every turn variant (K, warps, cluster), one block per item or a
-    persistent grid smaller than the work, and both straight widths:
-    identical V and L, equal to the oracle."""
+    persistent grid smaller than the work (at N_theta = 512 the kernel whose
+    rows arrive by bulk copies; at Nx = 32 every chain row it copies wraps
+    around x = Nx), and both straight widths: identical V and L, equal to
+    the oracle."""
     R = 0.9 * (1 << lx) / 8
     sc, img = scenes.tiny(40 + lx + lt, lx, lt, fill=0.03, turn_radius=R, footprint=(3, 1, 1), soft=True,
                           transition=350)
