@@ -122,16 +122,27 @@ def dist_setup():
 
 def cpu_baseline(sc, img):
     """The oracle, as it stands, on a bounded sample: one maneuver cycle (6
-    layers) of the same 512^3 workload on one host core."""
+    layers) of the same 512^3 workload on one host core.  Beside it, the
+    kernel-style sweep on all host cores (OpenMP, oracle/cpu_sweep.c; not the
+    oracle, checked against it in the tests), the counterpart of the paper's
+    CPU kernel rows, over the whole N-cycle sweep of the workload."""
     import oracle as O
     o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
     B = o.render_rows(img, sc.footprint)
     t0 = time.perf_counter()
     o.sweep(B, o.cell(sc.start), 1, mode=1)
     dt = time.perf_counter() - t0
-    return {"value": 6 * sc.cells / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"1 maneuver cycle (6 layers) of {WORKLOAD}, single-threaded C oracle, "
-                      f"{dt:.1f} s; host has {os.cpu_count()} cores"}
+    oracle_line = {"value": 6 * sc.cells / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "sample": f"1 maneuver cycle (6 layers) of {WORKLOAD}, single-threaded C oracle, "
+                             f"{dt:.1f} s; host has {os.cpu_count()} cores"}
+    t0 = time.perf_counter()
+    _, _, _, threads = O.cpu_sweep(o, B, o.cell(sc.start), sc.n_cycles)
+    dk = time.perf_counter() - t0
+    kernel_line = {"value": 6 * sc.n_cycles * sc.cells / dk, "unit": METRIC, "threads": threads,
+                   "plans_per_s": 1.0 / dk, "kind": "kernel-style sweep on all host cores (OpenMP), not the oracle",
+                   "sample": f"the whole {sc.n_cycles}-cycle sweep of {WORKLOAD} (B rendered beforehand), "
+                             f"{dk:.2f} s; host has {os.cpu_count()} cores"}
+    return oracle_line, kernel_line
 
 
 def run_reference(args):
@@ -295,7 +306,7 @@ def run_ours(args):
     if world == 1 and not args.no_served:
         line["served"] = run_served(args, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, img)
+        line["cpu_baseline"], line["cpu_kernel_baseline"] = cpu_baseline(sc, img)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

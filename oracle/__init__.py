@@ -12,6 +12,11 @@ Every function cites the passage it follows in the C source.  All of them are
 pinned by ``tests/test_oracle_pins.py`` (hand-worked table values, closed
 forms, brute-force enumeration, Dijkstra convergence, symmetries, an
 independent library distance transform).
+
+``cpu_sweep`` (``cpu_sweep.c``) is not part of the oracle: it is the same
+kernel-style sweep spread over all host cores with OpenMP, the CPU baseline
+that ``bench.py`` times beside the oracle (the counterpart of the paper's
+CPU kernel timings); ``tests/test_cpu_sweep.py`` checks it against the oracle.
 """
 from __future__ import annotations
 
@@ -25,6 +30,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_lib", "libnhp_oracle.so")
 _SRC = os.path.join(_HERE, "nhp_oracle.c")
 _HDR = os.path.join(_HERE, "nhp_oracle.h")
+_CS_SO = os.path.join(_HERE, "_lib", "libnhp_cpu_sweep.so")
+_CS_SRC = os.path.join(_HERE, "cpu_sweep.c")
 
 INF = 0xFFFFFFFF
 HARD = 0xFFFF
@@ -41,6 +48,11 @@ def build(force: bool = False) -> str:
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
+    if force or not os.path.exists(_CS_SO) or os.path.getmtime(_CS_SO) < os.path.getmtime(_CS_SRC):
+        tmp = _CS_SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O3", "-fopenmp", "-Wall", "-fPIC", "-shared", "-o", tmp,
+                               _CS_SRC])
+        os.replace(tmp, _CS_SO)
     return _SO
 
 
@@ -146,6 +158,7 @@ class Oracle:
         self.nx, self.nt = 1 << nx_log2, 1 << nt_log2
         self.nr = self.nx * self.nx * self.nt
         self.ct = transition
+        self.cin, self.cout = [transition] * 6, [0] * 6
         self._c = lib().orc_create(nx_log2, nt_log2, float(turn_radius), int(half_shift),
                                    step_straight, step_scale, transition)
         if not self._c:
@@ -270,6 +283,7 @@ class Oracle:
         co = np.ascontiguousarray(cost_out, dtype=np.uint32)
         if ci.shape != (6,) or co.shape != (6,) or lib().orc_set_transition(self._c, _ptr(ci), _ptr(co)) != 0:
             raise ValueError("transition costs need 6 + 6 values with every sum below 2^28")
+        self.cin, self.cout = [int(v) for v in ci], [int(v) for v in co]
 
     # ------------------------------------------------ Compact graph (Fig. 12)
     def sweep_compact(self, B: np.ndarray, start: int, n_cycles: int):
@@ -511,3 +525,36 @@ def soft_image(occupancy: np.ndarray, radius: int, soft_max: int) -> np.ndarray:
     img = np.zeros((nx, nx), np.uint16)
     lib().orc_soft_image(nx, _ptr(occ), int(radius), int(soft_max), _ptr(img))
     return img
+
+
+# ------------------------------------------------------------ CPU baseline
+_cs_lib = None
+
+
+def cpu_sweep(o: Oracle, B: np.ndarray, start: int, n_cycles: int, threads: int = 0):
+    """The kernel-style sweep of Section VIII.B-C on all host cores (OpenMP),
+    with the geometry tables and costs of oracle ``o``: V, L, the improved
+    cells per layer and the thread count used.  A timed CPU baseline, not
+    the oracle; it expects B as rendered (hard walls)."""
+    global _cs_lib
+    if _cs_lib is None:
+        build()
+        L_ = C.CDLL(_CS_SO)
+        L_.cs_sweep.restype = C.c_int
+        L_.cs_sweep.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 5 + [C.c_uint32] + [C.c_void_p] * 3 + \
+            [C.c_int64, C.c_int, C.c_int] + [C.c_void_p] * 3
+        _cs_lib = L_
+    t = o.tables()
+    bsh = np.ascontiguousarray(t["bshear"], dtype=np.int32)
+    cin = np.asarray(o.cin, dtype=np.uint32)
+    cout = np.asarray(o.cout, dtype=np.uint32)
+    B = np.ascontiguousarray(B, dtype=np.uint16)
+    V = np.empty(o.nr, np.uint32)
+    L = np.empty(o.nr, np.uint16)
+    imp = np.zeros(max(1, 6 * n_cycles), np.int64)
+    used = _cs_lib.cs_sweep(o.nx_log2, o.nt_log2, _ptr(t["beta"]), _ptr(t["iflag"]), _ptr(t["jsign"]), _ptr(bsh),
+                            _ptr(t["wS"]), t["wA"], _ptr(cin), _ptr(cout), _ptr(B), int(start), int(n_cycles),
+                            int(threads), _ptr(V), _ptr(L), _ptr(imp))
+    if used < 0:
+        raise ValueError("cpu_sweep: bad input")
+    return V, L, imp[:6 * n_cycles], used
