@@ -120,6 +120,17 @@ def dist_setup():
     return replicas.rank_env()
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(sc, img):
     """The oracle, as it stands, on a bounded sample: one maneuver cycle (6
     layers) of the same 512^3 workload on one host core.  Beside it, the
@@ -132,13 +143,13 @@ def cpu_baseline(sc, img):
     t0 = time.perf_counter()
     o.sweep(B, o.cell(sc.start), 1, mode=1)
     dt = time.perf_counter() - t0
-    oracle_line = {"value": 6 * sc.cells / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+    oracle_line = {"value": 6 * sc.cells / dt, "unit": METRIC, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                    "sample": f"1 maneuver cycle (6 layers) of {WORKLOAD}, single-threaded C oracle, "
                              f"{dt:.1f} s; host has {os.cpu_count()} cores"}
     t0 = time.perf_counter()
     _, _, _, threads = O.cpu_sweep(o, B, o.cell(sc.start), sc.n_cycles)
     dk = time.perf_counter() - t0
-    kernel_line = {"value": 6 * sc.n_cycles * sc.cells / dk, "unit": METRIC, "threads": threads,
+    kernel_line = {"value": 6 * sc.n_cycles * sc.cells / dk, "unit": METRIC, "threads": threads, "cpu": cpu_model(),
                    "plans_per_s": 1.0 / dk, "kind": "kernel-style sweep on all host cores (OpenMP), not the oracle",
                    "sample": f"the whole {sc.n_cycles}-cycle sweep of {WORKLOAD} (B rendered beforehand), "
                              f"{dk:.2f} s; host has {os.cpu_count()} cores"}
