@@ -393,9 +393,12 @@ int plan_device_volumes(plan_t* plan, uint32_t** V, uint16_t** L, uint16_t** B);
 
 /* Per-pass timing and work counters, for roofline accounting.  While
  * profiling is on, plan_render_cspace and plan_sweep record a CUDA event pair
- * around each kernel pass on the plan's stream, and the sweep kernels count
- * the cells whose value strictly decreased (the cells they write).  Counting
- * adds one atomic per warp; timing adds two event records per pass. */
+ * around each kernel pass on the plan's stream, and (PLAN_PROFILE_ALL) the
+ * sweep kernels count the cells whose value strictly decreased (the cells
+ * they write).  Counting adds a warp reduction and atomics per tile and one
+ * block barrier per turn tile; timing adds two event records per pass.  The
+ * counts of a sweep depend only on its inputs, so a timed run can leave
+ * counting off (PLAN_PROFILE_TIMING) and take them from an untimed sweep. */
 typedef struct {
     int64_t turn_passes;      /* fused or single turn sweeps */
     int64_t straight_passes;
@@ -407,7 +410,13 @@ typedef struct {
     uint64_t turn_tiles_improved; /* turn-kernel work items (32 chains) with any written cell */
 } plan_profile_stats;
 
-/* Turn profiling on (enable != 0) or off; either way the counters restart. */
+/* Profiling modes of plan_profile. */
+#define PLAN_PROFILE_OFF 0
+#define PLAN_PROFILE_ALL 1    /* event timing and improved-cell counters */
+#define PLAN_PROFILE_TIMING 2 /* event timing only */
+
+/* Set the profiling mode (PLAN_PROFILE_*; PLAN_EINVAL otherwise); either
+ * way the counters restart.  Synchronises. */
 int plan_profile(plan_t* plan, int enable);
 
 /* Read the counters accumulated since plan_profile(plan, 1).  Synchronises. */

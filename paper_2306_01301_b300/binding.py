@@ -509,8 +509,10 @@ class Planner:
         _check(lib().plan_device_volumes(self._h, C.byref(v), C.byref(l_), C.byref(b)), "plan_device_volumes")
         return v.value, l_.value, b.value
 
-    def profile(self, enable: bool = True):
-        _check(lib().plan_profile(self._h, 1 if enable else 0), "plan_profile")
+    def profile(self, enable: bool = True, counts: bool = True):
+        """Per-pass event timing; with counts, also the improved-cell
+        counters (which add work to the sweep kernels)."""
+        _check(lib().plan_profile(self._h, (1 if counts else 2) if enable else 0), "plan_profile")
 
     def profile_read(self) -> dict:
         st = ProfileStats()

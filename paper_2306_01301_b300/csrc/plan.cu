@@ -446,7 +446,7 @@ int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) 
     if (range_check_layers(p, 6 * n_cycles + (seeded ? 1 : 0)) != PLAN_OK) return PLAN_ERANGE;
     p->qd.start = cell_index(p, start);
     p->qd.n_cycles = n_cycles;
-    p->qd.v.improved = p->prof ? p->d_cnt : nullptr;
+    p->qd.v.improved = p->prof_count ? p->d_cnt : nullptr;
     p->vol_kind = VOL_NONE;
     int rc = upload_desc(p);
     if (rc != PLAN_OK) return rc;
@@ -851,13 +851,14 @@ int plan_device_volumes(plan_t* p, uint32_t** V, uint16_t** L, uint16_t** B) {
 }
 
 int plan_profile(plan_t* p, int enable) {
-    if (!p) return PLAN_EINVAL;
+    if (!p || enable < PLAN_PROFILE_OFF || enable > PLAN_PROFILE_TIMING) return PLAN_EINVAL;
     int rc = cuda_rc(cudaStreamSynchronize(p->stream));
     if (rc != PLAN_OK) return rc;
     for (auto& m : p->marks) { p->spare.push_back(m.a); p->spare.push_back(m.b); }
     p->marks.clear();
     p->acc = plan_profile_stats{};
-    p->prof = enable != 0;
+    p->prof = enable != PLAN_PROFILE_OFF;
+    p->prof_count = enable == PLAN_PROFILE_ALL;
     return cuda_rc(cudaMemsetAsync(p->d_cnt, 0, 32, p->stream));
 }
 

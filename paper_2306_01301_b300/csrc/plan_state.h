@@ -98,7 +98,8 @@ struct plan_s {
         return r;
     }
     // profiling (plan_profile)
-    bool prof = false;
+    bool prof = false;        // per-pass event timing
+    bool prof_count = false;  // improved-cell counters in the sweep kernels
     unsigned long long* d_cnt = nullptr;  // improved cells [0] turn, [1] straight; [2] turn tiles with any
     struct Mark { int kind; cudaEvent_t a, b; };
     std::vector<Mark> marks;

@@ -248,3 +248,55 @@ def test_every_kernel_shape_gives_the_same_bits(lx, lt):
         V, L, _ = p.volumes(B=False)
         assert np.array_equal(V, Vo) and np.array_equal(L, Lo), (v, g, sl, sg)
     p.close()
+
+
+def test_profile_modes_count_only_when_asked():
+    """plan_profile: PLAN_PROFILE_ALL times every pass and counts the cells
+    the sweeps write (the same counts as the oracle's per-layer improvements
+    summed over the passes); PLAN_PROFILE_TIMING times without counting;
+    other modes are refused.  Counting does not change the bits."""
+    from paper_2306_01301_b300 import binding
+    lx, lt, N = 5, 5, 2
+    sc, img = scenes.tiny(77, lx, lt, fill=0.06, turn_radius=3.0, soft=True, transition=300)
+    o = O.Oracle(lx, lt, 3.0, transition=sc.transition)
+    Bo = o.render(img, sc.footprint)
+    start = first_free(o, Bo, sc.pose_candidates)
+    Vo, Lo, imp = o.sweep(Bo, o.cell(start), N, mode=1)
+    p = planner(sc, img)
+    p.render()
+    p.profile(True, counts=True)
+    p.sweep(start, N)
+    a = p.profile_read()
+    V1, L1, _ = p.volumes(B=False)
+    p.profile(True, counts=False)
+    p.sweep(start, N)
+    t = p.profile_read()
+    V2, L2, _ = p.volumes(B=False)
+    p.profile(False)
+    assert a["turn_passes"] == t["turn_passes"] == 2 * N + 1 and a["straight_passes"] == t["straight_passes"] == 2 * N
+    assert a["turn_ms"] > 0 and t["turn_ms"] > 0 and t["straight_ms"] > 0
+    # cells written per pass = cells whose value the pass lowered (a cell
+    # lowered by both layers of a fused turn pair is written once)
+    passes = [[0]]
+    for c in range(N):
+        b0 = 6 * c
+        passes += [[b0 + 1], [b0 + 2, b0 + 3], [b0 + 4], [b0 + 5, b0 + 6] if c < N - 1 else [b0 + 5]]
+    Vr, Lr, _ = o.sweep(Bo, o.cell(start), 0, mode=1)
+    turn_w = straight_w = 0
+    for grp in passes:
+        Vn, Lr, _ = o.layers(Bo, Vr, Lr, grp[0], len(grp), mode=1)
+        w = int((Vn < Vr).sum())
+        if O.CYCLE_ORDER[grp[0] % 6] in (O.SF, O.SB):
+            straight_w += w
+        else:
+            turn_w += w
+        Vr = Vn
+    assert np.array_equal(Vr, Vo) and int(imp.sum()) >= turn_w + straight_w > 0
+    assert a["turn_improved"] == turn_w and a["straight_improved"] == straight_w
+    assert t["turn_improved"] == 0 and t["straight_improved"] == 0
+    for X in (V1, V2):
+        assert np.array_equal(X, Vo)
+    for X in (L1, L2):
+        assert np.array_equal(X, Lo)
+    assert binding.lib().plan_profile(p._h, 3) == binding.PLAN_EINVAL
+    p.close()
