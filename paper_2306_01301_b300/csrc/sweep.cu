@@ -457,17 +457,18 @@ int turn_occupancy() {
 //                    tile rows = grid rows, tile columns = the 16 steps.
 //   steep   (I = 1): cell = row y', column x' + Bs(y');
 //                    tile rows = the 16 steps, tile columns = grid columns.
-// Tiles are filled with 4-byte cp.async copies (whole row segments, so
+// Tiles are filled with 16-byte cp.async copies (whole row segments, so
 // global reads coalesce in both cases), two stages deep: the next chunk is in
-// flight while the current one is scanned.  Changed cells are marked in the
-// tile (bit 31 of the value, the label in place of the obstacle value) and
-// written back row segment by row segment.
+// flight while the current one is scanned.  The two stages take 54 KB, so four
+// 256-line blocks fit on an SM.  Changed cells are marked in the tile (bit 31
+// of the value, the label in place of the obstacle value) and written back
+// row segment by row segment.
 constexpr int kSteps = 16;
 constexpr int kMaxLines = 256;
 constexpr int kSpan = kMaxLines + kSteps;  // tile extent across lines (>= lines + 15)
 // Shallow tiles: rows = grid rows, 16 step columns, 16-byte aligned rows.
-constexpr int kShV = 20;                   // word pitch   (banks: 8 row classes)
-constexpr int kShB = 24;                   // half pitch
+constexpr int kShV = 16;                   // word pitch: 4 chunks of 16 B, swizzled (shv)
+constexpr int kShB = 16;                   // half pitch: 2 chunks of 16 B, swizzled (shb)
 // Steep tiles: 16 step rows, columns = an aligned superset of the segment.
 constexpr int kStV = kSpan + 8;            // word pitch   (segment + up to 3 lead + tail chunk)
 constexpr int kStB = kSpan + 16;           // half pitch
@@ -499,13 +500,20 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const int16_t* bs, int ch, int d
 }
 
 // Word / half index of tile element (step s, index a across lines).
+// Shallow tiles keep whole 16-byte chunks (cp.async granules) but place
+// chunk j of row r at j ^ (r >> 1) (V) or j ^ (r >> 2) (B), so a column read
+// across 32 consecutive rows meets 8 row classes of banks, as an 80-byte /
+// 48-byte padded pitch would, with no padding.
+__device__ __forceinline__ int shv(int r, int s) { return r * kShV + ((((s >> 2) ^ (r >> 1)) & 3) << 2) + (s & 3); }
+__device__ __forceinline__ int shb(int r, int s) { return r * kShB + ((((s >> 3) ^ (r >> 2)) & 1) << 3) + (s & 7); }
+
 template <bool STEEP>
 __device__ __forceinline__ int vidx(int s, int a, int base) {
-    return STEEP ? s * kStV + a + (base & 3) : a * kShV + s;
+    return STEEP ? s * kStV + a + (base & 3) : shv(a, s);
 }
 template <bool STEEP>
 __device__ __forceinline__ int bidx(int s, int a, int base) {
-    return STEEP ? s * kStB + a + (base & 7) : a * kShB + s;
+    return STEEP ? s * kStB + a + (base & 7) : shb(a, s);
 }
 
 template <bool STEEP>
@@ -518,8 +526,8 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
         for (int k = t; k < c.span * 6; k += nt) {
             const int r = k / 6, j = k - r * 6;
             const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
-            if (j < 4) cp_async16(&st.v[r * kShV + 4 * j], Vp + row + 4 * j);
-            else cp_async16(&st.b[r * kShB + 8 * (j - 4)], Bp + row + 8 * (j - 4));
+            if (j < 4) cp_async16(&st.v[shv(r, 4 * j)], Vp + row + 4 * j);
+            else cp_async16(&st.b[shb(r, 8 * (j - 4))], Bp + row + 8 * (j - 4));
         }
     } else {
         // step row s: the aligned chunks covering columns [base, base + span)
@@ -599,11 +607,11 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
             if (!STEEP) {
                 const int s = t & 15, rstep = lines >> 4;
                 for (int r = t >> 4; r < c.span; r += rstep) {
-                    const uint32_t x = st.v[r * kShV + s];
+                    const uint32_t x = st.v[shv(r, s)];
                     if ((x >> 30) == 2u) {
                         const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
                         Vp[id] = x & ~kMark;
-                        Lp[id] = st.b[r * kShB + s];
+                        Lp[id] = st.b[shb(r, s)];
                         nimp++;
                     }
                 }
@@ -638,7 +646,7 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
 // items of a query ordered plane by plane.  Without item_off every query has
 // Nx = 2^lx; with it, queries of any Nx >= lines follow each other.  Blocks
 // loop over items when the grid is smaller than the work.
-__global__ void __launch_bounds__(kMaxLines, 3)
+__global__ void __launch_bounds__(kMaxLines, 4)
 k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, int nq, int64_t items,
            int items_per_q, int pass_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
