@@ -476,10 +476,13 @@ constexpr int kVWords = (kSpan * kShV > kSteps * kStV) ? kSpan * kShV : kSteps *
 constexpr int kBHalves = (kSpan * kShB > kSteps * kStB) ? kSpan * kShB : kSteps * kStB;
 constexpr uint32_t kMark = 0x80000000u;    // changed; stored values are < TH
 
-struct StraightStage {
+constexpr int kMaskWords = (kSpan + 31) / 32;
+
+struct __align__(16) StraightStage {
     uint32_t v[kVWords];
     uint16_t b[kBHalves];
-    int16_t bs[kSteps];  // Bs(y0 + s) - min over the chunk, s = 0..15
+    uint32_t mask[kMaskWords];  // tile rows (shallow) or steps (steep, word 0) holding a changed cell
+    int16_t bs[kSteps];         // Bs(y0 + s) - min over the chunk, s = 0..15
 };
 
 
@@ -521,13 +524,19 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
                                                const uint32_t* Vp, const uint16_t* Bp, int lx, int mx) {
     const int t = threadIdx.x, nt = blockDim.x;
     if (t < kSteps) st.bs[t] = (int16_t)(bs[c.y0 + t] - min(bs[c.y0], bs[c.y0 + kSteps - 1]));
+    if (t < kMaskWords) st.mask[t] = 0;
     if (!STEEP) {
-        // row r: 16 V words = 4 chunks, 16 B halves = 2 chunks, all aligned
-        for (int k = t; k < c.span * 6; k += nt) {
-            const int r = k / 6, j = k - r * 6;
+        // row r: 16 V words = 4 chunks (thread t copies chunk t & 3 of every
+        // (nt/4)-th row), 16 B halves = 2 chunks (chunk t & 1 of every
+        // (nt/2)-th row), all aligned
+        const int jv = t & 3, jb = t & 1;
+        for (int r = t >> 2; r < c.span; r += nt >> 2) {
             const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
-            if (j < 4) cp_async16(&st.v[shv(r, 4 * j)], Vp + row + 4 * j);
-            else cp_async16(&st.b[shb(r, 8 * (j - 4))], Bp + row + 8 * (j - 4));
+            cp_async16(&st.v[shv(r, 4 * jv)], Vp + row + 4 * jv);
+        }
+        for (int r = t >> 1; r < c.span; r += nt >> 1) {
+            const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
+            cp_async16(&st.b[shb(r, 8 * jb)], Bp + row + 8 * jb);
         }
     } else {
         // step row s: the aligned chunks covering columns [base, base + span)
@@ -597,6 +606,8 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
                 st.v[vi] = v | kMark;
                 st.b[bi] = (uint16_t)(mtag | (uint32_t)(q - pv));
                 marked = true;
+                if (STEEP) atomicOr(&st.mask[0], 1u << s);
+                else atomicOr(&st.mask[a >> 5], 1u << (a & 31));
             }
             const uint32_t tt = u + ct;
             if (tt < v) { v = tt; pv = q; }
@@ -605,18 +616,38 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
         // write back the marked cells (only when the block has any)
         if (__syncthreads_or(marked)) {
             if (!STEEP) {
-                const int s = t & 15, rstep = lines >> 4;
-                for (int r = t >> 4; r < c.span; r += rstep) {
-                    const uint32_t x = st.v[shv(r, s)];
-                    if ((x >> 30) == 2u) {
-                        const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
-                        Vp[id] = x & ~kMark;
-                        Lp[id] = st.b[shb(r, s)];
-                        nimp++;
+                // the rows flagged in the mask, two per warp (16 lanes each)
+                const int lane = t & 31, s = lane & 15, upper = lane >> 4;
+                const bool two = lines >= 32;
+                for (int i = t >> 5; i < kMaskWords; i += (lines + 31) >> 5) {
+                    uint32_t m = st.mask[i];  // the same for the whole warp
+                    while (m) {
+                        int bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        bool act = !upper;
+                        if (two) {
+                            if (upper) {
+                                act = m != 0;
+                                bit = act ? __ffs(m) - 1 : 0;
+                            }
+                            if (m) m &= m - 1;
+                        }
+                        if (act) {
+                            const int r = i * 32 + bit;
+                            const uint32_t x = st.v[shv(r, s)];
+                            if ((x >> 30) == 2u) {
+                                const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
+                                Vp[id] = x & ~kMark;
+                                Lp[id] = st.b[shb(r, s)];
+                                nimp++;
+                            }
+                        }
                     }
                 }
             } else {
+                const uint32_t steps = st.mask[0];
                 for (int s = 0; s < kSteps; s++) {
+                    if (!(steps & (1u << s))) continue;
                     for (int xx = t; xx < c.span; xx += lines) {
                         const uint32_t x = st.v[vidx<true>(s, xx, c.base)];
                         if ((x >> 30) == 2u) {
