@@ -43,13 +43,33 @@ struct CWalk {
     int qe = 0, vs = 0;
 };
 
-__device__ __forceinline__ void cstep(CWalk& s, int64_t c, int q, int n, int mu, uint32_t w, const CompactLayer& a) {
+// What a step reads of its cell: obstacle cost, the value of the layer's
+// vertex type and of S.  A layer stores into a cell only at that cell's own
+// step of the second loop and never reads it afterwards, so every read sees
+// the value from before the layer however early it is made: the walks read
+// kAhead cells ahead.
+struct CCell {
+    uint16_t b;
+    uint32_t uT, uS;
+};
+constexpr int kAhead = 8;
+
+__device__ __forceinline__ CCell cread(const CompactLayer& a, int64_t c, int ty) {
+    CCell x;
+    x.b = a.B[c];
+    x.uT = (ty == 1 ? a.Vl : ty == 2 ? a.Vr : a.Vs)[c];
+    x.uS = a.Vs[c];
+    return x;
+}
+
+__device__ __forceinline__ void cstep(CWalk& s, int64_t c, const CCell& x, int q, int n, int mu, uint32_t w,
+                                      const CompactLayer& a) {
     const int ty = type_of(mu);
     uint32_t* Vt = ty == 1 ? a.Vl : ty == 2 ? a.Vr : a.Vs;
     uint16_t* Lt = ty == 1 ? a.Ll : ty == 2 ? a.Lr : a.Ls;
-    const uint16_t b = a.B[c];
+    const uint16_t b = x.b;
     const bool hard = b == HARD;
-    const uint32_t uT = Vt[c], uS = a.Vs[c];  // before this layer
+    const uint32_t uT = x.uT, uS = x.uS;  // before this layer
     if (q >= n && !hard) {
         const uint16_t lab = (uint16_t)((mu << 13) | (s.vs << 12) | (q - s.qe));
         if (s.v < uT) {
@@ -79,9 +99,19 @@ __global__ void __launch_bounds__(256) kc_turn(const CompactLayer a, int mu) {
     const int64_t chain = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (chain >= nxy) return;
     const int xq = (int)(chain & g.mx), yq = (int)(chain >> g.lx);
-    const int n = g.nt;
+    const int n = g.nt, ty = type_of(mu);
     CWalk s;
-    for (int q = 0; q < 2 * n; q++) cstep(s, turn_chain_cell(g, mu, xq, yq, q), q, n, mu, g.wA, a);
+    for (int q0 = 0; q0 < 2 * n; q0 += kAhead) {  // 2n is a multiple of kAhead
+        int64_t c[kAhead];
+        CCell x[kAhead];
+#pragma unroll
+        for (int j = 0; j < kAhead; j++) {
+            c[j] = turn_chain_cell(g, mu, xq, yq, q0 + j);
+            x[j] = cread(a, c[j], ty);
+        }
+#pragma unroll
+        for (int j = 0; j < kAhead; j++) cstep(s, c[j], x[j], q0 + j, n, mu, g.wA, a);
+    }
 }
 
 __global__ void __launch_bounds__(256) kc_straight(const CompactLayer a, int mu) {
@@ -90,9 +120,19 @@ __global__ void __launch_bounds__(256) kc_straight(const CompactLayer a, int mu)
     if (xq >= g.nx) return;
     const int T = blockIdx.y;
     const PlaneInfo pi = g.plane[T];
-    const int n = g.nx;
+    const int n = g.nx, ty = type_of(mu);
     CWalk s;
-    for (int q = 0; q < 2 * n; q++) cstep(s, line_cell(g, pi, mu, T, xq, q), q, n, mu, pi.wS, a);
+    for (int q0 = 0; q0 < 2 * n; q0 += kAhead) {
+        int64_t c[kAhead];
+        CCell x[kAhead];
+#pragma unroll
+        for (int j = 0; j < kAhead; j++) {
+            c[j] = line_cell(g, pi, mu, T, xq, q0 + j);
+            x[j] = cread(a, c[j], ty);
+        }
+#pragma unroll
+        for (int j = 0; j < kAhead; j++) cstep(s, c[j], x[j], q0 + j, n, mu, pi.wS, a);
+    }
 }
 
 __global__ void kc_init(CompactLayer a, int64_t nr, int64_t start) {
