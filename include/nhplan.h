@@ -65,6 +65,7 @@ extern "C" {
 #define PLAN_ERANGE (-6)       /* output capacity too small, or costs could overflow */
 #define PLAN_EINTERNAL (-7)    /* device-side consistency check failed */
 #define PLAN_ESTATE (-8)       /* call out of order (e.g. sweep before render) */
+#define PLAN_ECANCELED (-9)    /* request cancelled (plan_server_cancel) */
 
 #define PLAN_INF 0xFFFFFFFFu
 #define PLAN_NO_DIRECTION 0xFFFFu /* no preferred heading (plan_set_direction_field) */
@@ -561,11 +562,25 @@ typedef struct {
     int64_t heavy_cells;
     int64_t big_cells;
     int32_t max_heavy;
-    int32_t reserved;
+    int32_t flags;        /* PLAN_SERVE_* flags below */
+    /* Launch-descriptor bytes reserved per step slot (3 slots per stream, 3
+     * streams) when the server is created; 0 = 64 KiB, about 140 requests
+     * per step.  At least 4096. */
+    int64_t slot_bytes;
 } plan_server_config;
 
+/* Stop a request's sweep once it has converged: when four consecutive passes
+ * (every maneuver once, from the first cycle's SF on) have lowered no cell,
+ * V and L are a fixed point of every maneuver layer, so the remaining passes
+ * of its N cycles would change nothing.  Each pass records on the device
+ * whether it lowered a cell; later passes of a converged request read those
+ * records and return without touching its volumes.  Results are identical
+ * with and without the flag; served latency drops for requests that converge
+ * before their N-th cycle. */
+#define PLAN_SERVE_STOP_AT_CONVERGENCE 1
+
 typedef struct {
-    int32_t status;     /* PLAN_OK, PLAN_EUNREACHABLE, PLAN_ENOMEM (can never fit), PLAN_ECUDA ... */
+    int32_t status;     /* PLAN_OK, PLAN_EUNREACHABLE, PLAN_ENOMEM (can never fit), PLAN_ECANCELED, PLAN_ECUDA ... */
     uint32_t cost;      /* V(goal) */
     int32_t n_segments;
     int32_t scene;
@@ -578,11 +593,19 @@ typedef struct {
     int64_t launches;      /* kernels launched for requests */
     int64_t peak_inflight; /* most requests admitted at once */
     int64_t arena_bytes, peak_bytes, scene_bytes;
+    int64_t reserved_bytes; /* arena bytes held from creation on for launch descriptors */
+    int64_t cancelled;      /* requests ended by plan_server_cancel */
+    int64_t partial_steps;  /* steps that advanced only some requests (descriptor space) */
 } plan_server_stats;
 
 /* Create a server and start its scheduler thread.  allocator (NULL =
  * cudaMalloc) provides the one arena block; cuda_stream's earlier work is
- * waited for once.  The server uses the device current at creation. */
+ * waited for once.  The server uses the device current at creation.  The
+ * launch descriptors of every stream's steps are carved from the arena at
+ * creation (reserved_bytes in the stats, PLAN_ENOMEM when the budget cannot
+ * hold them), so scenes and requests get the rest.  Descriptor space grows
+ * only from arena memory nobody else holds; when it cannot grow, a step
+ * advances the requests that fit and the others wait for the next step. */
 int plan_server_create(const plan_server_config* cfg, const plan_allocator* allocator, void* cuda_stream,
                        plan_server_t** out);
 
@@ -605,6 +628,15 @@ int plan_server_submit(plan_server_t* server, int32_t scene_id, plan_pose start,
  * releases the ticket. */
 int plan_server_wait(plan_server_t* server, uint64_t ticket, double timeout_s, plan_request_info* info,
                      plan_segment* out, int cap, int* n_out);
+
+/* Cancel a request (thread-safe, does not wait).  A request not yet admitted
+ * is dropped; an admitted one runs no further passes and its memory is
+ * released once the work already queued for it has finished; its wait then
+ * reports PLAN_ECANCELED in info->status.  A request whose label walk is
+ * already on the GPU, or that is done, keeps its result.  In one-at-a-time
+ * mode the request being planned is not interrupted.  PLAN_EINVAL for an
+ * unknown ticket. */
+int plan_server_cancel(plan_server_t* server, uint64_t ticket);
 
 /* Counters since creation. */
 int plan_server_stats_read(plan_server_t* server, plan_server_stats* out);

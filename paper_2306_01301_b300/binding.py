@@ -642,12 +642,14 @@ class Batch:
 # ---------------------------------------------------------------- serving
 PLAN_SERVE_CONTINUOUS = 0
 PLAN_SERVE_ONE_AT_A_TIME = 1
+PLAN_SERVE_STOP_AT_CONVERGENCE = 1
+PLAN_ECANCELED = -9
 
 
 class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("max_inflight", C.c_int32), ("mode", C.c_int32),
                 ("heavy_cells", C.c_int64), ("big_cells", C.c_int64), ("max_heavy", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32), ("slot_bytes", C.c_int64)]
 
 
 class RequestInfo(C.Structure):
@@ -658,7 +660,7 @@ class RequestInfo(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("scenes", "submitted", "admitted", "completed", "rejected", "steps",
                                          "launches", "peak_inflight", "arena_bytes", "peak_bytes",
-                                         "scene_bytes")]
+                                         "scene_bytes", "reserved_bytes", "cancelled", "partial_steps")]
 
 
 def _server_signatures(L):
@@ -673,6 +675,8 @@ def _server_signatures(L):
     L.plan_server_wait.restype = C.c_int
     L.plan_server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(RequestInfo), C.POINTER(Segment), C.c_int,
                                    C.POINTER(C.c_int)]
+    L.plan_server_cancel.restype = C.c_int
+    L.plan_server_cancel.argtypes = [vp, C.c_uint64]
     L.plan_server_stats_read.restype = C.c_int
     L.plan_server_stats_read.argtypes = [vp, C.POINTER(ServerStats)]
     L.plan_server_destroy.restype = C.c_int
@@ -684,7 +688,8 @@ class Server:
     admitted by an HBM budget, continuous batching or one at a time."""
 
     def __init__(self, budget_bytes: int, max_inflight: int = 0, one_at_a_time: bool = False,
-                 heavy_cells: int = 0, big_cells: int = 0, max_heavy: int = 0, stream=None):
+                 heavy_cells: int = 0, big_cells: int = 0, max_heavy: int = 0, stop_at_convergence: bool = False,
+                 slot_bytes: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("nhplan needs a CUDA device; there is no CPU fallback")
@@ -696,7 +701,8 @@ class Server:
         self._alloc = _TorchAllocator(torch, self.stream)
         cfg = ServerConfig(int(budget_bytes), int(max_inflight),
                            PLAN_SERVE_ONE_AT_A_TIME if one_at_a_time else PLAN_SERVE_CONTINUOUS,
-                           int(heavy_cells), int(big_cells), int(max_heavy), 0)
+                           int(heavy_cells), int(big_cells), int(max_heavy),
+                           PLAN_SERVE_STOP_AT_CONVERGENCE if stop_at_convergence else 0, int(slot_bytes))
         h = C.c_void_p()
         _check(L.plan_server_create(C.byref(cfg), C.byref(self._alloc.struct), C.c_void_p(self.stream.cuda_stream),
                                     C.byref(h)), "plan_server_create")
@@ -734,6 +740,9 @@ class Server:
         if info.status != PLAN_OK:
             raise PlanError(info.status, "served request")
         return d, PlanResult(int(info.cost), _segments(segs, n.value))
+
+    def cancel(self, ticket: int):
+        _check(lib().plan_server_cancel(self._h, int(ticket)), "plan_server_cancel")
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -75,7 +75,18 @@ struct QueryDesc {
     int32_t* status;          // [0] segment count or error, [1] V(goal) low, [2] high
     int32_t seg_cap;
     int32_t max_runs;         // footprint runs of the widest heading
+    // Optional (null = off): one word per pass (4N + 1), set to 1 by a pass
+    // that lowered some cell of this query.  Once four consecutive passes
+    // starting at pass 1 or later -- every maneuver once -- lowered nothing,
+    // V and L are a fixed point of every maneuver layer, so later passes of
+    // the query change nothing and skip their work (same values and labels).
+    uint32_t* conv;
 };
+
+// True when pass p of a query with convergence flags has nothing left to do.
+__device__ __forceinline__ bool pass_converged(const uint32_t* conv, int p) {
+    return conv != nullptr && p >= 5 && (conv[p - 1] | conv[p - 2] | conv[p - 3] | conv[p - 4]) == 0u;
+}
 
 // One launch group: nq descriptors on the device.  Without `item_off` every
 // query has the shape (lx, lt) and a launch gives each work item its own

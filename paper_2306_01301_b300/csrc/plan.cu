@@ -915,6 +915,7 @@ const char* plan_strerror(int code) {
         case PLAN_ERANGE: return "capacity or cost range exceeded";
         case PLAN_EINTERNAL: return "internal consistency check failed";
         case PLAN_ESTATE: return "call out of order";
+        case PLAN_ECANCELED: return "request cancelled";
         default: return "unknown error";
     }
 }

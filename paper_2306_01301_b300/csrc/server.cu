@@ -21,6 +21,7 @@
 // sequence (init, 4N + 1 passes, label walk, synchronise) before the next
 // starts.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,6 +43,10 @@ namespace {
 constexpr int kDepth = 2;            // steps queued on the GPU ahead of the host
 constexpr int kSlots = kDepth + 1;   // descriptor / result slots in rotation
 constexpr size_t kAlign = 256;
+// Default descriptor (arena) and result (mapped host) bytes of every slot,
+// reserved at creation: room for about 140 requests in one step.
+constexpr size_t kDescMin = (size_t)64 << 10;
+constexpr size_t kResMin = (size_t)64 << 10;
 constexpr int kMaxScenes = 4096;
 constexpr int kTracks = 3;           // 0: big, 1: heavy, 2: light requests
 constexpr int kLight = kTracks - 1;
@@ -138,6 +143,7 @@ struct Request {
     std::vector<plan_segment> segs;
     int res_off = 0;          // offset of its result in the step's result area
     int track = kLight;
+    std::atomic<bool> cancel{false};  // set by plan_server_cancel
 };
 using ReqPtr = std::shared_ptr<Request>;
 
@@ -154,6 +160,10 @@ struct Step {
     cudaEvent_t ev = nullptr;
     int slot = 0;
     std::vector<ReqPtr> finishing;
+    // requests taken out of the schedule in this step (cancelled, or whose
+    // step could not get descriptor space): their memory is released and
+    // their status set once the work queued before them has finished
+    std::vector<std::pair<ReqPtr, int>> dropped;
 };
 
 // A sequence of steps on its own stream.  Requests are classed by size:
@@ -211,6 +221,7 @@ struct plan_server_s {
     std::vector<cudaEvent_t> spare_events;
     std::thread worker;
 
+    bool conv() const { return (cfg.flags & PLAN_SERVE_STOP_AT_CONVERGENCE) != 0; }
     int inflight() const {
         int n = 0;
         for (auto& t : tracks) n += (int)t.active.size();
@@ -225,14 +236,21 @@ struct plan_server_s {
 
 namespace {
 
-size_t request_bytes(const plan_s* sc) { return align_up((size_t)sc->nr * 4, kAlign) + (size_t)sc->nr * 2; }
+// A request's arena block: V, L and (with PLAN_SERVE_STOP_AT_CONVERGENCE)
+// one convergence word per pass.
+size_t l_offset(const plan_s* sc) { return align_up((size_t)sc->nr * 4, kAlign); }
+size_t conv_offset(const plan_s* sc) { return align_up(l_offset(sc) + (size_t)sc->nr * 2, kAlign); }
+size_t request_bytes(const plan_s* sc, int n_cycles, bool conv) {
+    return conv ? conv_offset(sc) + 4 * ((size_t)4 * n_cycles + 1) : l_offset(sc) + (size_t)sc->nr * 2;
+}
 
 int lane_nx_key(int nx) { return nx >= 256 ? 256 : nx; }
 
-QueryDesc request_desc(const plan_s* sc, const Request& r) {
+QueryDesc request_desc(const plan_s* sc, const Request& r, bool conv) {
     QueryDesc d = sc->qd;
     d.v.V = (uint32_t*)r.mem;
-    d.v.L = (uint16_t*)(r.mem + align_up((size_t)sc->nr * 4, kAlign));
+    d.v.L = (uint16_t*)(r.mem + l_offset(sc));
+    d.conv = conv ? (uint32_t*)(r.mem + conv_offset(sc)) : nullptr;
     d.v.improved = nullptr;
     d.start = cell_index(sc, r.start);
     d.goal = cell_index(sc, r.goal);
@@ -253,34 +271,55 @@ void free_slot(Slot& s, plan_server_s* v) {
     s = Slot{};
 }
 
+// Fresh buffers for one slot; false (and nothing held) when any allocation fails.
+bool alloc_slot(plan_server_s* v, Slot& s, size_t desc, size_t res) {
+    s = Slot{};
+    s.d_desc = v->arena.alloc(desc);
+    bool ok = s.d_desc != nullptr;
+    ok = ok && cudaHostAlloc((void**)&s.h_desc, desc, cudaHostAllocDefault) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void**)&s.h_res, res, cudaHostAllocMapped) == cudaSuccess;
+    ok = ok && cudaHostGetDevicePointer((void**)&s.d_res, s.h_res, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();  // a failed host allocation is not a sticky error
+        free_slot(s, v);
+        return false;
+    }
+    s.desc_cap = desc;
+    s.res_cap = res;
+    return true;
+}
+
 void retire(plan_server_s* v, Track& tr, Step& st);
 
-// Make every slot of the track hold at least `desc` descriptor bytes and
-// `res` result bytes.  Growing waits for the track's steps in flight (they
-// use the old buffers).
-int ensure_slots(plan_server_s* v, Track& tr, size_t desc, size_t res) {
-    bool grow = false;
-    for (auto& s : tr.slots) grow = grow || s.desc_cap < desc || s.res_cap < res;
-    if (!grow) return PLAN_OK;
-    NHP_CK(cudaStreamSynchronize(tr.stream));
+// Grow every slot of the track to hold `desc` descriptor and `res` result
+// bytes.  The new buffers are taken before the old ones are given back, so a
+// failed growth changes nothing and returns false; the track's steps in
+// flight (which use the old buffers) are waited for only once the new ones
+// exist.  A CUDA error while waiting is returned through *rc.
+bool grow_slots(plan_server_s* v, Track& tr, size_t desc, size_t res, int* rc) {
+    desc = align_up(desc, 4096);
+    res = align_up(res, 4096);
+    Slot fresh[kSlots];
+    for (int i = 0; i < kSlots; i++) {
+        if (!alloc_slot(v, fresh[i], std::max(desc, tr.slots[i].desc_cap), std::max(res, tr.slots[i].res_cap))) {
+            for (int j = 0; j < i; j++) free_slot(fresh[j], v);
+            return false;
+        }
+    }
+    if (cudaStreamSynchronize(tr.stream) != cudaSuccess) {
+        for (auto& f : fresh) free_slot(f, v);
+        *rc = cuda_fail(cudaGetLastError(), "server track synchronise");
+        return false;
+    }
     while (!tr.steps.empty()) {
         retire(v, tr, tr.steps.front());
         tr.steps.pop_front();
     }
-    desc = align_up(std::max(desc, (size_t)64 << 10), 4096);
-    res = align_up(std::max(res, (size_t)64 << 10), 4096);
-    for (auto& s : tr.slots) {
-        const size_t dcap = std::max(desc, s.desc_cap), rcap = std::max(res, s.res_cap);
-        free_slot(s, v);
-        s.d_desc = v->arena.alloc(dcap);
-        if (!s.d_desc) return PLAN_ENOMEM;
-        s.desc_cap = dcap;
-        NHP_CK(cudaHostAlloc((void**)&s.h_desc, dcap, cudaHostAllocDefault));
-        NHP_CK(cudaHostAlloc((void**)&s.h_res, rcap, cudaHostAllocMapped));
-        NHP_CK(cudaHostGetDevicePointer((void**)&s.d_res, s.h_res, 0));
-        s.res_cap = rcap;
+    for (int i = 0; i < kSlots; i++) {
+        free_slot(tr.slots[i], v);
+        tr.slots[i] = fresh[i];
     }
-    return PLAN_OK;
+    return true;
 }
 
 cudaEvent_t take_event(plan_server_s* v) {
@@ -318,7 +357,28 @@ void retire(plan_server_s* v, Track& tr, Step& st) {
         r->done = true;
         v->stats.completed++;
     }
+    for (auto& d : st.dropped) {
+        const ReqPtr& r = d.first;
+        v->arena.release(r->mem);
+        r->mem = nullptr;
+        r->status = d.second;
+        r->t_done = t;
+        r->done = true;
+        if (d.second == PLAN_ECANCELED) v->stats.cancelled++;
+        else v->stats.rejected++;
+    }
     v->spare_events.push_back(st.ev);
+    v->cv_done.notify_all();
+}
+
+// End a request that holds no memory and has nothing on the GPU.
+void finish_now(plan_server_s* v, const ReqPtr& r, int status) {
+    std::lock_guard<std::mutex> lk(v->mu);
+    r->status = status;
+    r->done = true;
+    r->t_done = now_s();
+    if (status == PLAN_ECANCELED) v->stats.cancelled++;
+    else v->stats.rejected++;
     v->cv_done.notify_all();
 }
 
@@ -356,15 +416,20 @@ void admit(plan_server_s* v) {
     int running[kTracks];
     for (int k = 0; k < kTracks; k++) running[k] = (int)v->tracks[k].active.size();
     for (auto it = v->pending.begin(); it != v->pending.end();) {
-        if (v->cfg.max_inflight > 0 && v->inflight() >= v->cfg.max_inflight) break;
         ReqPtr r = *it;
+        if (r->cancel.load()) {
+            it = v->pending.erase(it);
+            finish_now(v, r, PLAN_ECANCELED);
+            continue;
+        }
+        if (v->cfg.max_inflight > 0 && v->inflight() >= v->cfg.max_inflight) break;
         const plan_s* sc = v->scenes[r->scene];
         const int k = track_of(v, sc);
         if (k != kLight && v->cfg.max_heavy > 0 && running[k] >= v->cfg.max_heavy) {
             ++it;
             continue;
         }
-        r->mem_bytes = request_bytes(sc);
+        r->mem_bytes = request_bytes(sc, r->n_cycles, v->conv());
         r->mem = v->arena.alloc(r->mem_bytes);
         if (!r->mem) break;
         r->t_admit = now_s();
@@ -379,111 +444,152 @@ void admit(plan_server_s* v) {
     }
 }
 
-// Build and enqueue one continuous-batching step of a track.
-int launch_step(plan_server_s* v, Track& tr) {
+// Descriptor layout of one step for the first n requests of `reqs` (none
+// of them finishing): requests not yet initialised get init and pass 0,
+// every request one pass (one launch per lane and pass kind), and requests
+// whose last pass this is a label walk.
+struct StepPlan {
     std::vector<ReqPtr> init, fin;
     std::vector<LaunchSet> sets;
-    for (auto& r : tr.active) {
-        if (r->finishing) continue;
-        if (r->pass < 0) {
-            init.push_back(r);
-            r->pass = 0;
-        }
+    std::vector<size_t> o_set, o_items;
+    size_t o_init = 0, o_fin = 0, desc = 0, res = 0;
+};
+
+StepPlan plan_step(const plan_server_s* v, const std::vector<ReqPtr>& reqs, size_t n) {
+    StepPlan P;
+    for (size_t i = 0; i < n; i++) {
+        const ReqPtr& r = reqs[i];
+        if (r->pass < 0) P.init.push_back(r);
+        const int pass = r->pass < 0 ? 0 : r->pass;
         const plan_s* sc = v->scenes[r->scene];
-        const bool turn = pass_is_turn(r->pass);
+        const bool turn = pass_is_turn(pass);
         const int key = lane_nx_key(sc->nx);
         LaunchSet* ls = nullptr;
-        for (auto& s : sets)
-            if (s.lt == sc->lt && s.nx_key == key && s.turn == turn) ls = &s;
+        for (auto& st : P.sets)
+            if (st.lt == sc->lt && st.nx_key == key && st.turn == turn) ls = &st;
         if (!ls) {
-            sets.emplace_back();
-            ls = &sets.back();
+            P.sets.emplace_back();
+            ls = &P.sets.back();
             ls->lt = sc->lt;
             ls->nx_key = key;
             ls->turn = turn;
         }
         ls->reqs.push_back(r);
-        if (r->pass + 1 == pass_count(r->n_cycles)) fin.push_back(r);
+        if (pass + 1 == pass_count(r->n_cycles)) P.fin.push_back(r);
     }
-    if (init.empty() && sets.empty()) return PLAN_OK;
-    // descriptor layout
     size_t off = 0;
-    const size_t o_init = off;
-    off = align_up(off + sizeof(QueryDesc) * init.size(), kAlign);
-    std::vector<size_t> o_set(sets.size()), o_items(sets.size());
-    for (size_t k = 0; k < sets.size(); k++) {
-        o_set[k] = off;
-        off = align_up(off + sizeof(QueryDesc) * sets[k].reqs.size(), kAlign);
-        o_items[k] = off;
-        off = align_up(off + sizeof(int32_t) * (sets[k].reqs.size() + 1), kAlign);
+    P.o_init = off;
+    off = align_up(off + sizeof(QueryDesc) * P.init.size(), kAlign);
+    P.o_set.resize(P.sets.size());
+    P.o_items.resize(P.sets.size());
+    for (size_t k = 0; k < P.sets.size(); k++) {
+        P.o_set[k] = off;
+        off = align_up(off + sizeof(QueryDesc) * P.sets[k].reqs.size(), kAlign);
+        P.o_items[k] = off;
+        off = align_up(off + sizeof(int32_t) * (P.sets[k].reqs.size() + 1), kAlign);
     }
-    const size_t o_fin = off;
-    off = align_up(off + sizeof(QueryDesc) * fin.size(), kAlign);
+    P.o_fin = off;
+    off = align_up(off + sizeof(QueryDesc) * P.fin.size(), kAlign);
+    P.desc = off;
+    for (auto& r : P.fin) P.res = align_up(P.res + result_bytes(*r), 16);
+    return P;
+}
+
+// Build and enqueue one continuous-batching step of a track.
+int launch_step(plan_server_s* v, Track& tr) {
+    Step st;
+    std::vector<ReqPtr> sched;
+    for (auto& r : tr.active) {
+        if (r->finishing) continue;
+        if (r->cancel.load()) {  // no further passes; memory back once its queued work is done
+            st.dropped.emplace_back(r, PLAN_ECANCELED);
+            r->finishing = true;
+            continue;
+        }
+        sched.push_back(r);
+    }
+    size_t n = sched.size();
+    StepPlan P = plan_step(v, sched, n);
+    bool partial = false;
+    if (n > 0 && (P.desc > tr.slots[0].desc_cap || P.res > tr.slots[0].res_cap)) {
+        int rc = PLAN_OK;
+        if (!grow_slots(v, tr, P.desc, P.res, &rc)) {
+            if (rc != PLAN_OK) return rc;
+            // no room to grow: advance the requests that fit, the rest wait
+            while (n > 0 && (P.desc > tr.slots[0].desc_cap || P.res > tr.slots[0].res_cap)) P = plan_step(v, sched, --n);
+            partial = true;
+            if (n == 0) {  // even the oldest request alone never fits
+                st.dropped.emplace_back(sched[0], PLAN_ENOMEM);
+                sched[0]->finishing = true;
+            }
+        }
+    }
+    if (n == 0 && st.dropped.empty()) return PLAN_OK;
+    for (size_t i = 0; i < n; i++)
+        if (sched[i]->pass < 0) sched[i]->pass = 0;
     size_t res = 0;
-    for (auto& r : fin) {
+    for (auto& r : P.fin) {
         r->res_off = (int)res;
         res = align_up(res + result_bytes(*r), 16);
     }
-    int rc = ensure_slots(v, tr, off, res);
-    if (rc != PLAN_OK) return rc;
     const int si = (int)(tr.step_count % kSlots);
     Slot& sl = tr.slots[si];
     unsigned char* h = sl.h_desc;
     cudaStream_t s = tr.stream;
+    const bool conv = v->conv();
     int64_t launches = 0;
-    // fill
-    for (size_t k = 0; k < init.size(); k++) {
-        QueryDesc d = request_desc(v->scenes[init[k]->scene], *init[k]);
-        memcpy(h + o_init + k * sizeof(QueryDesc), &d, sizeof d);
+    for (size_t k = 0; k < P.init.size(); k++) {
+        QueryDesc d = request_desc(v->scenes[P.init[k]->scene], *P.init[k], conv);
+        memcpy(h + P.o_init + k * sizeof(QueryDesc), &d, sizeof d);
     }
-    std::vector<int64_t> items(sets.size(), 0);
-    for (size_t k = 0; k < sets.size(); k++) {
-        int32_t* it = (int32_t*)(h + o_items[k]);
+    std::vector<int64_t> items(P.sets.size(), 0);
+    for (size_t k = 0; k < P.sets.size(); k++) {
+        int32_t* it = (int32_t*)(h + P.o_items[k]);
         it[0] = 0;
-        for (size_t j = 0; j < sets[k].reqs.size(); j++) {
-            const Request& r = *sets[k].reqs[j];
+        for (size_t j = 0; j < P.sets[k].reqs.size(); j++) {
+            const Request& r = *P.sets[k].reqs[j];
             const plan_s* sc = v->scenes[r.scene];
-            QueryDesc d = request_desc(sc, r);
-            memcpy(h + o_set[k] + j * sizeof(QueryDesc), &d, sizeof d);
-            const int64_t n = sets[k].turn ? turn_items(sc->lx)
-                                           : (sc->nx >= 256 ? straight_items(sc->lx, sc->lt, 256) : 0);
-            it[j + 1] = (int32_t)(it[j] + n);
+            QueryDesc d = request_desc(sc, r, conv);
+            memcpy(h + P.o_set[k] + j * sizeof(QueryDesc), &d, sizeof d);
+            const int64_t ni = P.sets[k].turn ? turn_items(sc->lx)
+                                              : (sc->nx >= 256 ? straight_items(sc->lx, sc->lt, 256) : 0);
+            it[j + 1] = (int32_t)(it[j] + ni);
         }
-        items[k] = it[sets[k].reqs.size()];
+        items[k] = it[P.sets[k].reqs.size()];
     }
-    for (size_t k = 0; k < fin.size(); k++) {
-        const Request& r = *fin[k];
-        QueryDesc d = request_desc(v->scenes[r.scene], r);
+    for (size_t k = 0; k < P.fin.size(); k++) {
+        const Request& r = *P.fin[k];
+        QueryDesc d = request_desc(v->scenes[r.scene], r, conv);
         d.status = (int32_t*)(sl.d_res + r.res_off);
         d.seg = (plan_segment*)(sl.d_res + r.res_off + 16);
         d.seg_cap = 6 * r.n_cycles;
-        memcpy(h + o_fin + k * sizeof(QueryDesc), &d, sizeof d);
+        memcpy(h + P.o_fin + k * sizeof(QueryDesc), &d, sizeof d);
     }
-    NHP_CK(cudaMemcpyAsync(sl.d_desc, h, off, cudaMemcpyHostToDevice, s));
-    if (!init.empty()) {
+    if (P.desc) NHP_CK(cudaMemcpyAsync(sl.d_desc, h, P.desc, cudaMemcpyHostToDevice, s));
+    if (!P.init.empty()) {
         Group g{};
-        g.d = (const QueryDesc*)(sl.d_desc + o_init);
-        g.nq = (int)init.size();
-        for (auto& r : init) {
+        g.d = (const QueryDesc*)(sl.d_desc + P.o_init);
+        g.nq = (int)P.init.size();
+        for (auto& r : P.init) {
             g.lx = std::max(g.lx, v->scenes[r->scene]->lx);
             g.lt = std::max(g.lt, v->scenes[r->scene]->lt);
         }
         NHP_CK(launch_init(g, s));
         launches++;
     }
-    for (size_t k = 0; k < sets.size(); k++) {
-        const LaunchSet& ls = sets[k];
+    for (size_t k = 0; k < P.sets.size(); k++) {
+        const LaunchSet& ls = P.sets[k];
         const plan_s* sc0 = v->scenes[ls.reqs[0]->scene];
         bool uniform = true;
         for (auto& r : ls.reqs) uniform = uniform && v->scenes[r->scene]->lx == sc0->lx;
         Group g{};
-        g.d = (const QueryDesc*)(sl.d_desc + o_set[k]);
+        g.d = (const QueryDesc*)(sl.d_desc + P.o_set[k]);
         g.nq = (int)ls.reqs.size();
         g.lx = sc0->lx;
         g.lt = ls.lt;
         g.max_runs = 1;
         if (!uniform) {
-            g.item_off = (const int32_t*)(sl.d_desc + o_items[k]);
+            g.item_off = (const int32_t*)(sl.d_desc + P.o_items[k]);
             g.items = items[k];
         }
         // pass -1: every request at its own pass (QueryDesc::pass)
@@ -491,57 +597,65 @@ int launch_step(plan_server_s* v, Track& tr) {
         NHP_CK(ls.turn ? launch_turn(g, -1, -1, s) : launch_straight(g, -1, lines, s));
         launches++;
     }
-    if (!fin.empty()) {
+    if (!P.fin.empty()) {
         Group g{};
-        g.d = (const QueryDesc*)(sl.d_desc + o_fin);
-        g.nq = (int)fin.size();
+        g.d = (const QueryDesc*)(sl.d_desc + P.o_fin);
+        g.nq = (int)P.fin.size();
         NHP_CK(launch_extract(g, s));
         launches++;
     }
-    Step st;
     st.ev = take_event(v);
     st.slot = si;
-    st.finishing = fin;
+    st.finishing = P.fin;
     if (!st.ev) return PLAN_ECUDA;
     NHP_CK(cudaEventRecord(st.ev, s));
     tr.steps.push_back(std::move(st));
     tr.step_count++;
-    for (auto& r : tr.active) {
-        if (r->finishing) continue;
-        r->pass++;
-        if (r->pass == pass_count(r->n_cycles)) r->finishing = true;
+    for (size_t i = 0; i < n; i++) {
+        Request& r = *sched[i];
+        r.pass++;
+        if (r.pass == pass_count(r.n_cycles)) r.finishing = true;
     }
     tr.active.erase(std::remove_if(tr.active.begin(), tr.active.end(), [](const ReqPtr& r) { return r->finishing; }),
                     tr.active.end());
     std::lock_guard<std::mutex> lk(v->mu);
     v->stats.steps++;
     v->stats.launches += launches;
+    if (partial) v->stats.partial_steps++;
     return PLAN_OK;
 }
 
 // One-at-a-time: the single-plan launch sequence for the oldest request.
 int run_one(plan_server_s* v) {
     ReqPtr r = v->pending.front();
-    const plan_s* sc = v->scenes[r->scene];
-    r->mem_bytes = request_bytes(sc);
-    r->mem = v->arena.alloc(r->mem_bytes);
     v->pending.pop_front();
+    if (r->cancel.load()) {
+        finish_now(v, r, PLAN_ECANCELED);
+        return PLAN_OK;
+    }
+    const plan_s* sc = v->scenes[r->scene];
+    const bool conv = v->conv();
+    r->mem_bytes = request_bytes(sc, r->n_cycles, conv);
+    r->mem = v->arena.alloc(r->mem_bytes);
     if (!r->mem) {  // nothing else holds memory: the request can never fit
-        std::lock_guard<std::mutex> lk(v->mu);
-        r->status = PLAN_ENOMEM;
-        r->done = true;
-        r->t_done = now_s();
-        v->stats.rejected++;
-        v->cv_done.notify_all();
+        finish_now(v, r, PLAN_ENOMEM);
         return PLAN_OK;
     }
     r->t_admit = now_s();
     Track& tr = v->tracks[kLight];
-    int rc = ensure_slots(v, tr, sizeof(QueryDesc), result_bytes(*r));
-    if (rc != PLAN_OK) return rc;
+    if (sizeof(QueryDesc) > tr.slots[0].desc_cap || result_bytes(*r) > tr.slots[0].res_cap) {
+        int rc = PLAN_OK;
+        if (!grow_slots(v, tr, sizeof(QueryDesc), result_bytes(*r), &rc)) {
+            v->arena.release(r->mem);
+            r->mem = nullptr;
+            if (rc != PLAN_OK) return rc;
+            finish_now(v, r, PLAN_ENOMEM);
+            return PLAN_OK;
+        }
+    }
     Slot& sl = tr.slots[0];
     cudaStream_t s = tr.stream;
-    QueryDesc d = request_desc(sc, *r);
+    QueryDesc d = request_desc(sc, *r, conv);
     d.pass = -1;
     d.status = (int32_t*)sl.d_res;
     d.seg = (plan_segment*)(sl.d_res + 16);
@@ -639,12 +753,7 @@ void worker_main(plan_server_s* v) {
                 // nothing on the GPU and the head request still does not fit
                 ReqPtr r = v->pending.front();
                 v->pending.pop_front();
-                std::lock_guard<std::mutex> lk(v->mu);
-                r->status = PLAN_ENOMEM;
-                r->done = true;
-                r->t_done = now_s();
-                v->stats.rejected++;
-                v->cv_done.notify_all();
+                finish_now(v, r, r->cancel.load() ? PLAN_ECANCELED : PLAN_ENOMEM);
             }
         }
         if (rc != PLAN_OK) {
@@ -687,7 +796,8 @@ int plan_server_create(const plan_server_config* cfg, const plan_allocator* allo
     if (!out) return PLAN_EINVAL;
     *out = nullptr;
     if (!cfg || cfg->budget_bytes < ((size_t)1 << 20) || cfg->max_inflight < 0 || cfg->max_heavy < 0 ||
-        cfg->heavy_cells < 0 || cfg->big_cells < 0 ||
+        cfg->heavy_cells < 0 || cfg->big_cells < 0 || (cfg->flags & ~PLAN_SERVE_STOP_AT_CONVERGENCE) != 0 ||
+        (cfg->slot_bytes != 0 && (cfg->slot_bytes < 4096 || cfg->slot_bytes > ((int64_t)1 << 30))) ||
         (cfg->mode != PLAN_SERVE_CONTINUOUS && cfg->mode != PLAN_SERVE_ONE_AT_A_TIME))
         return PLAN_EINVAL;
     if (allocator && (!allocator->alloc || !allocator->free)) return PLAN_EINVAL;
@@ -716,6 +826,12 @@ int plan_server_create(const plan_server_config* cfg, const plan_allocator* allo
         if (!v->arena_base) rc = PLAN_ENOMEM;
         else v->arena.init(v->arena_base, cfg->budget_bytes);
     }
+    // every track's launch descriptors, before any scene or request
+    for (int k = 0; k < kTracks && rc == PLAN_OK; k++)
+        for (auto& sl : v->tracks[k].slots)
+            if (rc == PLAN_OK && !alloc_slot(v, sl, cfg->slot_bytes ? (size_t)cfg->slot_bytes : kDescMin, kResMin))
+                rc = PLAN_ENOMEM;
+    if (rc == PLAN_OK) v->stats.reserved_bytes = (int64_t)v->arena.used();
     if (rc == PLAN_OK && v->user_stream) {
         // the arena may still be in use by the caller's stream's earlier work
         if (cudaStreamSynchronize(v->user_stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "caller stream");
@@ -758,7 +874,7 @@ int plan_server_add_scene(plan_server_t* v, const plan_grid* grid, const plan_fo
     v->scenes[v->n_scenes] = p;
     *scene_id = (int32_t)v->n_scenes++;
     v->stats.scenes = v->n_scenes;
-    v->stats.scene_bytes = (int64_t)v->arena.used();
+    v->stats.scene_bytes = (int64_t)v->arena.used() - v->stats.reserved_bytes;
     return PLAN_OK;
 }
 
@@ -776,7 +892,8 @@ int plan_server_submit(plan_server_t* v, int32_t scene_id, plan_pose start, plan
     if (rc != PLAN_OK) return rc;
     if (!pose_ok(sc, goal)) return PLAN_EINVAL;
     // scenes stay for the server's lifetime: the rest is all a request can get
-    if (request_bytes(sc) > v->arena.size() - (size_t)v->stats.scene_bytes) return PLAN_ENOMEM;
+    const size_t held = (size_t)(v->stats.scene_bytes + v->stats.reserved_bytes);
+    if (request_bytes(sc, n_cycles, v->conv()) > v->arena.size() - held) return PLAN_ENOMEM;
     auto r = std::make_shared<Request>();
     r->ticket = v->next_ticket++;
     r->scene = scene_id;
@@ -815,6 +932,16 @@ int plan_server_wait(plan_server_t* v, uint64_t ticket, double timeout_s, plan_r
     const int n = std::min(cap, (int)r->segs.size());
     for (int k = 0; k < n; k++) out[k] = r->segs[k];
     return (int)r->segs.size() > cap && r->status == PLAN_OK ? PLAN_ERANGE : PLAN_OK;
+}
+
+int plan_server_cancel(plan_server_t* v, uint64_t ticket) {
+    if (!v) return PLAN_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    auto it = v->tickets.find(ticket);
+    if (it == v->tickets.end()) return PLAN_EINVAL;
+    if (!it->second->done) it->second->cancel.store(true);
+    v->cv_in.notify_one();
+    return PLAN_OK;
 }
 
 int plan_server_stats_read(plan_server_t* v, plan_server_stats* out) {

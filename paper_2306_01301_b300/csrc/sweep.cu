@@ -289,7 +289,7 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq
 // One 32-chain tile of one query: load, scan (one or two maneuvers), store.
 // `scans` counts the block's scans so far (it picks the set of section maps).
 template <int K, int SL, int CL>
-__device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int64_t tile, int rank,
+__device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int pass, int64_t tile, int rank,
                                           TurnSmem<K, SL, CL>& sm, int& scans, uint32_t ct_a, uint32_t ct_b) {
     constexpr int NTL = K * SL;  // headings held by this block
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
@@ -362,6 +362,7 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         count_improved(vol.improved, __popc(chg));
         if (__syncthreads_or(chg != 0) && threadIdx.x == 0) atomicAdd(vol.improved + 2, 1ull);
     }
+    if (Q.conv && __any_sync(0xFFFFFFFFu, chg != 0) && lane == 0) Q.conv[pass] = 1u;
     if (valid && chg) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
@@ -397,9 +398,11 @@ k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, i
             tile = it - (int64_t)q * tiles_per_q;
         }
         const QueryDesc& Q = qd[q];
-        const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
-        if (!ps.active || !ps.turn) continue;  // uniform over the block and the cluster
-        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm, scans, ct_a, ct_b);
+        const int p = pass_all >= 0 ? pass_all : Q.pass;
+        const PassInfo ps = decode_pass(p, Q.n_cycles);
+        // uniform over the block and the cluster
+        if (!ps.active || !ps.turn || pass_converged(Q.conv, p)) continue;
+        turn_tile<K, SL, CL>(Q, ps, p, tile, rank, sm, scans, ct_a, ct_b);
         // the partner blocks read this block's shared memory, and the next
         // item rewrites it: a cluster leaves the tile together.  Without a
         // cluster the next tile needs no barrier (own row entries, per-thread
@@ -557,7 +560,7 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
 
 template <bool STEEP, bool FWD>
 __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, int T, int lblock,
-                                              StraightStage* stage, const PlaneInfo& pi) {
+                                              StraightStage* stage, const PlaneInfo& pi, uint32_t* conv_p) {
     const int lines = blockDim.x;  // min(Nx, 128 or 256)
     const int X0 = lblock * lines;
     const int t = threadIdx.x;
@@ -615,6 +618,7 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
         }
         // write back the marked cells (only when the block has any)
         if (__syncthreads_or(marked)) {
+            if (conv_p && t == 0) *conv_p = 1u;
             if (!STEEP) {
                 // the rows flagged in the mask, two per warp (16 lanes each)
                 const int lane = t & 31, s = lane & 15, upper = lane >> 4;
@@ -694,8 +698,10 @@ k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_of
             rem = it - (int64_t)q * items_per_q;
         }
         const QueryDesc& Q = qd[q];
-        const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
-        if (!ps.active || ps.turn) continue;  // uniform over the block
+        const int p = pass_all >= 0 ? pass_all : Q.pass;
+        const PassInfo ps = decode_pass(p, Q.n_cycles);
+        if (!ps.active || ps.turn || pass_converged(Q.conv, p)) continue;  // uniform over the block
+        uint32_t* conv_p = Q.conv ? Q.conv + p : nullptr;
         const DevGrid g = Q.g;
         const Volumes vol = Q.v;
         const int mu = ps.mu;
@@ -704,11 +710,11 @@ k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_of
         const PlaneInfo pi = g.plane[T];
         const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
         if (pi.iflag) {
-            if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi);
-            else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi);
+            if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi, conv_p);
+            else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi, conv_p);
         } else {
-            if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi);
-            else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi);
+            if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi, conv_p);
+            else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi, conv_p);
         }
         if (it + gridDim.x < items) __syncthreads();  // the stages are refilled by the next item
     }
@@ -717,8 +723,9 @@ k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_of
 // Grids narrower than one 16-step chunk: the plain per-thread loop.
 __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all) {
     const QueryDesc& Q = qd[blockIdx.x];
-    const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
-    if (!ps.active || ps.turn) return;
+    const int p = pass_all >= 0 ? pass_all : Q.pass;
+    const PassInfo ps = decode_pass(p, Q.n_cycles);
+    if (!ps.active || ps.turn || pass_converged(Q.conv, p)) return;
     const DevGrid g = Q.g;
     const Volumes vol = Q.v;
     const int mu = ps.mu;
@@ -751,6 +758,7 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
         v += e;
     }
     if (vol.improved) count_improved(vol.improved + 1, nimp);
+    if (Q.conv && nimp) Q.conv[p] = 1u;
 }
 
 __global__ void k_init(const QueryDesc* __restrict__ qd) {
@@ -758,6 +766,8 @@ __global__ void k_init(const QueryDesc* __restrict__ qd) {
     const Volumes vol = Q.v;
     const int64_t n = (int64_t)Q.g.nx * Q.g.nx * Q.g.nt, start = Q.start;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (Q.conv && blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= 4 * Q.n_cycles; i += blockDim.x) Q.conv[i] = 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         vol.V[i] = i == start ? 0u : 0xFFFFFFFFu;
         vol.L[i] = NONE;

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_strerror_names_every_code(lib):
-    for code in range(0, -9, -1):
+    for code in range(0, -10, -1):
         s = lib.plan_strerror(code).decode()
         assert s and s != "unknown error"
 
@@ -104,11 +104,13 @@ def test_server_entry_points_reject_bad_arguments_on_host(lib):
     cfg = binding.ServerConfig(1 << 30, 0, 7, 0, 0, 0, 0)  # unknown mode
     assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
     for bad in ((1 << 30, -1, 0, 0, 0, 0, 0), (1 << 30, 0, 0, -5, 0, 1, 0), (1 << 30, 0, 0, 100, 0, -1, 0),
-                (1 << 30, 0, 0, 0, -3, 1, 0)):
+                (1 << 30, 0, 0, 0, -3, 1, 0), (1 << 30, 0, 0, 0, 0, 0, 6),  # unknown flag bits
+                (1 << 30, 0, 0, 0, 0, 0, 0, 100)):  # descriptor slots below 4 KiB
         cfg = binding.ServerConfig(*bad)
         assert lib.plan_server_create(C.byref(cfg), None, None, C.byref(h)) == -1
     t = C.c_uint64(0)
     assert lib.plan_server_submit(None, 0, binding.Pose(0, 0, 0), binding.Pose(0, 0, 0), 1, C.byref(t)) == -1
     info = binding.RequestInfo()
     assert lib.plan_server_wait(None, 1, 0.0, C.byref(info), None, 0, None) == -1
+    assert lib.plan_server_cancel(None, 1) == -1
     assert lib.plan_server_destroy(None) == -1

@@ -129,6 +129,126 @@ def test_one_at_a_time_and_budget_squeeze_give_the_same_plans(world, oracle_keys
     assert [_key(r) for _, r in got] == want
 
 
+def _request_bytes(sc, n_cycles=1, conv=False):
+    """Arena bytes of one request: V (4 B per pose, 256-aligned), L (2 B),
+    and with convergence records one word per pass, the block 256-aligned."""
+    up = lambda x: (x + 255) // 256 * 256
+    nr = sc.cells
+    b = up(nr * 4) + nr * 2
+    if conv:
+        b = up(b) + 4 * (4 * n_cycles + 1)
+    return up(b)
+
+
+def test_budget_of_exactly_the_scenes_and_two_requests(world, oracle_keys):
+    """The launch descriptors are reserved when the server is created, so a
+    budget of exactly reserved + scene + k requests runs every request (no
+    step fails for want of descriptor space)."""
+    ws, reqs = world
+    big = max(range(len(ws)), key=lambda k: ws[k]["sc"].cells)
+    probe = _server([ws[big]], budget_bytes=1 << 30)
+    st0 = probe.stats()
+    probe.close()
+    assert st0["reserved_bytes"] > 0
+    budget = st0["reserved_bytes"] + st0["scene_bytes"] + 2 * _request_bytes(ws[big]["sc"])
+    srv = _server([ws[big]], budget_bytes=budget)
+    mine = [(0, s, g, N) for (k, s, g, N) in reqs if k == big] * 2
+    assert len(mine) >= 4
+    got = _run(srv, mine)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(mine) and st["rejected"] == 0
+    assert st["peak_bytes"] <= budget and 1 <= st["peak_inflight"] <= 2
+    want = [oracle_keys[reqs.index((big, s, g, N))] for (_, s, g, N) in mine]
+    assert [_key(r) for _, r in got] == want
+
+
+def test_full_arena_gives_partial_steps_not_failure():
+    """Many tiny requests in flight at once need more descriptor space than
+    the reserved slots (4 KiB here, about eight requests per step) hold, and
+    the arena (exactly the scene and 40 requests, with more waiting) has none
+    to spare: steps advance the requests that fit, the others wait, and every
+    plan is still the oracle's."""
+    lx, lt, R, fp = 4, 4, 3.0, (1, 0, 0)
+    sc, img = scenes.tiny(4242, lx, lt, fill=0.05, turn_radius=R, footprint=fp, transition=400)
+    o = O.Oracle(lx, lt, R, transition=sc.transition)
+    B = o.render(img, fp)
+    free = np.flatnonzero(B != O.HARD)
+    rng = np.random.default_rng(5)
+    w = dict(sc=sc, img=img)
+    n_req = 120
+    reqs = []
+    for _ in range(n_req):
+        s_, g_ = rng.choice(free, size=2, replace=False)
+        reqs.append((0, o.pose(int(s_)), o.pose(int(g_)), 6))
+    probe = _server([w], budget_bytes=1 << 30)
+    st0 = probe.stats()
+    probe.close()
+    held = 40  # requests the arena holds at once; the others wait for memory
+    budget = st0["reserved_bytes"] + st0["scene_bytes"] + held * _request_bytes(sc)
+    probe = _server([w], budget_bytes=1 << 30, slot_bytes=4096)
+    small = probe.stats()["reserved_bytes"]
+    probe.close()
+    budget += small - st0["reserved_bytes"]
+    assert budget >= 1 << 20
+    srv = _server([w], budget_bytes=budget, slot_bytes=4096)
+    got = _run(srv, reqs)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == n_req and st["rejected"] == 0
+    assert 8 < st["peak_inflight"] <= held and st["partial_steps"] > 0
+    keys = {}
+    for (k, s_, g_, N), (info, res) in zip(reqs, got):
+        if (s_, g_) not in keys:
+            keys[(s_, g_)] = _oracle_key(dict(o=o, B=B), s_, g_, N)
+        assert _key(res) == keys[(s_, g_)]
+
+
+def test_cancel_pending_and_running_requests(world, oracle_keys):
+    """Cancelled requests end with PLAN_ECANCELED (or keep their plan when
+    the cancel came after their label walk was queued); every other request
+    gets exactly its oracle plan."""
+    from paper_2306_01301_b300 import binding
+    ws, reqs = world
+    for one_at_a_time in (False, True):
+        srv = _server(ws, budget_bytes=2 << 30, max_inflight=4, one_at_a_time=one_at_a_time)
+        tickets = [srv.submit(*r) for r in reqs]
+        cancel = set(range(0, len(reqs), 3))
+        for i in sorted(cancel):
+            srv.cancel(tickets[i])
+        n_cancelled = 0
+        for i, t in enumerate(tickets):
+            try:
+                info, res = srv.wait(t, timeout=120.0)
+            except binding.PlanError as e:
+                assert i in cancel and e.code == binding.PLAN_ECANCELED, (i, e.code)
+                n_cancelled += 1
+                continue
+            assert _key(res) == oracle_keys[i], i
+        st = srv.stats()
+        with pytest.raises(binding.PlanError):
+            srv.cancel(tickets[0])  # ticket released by its wait
+        srv.close()
+        assert st["cancelled"] == n_cancelled >= 1
+        assert st["completed"] + st["cancelled"] == len(reqs)
+
+
+@pytest.mark.parametrize("one_at_a_time", [False, True])
+def test_stop_at_convergence_gives_the_same_plans(world, oracle_keys, one_at_a_time):
+    """With PLAN_SERVE_STOP_AT_CONVERGENCE the passes after four that lowered
+    nothing return at once; the plans are the oracle's, also for requests
+    with many more cycles than they need."""
+    ws, reqs = world
+    srv = _server(ws, budget_bytes=2 << 30, stop_at_convergence=True, one_at_a_time=one_at_a_time)
+    got = _run(srv, reqs)
+    long_reqs = [(k, s, g, 12) for (k, s, g, N) in reqs[:6]]
+    got_long = _run(srv, long_reqs)
+    srv.close()
+    assert [_key(r) for _, r in got] == oracle_keys
+    for (k, s, g, N), (info, res) in zip(long_reqs, got_long):
+        assert _key(res) == _oracle_key(ws[k], s, g, N)
+
+
 def test_heavy_track_gives_the_same_plans(world, oracle_keys):
     """Big requests (the largest scene) and heavy ones (the next two) each
     one at a time on streams of their own, light ones batched beside them."""
