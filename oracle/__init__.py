@@ -46,7 +46,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(_SRC),
                                                                        os.path.getmtime(_HDR)):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fopenmp", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _SO)
     if force or not os.path.exists(_CS_SO) or os.path.getmtime(_CS_SO) < os.path.getmtime(_CS_SRC):
         tmp = _CS_SO + f".tmp{os.getpid()}"
@@ -83,6 +84,8 @@ def lib():
         L.orc_edge.argtypes = [p, p, C.c_int, C.c_int64]
         L.orc_sweep.restype = C.c_int
         L.orc_sweep.argtypes = [p, p, C.c_int64, C.c_int, C.c_int, p, p, p]
+        L.orc_set_threads.restype = None
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_layers.restype = C.c_int
         L.orc_layers.argtypes = [p, p, C.c_int, C.c_int, C.c_int, p, p, p]
         L.orc_dijkstra.restype = C.c_int
@@ -232,6 +235,13 @@ class Oracle:
         return int(lib().orc_edge(self._c, _ptr(B), mu, int(cell)))
 
     # ----------------------------------------------------------- Section VIII
+    @staticmethod
+    def set_threads(n: int):
+        """Host threads of the lockstep mode (mode 1); 1 by default.  The
+        chains of a layer are independent, so the results do not depend on
+        the count (tests/test_oracle_pins.py checks 1 against 8)."""
+        lib().orc_set_threads(int(n))
+
     def sweep(self, B: np.ndarray, start: int, n_cycles: int, mode: int = 0):
         B = np.ascontiguousarray(B, dtype=np.uint16)
         V = np.zeros(self.nr, np.uint32)

@@ -511,8 +511,47 @@ static int layer_edgelist(const star_graph* g, int mu, layer_io* io, int use_def
 /* mode 1: edges evaluated on the fly; all cycles of the maneuver advance in
  * lockstep (as the paper's threads do), each started at one cell of its own:
  * turn chains at their heading-0 cell, straight lines at their wall cell.
- * Each chain is checked to close after n steps. */
-static int layer_lockstep(const orc_ctx* c, const uint16_t* B, int mu, layer_io* io) {
+ * Each chain is checked to close after n steps.
+ *
+ * The chains of one layer touch disjoint cells (each cell lies on exactly
+ * one chain of a maneuver, eqs. 18 and 23) and read only the layer's input
+ * V, so they may run on several host threads (orc_set_threads; one by
+ * default): the turn chains of each lockstep step, or whole heading planes
+ * of straight lines.  Every chain does the same steps as on one thread. */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+
+/* One lockstep step q of the chains k in [0, nchains): returns the number
+ * of cells improved. */
+static int64_t lockstep_step(const orc_ctx* c, const uint16_t* B, int mu, layer_io* io, int n, int q,
+                             int64_t nchains, int64_t* cur, uint32_t* v, int32_t* qe, int threads) {
+    int64_t improved = 0;
+#pragma omp parallel for reduction(+ : improved) num_threads(threads) if (threads > 1) schedule(static)
+    for (int64_t k = 0; k < nchains; k++) {
+        int64_t x = cur[k];
+        int hard = B[x] == ORC_HARD;
+        uint32_t u = io->Vin[x];
+        if (q >= n) {
+            uint32_t cand = hard ? ORC_INF : sadd(v[k], c->cout[mu]);
+            if (cand < u) {
+                io->Vout[x] = cand;
+                io->L[x] = (uint16_t)((io->mu << 13) | (q - qe[k]));
+                improved++;
+            }
+        }
+        uint32_t t = hard ? ORC_INF : sadd(u, c->cin[mu]);
+        if (t < v[k]) { v[k] = t; qe[k] = q; }
+        v[k] = sadd(v[k], orc_edge(c, B, mu, x));
+        cur[k] = orc_succ(c, mu, x);
+    }
+    return improved;
+}
+
+/* All chains of one heading plane (straights) or of the whole volume
+ * (turns), started at plane `plane`'s wall cells or at heading 0. */
+static int lockstep_plane(const orc_ctx* c, const uint16_t* B, int mu, layer_io* io, int plane, int threads,
+                          int64_t* improved) {
     int nx = c->nx;
     int64_t nchains;
     int n;
@@ -524,39 +563,39 @@ static int layer_lockstep(const orc_ctx* c, const uint16_t* B, int mu, layer_io*
     int32_t* qe = (int32_t*)malloc(sizeof(int32_t) * nchains);
     if (!start || !cur || !v || !qe) { free(start); free(cur); free(v); free(qe); return -1; }
     int rc = 0;
-    int nplanes = is_turn(mu) ? 1 : c->nt;
-    for (int plane = 0; plane < nplanes && rc == 0; plane++) {
-        for (int64_t k = 0; k < nchains; k++) {
-            if (is_turn(mu)) start[k] = k; /* cells of heading plane 0 */
-            else start[k] = c->iflag[plane] == 0 ? cell_of(c, 0, (int)k, plane) : cell_of(c, (int)k, 0, plane);
-            cur[k] = start[k];
-            v[k] = ORC_INF;
-            qe[k] = 0;
-        }
-        for (int q = 0; q < 2 * n; q++) {
-            for (int64_t k = 0; k < nchains; k++) {
-                int64_t x = cur[k];
-                int hard = B[x] == ORC_HARD;
-                uint32_t u = io->Vin[x];
-                if (q >= n) {
-                    uint32_t cand = hard ? ORC_INF : sadd(v[k], c->cout[mu]);
-                    if (cand < u) {
-                        io->Vout[x] = cand;
-                        io->L[x] = (uint16_t)((io->mu << 13) | (q - qe[k]));
-                        io->improved++;
-                    }
-                }
-                uint32_t t = hard ? ORC_INF : sadd(u, c->cin[mu]);
-                if (t < v[k]) { v[k] = t; qe[k] = q; }
-                v[k] = sadd(v[k], orc_edge(c, B, mu, x));
-                cur[k] = orc_succ(c, mu, x);
-            }
-            if (q == n - 1)
-                for (int64_t k = 0; k < nchains; k++)
-                    if (cur[k] != start[k]) rc = -1;
-        }
+    for (int64_t k = 0; k < nchains; k++) {
+        if (is_turn(mu)) start[k] = k; /* cells of heading plane 0 */
+        else start[k] = c->iflag[plane] == 0 ? cell_of(c, 0, (int)k, plane) : cell_of(c, (int)k, 0, plane);
+        cur[k] = start[k];
+        v[k] = ORC_INF;
+        qe[k] = 0;
+    }
+    for (int q = 0; q < 2 * n; q++) {
+        *improved += lockstep_step(c, B, mu, io, n, q, nchains, cur, v, qe, threads);
+        if (q == n - 1)
+            for (int64_t k = 0; k < nchains; k++)
+                if (cur[k] != start[k]) rc = -1;
     }
     free(start); free(cur); free(v); free(qe);
+    return rc;
+}
+
+static int layer_lockstep(const orc_ctx* c, const uint16_t* B, int mu, layer_io* io) {
+    int64_t improved = 0;
+    int rc = 0;
+    if (is_turn(mu)) {
+        rc = lockstep_plane(c, B, mu, io, 0, g_threads, &improved);
+    } else {
+        const int threads = g_threads;
+#pragma omp parallel for reduction(+ : improved) reduction(| : rc) num_threads(threads) if (threads > 1) \
+    schedule(dynamic, 1)
+        for (int plane = 0; plane < c->nt; plane++) {
+            int64_t imp = 0;
+            rc |= lockstep_plane(c, B, mu, io, plane, 1, &imp);
+            improved += imp;
+        }
+    }
+    io->improved += improved;
     return rc;
 }
 

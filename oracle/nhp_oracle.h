@@ -71,6 +71,10 @@ uint32_t orc_edge(const orc_ctx* c, const uint16_t* B, int mu, int64_t cell);
 int orc_sweep(const orc_ctx* c, const uint16_t* B, int64_t start, int n_cycles,
               int mode, uint32_t* V, uint16_t* L, int64_t* improved);
 
+/* Host threads for mode 1 (default 1): independent chains of a layer run
+ * on several threads; the results do not depend on the count. */
+void orc_set_threads(int n);
+
 /* Continue an existing (V, L) by more layers starting at layer index
  * first_layer (so first_layer % 6 selects the maneuver). */
 int orc_layers(const orc_ctx* c, const uint16_t* B, int first_layer, int n_layers,

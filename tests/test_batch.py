@@ -216,10 +216,26 @@ def test_batch_rejects_bad_queries(mixed):
     b.close()
 
 
-def test_full_batched_workload_matches_single_plans():
+def _oracle_sample(qs):
+    """Two queries of every grid shape of the batch (each lane and each grid
+    size of the mixed lane), the ones with the most cycles first, so the
+    sample holds a 512^2 x 256 query with N = 16."""
+    by_shape = {}
+    for i, sc in enumerate(qs):
+        by_shape.setdefault((sc.nx_log2, sc.nt_log2), []).append(i)
+    out = []
+    for key in sorted(by_shape):
+        out += sorted(by_shape[key], key=lambda i: -qs[i].n_cycles)[:2]
+    return out
+
+
+def test_full_batched_workload_matches_single_plans_and_oracle():
     """64 uneven queries in one batch (graph replay, tuned shapes) give each
-    query exactly its single-plan result; two 128^2 x 128 queries are also
-    compared with the oracle cell by cell."""
+    query exactly its single-plan result; two queries of every grid shape
+    (eight in all, every lane, the largest N first: a 512^2 x 256 query with
+    N = 16 among them) are compared with the oracle cell by cell and plan by
+    plan."""
+    import os
     from paper_2306_01301_b300 import binding
     qs = scenes.batched_queries()
     planners = [binding.Planner.from_scene(sc) for sc in qs]
@@ -229,11 +245,9 @@ def test_full_batched_workload_matches_single_plans():
     b.sync()
     got = b.results()
     assert len(b.lanes()) >= 3
-    sample = [i for i, sc in enumerate(qs) if sc.nx_log2 == 7][:2]
+    sample = _oracle_sample(qs)
+    assert len(sample) >= 6 and any(qs[i].nx_log2 == 9 and qs[i].n_cycles == 16 for i in sample)
     batch_vol = {i: planners[i].volumes() for i in sample}
-    for i in sample + [k for k in range(len(qs)) if k % 9 == 0 and k not in sample][:3]:
-        if i not in batch_vol:
-            batch_vol[i] = planners[i].volumes()
     # each query alone on the plain path
     for i, (sc, p) in enumerate(zip(qs, planners)):
         alone = p.plan(sc.start, sc.goal, sc.n_cycles)
@@ -244,13 +258,24 @@ def test_full_batched_workload_matches_single_plans():
             V, L, B = p.volumes()
             assert np.array_equal(V, batch_vol[i][0]) and np.array_equal(L, batch_vol[i][1])
             assert np.array_equal(B, batch_vol[i][2])
-    for i in sample:
-        sc = qs[i]
-        o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
-        Bo = o.render_rows(sc.hard_image(), sc.footprint)
-        assert np.array_equal(Bo, batch_vol[i][2])
-        Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
-        assert np.array_equal(Vo, batch_vol[i][0]) and np.array_equal(Lo, batch_vol[i][1])
+    try:
+        O.Oracle.set_threads(os.cpu_count() or 1)
+        for i in sample:
+            sc = qs[i]
+            o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+            Bo = o.render_rows(sc.hard_image(), sc.footprint)
+            assert np.array_equal(Bo, batch_vol[i][2])
+            Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
+            assert np.array_equal(Vo, batch_vol[i][0]) and np.array_equal(Lo, batch_vol[i][1]), f"query {i}"
+            ref = o.extract(Vo, Lo, o.cell(sc.goal))
+            assert (ref is None) == (got[i] is None), f"query {i}"
+            if ref is not None:
+                assert got[i].cost == Vo[o.cell(sc.goal)]
+                assert _segs(got[i]) == [(s["mu"], o.pose(s["entry"]), o.pose(s["exit"]), s["steps"], s["cost"])
+                                         for s in ref], f"query {i}"
+            del batch_vol[i]
+    finally:
+        O.Oracle.set_threads(1)
     b.close()
     for p in planners:
         p.close()

@@ -168,13 +168,18 @@ def test_parallel_parking_512cubed_full_size():
 def test_parallel_parking_512cubed_all_cycles_bit_exact():
     """The benchmark's workload end to end, every cycle: 512^3, N = 8, the
     kernel shapes the autotuner picks for it (as bench.py times them), the
-    whole V and L against the oracle's full 8-cycle sweep (about four
-    minutes of oracle time), and the plan to the goal."""
+    whole V and L against the oracle's full 8-cycle sweep (its chains spread
+    over the host's cores), and the plan to the goal."""
+    import os
     sc = scenes.parallel_parking()
     img = sc.hard_image()
     o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
     Bo = o.render_rows(img, sc.footprint)
-    Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
+    try:
+        O.Oracle.set_threads(os.cpu_count() or 1)
+        Vo, Lo, _ = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
+    finally:
+        O.Oracle.set_threads(1)
     p = planner(sc, img)
     p.render()
     p.autotune(sc.start)
@@ -193,12 +198,42 @@ def test_parallel_parking_512cubed_all_cycles_bit_exact():
     p.close()
 
 
-def test_maze_512cubed_full_size_soft_costs():
+def test_maze_512cubed_all_32_cycles_bit_exact():
+    """The maze workload end to end: 512^3, soft obstacle costs (Section
+    VII), N = 32 cycles (129 passes, Insert 1 over 192 layers), the kernel
+    shapes the autotuner picks for it, the whole V and L against the
+    oracle's 32-cycle sweep (its chains spread over the host's cores), and
+    the plan to the goal segment by segment."""
+    import os
     from paper_2306_01301_b300 import binding
     sc = scenes.maze()
     img = binding.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max)
     assert np.array_equal(img, O.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max))
-    _full_size(sc, img)
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    Bo = o.render_rows(img, sc.footprint)
+    try:
+        O.Oracle.set_threads(os.cpu_count() or 1)
+        Vo, Lo, imp = o.sweep(Bo, o.cell(sc.start), sc.n_cycles, mode=1)
+    finally:
+        O.Oracle.set_threads(1)
+    assert sc.n_cycles == 32 and imp[-12:].sum() >= 0
+    p = planner(sc, img)
+    p.render()
+    p.autotune(sc.start)
+    p.sweep(sc.start, sc.n_cycles)
+    V, L, B = p.volumes()
+    assert np.array_equal(B, Bo), "obstacle volume"
+    assert np.array_equal(V, Vo), f"values differ at {np.flatnonzero(V != Vo)[:5]}"
+    assert np.array_equal(L, Lo), f"labels differ at {np.flatnonzero(L != Lo)[:5]}"
+    del V, L, B
+    res = p.extract(sc.goal)
+    ref = o.extract(Vo, Lo, o.cell(sc.goal))
+    assert (res is None) == (ref is None)
+    if res is not None:
+        assert res.cost == Vo[o.cell(sc.goal)]
+        assert [(s["mu"], s["entry"], s["exit"], s["steps"], s["cost"]) for s in res.segments] == \
+               [(s["mu"], o.pose(s["entry"]), o.pose(s["exit"]), s["steps"], s["cost"]) for s in ref]
+    p.close()
 
 
 @pytest.mark.parametrize("case", [SMALL[4], SMALL[7], SMALL[9]], ids=["nt32", "nt128", "nt512"])

@@ -367,3 +367,21 @@ def test_extracted_plan_costs_resum_at_convergence():
     # unreachable goal
     hard = np.flatnonzero(B == O.HARD)
     assert o.extract(V2, L2, int(hard[0])) is None
+
+
+def test_lockstep_threads_give_the_same_volumes():
+    """The lockstep mode may spread the independent chains of a layer over
+    host threads; values, labels and per-layer counts do not change."""
+    sc, img = scenes.tiny(1234, 6, 6, fill=0.06, turn_radius=5.0, footprint=(2, 1, 1), soft=True, transition=400)
+    o = O.Oracle(6, 6, 5.0, transition=sc.transition)
+    B = o.render(img, sc.footprint)
+    start = next(c for c in sc.pose_candidates if B[o.cell(c)] != O.HARD)
+    try:
+        O.Oracle.set_threads(1)
+        V1, L1, i1 = o.sweep(B, o.cell(start), 2, mode=1)
+        O.Oracle.set_threads(8)
+        V8, L8, i8 = o.sweep(B, o.cell(start), 2, mode=1)
+    finally:
+        O.Oracle.set_threads(1)
+    assert (V1 != O.INF).sum() > 1000
+    assert np.array_equal(V1, V8) and np.array_equal(L1, L8) and np.array_equal(i1, i8)

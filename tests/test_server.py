@@ -302,3 +302,31 @@ def test_submit_rejects_bad_requests(world):
         small.wait(small.submit(0, s3, g3, 1), timeout=60.0)
     assert e.value.code == -2
     small.close()
+
+
+def test_served_512cubed_requests_match_oracle():
+    """Three 512^3 requests of the served stream's own trace (the stream's two
+    512^3 scenes, N = 8), served as the benchmark serves them (continuous
+    batching, stop at convergence), each equal to the oracle's plan."""
+    import os
+    from paper_2306_01301_b300 import binding
+    all_sc = scenes.served_scenes()
+    trace = scenes.served_trace(all_sc)
+    big = [k for k, sc in enumerate(all_sc) if sc.nx_log2 == 9 and sc.nt_log2 == 9]
+    picks = [r for r in trace if r[1] in big][:3]
+    assert len(big) >= 1 and len(picks) == 3
+    srv = binding.Server(budget_bytes=8 << 30, stop_at_convergence=True)
+    ids = {k: srv.add_scene(all_sc[k]) for k in big}
+    tickets = [srv.submit(ids[k], s, g, N) for (_, k, s, g, N) in picks]
+    got = [srv.wait(t, timeout=600.0)[1] for t in tickets]
+    srv.close()
+    try:
+        O.Oracle.set_threads(os.cpu_count() or 1)
+        for (_, k, s, g, N), res in zip(picks, got):
+            sc = all_sc[k]
+            img = O.soft_image(sc.occupancy, sc.soft_radius, sc.soft_max) if sc.soft_radius else sc.hard_image()
+            o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+            B = o.render_rows(img, sc.footprint)
+            assert _key(res) == _oracle_key(dict(o=o, B=B), s, g, N)
+    finally:
+        O.Oracle.set_threads(1)
