@@ -264,8 +264,7 @@ SHAPES = [(v, g, sl, sg) for v in range(3) for g in (0, 5, 37) for (sl, sg) in (
 @pytest.mark.parametrize("lx,lt", [(6, 7), (7, 8), (6, 9), (5, 9)], ids=["64x128", "128x256", "64x512", "32x512"])
 def test_every_kernel_shape_gives_the_same_bits(lx, lt):
     """Every turn variant (K, warps, cluster), one block per item or a
-    persistent grid smaller than the work (at N_theta = 512 the kernel whose
-    rows arrive by bulk copies; at Nx = 32 every chain row it copies wraps
+    persistent grid smaller than the work (at Nx = 32 every chain row wraps
     around x = Nx), and both straight widths: identical V and L, equal to
     the oracle."""
     R = 0.9 * (1 << lx) / 8
