@@ -79,7 +79,8 @@ struct QueryDesc {
     // that lowered some cell of this query.  Once four consecutive passes
     // starting at pass 1 or later -- every maneuver once -- lowered nothing,
     // V and L are a fixed point of every maneuver layer, so later passes of
-    // the query change nothing and skip their work (same values and labels).
+    // the query change nothing; launch_conv_gate then takes them out of the
+    // launches that follow (same values and labels).
     uint32_t* conv;
 };
 
@@ -134,6 +135,10 @@ constexpr uint32_t kCostPerQuery = 0xFFFFFFFFu;
 // Launchers.  `pass` < 0 means "each query's own QueryDesc::pass"; queries
 // whose pass is outside 0 .. 4N do nothing.  Each returns cudaGetLastError().
 cudaError_t launch_init(const Group& gr, cudaStream_t s);
+// Before a sweep launch over nq device descriptors with convergence records:
+// converged queries get pass -1, the others pass_all (or keep their pass
+// when pass_all < 0).
+cudaError_t launch_conv_gate(QueryDesc* qd, int nq, int pass_all, cudaStream_t s);
 // Rendering: bit-parallel hard test for Nx >= 32 (uint16 maxima for the
 // non-hard poses when `soft`), uint16 sparse-table path otherwise.  Returns
 // the number of kernels launched through *launches.

@@ -592,7 +592,12 @@ int launch_step(plan_server_s* v, Track& tr) {
             g.item_off = (const int32_t*)(sl.d_desc + P.o_items[k]);
             g.items = items[k];
         }
-        // pass -1: every request at its own pass (QueryDesc::pass)
+        // pass -1: every request at its own pass (QueryDesc::pass); with
+        // convergence records, converged requests first drop out of it
+        if (conv) {
+            NHP_CK(launch_conv_gate((QueryDesc*)(sl.d_desc + P.o_set[k]), g.nq, -1, s));
+            launches++;
+        }
         const int lines = ls.nx_key >= 256 ? 256 : (ls.nx_key >= 128 ? 128 : ls.nx_key);
         NHP_CK(ls.turn ? launch_turn(g, -1, -1, s) : launch_straight(g, -1, lines, s));
         launches++;
@@ -674,7 +679,13 @@ int run_one(plan_server_s* v) {
     launches++;
     const int np = pass_count(r->n_cycles);
     for (int p = 0; p < np; p++) {
-        NHP_CK(pass_is_turn(p) ? launch_turn(g, p, -1, s) : launch_straight(g, p, 0, s));
+        // with convergence records the descriptor carries the pass, -1 once converged
+        const int pl = conv ? -1 : p;
+        if (conv) {
+            NHP_CK(launch_conv_gate((QueryDesc*)sl.d_desc, 1, p, s));
+            launches++;
+        }
+        NHP_CK(pass_is_turn(p) ? launch_turn(g, pl, -1, s) : launch_straight(g, pl, 0, s));
         launches++;
     }
     NHP_CK(launch_extract(g, s));

@@ -289,8 +289,9 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq
 // One 32-chain tile of one query: load, scan (one or two maneuvers), store.
 // `scans` counts the block's scans so far (it picks the set of section maps).
 template <int K, int SL, int CL>
-__device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int pass, int64_t tile, int rank,
-                                          TurnSmem<K, SL, CL>& sm, int& scans, uint32_t ct_a, uint32_t ct_b) {
+__device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps, int64_t tile, int rank,
+                                          TurnSmem<K, SL, CL>& sm, int& scans, uint32_t ct_a, uint32_t ct_b,
+                                          int pass_all) {
     constexpr int NTL = K * SL;  // headings held by this block
     const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
     const DevGrid g = Q.g;
@@ -362,8 +363,9 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         count_improved(vol.improved, __popc(chg));
         if (__syncthreads_or(chg != 0) && threadIdx.x == 0) atomicAdd(vol.improved + 2, 1ull);
     }
-    if (Q.conv && __any_sync(0xFFFFFFFFu, chg != 0) && lane == 0) Q.conv[pass] = 1u;
     if (valid && chg) {
+        uint32_t* conv = Q.conv;  // convergence record: this pass lowered a cell
+        if (conv) conv[pass_all >= 0 ? pass_all : Q.pass] = 1u;
 #pragma unroll
         for (int k = 0; k < K; k++) {
             if (chg & (1u << k)) {
@@ -398,11 +400,9 @@ k_turn(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_off, i
             tile = it - (int64_t)q * tiles_per_q;
         }
         const QueryDesc& Q = qd[q];
-        const int p = pass_all >= 0 ? pass_all : Q.pass;
-        const PassInfo ps = decode_pass(p, Q.n_cycles);
-        // uniform over the block and the cluster
-        if (!ps.active || !ps.turn || pass_converged(Q.conv, p)) continue;
-        turn_tile<K, SL, CL>(Q, ps, p, tile, rank, sm, scans, ct_a, ct_b);
+        const PassInfo ps = decode_pass(pass_all >= 0 ? pass_all : Q.pass, Q.n_cycles);
+        if (!ps.active || !ps.turn) continue;  // uniform over the block and the cluster
+        turn_tile<K, SL, CL>(Q, ps, tile, rank, sm, scans, ct_a, ct_b, pass_all);
         // the partner blocks read this block's shared memory, and the next
         // item rewrites it: a cluster leaves the tile together.  Without a
         // cluster the next tile needs no barrier (own row entries, per-thread
@@ -700,7 +700,7 @@ k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_of
         const QueryDesc& Q = qd[q];
         const int p = pass_all >= 0 ? pass_all : Q.pass;
         const PassInfo ps = decode_pass(p, Q.n_cycles);
-        if (!ps.active || ps.turn || pass_converged(Q.conv, p)) continue;  // uniform over the block
+        if (!ps.active || ps.turn) continue;  // uniform over the block
         uint32_t* conv_p = Q.conv ? Q.conv + p : nullptr;
         const DevGrid g = Q.g;
         const Volumes vol = Q.v;
@@ -725,7 +725,7 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
     const QueryDesc& Q = qd[blockIdx.x];
     const int p = pass_all >= 0 ? pass_all : Q.pass;
     const PassInfo ps = decode_pass(p, Q.n_cycles);
-    if (!ps.active || ps.turn || pass_converged(Q.conv, p)) return;
+    if (!ps.active || ps.turn) return;
     const DevGrid g = Q.g;
     const Volumes vol = Q.v;
     const int mu = ps.mu;
@@ -759,6 +759,19 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
     }
     if (vol.improved) count_improved(vol.improved + 1, nimp);
     if (Q.conv && nimp) Q.conv[p] = 1u;
+}
+
+// Convergence gate of a launch group whose queries record convergence: a
+// query whose last four passes lowered nothing gets pass -1 in its device
+// descriptor, so the sweep kernel launched next skips its work items; with
+// pass_all >= 0 the others get that pass.  Queries without records keep
+// their pass.
+__global__ void k_conv_gate(QueryDesc* __restrict__ qd, int nq, int pass_all) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    QueryDesc& Q = qd[i];
+    const int p = pass_all >= 0 ? pass_all : Q.pass;
+    Q.pass = pass_converged(Q.conv, p) ? -1 : p;
 }
 
 __global__ void k_init(const QueryDesc* __restrict__ qd) {
@@ -903,6 +916,12 @@ int turn_blocks_per_sm(int lt, int variant) {
                                                                         : turn_occupancy<16, 32, 2>();
         default: return 0;
     }
+}
+
+cudaError_t launch_conv_gate(QueryDesc* qd, int nq, int pass_all, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    k_conv_gate<<<(nq + 255) / 256, 256, 0, s>>>(qd, nq, pass_all);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init(const Group& gr, cudaStream_t s) {
