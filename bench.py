@@ -313,6 +313,8 @@ def run_ours(args):
         "clocks": clk,
     }
     p.close()
+    if world == 1 and not args.no_single:
+        line["single_query_64"] = run_single_query(args, torch)
     if world == 1 and not args.no_maze:
         line["maze"] = run_maze(args, torch)
     if world == 1 and not args.no_reach:
@@ -358,6 +360,74 @@ def run_maze(args, torch):
     return {"workload": "maze_512x512x512_N32_soft", "ms_per_plan": ms, "plans_per_s": 1e3 / ms,
             "updates_per_s": updates / (ms / 1e3), "plan_cost": res.cost if res else None,
             "plan_maneuvers": len(res.segments) if res else 0, "steps": steps}
+
+
+def run_single_query(args, torch):
+    """The plain single-query sweep (64^3, point vehicle, N = 4): whole plans
+    (render, init, 17 passes, label walk) through the plain calls, timed on
+    the device with CUDA events and end to end (image copied from pinned host
+    memory every plan, the plan read back); and the same plan as a batch of
+    one replayed through a captured CUDA graph.  The volumes (7 MB) sit in
+    L2, so this size is launch-bound: plans/s, not a roofline figure."""
+    import numpy as np
+    from paper_2306_01301_b300 import binding, scenes
+    sc = scenes.single_query()
+    img = sc.hard_image()
+    stream = torch.cuda.current_stream()
+    p = binding.Planner.from_scene(sc, img, stream=stream)
+    p.render()
+    p.autotune(sc.start)
+    N = sc.n_cycles
+    steps = 200
+    for _ in range(20):
+        p.plan(sc.start, sc.goal, N)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        p.render()
+        p.sweep(sc.start, N)
+        res = p.extract(sc.goal)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pinned = torch.from_numpy(img).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        p.set_image(pinned)
+        p.render()
+        p.sweep(sc.start, N)
+        res2 = p.extract(sc.goal)
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / steps
+    launches_plain = p.kernel_launches()
+    b = binding.Batch([p], stream=stream)
+    q = [(sc.start, sc.goal, N)]
+    b.run(q, render=True)
+    b.sync()
+    for _ in range(20):
+        b.run(q, render=True)
+        b.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.run(q, render=True)
+        b.sync()
+        res3 = b.result(0)
+    graph_ms = 1e3 * (time.perf_counter() - t0) / steps
+    per_run, _ = b.kernel_launches()
+    b.close()
+    p.close()
+    same = all(r is not None and r.cost == res.cost and r.segments == res.segments for r in (res2, res3))
+    updates = 6 * N * sc.cells
+    return {"workload": "single_query_64x64x64_N4", "ms_per_plan": ms, "plans_per_s": 1e3 / ms,
+            "updates_per_s": updates / (ms / 1e3),
+            "e2e": {"ms_per_plan": e2e_ms, "plans_per_s": 1e3 / e2e_ms, "h2d_bytes_per_plan": img.nbytes},
+            "graph_replay": {"ms_per_plan": graph_ms, "plans_per_s": 1e3 / graph_ms, "gpu_launches": per_run,
+                             "timing": "host wall clock, result read back every plan"},
+            "graph_speedup_over_plain_e2e": e2e_ms / graph_ms, "same_plan_all_ways": same,
+            "plan_cost": res.cost if res else None, "steps": steps,
+            "note": "volumes of 7 MB stay in L2; launch-bound at this size"}
 
 
 def run_reach(args, torch):
@@ -480,7 +550,8 @@ def run_batched(args, torch):
     """64 uneven queries (sizes 128^2x128 .. 512^2x256, N in {4, 8, 16}) as
     one batch: render + sweeps + label walks of all queries per step, one
     graph replay, against the same queries planned one at a time through the
-    plain single-plan calls."""
+    plain single-plan calls; both timed on the host from a synchronised start
+    to the results on the host."""
     from paper_2306_01301_b300 import binding, scenes
     qs = scenes.batched_queries()
     stream = torch.cuda.current_stream()
@@ -494,15 +565,15 @@ def run_batched(args, torch):
         b.run(queries, render=True)
     b.sync()
     steps = max(3, args.batch_steps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # both arms on the same clock: host wall time from a synchronised start to
+    # the last result on the host
     torch.cuda.synchronize()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(steps):
         b.run(queries, render=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    res = b.results()
+        b.sync()
+        res = b.results()
+    ms = 1e3 * (time.perf_counter() - t0) / steps
     per_run, _ = b.kernel_launches()
     lanes = b.lanes()
     b.close()
@@ -529,8 +600,9 @@ def run_batched(args, torch):
     return {"workload": "batched_64_queries_128^2x128..512^2x256_N4-16", "queries": len(qs),
             "ms_per_batch": ms, "plans_per_s": len(qs) / (ms / 1e3), "updates_per_s": updates / (ms / 1e3),
             "gpu_launches_per_batch": per_run, "steps": steps,
+            "timing": "host wall clock for both arms, results read back on the host",
             "one_at_a_time": {"ms_per_batch": ms_single, "plans_per_s": len(qs) / (ms_single / 1e3),
-                              "updates_per_s": updates / (ms_single / 1e3), "timing": "host wall clock"},
+                              "updates_per_s": updates / (ms_single / 1e3)},
             "speedup_vs_one_at_a_time": ms_single / ms, "same_plans_as_one_at_a_time": same,
             "lanes": [{k: l[k] for k in ("n_queries", "ntheta_log2", "nx_min", "nx_max", "turn_k",
                                          "turn_sections", "turn_cluster", "turn_grid", "straight_lines",
@@ -547,16 +619,35 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if xs else None
 
 
-def run_served(args, torch, modes=("continuous", "one_at_a_time")):
+def _served_stats(lat, span, burst_s, n_burst, keys):
+    return {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "mean_ms": sum(lat) / len(lat), "max_ms": max(lat),
+            "plans_per_s": len(lat) / span, "saturated_plans_per_s": n_burst / burst_s,
+            "reachable": sum(1 for k in keys if k is not None)}
+
+
+def _wait_until(t):
+    while True:
+        dt = t - time.perf_counter()
+        if dt <= 0:
+            return
+        if dt > 0.0015:
+            time.sleep(dt - 0.001)
+
+
+def run_served(args, torch):
     """The served stream: 16 persistent scenes (c-space rendered once, kept in
     HBM), Poisson arrivals at --served-rate plans/s for --served-seconds (10 %
-    of requests at 512^3, the rest of the batched sizes; N = 8), admission by a
-    120 GB budget.  The same trace runs through the continuous-batching
-    server and through the one-at-a-time server (the single-plan launch
-    sequence per request, in arrival order).  Latency = result ready minus
-    submission, both taken on the host inside the library.  A burst of the
-    first 1000 requests submitted at once gives each mode's saturated
-    plans/s."""
+    of requests at 512^3, the rest of the batched sizes; N = 8).  The same
+    trace runs three ways:
+      continuous        the continuous-batching server (120 GB admission
+                        budget), stopping each request's sweep once it has
+                        converged (PLAN_SERVE_STOP_AT_CONVERGENCE);
+      continuous_all    the same server running every one of the N cycles;
+      one_at_a_time     plain calls in arrival order, plan_sweep +
+                        plan_extract on one plan object per scene whose
+                        c-space was rendered once.
+    Latency = result on the host minus arrival.  The first 1000 requests at
+    once give each way's saturated plans/s."""
     from paper_2306_01301_b300 import binding, scenes
     scs = scenes.served_scenes()
     trace = scenes.served_trace(scs, rate=args.served_rate, seconds=args.served_seconds)
@@ -567,10 +658,11 @@ def run_served(args, torch, modes=("continuous", "one_at_a_time")):
            "policy": {"heavy_cells": args.heavy_cells, "big_cells": args.big_cells, "max_heavy": args.max_heavy},
            "big_share": sum(1 for x in trace if scs[x[1]].nt_log2 == 9) / max(1, len(trace))}
     keys = {}
-    for mode in modes:
+    burst = trace[:1000]
+    for mode in ("continuous", "continuous_all"):
         torch.cuda.empty_cache()
-        srv = binding.Server(budget_bytes=budget, one_at_a_time=(mode == "one_at_a_time"),
-                             heavy_cells=args.heavy_cells, big_cells=args.big_cells, max_heavy=args.max_heavy)
+        srv = binding.Server(budget_bytes=budget, heavy_cells=args.heavy_cells, big_cells=args.big_cells,
+                             max_heavy=args.max_heavy, stop_at_convergence=(mode == "continuous"))
         for sc in scs:
             srv.add_scene(sc)
         for k, sc in enumerate(scs):  # warm-up: one request per scene
@@ -579,12 +671,7 @@ def run_served(args, torch, modes=("continuous", "one_at_a_time")):
         t0 = time.perf_counter()
         tickets = []
         for (ta, k, st, gl, N) in trace:
-            while True:
-                dt = t0 + ta - time.perf_counter()
-                if dt <= 0:
-                    break
-                if dt > 0.0015:
-                    time.sleep(dt - 0.001)
+            _wait_until(t0 + ta)
             tickets.append(srv.submit(k, st, gl, N))
         got = [srv.wait(t) for t in tickets]
         clk = clocks.stop()
@@ -592,24 +679,51 @@ def run_served(args, torch, modes=("continuous", "one_at_a_time")):
         span = max(i["t_done"] for i, _ in got) - min(i["t_submit"] for i, _ in got)
         stats = srv.stats()
         keys[mode] = [_res_key(r) for _, r in got]
-        # saturated: the first 1000 requests at once
-        burst = trace[:1000]
         tb = [srv.submit(k, st, gl, N) for (_, k, st, gl, N) in burst]
         gb = [srv.wait(t) for t in tb]
         bspan = max(i["t_done"] for i, _ in gb) - min(i["t_submit"] for i, _ in gb)
         srv.close()
-        out[mode] = {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "mean_ms": sum(lat) / len(lat),
-                     "max_ms": max(lat), "plans_per_s": len(got) / span,
-                     "saturated_plans_per_s": len(gb) / bspan, "gpu_launches": stats["launches"],
-                     "steps": stats["steps"], "peak_inflight": stats["peak_inflight"],
-                     "peak_arena_bytes": stats["peak_bytes"], "scene_bytes": stats["scene_bytes"],
-                     "reachable": sum(1 for k in keys[mode] if k is not None), "clocks": clk}
-    if len(modes) == 2:
-        out["same_plans_in_both_modes"] = keys["continuous"] == keys["one_at_a_time"]
-        c, o = out["continuous"], out["one_at_a_time"]
-        out["p50_ratio_one_at_a_time_over_continuous"] = o["p50_ms"] / c["p50_ms"]
-        out["p99_ratio_one_at_a_time_over_continuous"] = o["p99_ms"] / c["p99_ms"]
-        out["saturated_speedup"] = c["saturated_plans_per_s"] / o["saturated_plans_per_s"]
+        out[mode] = _served_stats(lat, span, bspan, len(gb), keys[mode])
+        out[mode].update({"gpu_launches": stats["launches"], "steps": stats["steps"],
+                          "peak_inflight": stats["peak_inflight"], "peak_arena_bytes": stats["peak_bytes"],
+                          "scene_bytes": stats["scene_bytes"], "clocks": clk})
+    # one at a time through the plain calls
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    planners = [binding.Planner.from_scene(sc, stream=stream) for sc in scs]
+    for p, sc in zip(planners, scs):
+        p.render()
+        p.plan(sc.pose_candidates[0], sc.pose_candidates[1], 8)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    t0 = time.perf_counter()
+    lat, got, launches0 = [], [], sum(p.kernel_launches() for p in planners)
+    for (ta, k, st, gl, N) in trace:
+        _wait_until(t0 + ta)
+        planners[k].sweep(st, N)
+        got.append(planners[k].extract(gl))
+        lat.append(1e3 * (time.perf_counter() - (t0 + ta)))
+    span = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = sum(p.kernel_launches() for p in planners) - launches0
+    keys["one_at_a_time"] = [_res_key(r) for r in got]
+    tb0 = time.perf_counter()
+    for (_, k, st, gl, N) in burst:
+        planners[k].sweep(st, N)
+        planners[k].extract(gl)
+    bspan = time.perf_counter() - tb0
+    for p in planners:
+        p.close()
+    out["one_at_a_time"] = _served_stats(lat, span, bspan, len(burst), keys["one_at_a_time"])
+    out["one_at_a_time"].update({"calls": "plan_sweep + plan_extract per request, c-space rendered once per scene",
+                                 "gpu_launches": launches, "clocks": clk})
+    out["same_plans_all_ways"] = keys["continuous"] == keys["continuous_all"] == keys["one_at_a_time"]
+    c, a, o = out["continuous"], out["continuous_all"], out["one_at_a_time"]
+    out["p50_ratio_one_at_a_time_over_continuous"] = o["p50_ms"] / c["p50_ms"]
+    out["p99_ratio_one_at_a_time_over_continuous"] = o["p99_ms"] / c["p99_ms"]
+    out["saturated_speedup"] = c["saturated_plans_per_s"] / o["saturated_plans_per_s"]
+    out["p99_ratio_one_at_a_time_over_continuous_all"] = o["p99_ms"] / a["p99_ms"]
+    out["saturated_speedup_continuous_all"] = a["saturated_plans_per_s"] / o["saturated_plans_per_s"]
     return out
 
 
@@ -622,6 +736,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-maze", action="store_true")
+    ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-reach", action="store_true")
     ap.add_argument("--no-extensions", action="store_true")
     ap.add_argument("--shapes", default="", help="pin turn variant,turn grid,straight lines,straight grid "
