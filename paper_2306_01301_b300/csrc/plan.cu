@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "footprint.h"
 #include "plan_state.h"
 
 using namespace nhp;
@@ -49,17 +50,10 @@ void build_tables(plan_s* p, std::vector<int>& beta, std::vector<int>& psi2) {
     p->planes.assign(nt, PlaneInfo{});
     p->bshear.assign((size_t)nt * nx, 0);
     uint32_t wmax = 0;
+    shift_tables(p->R, nt, half, beta.data(), psi2.data());
     for (int T = 0; T < nt; T++) {
         const double th = (2.0 * kPi) * (double)T / (double)nt;
         const double s = sin(th), c = cos(th);
-        const double alpha = p->R * s;
-        if (half) {
-            const long z = lround(2.0 * alpha);
-            beta[T] = (int)(z >= 0 ? z / 2 : -((-z + 1) / 2));
-            psi2[T] = (int)(z & 1);
-        } else {
-            beta[T] = (int)lround(alpha);
-        }
         const int halfN = nt / 2;
         const int r = T % halfN;
         const int m = std::min(r, halfN - r);
@@ -84,69 +78,35 @@ void build_tables(plan_s* p, std::vector<int>& beta, std::vector<int>& psi2) {
         p->beta4[T] = make_int4(beta[T], beta[(T + 3 * q) % nt], beta[(T + 2 * q) % nt], beta[(T + q) % nt]);
 }
 
-// Footprint (Section VI, Fig. 6): the closed rectangle [-rear, front] x
-// [-hw, hw] in vehicle coordinates, placed at the continuum pose of eq. 16
-// (i + Psi_0, j + Psi_1, theta).  World cell (i+dx, j+dy) is covered when its
-// centre lies in the rectangle (1e-9-cell tolerance, so exact multiples of 90
-// degrees keep their edge cells); the cell under the origin is always covered.
+// Footprint runs and cells of every heading (footprint.h).
 void build_runs(plan_s* p, const std::vector<int>& psi2) {
     const int nt = p->nt;
-    const plan_footprint& f = p->fp;
-    const int ext = std::max(f.front, f.rear);
-    const int lim = (int)ceil(sqrt((double)ext * ext + (double)f.half_width * f.half_width)) + 2;
     p->run_off.assign(nt + 1, 0);
     p->runs.clear();
     p->fp_off.assign(nt + 1, 0);
     p->fp_dx.clear();
     p->fp_dy.clear();
     p->max_runs = 0;
-    const double eps = 1e-9;
-    std::vector<char> row(2 * lim + 1);
-    for (int T = 0; T < nt; T++) {
-        const double th = (2.0 * kPi) * (double)T / (double)nt;
-        const double c = cos(th), s = sin(th);
-        const double px0 = 0.5 * psi2[T], py0 = 0.5 * psi2[(T + nt / 4) % nt];
-        const int first = (int)p->runs.size();
-        for (int dy = -lim; dy <= lim; dy++) {
-            for (int dx = -lim; dx <= lim; dx++) {
-                bool in = dx == 0 && dy == 0;
-                if (!in) {
-                    const double ax = (double)dx - px0, ay = (double)dy - py0;
-                    const double xv = c * ax + s * ay, yv = -s * ax + c * ay;
-                    in = xv >= -(double)f.rear - eps && xv <= (double)f.front + eps &&
-                         yv >= -(double)f.half_width - eps && yv <= (double)f.half_width + eps;
-                }
-                row[dx + lim] = in;
-                if (in) {
-                    p->fp_dx.push_back(dx);
-                    p->fp_dy.push_back(dy);
-                }
-            }
-            for (int a = 0; a <= 2 * lim;) {
-                if (!row[a]) { a++; continue; }
-                int b = a;
-                while (b + 1 <= 2 * lim && row[b + 1]) b++;
-                const int lo = a - lim, hi = b - lim, w = hi - lo + 1;
-                Run r;
-                r.dy = (int16_t)dy;
-                r.lo = (int16_t)lo;
-                if (w >= p->nx) {  // covers the whole (cyclic) row
-                    r.lvl = (int16_t)p->lx;
-                    r.hi2 = (int16_t)lo;
-                } else {
-                    int lvl = 0;
-                    while ((2 << lvl) <= w) lvl++;
-                    r.lvl = (int16_t)lvl;
-                    r.hi2 = (int16_t)(hi - (1 << lvl) + 1);
-                }
-                p->runs.push_back(r);
-                a = b + 1;
-            }
-        }
-        p->run_off[T + 1] = (int32_t)p->runs.size();
-        p->fp_off[T + 1] = (int32_t)p->fp_dx.size();
-        p->max_runs = std::max(p->max_runs, (int)p->runs.size() - first);
-    }
+    std::vector<char> row(reach_width(p->fp));
+    int first = 0;
+    footprint_rows(
+        p->lx, nt, p->fp, psi2.data(), row.data(),
+        [&](int dx, int dy) {
+            p->fp_dx.push_back(dx);
+            p->fp_dy.push_back(dy);
+            return true;
+        },
+        [&](const Run& r) {
+            p->runs.push_back(r);
+            return true;
+        },
+        [&](int T) {
+            p->run_off[T + 1] = (int32_t)p->runs.size();
+            p->fp_off[T + 1] = (int32_t)p->fp_dx.size();
+            p->max_runs = std::max(p->max_runs, (int)p->runs.size() - first);
+            first = (int)p->runs.size();
+            return true;
+        });
 }
 
 int check_image(const uint16_t* img, int64_t n, uint32_t* max_soft) {

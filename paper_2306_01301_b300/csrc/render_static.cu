@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "footprint.h"
 #include "internal.h"
 
 using namespace nhp;
@@ -63,68 +64,31 @@ int scratch_for_current_device(unsigned char** out) {
     return PLAN_OK;
 }
 
-// Footprint runs of every heading (same covering rule as plan_create: the
-// closed rectangle about the rear axle at the eq. 16 pose, cell centres,
-// 1e-9 tolerance, the origin cell always covered).
+// Footprint runs of every heading into the static staging arrays: the same
+// shift table and rasterisation as plan_create (footprint.h).
 int build_runs_static(int lx, int lt, const plan_footprint* f, double R, uint32_t flags, int* max_runs) {
-    const double kPi = 3.14159265358979323846;
-    const int nx = 1 << lx, nt = 1 << lt;
-    const bool half = (flags & PLAN_FLAG_HALF_SHIFT) != 0;
-    const int ext = std::max(f->front, f->rear);
-    const int lim = (int)ceil(sqrt((double)ext * ext + (double)f->half_width * f->half_width)) + 2;
-    int psi2[1 << kMaxNtLog2];
-    for (int T = 0; T < nt; T++) {
-        const long z = lround(2.0 * (R * sin((2.0 * kPi) * (double)T / (double)nt)));
-        psi2[T] = half ? (int)(z & 1) : 0;
-    }
-    char row[2 * 2900 + 8];
-    if (2 * lim + 1 > (int)sizeof(row)) return PLAN_EINVAL;
-    int n = 0;
+    const int nt = 1 << lt;
+    static int psi2[1 << kMaxNtLog2];
+    static char row[2 * 2900 + 8];
+    if (reach_width(*f) > (int)sizeof(row)) return PLAN_EINVAL;
+    shift_tables(R, nt, (flags & PLAN_FLAG_HALF_SHIFT) != 0, nullptr, psi2);
+    int n = 0, first = 0;
     *max_runs = 0;
     g_host_off[0] = 0;
-    const double eps = 1e-9;
-    for (int T = 0; T < nt; T++) {
-        const double th = (2.0 * kPi) * (double)T / (double)nt;
-        const double c = cos(th), s = sin(th);
-        const double px0 = 0.5 * psi2[T], py0 = 0.5 * psi2[(T + nt / 4) % nt];
-        const int first = n;
-        for (int dy = -lim; dy <= lim; dy++) {
-            for (int dx = -lim; dx <= lim; dx++) {
-                bool in = dx == 0 && dy == 0;
-                if (!in) {
-                    const double ax = (double)dx - px0, ay = (double)dy - py0;
-                    const double xv = c * ax + s * ay, yv = -s * ax + c * ay;
-                    in = xv >= -(double)f->rear - eps && xv <= (double)f->front + eps &&
-                         yv >= -(double)f->half_width - eps && yv <= (double)f->half_width + eps;
-                }
-                row[dx + lim] = in;
-            }
-            for (int a = 0; a <= 2 * lim;) {
-                if (!row[a]) { a++; continue; }
-                int b = a;
-                while (b + 1 <= 2 * lim && row[b + 1]) b++;
-                if (n >= kMaxRuns) return PLAN_ERANGE;
-                const int lo = a - lim, hi = b - lim, w = hi - lo + 1;
-                Run r;
-                r.dy = (int16_t)dy;
-                r.lo = (int16_t)lo;
-                if (w >= nx) {
-                    r.lvl = (int16_t)lx;
-                    r.hi2 = (int16_t)lo;
-                } else {
-                    int lvl = 0;
-                    while ((2 << lvl) <= w) lvl++;
-                    r.lvl = (int16_t)lvl;
-                    r.hi2 = (int16_t)(hi - (1 << lvl) + 1);
-                }
-                g_host_runs[n++] = r;
-                a = b + 1;
-            }
-        }
-        g_host_off[T + 1] = n;
-        *max_runs = std::max(*max_runs, n - first);
-    }
-    return PLAN_OK;
+    const bool fits = footprint_rows(
+        lx, nt, *f, psi2, row, [](int, int) { return true; },
+        [&](const Run& r) {
+            if (n >= kMaxRuns) return false;
+            g_host_runs[n++] = r;
+            return true;
+        },
+        [&](int T) {
+            g_host_off[T + 1] = n;
+            *max_runs = std::max(*max_runs, n - first);
+            first = n;
+            return true;
+        });
+    return fits ? PLAN_OK : PLAN_ERANGE;
 }
 
 }  // namespace

@@ -8,6 +8,18 @@ for the tests from the published constructions (Appendix B, Theorems 2-3):
   CC|CC, C|CC|C, C|C_{pi/2}SC, CSC_{pi/2}|C and C|C_{pi/2}SC_{pi/2}|C words and
   their time-flipped and reflected variants (Theorem 3).
 
+Formulation followed: the segment lengths (t, u, v) of the base words are
+Reeds and Shepp's closed forms (section 8 of their paper, formulas 8.1 to
+8.11), named here in their word notation with p/m for the + and - gears
+(L+S+L+ is `_LpSpLp`, L+R-L is `_LpRmL`, ...), with the helper that both
+four-arc words share (`_tau_omega`); every other word follows from a base
+word by the time-flip, reflection and backwards symmetries of their section
+7.  Base words plus symmetries is also how the common open-source
+implementations of Reeds-Shepp curves organise the computation, so the
+layout below resembles them; the formulas are the paper's.  The Dubins words
+are the six tangent constructions of Dubins (1957) in the normalised frame
+(start at the origin, goal at distance d on the x axis).
+
 Lengths are in units of the turn radius; `*_path` functions return the
 shortest word as a list of (kind, signed length) segments with kind in
 {"L", "R", "S"} and the sign giving the gear, so that tests can also drive
