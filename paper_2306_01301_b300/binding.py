@@ -248,7 +248,7 @@ class Planner:
 
     def __init__(self, nx_log2: int, nt_log2: int, image: np.ndarray, footprint: Tuple[int, int, int],
                  turn_radius: float, transition: int, step_straight: int = 100, step_scale: int = 100,
-                 half_shift: int = 1, stream=None):
+                 half_shift: int = 1, stream=None, allocator=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("nhplan needs a CUDA device; there is no CPU fallback")
@@ -257,7 +257,8 @@ class Planner:
         self.nx, self.nt = 1 << nx_log2, 1 << nt_log2
         self.cells = self.nx * self.nx * self.nt
         self.stream = stream or torch.cuda.current_stream()
-        self._alloc = _TorchAllocator(torch, self.stream)
+        # an object with a `struct` (Allocator) attribute; torch's caching allocator by default
+        self._alloc = allocator or _TorchAllocator(torch, self.stream)
         img = np.ascontiguousarray(image, dtype=np.uint16)
         assert img.shape == (self.nx, self.nx)
         grid = Grid(nx_log2, nt_log2, img.ctypes.data_as(C.c_void_p))
@@ -571,7 +572,8 @@ def _segments(segs, n) -> List[dict]:
 class Batch:
     """Many queries, one per Planner, run together (plan_batch_* in the C ABI)."""
 
-    def __init__(self, planners: List[Planner], graph: bool = True, tune: bool = True, stream=None):
+    def __init__(self, planners: List[Planner], graph: bool = True, tune: bool = True, stream=None,
+                 allocator=None):
         import torch
         L = lib()
         if not hasattr(L, "_batch_sig"):
@@ -579,7 +581,7 @@ class Batch:
             L._batch_sig = True
         self.planners = list(planners)
         self.stream = stream or torch.cuda.current_stream()
-        self._alloc = _TorchAllocator(torch, self.stream)
+        self._alloc = allocator or _TorchAllocator(torch, self.stream)
         arr = (C.c_void_p * len(self.planners))(*[p._h.value for p in self.planners])
         flags = (0 if graph else PLAN_BATCH_NO_GRAPH) | (0 if tune else PLAN_BATCH_NO_TUNE)
         h = C.c_void_p()

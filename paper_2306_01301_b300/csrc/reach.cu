@@ -436,7 +436,17 @@ int reach_alloc(plan_s* p, int n_cycles) {
         p->d_rt = (uint32_t*)p->dalloc(vol);
         p->d_ot = (uint32_t*)p->dalloc(vol);
         p->d_shallow = (int32_t*)p->dalloc(sizeof(int32_t) * (size_t)p->nt);
-        if (!p->d_hb || !p->d_hbt || !p->d_rt || !p->d_ot || !p->d_shallow) return PLAN_ENOMEM;
+        if (!p->d_hb || !p->d_hbt || !p->d_rt || !p->d_ot || !p->d_shallow) {
+            // give back what was taken: the next call starts from nothing
+            p->dfree(p->d_hb, vol);
+            p->dfree(p->d_hbt, vol);
+            p->dfree(p->d_rt, vol);
+            p->dfree(p->d_ot, vol);
+            p->dfree(p->d_shallow, sizeof(int32_t) * (size_t)p->nt);
+            p->d_hb = p->d_hbt = p->d_rt = p->d_ot = nullptr;
+            p->d_shallow = nullptr;
+            return PLAN_ENOMEM;
+        }
         std::vector<int32_t> sh;
         for (int T = 0; T < p->nt; T++)
             if (p->planes[T].iflag == 0) sh.push_back(T);
