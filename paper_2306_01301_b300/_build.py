@@ -17,6 +17,10 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libnhplan.so")
 OBJDIR = os.path.join(ROOT, "_build", "nhplan")
+# the bounds-check build: every index of the plain plan path's kernels is
+# checked on the device; the host reports a failure as PLAN_EINTERNAL
+LIB_CHECKED = os.path.join(LIBDIR, "libnhplan_checked.so")
+OBJDIR_CHECKED = os.path.join(ROOT, "_build", "nhplan_checked")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -35,14 +39,17 @@ def _headers():
             glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    lib, objdir = (LIB_CHECKED, OBJDIR_CHECKED) if checked else (LIB, OBJDIR)
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DPLAN_BOUNDS_CHECK",)
     os.makedirs(LIBDIR, exist_ok=True)
-    os.makedirs(OBJDIR, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = max(os.path.getmtime(h) for h in _headers())
-    objs, relink = [], force or not os.path.exists(LIB)
+    objs, relink = [], force or not os.path.exists(lib)
     for src in srcs:
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_time):
             cmd = [nvcc()] + ARCH + FLAGS + list(extra_flags) + ["-c", src, "-o", obj + ".tmp"]
@@ -51,18 +58,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             subprocess.check_call(cmd)
             os.replace(obj + ".tmp", obj)
             relink = True
-    if not relink and os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+    if not relink and os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
         relink = True
     if relink:
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -16,7 +16,11 @@ from typing import List, Optional, Tuple
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libnhplan.so")
+# NHPLAN_BOUNDS_CHECK=1 in the environment loads the bounds-check build
+# (every index of the plain plan path's kernels checked; a failure is
+# reported as PLAN_EINTERNAL), built by `_build.build(checked=True)`.
+LIB_PATH = os.path.join(_PKG, "_lib", "libnhplan_checked.so" if os.environ.get("NHPLAN_BOUNDS_CHECK") == "1"
+                        else "libnhplan.so")
 
 PLAN_OK = 0
 PLAN_EINVAL = -1

@@ -27,12 +27,14 @@ __global__ void k_extract(const QueryDesc* __restrict__ qd) {
     int64_t x = goal;
     int n = 0;
     const int guard = 1 << 20;
+    [[maybe_unused]] const int64_t nr = (int64_t)g.nx * g.nx * g.nt;
     while (vol.L[x] != NONE) {
         if (n >= guard) { status[0] = -3; return; }
         const uint16_t lab = vol.L[x];
         const int mu = lab >> 13, d = lab & 8191;
         if (mu > 5 || d == 0) { status[0] = -3; return; }
         const int64_t e = entry_cell(g, x, mu, d);
+        if (!NHP_IN(e, nr, Q.err, 20)) { status[0] = -3; return; }
         if (n < cap) {
             plan_segment s;
             s.maneuver = mu;

@@ -82,7 +82,26 @@ struct QueryDesc {
     // the query change nothing; launch_conv_gate then takes them out of the
     // launches that follow (same values and labels).
     uint32_t* conv;
+    // Built with PLAN_BOUNDS_CHECK: the first failed index check of the plain
+    // plan path's kernels records its site here (the host reports
+    // PLAN_EINTERNAL); null or unused otherwise.
+    int32_t* err;
 };
+
+// Index checks of the PLAN_BOUNDS_CHECK build: NHP_IN(i, n, err, site) is
+// true when 0 <= i < n; otherwise it records `site` in *err (first failure
+// wins) and is false, and the caller skips the access.  Without the build
+// flag it is the constant true and costs nothing.
+#ifdef PLAN_BOUNDS_CHECK
+__device__ __forceinline__ bool nhp_in(int64_t i, int64_t n, int32_t* err, int site) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicCAS(err, 0, site);
+    return false;
+}
+#define NHP_IN(i, n, err, site) ::nhp::nhp_in((int64_t)(i), (int64_t)(n), (err), (site))
+#else
+#define NHP_IN(i, n, err, site) true
+#endif
 
 // True when pass p of a query with convergence flags has nothing left to do.
 __device__ __forceinline__ bool pass_converged(const uint32_t* conv, int p) {

@@ -157,6 +157,10 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PLAN_OK : cuda_fail(e, "C
 
 const char* last_error_text() { return g_last_error; }
 
+void record_check_failure(int site) {
+    snprintf(g_last_error, sizeof(g_last_error), "bounds check failed at site %d", site);
+}
+
 uint64_t max_transition(const plan_s* p) {
     uint64_t m = 0;
     for (int k = 0; k < 6; k++) m = std::max<uint64_t>(m, (uint64_t)p->cin[k] + p->cout[k]);
@@ -373,9 +377,11 @@ int create_plan(const plan_grid* grid, const plan_footprint* footprint, double t
     q.table = p->d_table;
     q.seg = p->d_seg;
     q.status = p->d_status;
+    q.err = p->d_status + 3;  // the bounds-check build's error word (zero)
     q.seg_cap = kDevSegCap;
     q.max_runs = std::max(1, p->max_runs);
-    rc = upload_desc(p);
+    rc = cuda_rc(cudaMemsetAsync(p->d_status, 0, 16, p->stream));
+    if (rc == PLAN_OK) rc = upload_desc(p);
     if (rc != PLAN_OK) {
         release(p);
         delete p;
@@ -437,13 +443,22 @@ int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) 
     return rc;
 }
 
+// A failed index check of the bounds-check build (site recorded in the
+// error word): reported once as PLAN_EINTERNAL, the word cleared.
+int device_check_failed(plan_s* p, int32_t site) {
+    record_check_failure(site);
+    cudaMemsetAsync(p->d_status + 3, 0, 4, p->stream);
+    return PLAN_EINTERNAL;
+}
+
 // Status of the label walk just launched: segment count, V(goal); copies the
 // segments in driving order.  Synchronises.
 int finish_extract(plan_s* p, plan_segment* out, int cap, int* n_out, uint32_t* cost) {
-    int32_t status[3] = {0, 0, 0};
+    int32_t status[4] = {0, 0, 0, 0};
     int rc = cuda_rc(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
     if (rc != PLAN_OK) return rc;
+    if (status[3] != 0) return device_check_failed(p, status[3]);
     if (status[0] == -1) return PLAN_EUNREACHABLE;
     if (status[0] < 0) return PLAN_EINTERNAL;
     *cost = (uint32_t)(status[1] & 0xFFFF) | ((uint32_t)status[2] << 16);
@@ -798,7 +813,10 @@ int plan_copy_volumes(plan_t* p, uint32_t* V, uint16_t* L, uint16_t* B) {
     if (V) rc = cuda_rc(cudaMemcpyAsync(V, p->d_V, (size_t)p->nr * 4, cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK && L) rc = cuda_rc(cudaMemcpyAsync(L, p->d_L, (size_t)p->nr * 2, cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK && B) rc = cuda_rc(cudaMemcpyAsync(B, p->d_B, (size_t)p->nr * 2, cudaMemcpyDeviceToHost, p->stream));
+    int32_t err = 0;
+    if (rc == PLAN_OK) rc = cuda_rc(cudaMemcpyAsync(&err, p->d_status + 3, 4, cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    if (rc == PLAN_OK && err != 0) rc = device_check_failed(p, err);
     return rc;
 }
 

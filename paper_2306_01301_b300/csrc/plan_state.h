@@ -119,6 +119,8 @@ int cuda_rc(cudaError_t e);
 // Record a failed CUDA call (plan_last_error) and return PLAN_ECUDA.
 int cuda_fail(cudaError_t e, const char* where);
 const char* last_error_text();
+// Record a failed index check of the bounds-check build (plan_last_error).
+void record_check_failure(int site);
 bool pose_ok(const plan_s* p, plan_pose q);
 int64_t cell_index(const plan_s* p, plan_pose q);
 bool pose_hard(const plan_s* p, plan_pose q);

@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(256) k_render(const QueryDesc* __restrict__ qd
         for (int r = r0; r < r0 + 4; r++) {
             if (r < nr) {
                 const Run ru = runs[r];
-                const uint16_t* row = table + (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+                const int64_t ro = (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+                if (!NHP_IN(ro, (int64_t)(g.lx + 1) * nxy, Q.err, 10)) continue;
+                const uint16_t* row = table + ro;
                 const uint16_t a = __ldg(row + ((i + ru.lo) & g.mx));
                 const uint16_t b = __ldg(row + ((i + ru.hi2) & g.mx));
                 m = max(m, max(a, b));
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) k_render(const QueryDesc* __restrict__ qd
         }
         if (__all_sync(__activemask(), m == HARD)) break;
     }
-    B[(int64_t)T * nxy + cell] = m;
+    if (NHP_IN((int64_t)T * nxy + cell, nxy * g.nt, Q.err, 11)) B[(int64_t)T * nxy + cell] = m;
 }
 
 // ----------------------------------------------------------- bit-parallel
@@ -170,7 +172,9 @@ __global__ void __launch_bounds__(256) k_render_bits(const QueryDesc* __restrict
         for (int r = 0; r < nr; r++) {
             if ((r & 7) == 0 && __all_sync(0xFFFFFFFFu, hard == 0xFFFFFFFFu)) break;
             const RunW ru = rw[r];
-            const uint32_t* row = bits + ru.base + ((j + ru.dy) & g.mx) * nw;
+            const int64_t ro = ru.base + (int64_t)((j + ru.dy) & g.mx) * nw;
+            if (!NHP_IN(ro, (int64_t)(g.lx + 1) * plane_words, Q.err, 12)) continue;
+            const uint32_t* row = bits + ro;
             const uint32_t a1 = __ldg(row + ((w + ru.q1) & nm));
             const uint32_t b1 = __shfl_sync(0xFFFFFFFFu, a1, next, nw);
             const uint32_t a2 = __ldg(row + ((w + ru.q2) & nm));
@@ -185,6 +189,8 @@ __global__ void __launch_bounds__(256) k_render_bits(const QueryDesc* __restrict
                     row_window(row, 32 * (w + ru.q2) + ru.s2, nw - 1);
         }
     }
+    if (!NHP_IN((int64_t)T * g.nx * g.nx + (int64_t)j * g.nx + 32 * w + 31, (int64_t)g.nx * g.nx * g.nt, Q.err, 13))
+        return;
     uint4* out = (uint4*)(B + (int64_t)T * g.nx * g.nx + (int64_t)j * g.nx + 32 * w);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -221,7 +227,9 @@ __global__ void __launch_bounds__(256) k_render_soft(const QueryDesc* __restrict
     uint16_t m = 0;
     for (int r = 0; r < nr; r++) {
         const Run ru = runs[r];
-        const uint16_t* row = table + (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+        const int64_t ro = (int64_t)ru.lvl * nxy + ((int64_t)((j + ru.dy) & g.mx) << g.lx);
+        if (!NHP_IN(ro, (int64_t)(g.lx + 1) * nxy, Q.err, 14)) continue;
+        const uint16_t* row = table + ro;
         m = max(m, max(__ldg(row + ((i + ru.lo) & g.mx)), __ldg(row + ((i + ru.hi2) & g.mx))));
     }
     if (!hard) *dst = m;

@@ -335,7 +335,7 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         const uint32_t id = cell_index(sec * K + k);
         uint32_t vv = 0xFFFFFFFFu;
         uint16_t ob = HARD;
-        if (valid) {
+        if (valid && NHP_IN(id, nxy * g.nt, Q.err, 1)) {
             vv = __ldg(vol.V + id);
             ob = __ldg(vol.B + id);
         }
@@ -370,8 +370,10 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         for (int k = 0; k < K; k++) {
             if (chg & (1u << k)) {
                 const uint32_t id = cell_index(sec * K + k);
-                vol.V[id] = u[k];
-                vol.L[id] = sm.sh.lab[k][tid];
+                if (NHP_IN(id, nxy * g.nt, Q.err, 2)) {
+                    vol.V[id] = u[k];
+                    vol.L[id] = sm.sh.lab[k][tid];
+                }
             }
         }
     }
@@ -524,7 +526,8 @@ __device__ __forceinline__ int bidx(int s, int a, int base) {
 
 template <bool STEEP>
 __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeom& c, const int16_t* bs,
-                                               const uint32_t* Vp, const uint16_t* Bp, int lx, int mx) {
+                                               const uint32_t* Vp, const uint16_t* Bp, int lx, int mx,
+                                               int32_t* err) {
     const int t = threadIdx.x, nt = blockDim.x;
     if (t < kSteps) st.bs[t] = (int16_t)(bs[c.y0 + t] - min(bs[c.y0], bs[c.y0 + kSteps - 1]));
     if (t < kMaskWords) st.mask[t] = 0;
@@ -535,11 +538,13 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
         const int jv = t & 3, jb = t & 1;
         for (int r = t >> 2; r < c.span; r += nt >> 2) {
             const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
-            cp_async16(&st.v[shv(r, 4 * jv)], Vp + row + 4 * jv);
+            if (NHP_IN(row + 4 * jv + 3, (int64_t)1 << (2 * lx), err, 3) && NHP_IN(shv(r, 4 * jv) + 3, kVWords, err, 4))
+                cp_async16(&st.v[shv(r, 4 * jv)], Vp + row + 4 * jv);
         }
         for (int r = t >> 1; r < c.span; r += nt >> 1) {
             const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
-            cp_async16(&st.b[shb(r, 8 * jb)], Bp + row + 8 * jb);
+            if (NHP_IN(row + 8 * jb + 7, (int64_t)1 << (2 * lx), err, 3) && NHP_IN(shb(r, 8 * jb) + 7, kBHalves, err, 4))
+                cp_async16(&st.b[shb(r, 8 * jb)], Bp + row + 8 * jb);
         }
     } else {
         // step row s: the aligned chunks covering columns [base, base + span)
@@ -551,8 +556,15 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
         if (s0 < rpp) {
             for (int s = s0; s < kSteps; s += rpp) {
                 const uint32_t row = (uint32_t)(c.y0 + s) << lx;
-                if (j < nv) cp_async16(&st.v[s * kStV + 4 * j], Vp + row + ((a4 + 4 * j) & mx));
-                else cp_async16(&st.b[s * kStB + 8 * (j - nv)], Bp + row + ((a8 + 8 * (j - nv)) & mx));
+                if (j < nv) {
+                    if (NHP_IN(row + ((a4 + 4 * j) & mx) + 3, (int64_t)1 << (2 * lx), err, 3) &&
+                        NHP_IN(s * kStV + 4 * j + 3, kVWords, err, 4))
+                        cp_async16(&st.v[s * kStV + 4 * j], Vp + row + ((a4 + 4 * j) & mx));
+                } else {
+                    if (NHP_IN(row + ((a8 + 8 * (j - nv)) & mx) + 7, (int64_t)1 << (2 * lx), err, 3) &&
+                        NHP_IN(s * kStB + 8 * (j - nv) + 7, kBHalves, err, 4))
+                        cp_async16(&st.b[s * kStB + 8 * (j - nv)], Bp + row + ((a8 + 8 * (j - nv)) & mx));
+                }
             }
         }
     }
@@ -560,7 +572,8 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
 
 template <bool STEEP, bool FWD>
 __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, int T, int lblock,
-                                              StraightStage* stage, const PlaneInfo& pi, uint32_t* conv_p) {
+                                              StraightStage* stage, const PlaneInfo& pi, uint32_t* conv_p,
+                                              int32_t* err) {
     const int lines = blockDim.x;  // min(Nx, 128 or 256)
     const int X0 = lblock * lines;
     const int t = threadIdx.x;
@@ -581,11 +594,11 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
     const int nch = g.nx / kSteps;
 
     ChunkGeom geo0 = chunk_geom(bs, 0, dir, g.nx, X0, lines, g.mx), geo1 = geo0;
-    straight_issue<STEEP>(stage[0], geo0, bs, Vp, Bp, g.lx, g.mx);
+    straight_issue<STEEP>(stage[0], geo0, bs, Vp, Bp, g.lx, g.mx, err);
     cp_async_commit();
     if (nch > 1) {
         geo1 = chunk_geom(bs, 1, dir, g.nx, X0, lines, g.mx);
-        straight_issue<STEEP>(stage[1], geo1, bs, Vp, Bp, g.lx, g.mx);
+        straight_issue<STEEP>(stage[1], geo1, bs, Vp, Bp, g.lx, g.mx, err);
     }
     cp_async_commit();
     for (int ch = 0; ch < nch; ch++) {
@@ -601,6 +614,7 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
             const int s = FWD ? kk : kSteps - 1 - kk;
             const int a = t + st.bs[s];  // tile index across lines, in [0, span)
             const int vi = vidx<STEEP>(s, a, c.base), bi = bidx<STEEP>(s, a, c.base);
+            if (!NHP_IN(vi, kVWords, err, 5) || !NHP_IN(bi, kBHalves, err, 5)) continue;
             const uint16_t ob = st.b[bi];
             const uint32_t e = edge_cost(ob, w);
             const uint32_t u = ob == HARD ? 0u : min(st.v[vi], TH);
@@ -641,8 +655,10 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
                             const uint32_t x = st.v[shv(r, s)];
                             if ((x >> 30) == 2u) {
                                 const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s;
-                                Vp[id] = x & ~kMark;
-                                Lp[id] = st.b[shb(r, s)];
+                                if (NHP_IN(id, (int64_t)g.nx * g.nx, err, 6)) {
+                                    Vp[id] = x & ~kMark;
+                                    Lp[id] = st.b[shb(r, s)];
+                                }
                                 nimp++;
                             }
                         }
@@ -656,8 +672,10 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
                         const uint32_t x = st.v[vidx<true>(s, xx, c.base)];
                         if ((x >> 30) == 2u) {
                             const uint32_t id = ((uint32_t)(c.y0 + s) << g.lx) + ((c.base + xx) & g.mx);
-                            Vp[id] = x & ~kMark;
-                            Lp[id] = st.b[bidx<true>(s, xx, c.base)];
+                            if (NHP_IN(id, (int64_t)g.nx * g.nx, err, 6)) {
+                                Vp[id] = x & ~kMark;
+                                Lp[id] = st.b[bidx<true>(s, xx, c.base)];
+                            }
                             nimp++;
                         }
                     }
@@ -669,7 +687,7 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
             const ChunkGeom nxt = chunk_geom(bs, ch + 2, dir, g.nx, X0, lines, g.mx);
             if (sb) geo1 = nxt;
             else geo0 = nxt;
-            straight_issue<STEEP>(stage[sb], nxt, bs, Vp, Bp, g.lx, g.mx);
+            straight_issue<STEEP>(stage[sb], nxt, bs, Vp, Bp, g.lx, g.mx, err);
         }
         cp_async_commit();
     }
@@ -710,11 +728,11 @@ k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_of
         const PlaneInfo pi = g.plane[T];
         const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
         if (pi.iflag) {
-            if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi, conv_p);
-            else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi, conv_p);
+            if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
+            else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
         } else {
-            if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi, conv_p);
-            else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi, conv_p);
+            if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
+            else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
         }
         if (it + gridDim.x < items) __syncthreads();  // the stages are refilled by the next item
     }
@@ -745,6 +763,7 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
         const int y = (dir * q) & g.mx;
         const int col = (xq + bs[y]) & g.mx;
         const uint32_t id = pi.iflag ? (uint32_t)(col | (y << g.lx)) : (uint32_t)(y | (col << g.lx));
+        if (!NHP_IN(id, nxy, Q.err, 7)) continue;
         const uint16_t ob = Bp[id];
         const uint32_t e = edge_cost(ob, pi.wS);
         const uint32_t u = ob == HARD ? 0u : min(Vp[id], TH);
