@@ -7,11 +7,10 @@
 // the other one; leaving costs cost_out[mu] and returns to mu's gear's
 // state.  Each maneuver layer reads both states and writes its own gear's.
 //
-// A layer walks every curve of the maneuver twice around its cycle (turn
-// chains: one thread per chain over N_theta headings; straight lines: one
-// thread per line over Nx steps from the wall cell), as the paper's two
-// sequential loops do: the first loop warms the carried value up, the
-// second stores.  A cell is read once per step before its possible store,
+// A turn layer walks every chain twice around its cycle (one thread per
+// chain over N_theta headings), as the paper's two sequential loops do: the
+// first loop warms the carried value up, the second stores; a straight layer
+// walks each line once from its wall cell (one thread per line).  A cell is read once per step before its possible store,
 // so the values used for entering are those before the layer (only this
 // thread writes the cell, and only in the second loop).  Arithmetic
 // saturates at PLAN_INF.  Labels are (mu << 13) | (other << 12) | d with
@@ -20,6 +19,7 @@
 // both value volumes, B and the labels twice per layer.
 #include "curve.cuh"
 #include "internal.h"
+#include "turn_scan.cuh"
 
 namespace nhp {
 namespace {
@@ -78,6 +78,10 @@ __global__ void __launch_bounds__(256) k_gear_turn(const GearLayer a, int mu) {
     for (int q = 0; q < 2 * n; q++) walk_step(s, turn_chain_cell(g, mu, xq, yq, q), q, n, mu, g.wA, a);
 }
 
+// A straight line starts at its wall cell (y' = 0, always hard), which
+// drops whatever is carried into it, so the warm-up loop of the turn chains
+// is not needed: one storing loop from the wall gives the same values and
+// labels.
 __global__ void __launch_bounds__(256) k_gear_straight(const GearLayer a, int mu) {
     const DevGrid& g = a.g;
     const int xq = blockIdx.x * blockDim.x + threadIdx.x;  // line
@@ -86,7 +90,104 @@ __global__ void __launch_bounds__(256) k_gear_straight(const GearLayer a, int mu
     const PlaneInfo pi = g.plane[T];
     const int n = g.nx;
     Walk s;
-    for (int q = 0; q < 2 * n; q++) walk_step(s, line_cell(g, pi, mu, T, xq, q), q, n, mu, pi.wS, a);
+    for (int q = n; q < 2 * n; q++) walk_step(s, line_cell(g, pi, mu, T, xq, q - n), q, n, mu, pi.wS, a);
+}
+
+// ------------------------------------------------ turns on the sections scan
+// A turn layer as one maneuver scan of turn_scan.cuh over tiles of 32
+// chains and all N_theta headings (K = 16 per thread, SL = N_theta / 16
+// warps): the same relaxation as the two-loop walk above, each cell read
+// once.  Entering at a cell costs the cheaper of its own gear's value and
+// the other gear's value plus the penalty (own gear on a tie), with both
+// transition edges; a store must beat the own gear's value; the "entered
+// from the other gear" bit travels with the entry position to the label.
+// Values at or above TH mean unreached (the host picks this kernel only when
+// the finite costs stay below TH).
+template <int K, int NTH>
+struct GearCells {
+    uint32_t (&u)[K];        // own gear's value, TH when unreached, 0 when hard
+    const uint32_t (&w)[K];  // entering value
+    const uint32_t (*bp)[NTH];  // shared memory: B of cells 2j (low half) and 2j+1, by thread
+    int tid;
+    uint32_t oth;            // bit k: cell k is entered from the other gear's state
+    uint32_t wstep;
+    __device__ __forceinline__ uint32_t ent(int k) const { return w[k]; }
+    __device__ __forceinline__ uint32_t e(int k) const {
+        const uint32_t b = (bp[k >> 1][tid] >> ((k & 1) * 16)) & 0xFFFFu;
+        return b == HARD ? TH : (wstep * b) >> 8;
+    }
+    __device__ __forceinline__ int tag(int k) const { return (int)(((oth >> k) & 1u) << 16); }
+    __device__ __forceinline__ uint32_t label_bits(int pv, int q) const {
+        return (uint32_t)((((pv >> 16) & 1) << 12) | (q - (pv & 0xFFFF)));
+    }
+};
+
+template <int K, int SL>
+struct GearTurnSmem {
+    int2 cell[K * SL];
+    uint32_t bp[K / 2][32 * SL];  // each thread's B values, two per word (registers are full)
+    TurnShared<K, SL, 2> sh;
+};
+
+template <int K, int SL>
+__global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : 1024 / (32 * SL))
+k_gear_scan(const GearLayer a, int mu) {
+    extern __shared__ __align__(16) unsigned char gear_smem[];
+    GearTurnSmem<K, SL>& sm = *reinterpret_cast<GearTurnSmem<K, SL>*>(gear_smem);
+    const DevGrid& g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int64_t tile = blockIdx.x;
+    const int x0 = (int)((tile * 32) & g.mx), y0 = (int)((tile * 32 >> g.lx) & g.mx);
+    const bool left = mu == LF || mu == LB;
+    const bool asc = mu == LF || mu == RB;  // heading up along the sweep
+    const int G = gear_of(mu);
+    uint32_t* Vs = G ? a.Vr : a.Vf;
+    uint16_t* Ls = G ? a.Lr : a.Lf;
+    const uint32_t* Vo = G ? a.Vf : a.Vr;
+    if (lane < K) {  // this warp's headings: row offset and x of lane 0's cell
+        const int t = sec * K + lane;
+        const int4 b = __ldg(&g.beta4[t]);
+        const int bx = left ? b.x : b.z, by = left ? b.y : b.w;
+        sm.cell[t] = make_int2((int)(uint32_t)((((y0 + by) & g.mx) << g.lx) + (int64_t)t * nxy), (x0 + bx) & g.mx);
+    }
+    __syncwarp();
+    const uint32_t ct = a.cin + a.cout;
+    uint32_t u[K], w[K];
+    uint32_t oth = 0, sa = 0, bw = 0;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int2 c = sm.cell[sec * K + k];
+        const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
+        const uint16_t b = __ldg(a.B + id);
+        const uint32_t vs = min(__ldg(Vs + id), TH), vo = min(__ldg(Vo + id), TH);
+        const bool hard = b == HARD;
+        const uint32_t ts = vs + ct, to = vo + a.pen + ct;
+        const bool o = to < ts;
+        u[k] = hard ? 0u : vs;
+        w[k] = hard ? 0u : (o ? to : ts);
+        oth |= (uint32_t)(o && !hard) << k;
+        if (k & 1) sm.bp[k >> 1][tid] = bw | ((uint32_t)b << 16);
+        else bw = b;
+        sa = min(sa + (hard ? TH : (a.g.wA * (uint32_t)b) >> 8), TH);
+        live |= !hard && (vs < TH || vo < TH);
+    }
+    uint32_t chg = 0;
+    GearCells<K, 32 * SL> cl{u, w, sm.bp, tid, oth, g.wA};
+    if (asc) turn_scan<K, SL, 1, 2, true>(cl, chg, mu, sec, lane, 0, 0, 0, sa, live, sm.sh);
+    else turn_scan<K, SL, 1, 2, false>(cl, chg, mu, sec, lane, 0, 0, 0, sa, live, sm.sh);
+    if (chg) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (chg & (1u << k)) {
+                const int2 c = sm.cell[sec * K + k];
+                const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
+                Vs[id] = u[k];
+                Ls[id] = sm.sh.lab[k][tid];
+            }
+        }
+    }
 }
 
 __global__ void k_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
@@ -144,13 +245,38 @@ cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t*
     return cudaGetLastError();
 }
 
+namespace {
+template <int K, int SL>
+cudaError_t launch_gear_scan(const GearLayer& a, int mu, unsigned tiles, cudaStream_t s) {
+    // more than the default 48 KB of shared memory; the attribute is per
+    // device and setting it again is harmless
+    const int bytes = (int)sizeof(GearTurnSmem<K, SL>);
+    cudaError_t e = cudaFuncSetAttribute(k_gear_scan<K, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    k_gear_scan<K, SL><<<tiles, 32 * SL, bytes, s>>>(a, mu);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s) {
     if (mu == SF || mu == SB) {
+        if (a.scan && a.g.nx >= 16) return launch_gear_straight_tiled(a, mu, s);
         k_gear_straight<<<dim3((unsigned)((a.g.nx + 255) / 256), (unsigned)a.g.nt), 256, 0, s>>>(a, mu);
-    } else {
-        const int64_t chains = (int64_t)a.g.nx * a.g.nx;
-        k_gear_turn<<<(unsigned)((chains + 255) / 256), 256, 0, s>>>(a, mu);
+        return cudaGetLastError();
     }
+    const int64_t chains = (int64_t)a.g.nx * a.g.nx;
+    // the sections scan needs whole 32-chain rows and 16 headings per warp,
+    // and values below TH (a.scan); other grids walk their chains
+    if (a.scan && a.g.nx >= 32) {
+        const unsigned tiles = (unsigned)(chains / 32);
+        switch (a.g.nt) {
+            case 128: return launch_gear_scan<16, 8>(a, mu, tiles, s);
+            case 256: return launch_gear_scan<16, 16>(a, mu, tiles, s);
+            case 512: return launch_gear_scan<16, 32>(a, mu, tiles, s);
+            default: break;
+        }
+    }
+    k_gear_turn<<<(unsigned)((chains + 255) / 256), 256, 0, s>>>(a, mu);
     return cudaGetLastError();
 }
 

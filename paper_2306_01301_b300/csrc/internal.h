@@ -202,10 +202,14 @@ struct GearLayer {
     uint32_t *Vf, *Vr;
     uint16_t *Lf, *Lr;
     uint32_t pen, cin, cout;  // gear change; entering and leaving the layer's maneuver
+    bool scan;                // finite costs stay below TH: turn layers may run the sections scan
 };
 cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
                              int start_gear, cudaStream_t s);
 cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s);
+// A straight layer of the gear states on the staged tiles of the plain
+// straight kernel (sweep.cu); needs Nx >= 16 and a.scan.
+cudaError_t launch_gear_straight_tiled(const GearLayer& a, int mu, cudaStream_t s);
 cudaError_t launch_gear_extract(const GearLayer& a, int64_t goal, plan_segment* seg, int cap, int32_t* status,
                                 cudaStream_t s);
 

@@ -557,6 +557,9 @@ int plan_sweep_gear(plan_t* p, plan_pose start, int start_gear, int n_cycles) {
     a.Lf = p->d_L;
     a.Lr = p->d_Lr;
     a.pen = p->gear_pen;
+    // every layer adds at most one segment and one gear change
+    a.scan = range_check_layers(p, 6 * n_cycles) == PLAN_OK &&
+             (double)6 * n_cycles * (double)p->gear_pen + (double)6 * n_cycles * 65536.0 < (double)(1u << 29);
     cudaStream_t s = p->stream;
     p->vol_kind = VOL_NONE;
     int rc = cuda_rc(launch_gear_init(p->d_V, p->d_Vr, p->d_L, p->d_Lr, p->nr, cell_index(p, start), start_gear, s));

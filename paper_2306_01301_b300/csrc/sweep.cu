@@ -34,6 +34,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.h"
+#include "turn_scan.cuh"
 
 namespace nhp {
 namespace {
@@ -88,192 +89,11 @@ __device__ __forceinline__ void count_improved(unsigned long long* ctr, uint32_t
 // Scan-order positions: ascending r = T, descending r = NT-1-T; positions of
 // the storing (second) loop are r + NT.
 
-// Shared state of one turn scan: section maps, the cluster exchange slots
-// (NSLOT of them, rotated so that a block never overwrites a slot its
-// partners may still read) and the labels of improved cells.
-template <int K, int SL, int NSLOT>
-struct TurnShared {
-    static constexpr int P = 32 + 32 / SL;  // pitch: the carry scan's reads hit 32 banks
-    // two sets, used by alternate scans: a warp may start the next scan
-    // while a slower one still reads the previous scan's carries
-    uint32_t sa[2][SL][P];
-    uint32_t sb[2][SL][P];
-    int32_t sp[2][SL][P];
-    uint32_t tot[NSLOT][3][32];             // per scan: this block's composite (A, B, P)
-    uint16_t lab[K][32 * SL];               // labels of improved cells
-};
-
 template <int K, int SL, int CL>
 struct TurnSmem {
     int2 cell[K * SL];   // per heading: (offset of the chain row in the volume, x shift)
     TurnShared<K, SL, 2> sh;
 };
-
-// Compose an earlier stretch X with a later one Y (in place into Y):
-// x -> min(x + A, B @ P).  X's entry positions precede Y's, so ties go to X.
-__device__ __forceinline__ void combine(uint32_t xa, uint32_t xb, int xp, uint32_t& ya, uint32_t& yb,
-                                        int& yp) {
-    const uint32_t cand = xb + ya;  // xb <= 2TH + ct, ya <= TH: no wrap
-    if (cand <= yb) { yb = cand; yp = xp; }
-    ya = min(xa + ya, TH);
-}
-
-// One maneuver scan over the block's chains.  `live`: this thread's section
-// holds a reached, non-hard cell.  A warp whose sections hold none has no
-// entries (its maps are "nothing produced") and, when nothing is carried in
-// either, cannot improve any of its cells, so it skips those loops; the
-// results are the same cell for cell.
-template <int K, int SL, int CL, int NSLOT, bool ASC>
-__device__ __forceinline__ void turn_scan(uint32_t (&u)[K], const uint32_t (&e)[K], uint32_t& chg, int mu,
-                                          uint32_t ct, int sec, int lane, int rank, int slot, int mb, uint32_t a,
-                                          bool live, TurnShared<K, SL, NSLOT>& sm) {
-    constexpr int S = SL * CL, NT = K * S;
-    const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);  // this block's place in scan order
-    const int sl = ASC ? sec : SL - 1 - sec;                     // section index in scan order, local
-    const int ss = sr * SL + sl;                                 // ... global
-    // 1) this section's map (first-loop positions in [0, NT)); its slope
-    //    `a`, the section's summed edge costs, is the same in both directions.
-    //    "Nothing produced" must stay within the composition bound (<= 2TH + ct).
-    uint32_t b = TH;
-    int pb = 0;
-    if (__any_sync(0xFFFFFFFFu, live)) {
-        b = 0xFFFFFFFFu;  // lowered to <= TH + ct by the first cell
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = ASC ? kk : K - 1 - kk;
-            const uint32_t t = u[k] + ct;
-            if (t < b) { b = t; pb = ss * K + kk; }
-            b += e[k];
-        }
-    }
-    sm.sa[mb][sl][lane] = a;
-    sm.sb[mb][sl][lane] = b;
-    sm.sp[mb][sl][lane] = pb;
-    __syncthreads();
-    // 2) segmented warp scan over the SL local section maps of each chain
-    //    (32/SL chains per warp), then the carry into each section of the
-    //    second loop.
-    {
-        const int c = sec * (32 / SL) + lane / SL;
-        const int s = lane % SL;
-        uint32_t A = sm.sa[mb][s][c], B = sm.sb[mb][s][c];
-        int P = sm.sp[mb][s][c];
-#pragma unroll
-        for (int off = 1; off < SL; off <<= 1) {
-            const uint32_t xa = __shfl_up_sync(0xFFFFFFFFu, A, off, SL);
-            const uint32_t xb = __shfl_up_sync(0xFFFFFFFFu, B, off, SL);
-            const int xp = __shfl_up_sync(0xFFFFFFFFu, P, off, SL);
-            if (s >= off) combine(xa, xb, xp, A, B, P);
-        }
-        // this block's whole stretch (inclusive map of its last section)
-        const uint32_t tA = __shfl_sync(0xFFFFFFFFu, A, SL - 1, SL);
-        const uint32_t tB = __shfl_sync(0xFFFFFFFFu, B, SL - 1, SL);
-        const int tP = __shfl_sync(0xFFFFFFFFu, P, SL - 1, SL);
-        // map of the local sections before s
-        const uint32_t eA = __shfl_up_sync(0xFFFFFFFFu, A, 1, SL);
-        const uint32_t eB = __shfl_up_sync(0xFFFFFFFFu, B, 1, SL);
-        const int eP = __shfl_up_sync(0xFFFFFFFFu, P, 1, SL);
-        uint32_t cv;  // carry into the first local section of the second loop
-        int cp;
-        if (CL == 1) {
-            cv = tB;
-            cp = tP;
-        } else {
-            if (s == 0) {
-                sm.tot[slot][0][c] = tA;
-                sm.tot[slot][1][c] = tB;
-                sm.tot[slot][2][c] = tP;
-            }
-            cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
-            cluster.sync();
-            // composites of the blocks in scan order: j-th block holds scan
-            // positions [j*NT/CL, (j+1)*NT/CL)
-            uint32_t rA[CL], rB[CL];
-            int rP[CL];
-#pragma unroll
-            for (int j = 0; j < CL; j++) {
-                const int rk = ASC ? j : CL - 1 - j;  // cluster rank of scan-order block j
-                const TurnShared<K, SL, NSLOT>* o = cluster.map_shared_rank(&sm, rk);
-                rA[j] = o->tot[slot][0][c];
-                rB[j] = o->tot[slot][1][c];
-                rP[j] = o->tot[slot][2][c];
-            }
-            // the whole first loop applied to 'nothing carried'
-            uint32_t fA = rA[0], fB = rB[0];
-            int fP = rP[0];
-#pragma unroll
-            for (int j = 1; j < CL; j++) {
-                uint32_t a2 = rA[j], b2 = rB[j];
-                int p2 = rP[j];
-                combine(fA, fB, fP, a2, b2, p2);
-                fA = a2; fB = b2; fP = p2;
-            }
-            // then the second loop's blocks before this one
-            cv = fB;
-            cp = fP;
-#pragma unroll
-            for (int j = 0; j < CL - 1; j++) {
-                if (j < sr) {
-                    const uint32_t cand = cv + rA[j];
-                    if (!(cand <= rB[j])) { cv = rB[j]; cp = rP[j] + NT; }
-                    else cv = cand;
-                }
-            }
-        }
-        uint32_t iv = cv;
-        int ip = cp;
-        if (s > 0) {
-            const uint32_t cand = cv + eA;  // earlier entries are further upstream
-            if (cand <= eB) { iv = cand; ip = cp; }
-            else { iv = eB; ip = eP + NT; }
-        }
-        __syncwarp();
-        sm.sb[mb][s][c] = iv;
-        sm.sp[mb][s][c] = ip;
-    }
-    __syncthreads();
-    // 3) second loop: store where strictly better.
-    const uint32_t v0 = sm.sb[mb][sl][lane];
-    const int p0 = sm.sp[mb][sl][lane];
-    // Lean pass: the carried value alone, and whether any cell improves.
-    // Improvements are rare once the front has passed, so the pass that also
-    // tracks entry positions and writes labels runs only in warps that need it.
-    bool any = false;
-    if (__any_sync(0xFFFFFFFFu, live || v0 < TH)) {
-        uint32_t v = v0;
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = ASC ? kk : K - 1 - kk;
-            any |= v < u[k];
-            v = min(v, u[k] + ct) + e[k];
-        }
-    }
-    if (__any_sync(0xFFFFFFFFu, any)) {
-        uint32_t v = v0;
-        int pv = p0;
-        const uint32_t mtag = (uint32_t)mu << 13;
-        const int tid = sec * 32 + lane;
-#pragma unroll
-        for (int kk = 0; kk < K; kk++) {
-            const int k = ASC ? kk : K - 1 - kk;
-            const int q = NT + ss * K + kk;
-            const uint32_t uk = u[k];
-            if (v < uk) {
-                u[k] = v;
-                sm.lab[k][tid] = (uint16_t)(mtag | (uint32_t)(q - pv));
-                chg |= 1u << k;
-            }
-            const uint32_t t = uk + ct;
-            if (t < v) { v = t; pv = q; }
-            v += e[k];
-        }
-    }
-    // Without a cluster the next scan uses the other set of section maps,
-    // and every warp passes this scan's two barriers before any warp can
-    // reach the scan after next: no barrier here.  Cluster partners read
-    // the exchange slots remotely, so clusters keep one.
-    if (CL > 1) __syncthreads();
-}
 
 // Largest q with off[q] <= item (off[0] = 0, strictly increasing).
 __device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq, int64_t item) {
@@ -285,6 +105,19 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ off, int nq
     }
     return lo;
 }
+
+// The plain plan's cells for turn_scan: entering costs the cell's value
+// plus the maneuver's transition edges; labels are the step count alone.
+template <int K>
+struct PlainCells {
+    uint32_t (&u)[K];
+    const uint32_t (&ev)[K];
+    uint32_t ct;
+    __device__ __forceinline__ uint32_t ent(int k) const { return u[k] + ct; }
+    __device__ __forceinline__ uint32_t e(int k) const { return ev[k]; }
+    __device__ __forceinline__ int tag(int) const { return 0; }
+    __device__ __forceinline__ uint32_t label_bits(int pv, int q) const { return (uint32_t)(q - pv); }
+};
 
 // One 32-chain tile of one query: load, scan (one or two maneuvers), store.
 // `scans` counts the block's scans so far (it picks the set of section maps).
@@ -348,15 +181,17 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
     // the launch's costs (kernel parameters), else this query's own
     const uint32_t ct1 = ct_a != kCostPerQuery ? ct_a : __ldg(Q.g.ctm + mu1);
     int mb = scans & 1;
-    if (asc) turn_scan<K, SL, CL, 2, true>(u, e, chg, mu1, ct1, sec, lane, rank, 0, mb, a, live, sm.sh);
-    else turn_scan<K, SL, CL, 2, false>(u, e, chg, mu1, ct1, sec, lane, rank, 0, mb, a, live, sm.sh);
+    PlainCells<K> c1{u, e, ct1};
+    if (asc) turn_scan<K, SL, CL, 2, true>(c1, chg, mu1, sec, lane, rank, 0, mb, a, live, sm.sh);
+    else turn_scan<K, SL, CL, 2, false>(c1, chg, mu1, sec, lane, rank, 0, mb, a, live, sm.sh);
     scans++;
     if (mu2 >= 0) {
         live = live || chg != 0;
         mb = scans & 1;
         const uint32_t ct2 = ct_b != kCostPerQuery ? ct_b : __ldg(Q.g.ctm + mu2);
-        if (asc) turn_scan<K, SL, CL, 2, false>(u, e, chg, mu2, ct2, sec, lane, rank, 1, mb, a, live, sm.sh);
-        else turn_scan<K, SL, CL, 2, true>(u, e, chg, mu2, ct2, sec, lane, rank, 1, mb, a, live, sm.sh);
+        PlainCells<K> c2{u, e, ct2};
+        if (asc) turn_scan<K, SL, CL, 2, false>(c2, chg, mu2, sec, lane, rank, 1, mb, a, live, sm.sh);
+        else turn_scan<K, SL, CL, 2, true>(c2, chg, mu2, sec, lane, rank, 1, mb, a, live, sm.sh);
         scans++;
     }
     if (vol.improved) {
@@ -695,6 +530,163 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
     if (vol.improved) count_improved(vol.improved + 1, nimp);
 }
 
+// ------------------------------------------- straights of the gear states
+// A straight layer of the two gear states (gear.cu) on the staged tiles of
+// the plain straight kernel: the same chunks of the own gear's values and
+// B, plus the other gear's values in a third tile.  Entering a line at a
+// cell costs the cheaper of its own gear's value and the other gear's value
+// plus the penalty (own gear on a tie); a store must beat the own gear's
+// value and records whether the segment was entered from the other gear
+// (label bit 12).  Values at or above TH mean unreached (the host picks
+// this kernel only when the finite costs stay below TH).
+struct __align__(16) GearStage {
+    StraightStage s;  // own gear's values, B (labels of marked cells), mask, shear
+    uint32_t vo[kVWords];
+};
+
+// The other gear's chunk tile, copied like the own gear's values.
+template <bool STEEP>
+__device__ __forceinline__ void gear_issue_other(uint32_t* vo, const ChunkGeom& c, const uint32_t* Vop, int lx,
+                                                 int mx) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (!STEEP) {
+        const int jv = t & 3;
+        for (int r = t >> 2; r < c.span; r += nt >> 2) {
+            const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
+            cp_async16(&vo[shv(r, 4 * jv)], Vop + row + 4 * jv);
+        }
+    } else {
+        const int a4 = c.base & ~3, nv = ((c.base & 3) + c.span + 3) >> 2;
+        const int rpp = max(1, nt / nv);
+        const int s0 = t / nv, j = t - s0 * nv;
+        if (s0 < rpp)
+            for (int s = s0; s < kSteps; s += rpp)
+                cp_async16(&vo[s * kStV + 4 * j], Vop + ((uint32_t)(c.y0 + s) << lx) + ((a4 + 4 * j) & mx));
+    }
+}
+
+template <bool STEEP, bool FWD>
+__device__ __forceinline__ void gear_straight_body(const GearLayer& a, int mu, int T, int lblock, GearStage* stage) {
+    const DevGrid& g = a.g;
+    const int lines = blockDim.x;
+    const int X0 = lblock * lines;
+    const int t = threadIdx.x;
+    constexpr int dir = FWD ? 1 : -1;
+    const PlaneInfo pi = g.plane[T];
+    const int16_t* bs = g.bshear + (int64_t)T * g.nx;
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int G = (mu == SB) ? 1 : 0;  // the backward straight belongs to the reverse gear
+    uint32_t* Vp = (G ? a.Vr : a.Vf) + (int64_t)T * nxy;
+    uint16_t* Lp = (G ? a.Lr : a.Lf) + (int64_t)T * nxy;
+    const uint32_t* Vop = (G ? a.Vf : a.Vr) + (int64_t)T * nxy;
+    const uint16_t* Bp = a.B + (int64_t)T * nxy;
+    const uint32_t w = pi.wS, ct = a.cin + a.cout, pen = a.pen;
+    const uint32_t mtag = (uint32_t)mu << 13;
+    uint32_t v = 0xFFFFFFFFu;
+    int pv = 0;
+    uint32_t pvo = 0;  // the carried segment was entered from the other gear
+    const int nch = g.nx / kSteps;
+    ChunkGeom geo0 = chunk_geom(bs, 0, dir, g.nx, X0, lines, g.mx), geo1 = geo0;
+    straight_issue<STEEP>(stage[0].s, geo0, bs, Vp, Bp, g.lx, g.mx, nullptr);
+    gear_issue_other<STEEP>(stage[0].vo, geo0, Vop, g.lx, g.mx);
+    cp_async_commit();
+    if (nch > 1) {
+        geo1 = chunk_geom(bs, 1, dir, g.nx, X0, lines, g.mx);
+        straight_issue<STEEP>(stage[1].s, geo1, bs, Vp, Bp, g.lx, g.mx, nullptr);
+        gear_issue_other<STEEP>(stage[1].vo, geo1, Vop, g.lx, g.mx);
+    }
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ch++) {
+        const int sb = ch & 1;
+        StraightStage& st = stage[sb].s;
+        const uint32_t* vo = stage[sb].vo;
+        const ChunkGeom c = sb ? geo1 : geo0;
+        cp_async_wait1();
+        __syncthreads();
+        const int qbase = FWD ? c.y0 : g.nx - c.y0;
+        bool marked = false;
+#pragma unroll
+        for (int kk = 0; kk < kSteps; kk++) {
+            const int s = FWD ? kk : kSteps - 1 - kk;
+            const int ai = t + st.bs[s];
+            const int vi = vidx<STEEP>(s, ai, c.base), bi = bidx<STEEP>(s, ai, c.base);
+            const uint16_t ob = st.b[bi];
+            const bool hard = ob == HARD;
+            const uint32_t e = edge_cost(ob, w);
+            const uint32_t us = hard ? 0u : min(st.v[vi], TH);
+            const uint32_t to = min(vo[vi], TH) + pen + ct, ts = us + ct;
+            const int q = qbase + (FWD ? s : -s);
+            if (v < us) {
+                st.v[vi] = v | kMark;
+                st.b[bi] = (uint16_t)(mtag | (pvo << 12) | (uint32_t)(q - pv));
+                marked = true;
+                if (STEEP) atomicOr(&st.mask[0], 1u << s);
+                else atomicOr(&st.mask[ai >> 5], 1u << (ai & 31));
+            }
+            const bool o = !hard && to < ts;
+            const uint32_t tt = o ? to : ts;
+            if (tt < v) { v = tt; pv = q; pvo = o; }
+            v += e;
+        }
+        if (__syncthreads_or(marked)) {
+            if (!STEEP) {
+                for (int r = t; r < c.span; r += lines) {
+                    if (!(st.mask[r >> 5] & (1u << (r & 31)))) continue;
+                    for (int s2 = 0; s2 < kSteps; s2++) {
+                        const uint32_t x = st.v[shv(r, s2)];
+                        if ((x >> 30) == 2u) {
+                            const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s2;
+                            Vp[id] = x & ~kMark;
+                            Lp[id] = st.b[shb(r, s2)];
+                        }
+                    }
+                }
+            } else {
+                const uint32_t steps = st.mask[0];
+                for (int s2 = 0; s2 < kSteps; s2++) {
+                    if (!(steps & (1u << s2))) continue;
+                    for (int xx = t; xx < c.span; xx += lines) {
+                        const uint32_t x = st.v[vidx<true>(s2, xx, c.base)];
+                        if ((x >> 30) == 2u) {
+                            const uint32_t id = ((uint32_t)(c.y0 + s2) << g.lx) + ((c.base + xx) & g.mx);
+                            Vp[id] = x & ~kMark;
+                            Lp[id] = st.b[bidx<true>(s2, xx, c.base)];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (ch + 2 < nch) {
+            const ChunkGeom nxt = chunk_geom(bs, ch + 2, dir, g.nx, X0, lines, g.mx);
+            if (sb) geo1 = nxt;
+            else geo0 = nxt;
+            straight_issue<STEEP>(stage[sb].s, nxt, bs, Vp, Bp, g.lx, g.mx, nullptr);
+            gear_issue_other<STEEP>(stage[sb].vo, nxt, Vop, g.lx, g.mx);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait0();
+}
+
+// One block per (heading plane, block of `lines` lines).
+__global__ void __launch_bounds__(kMaxLines, 2) k_gear_straight_tiled(const GearLayer a, int mu) {
+    extern __shared__ __align__(16) unsigned char gear_straight_smem[];
+    GearStage* stage = reinterpret_cast<GearStage*>(gear_straight_smem);
+    const int lines = blockDim.x;
+    const int bpp = a.g.nx / lines;
+    const int T = (int)(blockIdx.x / bpp), lblock = (int)(blockIdx.x - (unsigned)T * bpp);
+    const PlaneInfo pi = a.g.plane[T];
+    const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
+    if (pi.iflag) {
+        if (fwd) gear_straight_body<true, true>(a, mu, T, lblock, stage);
+        else gear_straight_body<true, false>(a, mu, T, lblock, stage);
+    } else {
+        if (fwd) gear_straight_body<false, true>(a, mu, T, lblock, stage);
+        else gear_straight_body<false, false>(a, mu, T, lblock, stage);
+    }
+}
+
 // Grid: one block per (query, heading plane, line block) work item, the
 // items of a query ordered plane by plane.  Without item_off every query has
 // Nx = 2^lx; with it, queries of any Nx >= lines follow each other.  Blocks
@@ -935,6 +927,18 @@ int turn_blocks_per_sm(int lt, int variant) {
                                                                         : turn_occupancy<16, 32, 2>();
         default: return 0;
     }
+}
+
+cudaError_t launch_gear_straight_tiled(const GearLayer& a, int mu, cudaStream_t s) {
+    const int nx = a.g.nx;
+    if (nx < kSteps) return cudaErrorInvalidValue;
+    const int lines = nx < kMaxLines ? nx : kMaxLines;
+    const int bytes = (int)(2 * sizeof(GearStage));
+    cudaError_t e = cudaFuncSetAttribute(k_gear_straight_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)a.g.nt * (unsigned)(nx / lines);
+    k_gear_straight_tiled<<<blocks, lines, bytes, s>>>(a, mu);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_conv_gate(QueryDesc* qd, int nq, int pass_all, cudaStream_t s) {
