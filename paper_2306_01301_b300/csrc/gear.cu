@@ -31,7 +31,7 @@ __device__ __forceinline__ uint32_t sadd(uint32_t a, uint32_t b) {
     return s >= INF32 ? INF32 : (uint32_t)s;
 }
 
-__device__ __forceinline__ int gear_of(int mu) { return (mu == LB || mu == SB || mu == RB) ? 1 : 0; }
+__host__ __device__ __forceinline__ int gear_of(int mu) { return (mu == LB || mu == SB || mu == RB) ? 1 : 0; }
 
 // One step of the two-loop walk at cell c, position q of 2n.
 struct Walk {
@@ -103,15 +103,24 @@ __global__ void __launch_bounds__(256) k_gear_straight(const GearLayer a, int mu
 // from the other gear" bit travels with the entry position to the label.
 // Values at or above TH mean unreached (the host picks this kernel only when
 // the finite costs stay below TH).
+//
+// The turns of one chain family come in pairs in the cycle order (RB then
+// RF on the right chains, LB then the next cycle's LF on the left chains),
+// each pair's maneuvers of opposite gears and opposite scan directions, as
+// in the plain sweep's fused pairs: the tile's values of both gears stay in
+// registers, the first scan's results are stored and then seen by the
+// second scan as the other gear's values.
 template <int K, int NTH>
 struct GearCells {
     uint32_t (&u)[K];        // own gear's value, TH when unreached, 0 when hard
-    const uint32_t (&w)[K];  // entering value
+    const uint32_t (&o)[K];  // the other gear's value, the same way
     const uint32_t (*bp)[NTH];  // shared memory: B of cells 2j (low half) and 2j+1, by thread
     int tid;
-    uint32_t oth;            // bit k: cell k is entered from the other gear's state
+    uint32_t ct, pct;        // transition edges; the same plus the gear-change penalty
+    uint32_t oth;            // bit k: entering at cell k from the other gear is strictly cheaper
     uint32_t wstep;
-    __device__ __forceinline__ uint32_t ent(int k) const { return w[k]; }
+    // a hard cell enters at ct, which its edge (TH) makes unusable
+    __device__ __forceinline__ uint32_t ent(int k) const { return min(u[k] + ct, o[k] + pct); }
     __device__ __forceinline__ uint32_t e(int k) const {
         const uint32_t b = (bp[k >> 1][tid] >> ((k & 1) * 16)) & 0xFFFFu;
         return b == HARD ? TH : (wstep * b) >> 8;
@@ -122,6 +131,15 @@ struct GearCells {
     }
 };
 
+template <int K>
+__device__ __forceinline__ uint32_t other_cheaper(const uint32_t (&u)[K], const uint32_t (&o)[K], uint32_t ct,
+                                                  uint32_t pct) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) m |= (uint32_t)(o[k] + pct < u[k] + ct) << k;
+    return m;
+}
+
 template <int K, int SL>
 struct GearTurnSmem {
     int2 cell[K * SL];
@@ -129,9 +147,11 @@ struct GearTurnSmem {
     TurnShared<K, SL, 2> sh;
 };
 
+// One tile: maneuver mu1 (transition edges ct1), then mu2 (ct2) when
+// mu2 >= 0; mu2 is of the other gear and scans the other way.
 template <int K, int SL>
 __global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : 1024 / (32 * SL))
-k_gear_scan(const GearLayer a, int mu) {
+k_gear_scan(const GearLayer a, int mu1, int mu2, uint32_t ct1, uint32_t ct2) {
     extern __shared__ __align__(16) unsigned char gear_smem[];
     GearTurnSmem<K, SL>& sm = *reinterpret_cast<GearTurnSmem<K, SL>*>(gear_smem);
     const DevGrid& g = a.g;
@@ -139,12 +159,13 @@ k_gear_scan(const GearLayer a, int mu) {
     const int64_t nxy = (int64_t)g.nx * g.nx;
     const int64_t tile = blockIdx.x;
     const int x0 = (int)((tile * 32) & g.mx), y0 = (int)((tile * 32 >> g.lx) & g.mx);
-    const bool left = mu == LF || mu == LB;
-    const bool asc = mu == LF || mu == RB;  // heading up along the sweep
-    const int G = gear_of(mu);
-    uint32_t* Vs = G ? a.Vr : a.Vf;
-    uint16_t* Ls = G ? a.Lr : a.Lf;
-    const uint32_t* Vo = G ? a.Vf : a.Vr;
+    const bool left = mu1 == LF || mu1 == LB;
+    const bool asc = mu1 == LF || mu1 == RB;  // heading up along the first scan
+    const int G = gear_of(mu1);
+    uint32_t* V1 = G ? a.Vr : a.Vf;
+    uint16_t* L1 = G ? a.Lr : a.Lf;
+    uint32_t* V2 = G ? a.Vf : a.Vr;
+    uint16_t* L2 = G ? a.Lf : a.Lr;
     if (lane < K) {  // this warp's headings: row offset and x of lane 0's cell
         const int t = sec * K + lane;
         const int4 b = __ldg(&g.beta4[t]);
@@ -152,42 +173,52 @@ k_gear_scan(const GearLayer a, int mu) {
         sm.cell[t] = make_int2((int)(uint32_t)((((y0 + by) & g.mx) << g.lx) + (int64_t)t * nxy), (x0 + bx) & g.mx);
     }
     __syncwarp();
-    const uint32_t ct = a.cin + a.cout;
-    uint32_t u[K], w[K];
-    uint32_t oth = 0, sa = 0, bw = 0;
+    uint32_t v1[K], v2[K];  // the first scan's gear, the other gear
+    uint32_t sa = 0, bw = 0;
     bool live = false;
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const int2 c = sm.cell[sec * K + k];
         const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
         const uint16_t b = __ldg(a.B + id);
-        const uint32_t vs = min(__ldg(Vs + id), TH), vo = min(__ldg(Vo + id), TH);
+        const uint32_t x1 = min(__ldg(V1 + id), TH), x2 = min(__ldg(V2 + id), TH);
         const bool hard = b == HARD;
-        const uint32_t ts = vs + ct, to = vo + a.pen + ct;
-        const bool o = to < ts;
-        u[k] = hard ? 0u : vs;
-        w[k] = hard ? 0u : (o ? to : ts);
-        oth |= (uint32_t)(o && !hard) << k;
+        v1[k] = hard ? 0u : x1;
+        v2[k] = hard ? 0u : x2;
         if (k & 1) sm.bp[k >> 1][tid] = bw | ((uint32_t)b << 16);
         else bw = b;
         sa = min(sa + (hard ? TH : (a.g.wA * (uint32_t)b) >> 8), TH);
-        live |= !hard && (vs < TH || vo < TH);
+        live |= !hard && (x1 < TH || x2 < TH);
     }
-    uint32_t chg = 0;
-    GearCells<K, 32 * SL> cl{u, w, sm.bp, tid, oth, g.wA};
-    if (asc) turn_scan<K, SL, 1, 2, true>(cl, chg, mu, sec, lane, 0, 0, 0, sa, live, sm.sh);
-    else turn_scan<K, SL, 1, 2, false>(cl, chg, mu, sec, lane, 0, 0, 0, sa, live, sm.sh);
-    if (chg) {
+    auto store = [&](uint32_t chg, const uint32_t (&v)[K], uint32_t* V, uint16_t* L) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
             if (chg & (1u << k)) {
                 const int2 c = sm.cell[sec * K + k];
                 const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
-                Vs[id] = u[k];
-                Ls[id] = sm.sh.lab[k][tid];
+                V[id] = v[k];
+                L[id] = sm.sh.lab[k][tid];
             }
         }
+    };
+    uint32_t chg = 0;
+    {
+        const uint32_t pct = ct1 + a.pen;
+        GearCells<K, 32 * SL> cl{v1, v2, sm.bp, tid, ct1, pct, other_cheaper(v1, v2, ct1, pct), g.wA};
+        if (asc) turn_scan<K, SL, 1, 2, true>(cl, chg, mu1, sec, lane, 0, 0, 0, sa, live, sm.sh);
+        else turn_scan<K, SL, 1, 2, false>(cl, chg, mu1, sec, lane, 0, 0, 0, sa, live, sm.sh);
     }
+    if (chg) store(chg, v1, V1, L1);  // labels are per thread: the second scan may reuse them
+    if (mu2 < 0) return;
+    live = live || chg != 0;
+    chg = 0;
+    {
+        const uint32_t pct = ct2 + a.pen;
+        GearCells<K, 32 * SL> cl{v2, v1, sm.bp, tid, ct2, pct, other_cheaper(v2, v1, ct2, pct), g.wA};
+        if (asc) turn_scan<K, SL, 1, 2, false>(cl, chg, mu2, sec, lane, 0, 1, 1, sa, live, sm.sh);
+        else turn_scan<K, SL, 1, 2, true>(cl, chg, mu2, sec, lane, 0, 1, 1, sa, live, sm.sh);
+    }
+    if (chg) store(chg, v2, V2, L2);
 }
 
 __global__ void k_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
@@ -247,14 +278,31 @@ cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t*
 
 namespace {
 template <int K, int SL>
-cudaError_t launch_gear_scan(const GearLayer& a, int mu, unsigned tiles, cudaStream_t s) {
+cudaError_t launch_gear_scan(const GearLayer& a, int mu1, int mu2, uint32_t ct1, uint32_t ct2, unsigned tiles,
+                             cudaStream_t s) {
     // more than the default 48 KB of shared memory; the attribute is per
     // device and setting it again is harmless
     const int bytes = (int)sizeof(GearTurnSmem<K, SL>);
     cudaError_t e = cudaFuncSetAttribute(k_gear_scan<K, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_gear_scan<K, SL><<<tiles, 32 * SL, bytes, s>>>(a, mu);
+    k_gear_scan<K, SL><<<tiles, 32 * SL, bytes, s>>>(a, mu1, mu2, ct1, ct2);
     return cudaGetLastError();
+}
+
+// The sections scan needs whole 32-chain rows and 16 headings per warp, and
+// values below TH (a.scan).
+bool gear_scan_fits(const GearLayer& a) {
+    return a.scan && a.g.nx >= 32 && (a.g.nt == 128 || a.g.nt == 256 || a.g.nt == 512);
+}
+
+cudaError_t launch_gear_scan_any(const GearLayer& a, int mu1, int mu2, uint32_t ct1, uint32_t ct2,
+                                 cudaStream_t s) {
+    const unsigned tiles = (unsigned)((int64_t)a.g.nx * a.g.nx / 32);
+    switch (a.g.nt) {
+        case 128: return launch_gear_scan<16, 8>(a, mu1, mu2, ct1, ct2, tiles, s);
+        case 256: return launch_gear_scan<16, 16>(a, mu1, mu2, ct1, ct2, tiles, s);
+        default: return launch_gear_scan<16, 32>(a, mu1, mu2, ct1, ct2, tiles, s);
+    }
 }
 }  // namespace
 
@@ -264,20 +312,17 @@ cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s) {
         k_gear_straight<<<dim3((unsigned)((a.g.nx + 255) / 256), (unsigned)a.g.nt), 256, 0, s>>>(a, mu);
         return cudaGetLastError();
     }
+    if (gear_scan_fits(a)) return launch_gear_scan_any(a, mu, -1, a.cin + a.cout, 0u, s);
     const int64_t chains = (int64_t)a.g.nx * a.g.nx;
-    // the sections scan needs whole 32-chain rows and 16 headings per warp,
-    // and values below TH (a.scan); other grids walk their chains
-    if (a.scan && a.g.nx >= 32) {
-        const unsigned tiles = (unsigned)(chains / 32);
-        switch (a.g.nt) {
-            case 128: return launch_gear_scan<16, 8>(a, mu, tiles, s);
-            case 256: return launch_gear_scan<16, 16>(a, mu, tiles, s);
-            case 512: return launch_gear_scan<16, 32>(a, mu, tiles, s);
-            default: break;
-        }
-    }
     k_gear_turn<<<(unsigned)((chains + 255) / 256), 256, 0, s>>>(a, mu);
     return cudaGetLastError();
+}
+
+bool gear_pair_fused(const GearLayer& a) { return gear_scan_fits(a); }
+
+cudaError_t launch_gear_pair(const GearLayer& a, int mu1, int mu2, uint32_t ct1, uint32_t ct2, cudaStream_t s) {
+    if (!gear_scan_fits(a) || gear_of(mu1) == gear_of(mu2)) return cudaErrorInvalidValue;
+    return launch_gear_scan_any(a, mu1, mu2, ct1, ct2, s);
 }
 
 cudaError_t launch_gear_extract(const GearLayer& a, int64_t goal, plan_segment* seg, int cap, int32_t* status,

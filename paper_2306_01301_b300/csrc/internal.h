@@ -207,6 +207,11 @@ struct GearLayer {
 cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
                              int start_gear, cudaStream_t s);
 cudaError_t launch_gear_layer(const GearLayer& a, int mu, cudaStream_t s);
+// Whether this grid runs a turn pair (RB then RF, or LB then LF: opposite
+// gears on the same chains) as one fused launch, and that launch; ct1, ct2
+// are the two maneuvers' entering plus leaving edges.
+bool gear_pair_fused(const GearLayer& a);
+cudaError_t launch_gear_pair(const GearLayer& a, int mu1, int mu2, uint32_t ct1, uint32_t ct2, cudaStream_t s);
 // A straight layer of the gear states on the staged tiles of the plain
 // straight kernel (sweep.cu); needs Nx >= 16 and a.scan.
 cudaError_t launch_gear_straight_tiled(const GearLayer& a, int mu, cudaStream_t s);

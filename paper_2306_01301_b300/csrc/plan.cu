@@ -564,11 +564,21 @@ int plan_sweep_gear(plan_t* p, plan_pose start, int start_gear, int n_cycles) {
     p->vol_kind = VOL_NONE;
     int rc = cuda_rc(launch_gear_init(p->d_V, p->d_Vr, p->d_L, p->d_Lr, p->nr, cell_index(p, start), start_gear, s));
     p->launches++;
+    // Maneuver ids are the cycle order.  Where the grid allows, RB, RF and
+    // LB, next cycle's LF run as fused pairs (the same layers in the same
+    // order, each pair one launch).
+    const bool fuse = gear_pair_fused(a);
     for (int l = 0; l < 6 * n_cycles && rc == PLAN_OK; l++) {
-        const int mu = l % 6;  // maneuver ids are the cycle order
-        a.cin = p->cin[mu];
-        a.cout = p->cout[mu];
-        rc = cuda_rc(launch_gear_layer(a, mu, s));
+        const int mu = l % 6;
+        const int mu2 = mu == RB ? RF : (mu == LB && l + 1 < 6 * n_cycles ? LF : -1);
+        if (fuse && mu2 >= 0) {
+            rc = cuda_rc(launch_gear_pair(a, mu, mu2, p->cin[mu] + p->cout[mu], p->cin[mu2] + p->cout[mu2], s));
+            l++;
+        } else {
+            a.cin = p->cin[mu];
+            a.cout = p->cout[mu];
+            rc = cuda_rc(launch_gear_layer(a, mu, s));
+        }
         p->launches++;
     }
     if (rc == PLAN_OK) p->vol_kind = VOL_GEAR;

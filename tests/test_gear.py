@@ -26,6 +26,9 @@ CASES = [
     (5, 7, 7.5, (2, 1, 1), 1, 1500, 0, None),
     (6, 6, 10.0, (4, 1, 2), 2, 700, 2, ([100, 50, 400, 120, 450, 380], [150, 60, 300, 170, 250, 320])),
     (7, 9, 14.0, (3, 1, 1), 1, 2500, 1, None),
+    # the fused turn pairs across cycles (LB, then the next cycle's LF)
+    (5, 8, 6.0, (2, 1, 1), 2, 1100, 2, ([200, 80, 500, 150, 600, 450], [40, 0, 90, 30, 20, 70])),
+    (6, 7, 9.0, (3, 1, 1), 3, 600, 0, None),
 ]
 
 
