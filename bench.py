@@ -42,16 +42,20 @@ def load_peaks():
 
 def source_hash():
     """Hash of what the turn kernel is built from: the turn section of
-    sweep.cu (kernel and launcher) and the structures it reads."""
+    sweep.cu (kernel and launcher), the scan it runs (turn_scan.cuh) and the
+    structures it reads."""
     csrc = os.path.join(ROOT, "paper_2306_01301_b300", "csrc")
     with open(os.path.join(csrc, "sweep.cu")) as f:
         sweep = f.read()
+    with open(os.path.join(csrc, "turn_scan.cuh")) as f:
+        scan = f.read()
     with open(os.path.join(csrc, "internal.h")) as f:
         internal = f.read()
     a = sweep.index("// ------------------------------------------------------------------- turns")
     b = sweep.index("// ---------------------------------------------------------------- straights", a)
     h = hashlib.sha256()
     h.update(sweep[a:b].encode())
+    h.update(scan.encode())
     for name in ("PlaneInfo", "DevGrid", "Volumes", "QueryDesc"):
         i = internal.index("struct " + name + " {")
         h.update(internal[i:internal.index("\n};", i) + 3].encode())

@@ -237,6 +237,19 @@ void build_clothoids(plan_s* p) {
         }
 }
 
+// Whether every finite value of an N-cycle sweep over the levels stays below
+// TH (each layer adds at most one segment: its transition cost and at most
+// max(Nx, N_theta) - 1 edges on a 3D layer, N_levels - 1 on a clothoid), so
+// that the 3D layers may run on the plain sweep kernels, which clamp there.
+bool levels_in_range(const plan_s* p, int n_cycles) {
+    const double b_max = (double)obstacle_bound(p);
+    uint64_t ct = 0;
+    for (int k = 0; k < 6; k++) ct = std::max<uint64_t>(ct, (uint64_t)p->cin[k] + p->cout[k]);
+    const double layer3 = (double)ct + (double)(std::max(p->nx, p->nt) - 1) * std::floor((double)p->w_max * b_max / 256.0);
+    const double layerc = (double)p->curv_ct + (double)(p->curv_nk - 1) * std::floor((double)p->curv_w * b_max / 256.0);
+    return (double)n_cycles * (6.0 * layer3 + 4.0 * layerc) < (double)TH;
+}
+
 Layer4 layer_args(const plan_s* p) {
     Layer4 a{};
     a.g = p->g;
@@ -260,6 +273,8 @@ void curv4_release(plan_s* p) {
     p->dfree(p->d_cdx, p->cdx.size() * 2);
     p->dfree(p->d_cdy, p->cdy.size() * 2);
     p->dfree(p->d_cdth, p->cdth.size() * 4);
+    p->dfree(p->d_qd4, 3 * sizeof(QueryDesc));
+    p->d_qd4 = nullptr;
     p->d_V4 = nullptr;
     p->d_L4 = nullptr;
     p->d_cdx = p->d_cdy = nullptr;
@@ -298,7 +313,8 @@ int plan_set_curvature_levels(plan_t* p, int levels_per_side, double arc_per_lev
     p->d_cdx = (int16_t*)p->dalloc(p->cdx.size() * 2);
     p->d_cdy = (int16_t*)p->dalloc(p->cdy.size() * 2);
     p->d_cdth = (int32_t*)p->dalloc(p->cdth.size() * 4);
-    if (!p->d_V4 || !p->d_L4 || !p->d_cdx || !p->d_cdy || !p->d_cdth) {
+    p->d_qd4 = (QueryDesc*)p->dalloc(3 * sizeof(QueryDesc));
+    if (!p->d_V4 || !p->d_L4 || !p->d_cdx || !p->d_cdy || !p->d_cdth || !p->d_qd4) {
         curv4_release(p);
         return PLAN_ENOMEM;
     }
@@ -327,6 +343,46 @@ int plan_sweep4(plan_t* p, plan_pose start, int start_level, int n_cycles) {
     const int64_t start4 = (int64_t)(start_level + p->curv_M) * p->nr + cell_index(p, start);
     int rc = cuda_rc(launch4_init(p->d_V4, p->d_L4, p->nr * p->curv_nk, start4, s));
     p->launches++;
+    if (rc == PLAN_OK && levels_in_range(p, n_cycles)) {
+        // The 3D layers are plain turn and straight layers on one level: the
+        // plain sweep kernels run them, one descriptor per level, each a
+        // one-cycle query whose passes 0 .. 4 are LF, SF, {RB, RF}, SB and a
+        // lone LB (the next cycle's clothoids come between LB and LF).
+        QueryDesc q[3];
+        const int lvl[3] = {p->curv_nk - 1, p->curv_M, 0};  // left limit, kappa = 0, right limit
+        for (int i = 0; i < 3; i++) {
+            q[i] = p->qd;
+            q[i].v = Volumes{p->d_V4 + (int64_t)lvl[i] * p->nr, p->d_L4 + (int64_t)lvl[i] * p->nr, p->d_B, nullptr};
+            q[i].n_cycles = 1;
+            q[i].pass = -1;
+            q[i].conv = nullptr;
+            q[i].mu_shift = 12;
+        }
+        rc = cuda_rc(cudaMemcpyAsync(p->d_qd4, q, sizeof(q), cudaMemcpyHostToDevice, s));
+        // the host copy must outlive the copy
+        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+        static const int pass_desc[5] = {0, 1, 2, 1, 0};
+        for (int c = 0; c < n_cycles && rc == PLAN_OK; c++) {
+            for (int l = 0; l < 4 && rc == PLAN_OK; l++) {
+                a.w = p->curv_w;
+                a.cin = p->curv_ct;
+                a.cout = 0;
+                rc = cuda_rc(launch4_layer(a, order[l], -1, s));
+                p->launches++;
+            }
+            for (int pass = 0; pass < 5 && rc == PLAN_OK; pass++) {
+                Group gr{p->d_qd4 + pass_desc[pass], 1, p->lx, p->lt, p->max_runs > 0 ? p->max_runs : 1};
+                gr.ctm = p->g.ctm;
+                const bool turn = pass_is_turn(pass);
+                gr.grid = turn ? p->turn_grid : p->straight_grid;
+                rc = cuda_rc(turn ? launch_turn(gr, pass, p->turn_variant, s)
+                                  : launch_straight(gr, pass, p->straight_lines, s));
+                p->launches++;
+            }
+        }
+        if (rc == PLAN_OK) p->vol4_kind = VOL4_SWEPT;
+        return rc;
+    }
     for (int l = 0; l < 10 * n_cycles && rc == PLAN_OK; l++) {
         const int mu = order[l % 10];
         int level = p->curv_M;  // straights

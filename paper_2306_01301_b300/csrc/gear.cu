@@ -205,8 +205,8 @@ k_gear_scan(const GearLayer a, int mu1, int mu2, uint32_t ct1, uint32_t ct2) {
     {
         const uint32_t pct = ct1 + a.pen;
         GearCells<K, 32 * SL> cl{v1, v2, sm.bp, tid, ct1, pct, other_cheaper(v1, v2, ct1, pct), g.wA};
-        if (asc) turn_scan<K, SL, 1, 2, true>(cl, chg, mu1, sec, lane, 0, 0, 0, sa, live, sm.sh);
-        else turn_scan<K, SL, 1, 2, false>(cl, chg, mu1, sec, lane, 0, 0, 0, sa, live, sm.sh);
+        if (asc) turn_scan<K, SL, 1, 2, true>(cl, chg, (uint32_t)mu1 << 13, sec, lane, 0, 0, 0, sa, live, sm.sh);
+        else turn_scan<K, SL, 1, 2, false>(cl, chg, (uint32_t)mu1 << 13, sec, lane, 0, 0, 0, sa, live, sm.sh);
     }
     if (chg) store(chg, v1, V1, L1);  // labels are per thread: the second scan may reuse them
     if (mu2 < 0) return;
@@ -215,8 +215,8 @@ k_gear_scan(const GearLayer a, int mu1, int mu2, uint32_t ct1, uint32_t ct2) {
     {
         const uint32_t pct = ct2 + a.pen;
         GearCells<K, 32 * SL> cl{v2, v1, sm.bp, tid, ct2, pct, other_cheaper(v2, v1, ct2, pct), g.wA};
-        if (asc) turn_scan<K, SL, 1, 2, false>(cl, chg, mu2, sec, lane, 0, 1, 1, sa, live, sm.sh);
-        else turn_scan<K, SL, 1, 2, true>(cl, chg, mu2, sec, lane, 0, 1, 1, sa, live, sm.sh);
+        if (asc) turn_scan<K, SL, 1, 2, false>(cl, chg, (uint32_t)mu2 << 13, sec, lane, 0, 1, 1, sa, live, sm.sh);
+        else turn_scan<K, SL, 1, 2, true>(cl, chg, (uint32_t)mu2 << 13, sec, lane, 0, 1, 1, sa, live, sm.sh);
     }
     if (chg) store(chg, v2, V2, L2);
 }

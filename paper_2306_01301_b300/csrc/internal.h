@@ -86,7 +86,15 @@ struct QueryDesc {
     // plan path's kernels records its site here (the host reports
     // PLAN_EINTERNAL); null or unused otherwise.
     int32_t* err;
+    // Bit position of the maneuver in the labels the sweeps write: 0 means
+    // 13 (plain labels, (mu << 13) | steps); the curvature levels' 3D
+    // layers use 12 (maneuvers up to 9, steps up to 4095).
+    int32_t mu_shift;
 };
+
+__device__ __forceinline__ uint32_t label_tag(const QueryDesc& Q, int mu) {
+    return (uint32_t)mu << (Q.mu_shift ? Q.mu_shift : 13);
+}
 
 // Index checks of the PLAN_BOUNDS_CHECK build: NHP_IN(i, n, err, site) is
 // true when 0 <= i < n; otherwise it records `site` in *err (first failure

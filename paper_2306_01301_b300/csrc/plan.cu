@@ -176,12 +176,16 @@ void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout) {
     }
 }
 
+uint64_t obstacle_bound(const plan_s* p) {
+    return p->d_dir ? std::min<uint64_t>((uint64_t)p->img_max_soft * p->dir_pen >> 8, HARD - 1u)
+                    : p->img_max_soft;
+}
+
 int range_check_layers(const plan_s* p, int layers) {
     // Every finite value is a sum over at most one segment per layer of ct
     // plus at most max(Nx, N_theta) - 1 edges; it must stay below the
     // kernels' TH.
-    const uint64_t b_max = p->d_dir ? std::min<uint64_t>((uint64_t)p->img_max_soft * p->dir_pen >> 8, HARD - 1u)
-                                    : p->img_max_soft;
+    const uint64_t b_max = obstacle_bound(p);
     const double e_max = (double)(((uint64_t)p->w_max * b_max) >> 8);
     const double bound =
         (double)layers * ((double)max_transition(p) + (double)(std::max(p->nx, p->nt) - 1) * e_max);

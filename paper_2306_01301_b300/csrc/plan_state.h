@@ -29,6 +29,9 @@ struct plan_s {
     double curv_L = 0.0;
     uint32_t curv_w = 0, curv_ct = 0;
     uint32_t* d_V4 = nullptr;
+    // the 3D layers' descriptors on the levels they run on (left limit,
+    // kappa = 0, right limit), for the plain sweep kernels
+    nhp::QueryDesc* d_qd4 = nullptr;
     uint16_t* d_L4 = nullptr;
     int16_t *d_cdx = nullptr, *d_cdy = nullptr;
     int32_t* d_cdth = nullptr;
@@ -127,6 +130,8 @@ bool pose_hard(const plan_s* p, plan_pose q);
 // PLAN_ERANGE when finite costs of an N-cycle sweep could reach TH.
 int range_check(const plan_s* p, int n_cycles);
 int range_check_layers(const plan_s* p, int layers);
+// Largest non-hard obstacle value B can hold (image, direction field).
+uint64_t obstacle_bound(const plan_s* p);
 void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout);
 void curv4_release(plan_s* p);  // the curvature levels' buffers
 void compact_release(plan_s* p);  // the Compact graph's L and R volumes

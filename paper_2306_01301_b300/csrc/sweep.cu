@@ -182,16 +182,16 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
     const uint32_t ct1 = ct_a != kCostPerQuery ? ct_a : __ldg(Q.g.ctm + mu1);
     int mb = scans & 1;
     PlainCells<K> c1{u, e, ct1};
-    if (asc) turn_scan<K, SL, CL, 2, true>(c1, chg, mu1, sec, lane, rank, 0, mb, a, live, sm.sh);
-    else turn_scan<K, SL, CL, 2, false>(c1, chg, mu1, sec, lane, rank, 0, mb, a, live, sm.sh);
+    if (asc) turn_scan<K, SL, CL, 2, true>(c1, chg, label_tag(Q, mu1), sec, lane, rank, 0, mb, a, live, sm.sh);
+    else turn_scan<K, SL, CL, 2, false>(c1, chg, label_tag(Q, mu1), sec, lane, rank, 0, mb, a, live, sm.sh);
     scans++;
     if (mu2 >= 0) {
         live = live || chg != 0;
         mb = scans & 1;
         const uint32_t ct2 = ct_b != kCostPerQuery ? ct_b : __ldg(Q.g.ctm + mu2);
         PlainCells<K> c2{u, e, ct2};
-        if (asc) turn_scan<K, SL, CL, 2, false>(c2, chg, mu2, sec, lane, rank, 1, mb, a, live, sm.sh);
-        else turn_scan<K, SL, CL, 2, true>(c2, chg, mu2, sec, lane, rank, 1, mb, a, live, sm.sh);
+        if (asc) turn_scan<K, SL, CL, 2, false>(c2, chg, label_tag(Q, mu2), sec, lane, rank, 1, mb, a, live, sm.sh);
+        else turn_scan<K, SL, CL, 2, true>(c2, chg, label_tag(Q, mu2), sec, lane, rank, 1, mb, a, live, sm.sh);
         scans++;
     }
     if (vol.improved) {
@@ -406,9 +406,9 @@ __device__ __forceinline__ void straight_issue(StraightStage& st, const ChunkGeo
 }
 
 template <bool STEEP, bool FWD>
-__device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, int T, int lblock,
-                                              StraightStage* stage, const PlaneInfo& pi, uint32_t* conv_p,
-                                              int32_t* err) {
+__device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& vol, int mu, uint32_t mtag, int T,
+                                              int lblock, StraightStage* stage, const PlaneInfo& pi,
+                                              uint32_t* conv_p, int32_t* err) {
     const int lines = blockDim.x;  // min(Nx, 128 or 256)
     const int X0 = lblock * lines;
     const int t = threadIdx.x;
@@ -419,7 +419,6 @@ __device__ __forceinline__ void straight_body(const DevGrid& g, const Volumes& v
     uint16_t* Lp = vol.L + (int64_t)T * nxy;
     const uint16_t* Bp = vol.B + (int64_t)T * nxy;
     const uint32_t w = pi.wS, ct = mu == SF ? g.ctm[SF] : g.ctm[SB];
-    const uint32_t mtag = (uint32_t)mu << 13;
     // Sweep order: dir > 0 visits y' = 0, 1, .., Nx-1 (q = y'); dir < 0
     // visits Nx-1, .., 1, 0 (q = Nx - y').  Starting at Nx-1 with nothing
     // carried equals starting at the wall cell y' = 0, which carries nothing.
@@ -715,16 +714,17 @@ k_straight(const QueryDesc* __restrict__ qd, const int32_t* __restrict__ item_of
         const DevGrid g = Q.g;
         const Volumes vol = Q.v;
         const int mu = ps.mu;
+        const uint32_t mtag = label_tag(Q, mu);
         const int bpp = g.nx / lines;  // line blocks per plane (powers of two)
         const int T = (int)(rem / bpp), lblock = (int)(rem - (int64_t)T * bpp);
         const PlaneInfo pi = g.plane[T];
         const bool fwd = (mu == SF ? pi.jsign : -pi.jsign) > 0;
         if (pi.iflag) {
-            if (fwd) straight_body<true, true>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
-            else straight_body<true, false>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
+            if (fwd) straight_body<true, true>(g, vol, mu, mtag, T, lblock, stage, pi, conv_p, Q.err);
+            else straight_body<true, false>(g, vol, mu, mtag, T, lblock, stage, pi, conv_p, Q.err);
         } else {
-            if (fwd) straight_body<false, true>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
-            else straight_body<false, false>(g, vol, mu, T, lblock, stage, pi, conv_p, Q.err);
+            if (fwd) straight_body<false, true>(g, vol, mu, mtag, T, lblock, stage, pi, conv_p, Q.err);
+            else straight_body<false, false>(g, vol, mu, mtag, T, lblock, stage, pi, conv_p, Q.err);
         }
         if (it + gridDim.x < items) __syncthreads();  // the stages are refilled by the next item
     }
@@ -748,7 +748,7 @@ __global__ void k_straight_small(const QueryDesc* __restrict__ qd, int pass_all)
     uint32_t* Vp = vol.V + (int64_t)T * nxy;
     uint16_t* Lp = vol.L + (int64_t)T * nxy;
     const uint16_t* Bp = vol.B + (int64_t)T * nxy;
-    const uint32_t mtag = (uint32_t)mu << 13;
+    const uint32_t mtag = label_tag(Q, mu);
     uint32_t v = 0xFFFFFFFFu, nimp = 0;
     int pv = 0;
     for (int q = 0; q < g.nx; q++) {

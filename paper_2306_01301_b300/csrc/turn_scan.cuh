@@ -56,14 +56,15 @@ __device__ __forceinline__ void combine(uint32_t xa, uint32_t xb, int xp, uint32
     ya = min(xa + ya, TH);
 }
 
-// One maneuver scan over the block's chains.  `live`: this thread's section
+// One maneuver scan over the block's chains; `mtag` is the maneuver's bits of
+// every label the scan writes.  `live`: this thread's section
 // holds a reached, non-hard cell.  A warp whose sections hold none has no
 // entries (its maps are "nothing produced") and, when nothing is carried in
 // either, cannot improve any of its cells, so it skips those loops; the
 // results are the same cell for cell.
 template <int K, int SL, int CL, int NSLOT, bool ASC, class Cells>
-__device__ __forceinline__ void turn_scan(Cells& cl, uint32_t& chg, int mu, int sec, int lane, int rank, int slot,
-                                          int mb, uint32_t a, bool live, TurnShared<K, SL, NSLOT>& sm) {
+__device__ __forceinline__ void turn_scan(Cells& cl, uint32_t& chg, uint32_t mtag, int sec, int lane, int rank,
+                                          int slot, int mb, uint32_t a, bool live, TurnShared<K, SL, NSLOT>& sm) {
     constexpr int S = SL * CL, NT = K * S;
     const int sr = CL == 1 ? 0 : (ASC ? rank : CL - 1 - rank);  // this block's place in scan order
     const int sl = ASC ? sec : SL - 1 - sec;                     // section index in scan order, local
@@ -188,7 +189,6 @@ __device__ __forceinline__ void turn_scan(Cells& cl, uint32_t& chg, int mu, int 
     if (__any_sync(0xFFFFFFFFu, any)) {
         uint32_t v = v0;
         int pv = p0;
-        const uint32_t mtag = (uint32_t)mu << 13;
         const int tid = sec * 32 + lane;
 #pragma unroll
         for (int kk = 0; kk < K; kk++) {

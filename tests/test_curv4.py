@@ -26,6 +26,8 @@ CASES = [
     (5, 6, 6.0, (2, 1, 1), 3, 0.75, 300, 2, -2),
     (6, 7, 10.0, (3, 1, 1), 4, 0.9, 250, 1, 0),
     (7, 7, 14.0, (4, 1, 2), 4, 1.0, 400, 1, 3),
+    # several cycles on a grid whose 3D layers take the persistent turn shape
+    (7, 8, 12.0, (3, 1, 1), 4, 1.0, 350, 3, -1),
 ]
 
 
