@@ -11,11 +11,19 @@
 // before its possible store and written only by its own chain, so the layer
 // sees the values from before it.  Labels (maneuver << 13) | (entered from S
 // << 12) | d, d <= n (a whole turn circle from S reaches the turn state of
-// the same cell), so grids up to 2048.  Feature path: one thread per chain.
+// the same cell), so grids up to 2048.
+//
+// When the finite costs stay below TH, the turn layers run as maneuver
+// scans of turn_scan.cuh over 32-chain tiles (the turn pairs of the cycle
+// order, RB then RF and LB then the next cycle's LF, each on one turn type,
+// fused into one launch) and the straight layers, which move within S with
+// no transition cost, on the plain straight kernel; otherwise, and on grids
+// the scan does not take, one thread walks each chain twice.
 #include <algorithm>
 
 #include "curve.cuh"
 #include "plan_state.h"
+#include "turn_scan.cuh"
 
 namespace nhp {
 
@@ -135,6 +143,139 @@ __global__ void __launch_bounds__(256) kc_straight(const CompactLayer a, int mu)
     }
 }
 
+// ------------------------------------------------ turns on the sections scan
+// A turn cell holds its turn state's value u and S's value s; entering costs
+// min(u, s + ct) (the turn state on a tie) and a carried value stores into
+// each of the two it beats, with the same label.
+template <int K, int NTH>
+struct CompactCells {
+    uint32_t (&u)[K];           // the turn state's value, TH when unreached, 0 when hard
+    uint32_t (&s)[K];           // S's value, the same way
+    const uint32_t (*bp)[NTH];  // shared memory: B of cells 2j (low half) and 2j+1, by thread
+    int tid;
+    uint32_t ct;                // S -> turn state
+    uint32_t oth;               // bit k: entering at cell k from S is strictly cheaper
+    uint32_t wstep;
+    __device__ __forceinline__ uint32_t bound(int k) const { return max(u[k], s[k]); }
+    // which of the two took the value is read off at the write-back, against
+    // the volumes, which still hold the values from before the layer
+    __device__ __forceinline__ void store(int k, uint32_t v) {
+        u[k] = min(u[k], v);
+        s[k] = min(s[k], v);
+    }
+    __device__ __forceinline__ uint32_t ent(int k) const { return min(u[k], s[k] + ct); }
+    __device__ __forceinline__ uint32_t e(int k) const {
+        const uint32_t b = (bp[k >> 1][tid] >> ((k & 1) * 16)) & 0xFFFFu;
+        return b == HARD ? TH : (wstep * b) >> 8;
+    }
+    __device__ __forceinline__ int tag(int k) const { return (int)(((oth >> k) & 1u) << 16); }
+    __device__ __forceinline__ uint32_t label_bits(int pv, int q) const {
+        return (uint32_t)((((pv >> 16) & 1) << 12) | (q - (pv & 0xFFFF)));
+    }
+};
+
+template <int K, int SL>
+struct CompactTurnSmem {
+    int2 cell[K * SL];
+    uint32_t bp[K / 2][32 * SL];
+    TurnShared<K, SL, 2> sh;
+};
+
+// One tile: maneuver mu1, then mu2 (the same turn type, the other scan
+// direction) when mu2 >= 0.
+template <int K, int SL>
+__global__ void __launch_bounds__(32 * SL, 1024 / (32 * SL) > 4 ? 4 : 1024 / (32 * SL))
+kc_scan(const CompactLayer a, int mu1, int mu2) {
+    extern __shared__ __align__(16) unsigned char compact_smem[];
+    CompactTurnSmem<K, SL>& sm = *reinterpret_cast<CompactTurnSmem<K, SL>*>(compact_smem);
+    const DevGrid& g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, sec = tid >> 5;
+    const int64_t nxy = (int64_t)g.nx * g.nx;
+    const int64_t tile = blockIdx.x;
+    const int x0 = (int)((tile * 32) & g.mx), y0 = (int)((tile * 32 >> g.lx) & g.mx);
+    const int ty = type_of(mu1);
+    const bool asc = mu1 == LF || mu1 == RB;  // heading up along the first scan
+    uint32_t* Vt = ty == 1 ? a.Vl : a.Vr;
+    uint16_t* Lt = ty == 1 ? a.Ll : a.Lr;
+    if (lane < K) {
+        const int t = sec * K + lane;
+        const int4 b = __ldg(&g.beta4[t]);
+        const int bx = ty == 1 ? b.x : b.z, by = ty == 1 ? b.y : b.w;
+        sm.cell[t] = make_int2((int)(uint32_t)((((y0 + by) & g.mx) << g.lx) + (int64_t)t * nxy), (x0 + bx) & g.mx);
+    }
+    __syncwarp();
+    uint32_t u[K], s[K];
+    uint32_t sa = 0, bw = 0;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int2 c = sm.cell[sec * K + k];
+        const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
+        const uint16_t b = __ldg(a.B + id);
+        const uint32_t xt = min(__ldg(Vt + id), TH), xs = min(__ldg(a.Vs + id), TH);
+        const bool hard = b == HARD;
+        u[k] = hard ? 0u : xt;
+        s[k] = hard ? 0u : xs;
+        if (k & 1) sm.bp[k >> 1][tid] = bw | ((uint32_t)b << 16);
+        else bw = b;
+        sa = min(sa + (hard ? TH : (g.wA * (uint32_t)b) >> 8), TH);
+        live |= !hard && (xt < TH || xs < TH);
+    }
+    auto cheaper_from_s = [&]() {
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) m |= (uint32_t)(s[k] + a.ct < u[k]) << k;
+        return m;
+    };
+    // cells with a label from this scan: store where the value went down
+    auto write_back = [&](uint32_t chg) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (chg & (1u << k)) {
+                const int2 c = sm.cell[sec * K + k];
+                const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
+                const uint16_t lab = sm.sh.lab[k][tid];
+                if (u[k] < min(Vt[id], TH)) { Vt[id] = u[k]; Lt[id] = lab; }
+                if (s[k] < min(a.Vs[id], TH)) { a.Vs[id] = s[k]; a.Ls[id] = lab; }
+            }
+        }
+    };
+    uint32_t chg = 0, any = 0;
+    {
+        CompactCells<K, 32 * SL> cl{u, s, sm.bp, tid, a.ct, cheaper_from_s(), g.wA};
+        if (asc) turn_scan<K, SL, 1, 2, true>(cl, chg, (uint32_t)mu1 << 13, sec, lane, 0, 0, 0, sa, live, sm.sh);
+        else turn_scan<K, SL, 1, 2, false>(cl, chg, (uint32_t)mu1 << 13, sec, lane, 0, 0, 0, sa, live, sm.sh);
+        if (chg) write_back(chg);  // labels are per thread: the second scan may reuse them
+        any = chg;
+    }
+    if (mu2 < 0) return;
+    live = live || any != 0;
+    chg = 0;
+    {
+        CompactCells<K, 32 * SL> cl{u, s, sm.bp, tid, a.ct, cheaper_from_s(), g.wA};
+        if (asc) turn_scan<K, SL, 1, 2, false>(cl, chg, (uint32_t)mu2 << 13, sec, lane, 0, 1, 1, sa, live, sm.sh);
+        else turn_scan<K, SL, 1, 2, true>(cl, chg, (uint32_t)mu2 << 13, sec, lane, 0, 1, 1, sa, live, sm.sh);
+        if (chg) write_back(chg);
+    }
+}
+
+template <int K, int SL>
+cudaError_t launch_kc_scan(const CompactLayer& a, int mu1, int mu2, cudaStream_t s) {
+    const int bytes = (int)sizeof(CompactTurnSmem<K, SL>);
+    cudaError_t e = cudaFuncSetAttribute(kc_scan<K, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    kc_scan<K, SL><<<(unsigned)((int64_t)a.g.nx * a.g.nx / 32), 32 * SL, bytes, s>>>(a, mu1, mu2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kc_scan_any(const CompactLayer& a, int mu1, int mu2, cudaStream_t s) {
+    switch (a.g.nt) {
+        case 128: return launch_kc_scan<16, 8>(a, mu1, mu2, s);
+        case 256: return launch_kc_scan<16, 16>(a, mu1, mu2, s);
+        default: return launch_kc_scan<16, 32>(a, mu1, mu2, s);
+    }
+}
+
 __global__ void kc_init(CompactLayer a, int64_t nr, int64_t start) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x) {
         a.Vs[i] = i == start ? 0u : INF32;
@@ -180,6 +321,16 @@ __global__ void kc_extract(const CompactLayer a, int64_t goal, plan_segment* seg
     }
 }
 
+// The scan path: whole 32-chain rows, 16 headings per warp, and finite
+// costs below TH (each layer adds at most one segment: ct and at most
+// max(Nx, N_theta) - 1 edges).
+bool compact_scan_fits(const plan_s* p, int n_cycles) {
+    if (p->nx < 32 || (p->nt != 128 && p->nt != 256 && p->nt != 512)) return false;
+    const double e_max = std::floor((double)p->w_max * (double)obstacle_bound(p) / 256.0);
+    const double layer = (double)p->costs.transition + (double)(std::max(p->nx, p->nt) - 1) * e_max;
+    return 6.0 * n_cycles * layer < (double)TH;
+}
+
 CompactLayer layer_args(const plan_s* p) {
     CompactLayer a{};
     a.g = p->g;
@@ -201,8 +352,10 @@ void compact_release(plan_s* p) {
     p->dfree(p->d_Vcr, (size_t)p->nr * 4);
     p->dfree(p->d_Lcl, (size_t)p->nr * 2);
     p->dfree(p->d_Lcr, (size_t)p->nr * 2);
+    p->dfree(p->d_qdc, sizeof(QueryDesc));
     p->d_Vcl = p->d_Vcr = nullptr;
     p->d_Lcl = p->d_Lcr = nullptr;
+    p->d_qdc = nullptr;
     if (p->vol_kind == VOL_COMPACT) p->vol_kind = VOL_NONE;
 }
 
@@ -225,7 +378,8 @@ int plan_set_compact_graph(plan_t* p, int enable) {
     p->d_Vcr = (uint32_t*)p->dalloc((size_t)p->nr * 4);
     p->d_Lcl = (uint16_t*)p->dalloc((size_t)p->nr * 2);
     p->d_Lcr = (uint16_t*)p->dalloc((size_t)p->nr * 2);
-    if (!p->d_Vcl || !p->d_Vcr || !p->d_Lcl || !p->d_Lcr) {
+    p->d_qdc = (QueryDesc*)p->dalloc(sizeof(QueryDesc));
+    if (!p->d_Vcl || !p->d_Vcr || !p->d_Lcl || !p->d_Lcr || !p->d_qdc) {
         compact_release(p);
         return PLAN_ENOMEM;
     }
@@ -244,6 +398,35 @@ int plan_sweep_compact(plan_t* p, plan_pose start, int n_cycles) {
     kc_init<<<(unsigned)blocks, 256, 0, s>>>(a, p->nr, cell_index(p, start));
     int rc = cuda_rc(cudaGetLastError());
     p->launches++;
+    if (rc == PLAN_OK && compact_scan_fits(p, n_cycles)) {
+        // Passes of the plain cycle schedule: a lone LF, then per cycle SF,
+        // {RB, RF}, SB and {LB, next LF} (a lone LB at the end).  The
+        // straights run on the plain kernel as passes 1 and 3 of a one-cycle
+        // query on S with no transition cost.
+        QueryDesc q = p->qd;
+        for (int k = 0; k < 6; k++) q.g.ctm[k] = 0;
+        q.n_cycles = 1;
+        q.pass = -1;
+        q.conv = nullptr;
+        q.v.improved = nullptr;
+        rc = cuda_rc(cudaMemcpyAsync(p->d_qdc, &q, sizeof(q), cudaMemcpyHostToDevice, s));
+        if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(s));  // the host copy must outlive the copy
+        Group gr{p->d_qdc, 1, p->lx, p->lt, p->max_runs > 0 ? p->max_runs : 1};
+        gr.grid = p->straight_grid;
+        for (int pass = 0; pass < pass_count(n_cycles) && rc == PLAN_OK; pass++) {
+            if (pass_is_turn(pass)) {
+                int m1, m2;
+                turn_pass_maneuvers(pass, &m1, &m2);
+                if (pass == 4 * n_cycles) m2 = -1;  // the last cycle's LB has no LF after it
+                rc = cuda_rc(launch_kc_scan_any(a, m1, m2, s));
+            } else {
+                rc = cuda_rc(launch_straight(gr, (pass & 3) == 1 ? 1 : 3, p->straight_lines, s));
+            }
+            p->launches++;
+        }
+        if (rc == PLAN_OK) p->vol_kind = VOL_COMPACT;
+        return rc;
+    }
     for (int l = 0; l < 6 * n_cycles && rc == PLAN_OK; l++) {
         const int mu = order[l % 6];
         if (mu == SF || mu == SB)

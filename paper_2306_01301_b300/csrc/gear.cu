@@ -119,6 +119,8 @@ struct GearCells {
     uint32_t ct, pct;        // transition edges; the same plus the gear-change penalty
     uint32_t oth;            // bit k: entering at cell k from the other gear is strictly cheaper
     uint32_t wstep;
+    __device__ __forceinline__ uint32_t bound(int k) const { return u[k]; }
+    __device__ __forceinline__ void store(int k, uint32_t v) { u[k] = v; }
     // a hard cell enters at ct, which its edge (TH) makes unusable
     __device__ __forceinline__ uint32_t ent(int k) const { return min(u[k] + ct, o[k] + pct); }
     __device__ __forceinline__ uint32_t e(int k) const {

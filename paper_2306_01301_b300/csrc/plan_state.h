@@ -32,6 +32,8 @@ struct plan_s {
     // the 3D layers' descriptors on the levels they run on (left limit,
     // kappa = 0, right limit), for the plain sweep kernels
     nhp::QueryDesc* d_qd4 = nullptr;
+    // the Compact graph's straights as a one-cycle query on S (plain kernel)
+    nhp::QueryDesc* d_qdc = nullptr;
     uint16_t* d_L4 = nullptr;
     int16_t *d_cdx = nullptr, *d_cdy = nullptr;
     int32_t* d_cdth = nullptr;

@@ -113,6 +113,8 @@ struct PlainCells {
     uint32_t (&u)[K];
     const uint32_t (&ev)[K];
     uint32_t ct;
+    __device__ __forceinline__ uint32_t bound(int k) const { return u[k]; }
+    __device__ __forceinline__ void store(int k, uint32_t v) { u[k] = v; }
     __device__ __forceinline__ uint32_t ent(int k) const { return u[k] + ct; }
     __device__ __forceinline__ uint32_t e(int k) const { return ev[k]; }
     __device__ __forceinline__ int tag(int) const { return 0; }

@@ -13,8 +13,10 @@
 //
 // What a cell contributes comes from a `Cells` policy with, for the
 // thread's cell k of its section:
-//   u[k]            the value a carried segment must beat to store (updated
-//                   in place when it does),
+//   bound(k)        the value a carried segment must beat to store anything
+//                   at the cell,
+//   store(k, v)     store a carried value v < bound(k) (the policy updates
+//                   the values it holds and notes what it stored),
 //   ent(k)          the value of entering the maneuver at the cell (both
 //                   transition edges included), read before any store of
 //                   this scan,
@@ -182,7 +184,7 @@ __device__ __forceinline__ void turn_scan(Cells& cl, uint32_t& chg, uint32_t mta
 #pragma unroll
         for (int kk = 0; kk < K; kk++) {
             const int k = ASC ? kk : K - 1 - kk;
-            any |= v < cl.u[k];
+            any |= v < cl.bound(k);
             v = min(v, cl.ent(k)) + cl.e(k);
         }
     }
@@ -195,8 +197,8 @@ __device__ __forceinline__ void turn_scan(Cells& cl, uint32_t& chg, uint32_t mta
             const int k = ASC ? kk : K - 1 - kk;
             const int q = NT + ss * K + kk;
             const uint32_t t = cl.ent(k);  // before this cell's store
-            if (v < cl.u[k]) {
-                cl.u[k] = v;
+            if (v < cl.bound(k)) {
+                cl.store(k, v);
                 sm.lab[k][tid] = (uint16_t)(mtag | cl.label_bits(pv, q));
                 chg |= 1u << k;
             }

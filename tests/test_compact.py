@@ -24,6 +24,9 @@ CASES = [
     (5, 7, 7.5, (2, 1, 1), 2),
     (6, 6, 10.0, (4, 1, 2), 2),
     (7, 9, 14.0, (3, 1, 1), 1),
+    # several cycles through the fused turn pairs (LB, then the next cycle's LF)
+    (5, 8, 6.0, (2, 1, 1), 3),
+    (6, 7, 9.0, (3, 1, 1), 2),
 ]
 
 
