@@ -110,6 +110,44 @@ __global__ void __launch_bounds__(256) k4_clothoid(const Layer4 a, int mu) {
     }
 }
 
+// The clothoid layer in the value domain of the plain sweeps (finite costs
+// below TH, checked on the host): 32-bit cell offsets within a level, no
+// saturation, the transition costs added on entering.  A hard cell reads as
+// 0, so nothing is stored there, and the TH on its leaving edge cancels an
+// entry there before it reaches another cell.  Same values and labels as
+// the saturating walk.
+__global__ void __launch_bounds__(256) k4_clothoid_th(const Layer4 a, int mu) {
+    const DevGrid& g = a.g;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // chain = its kappa = 0 pose
+    if (t >= a.nr) return;
+    const int x0 = (int)(t & g.mx), y0 = (int)((t >> g.lx) & g.mx), T0 = (int)(t >> (2 * g.lx));
+    const int f = family_of(mu), dir = dir_of(mu);
+    const int16_t* dxf = a.dx + (int64_t)f * a.nk * g.nt + T0;  // level K at [K * N_theta]
+    const int16_t* dyf = a.dy + (int64_t)f * a.nk * g.nt + T0;
+    const int32_t* dthf = a.dth + f * a.nk;
+    const uint32_t ct = a.cin + a.cout, tag = (uint32_t)mu << 12;
+    uint32_t v = 0xFFFFFFFFu;
+    int pv = 0;
+    for (int q = 0; q < a.nk; q++) {
+        const int K = dir > 0 ? q : a.nk - 1 - q;
+        const uint32_t x = (uint32_t)(x0 + __ldg(dxf + K * g.nt)) & (uint32_t)g.mx;
+        const uint32_t y = (uint32_t)(y0 + __ldg(dyf + K * g.nt)) & (uint32_t)g.mx;
+        const uint32_t T = (uint32_t)(T0 + __ldg(dthf + K)) & (uint32_t)g.mt;
+        const uint32_t c = x | (y << g.lx) | (T << (2 * g.lx));
+        uint32_t* Vk = a.V + (int64_t)K * a.nr;
+        const uint16_t b = __ldg(a.B + c);
+        const bool hard = b == HARD;
+        const uint32_t u = hard ? 0u : min(Vk[c], TH);
+        if (v < u) {
+            Vk[c] = v;
+            a.L[(int64_t)K * a.nr + c] = (uint16_t)(tag | (uint32_t)(q - pv));
+        }
+        const uint32_t tt = u + ct;
+        if (tt < v) { v = tt; pv = q; }
+        v += hard ? TH : (uint32_t)(((uint64_t)a.w * b) >> 8);
+    }
+}
+
 __global__ void k4_init(uint32_t* V, uint16_t* L, int64_t n4, int64_t start4) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         V[i] = i == start4 ? 0u : INF32;
@@ -174,7 +212,8 @@ cudaError_t launch4_init(uint32_t* V, uint16_t* L, int64_t n4, int64_t start4, c
 
 cudaError_t launch4_layer(const Layer4& a, int mu, int level, cudaStream_t s) {
     if (mu >= PLAN_C1F) {
-        k4_clothoid<<<(unsigned)((a.nr + 255) / 256), 256, 0, s>>>(a, mu);
+        if (a.th) k4_clothoid_th<<<(unsigned)((a.nr + 255) / 256), 256, 0, s>>>(a, mu);
+        else k4_clothoid<<<(unsigned)((a.nr + 255) / 256), 256, 0, s>>>(a, mu);
     } else if (mu == SF || mu == SB) {
         k4_straight<<<dim3((unsigned)((a.g.nx + 255) / 256), (unsigned)a.g.nt), 256, 0, s>>>(a, mu, level);
     } else {
@@ -344,6 +383,7 @@ int plan_sweep4(plan_t* p, plan_pose start, int start_level, int n_cycles) {
     int rc = cuda_rc(launch4_init(p->d_V4, p->d_L4, p->nr * p->curv_nk, start4, s));
     p->launches++;
     if (rc == PLAN_OK && levels_in_range(p, n_cycles)) {
+        a.th = true;
         // The 3D layers are plain turn and straight layers on one level: the
         // plain sweep kernels run them, one descriptor per level, each a
         // one-cycle query whose passes 0 .. 4 are LF, SF, {RB, RF}, SB and a

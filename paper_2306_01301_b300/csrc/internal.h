@@ -239,6 +239,7 @@ struct Layer4 {
     const int16_t *dx, *dy;
     const int32_t* dth;
     uint32_t w, cin, cout;  // step weight of the layer's maneuver; entering, leaving
+    bool th;                // finite costs stay below TH: clothoids in the plain sweeps' value domain
 };
 cudaError_t launch4_init(uint32_t* V, uint16_t* L, int64_t n4, int64_t start4, cudaStream_t s);
 cudaError_t launch4_layer(const Layer4& a, int mu, int level, cudaStream_t s);
