@@ -16,6 +16,7 @@
 // (maneuver << 12) | d.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "curve.cuh"
 #include "plan_state.h"
@@ -116,35 +117,57 @@ __global__ void __launch_bounds__(256) k4_clothoid(const Layer4 a, int mu) {
 // 0, so nothing is stored there, and the TH on its leaving edge cancels an
 // entry there before it reaches another cell.  Same values and labels as
 // the saturating walk.
+// Each thread carries kClothoidRows chains of one heading and column, rows
+// y0 + j Nx / kClothoidRows: a level's table entry, x and heading are the
+// same for all of them.
+constexpr int kClothoidRows = 4;
+
 __global__ void __launch_bounds__(256) k4_clothoid_th(const Layer4 a, int mu) {
+    constexpr int J = kClothoidRows;
     const DevGrid& g = a.g;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // chain = its kappa = 0 pose
-    if (t >= a.nr) return;
-    const int x0 = (int)(t & g.mx), y0 = (int)((t >> g.lx) & g.mx), T0 = (int)(t >> (2 * g.lx));
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nr / J) return;
+    const int lq = g.lx - 2;  // log2(Nx / J)
+    const int x0 = (int)(t & g.mx), yb = (int)((t >> g.lx) & ((1 << lq) - 1)), T0 = (int)(t >> (g.lx + lq));
     const int f = family_of(mu), dir = dir_of(mu);
-    const int16_t* dxf = a.dx + (int64_t)f * a.nk * g.nt + T0;  // level K at [K * N_theta]
-    const int16_t* dyf = a.dy + (int64_t)f * a.nk * g.nt + T0;
-    const int32_t* dthf = a.dth + f * a.nk;
+    // the chains' first level, then one level per step in direction dir
+    const int K0 = dir > 0 ? 0 : a.nk - 1;
+    const int64_t lstep = dir > 0 ? a.nr : -a.nr;
+    uint32_t* Vk = a.V + (int64_t)K0 * a.nr;
+    uint16_t* Lk = a.L + (int64_t)K0 * a.nr;
+    const int32_t* dxy = a.dxy + ((int64_t)f * a.nk + K0) * g.nt + T0;
+    const int32_t* dth = a.dth + f * a.nk + K0;
+    const int dxy_step = dir * g.nt;
     const uint32_t ct = a.cin + a.cout, tag = (uint32_t)mu << 12;
-    uint32_t v = 0xFFFFFFFFu;
-    int pv = 0;
+    uint32_t v[J];
+    int pv[J];
+#pragma unroll
+    for (int j = 0; j < J; j++) { v[j] = 0xFFFFFFFFu; pv[j] = 0; }
     for (int q = 0; q < a.nk; q++) {
-        const int K = dir > 0 ? q : a.nk - 1 - q;
-        const uint32_t x = (uint32_t)(x0 + __ldg(dxf + K * g.nt)) & (uint32_t)g.mx;
-        const uint32_t y = (uint32_t)(y0 + __ldg(dyf + K * g.nt)) & (uint32_t)g.mx;
-        const uint32_t T = (uint32_t)(T0 + __ldg(dthf + K)) & (uint32_t)g.mt;
-        const uint32_t c = x | (y << g.lx) | (T << (2 * g.lx));
-        uint32_t* Vk = a.V + (int64_t)K * a.nr;
-        const uint16_t b = __ldg(a.B + c);
-        const bool hard = b == HARD;
-        const uint32_t u = hard ? 0u : min(Vk[c], TH);
-        if (v < u) {
-            Vk[c] = v;
-            a.L[(int64_t)K * a.nr + c] = (uint16_t)(tag | (uint32_t)(q - pv));
+        const int32_t o = __ldg(dxy);
+        const uint32_t x = (uint32_t)(x0 + (int16_t)(o & 0xFFFF)) & (uint32_t)g.mx;
+        const uint32_t T = (uint32_t)(T0 + __ldg(dth)) & (uint32_t)g.mt;
+        const uint32_t base = x | (T << (2 * g.lx));
+        const int dy = o >> 16;
+#pragma unroll
+        for (int j = 0; j < J; j++) {
+            const uint32_t y = (uint32_t)(yb + (j << lq) + dy) & (uint32_t)g.mx;
+            const uint32_t c = base | (y << g.lx);
+            const uint16_t b = __ldg(a.B + c);
+            const bool hard = b == HARD;
+            const uint32_t u = hard ? 0u : min(Vk[c], TH);
+            if (v[j] < u) {
+                Vk[c] = v[j];
+                Lk[c] = (uint16_t)(tag | (uint32_t)(q - pv[j]));
+            }
+            const uint32_t tt = u + ct;
+            if (tt < v[j]) { v[j] = tt; pv[j] = q; }
+            v[j] += hard ? TH : (uint32_t)(((uint64_t)a.w * b) >> 8);
         }
-        const uint32_t tt = u + ct;
-        if (tt < v) { v = tt; pv = q; }
-        v += hard ? TH : (uint32_t)(((uint64_t)a.w * b) >> 8);
+        Vk += lstep;
+        Lk += lstep;
+        dxy += dxy_step;
+        dth += dir;
     }
 }
 
@@ -212,7 +235,7 @@ cudaError_t launch4_init(uint32_t* V, uint16_t* L, int64_t n4, int64_t start4, c
 
 cudaError_t launch4_layer(const Layer4& a, int mu, int level, cudaStream_t s) {
     if (mu >= PLAN_C1F) {
-        if (a.th) k4_clothoid_th<<<(unsigned)((a.nr + 255) / 256), 256, 0, s>>>(a, mu);
+        if (a.th && a.g.lx >= 2) k4_clothoid_th<<<(unsigned)((a.nr / kClothoidRows + 255) / 256), 256, 0, s>>>(a, mu);
         else k4_clothoid<<<(unsigned)((a.nr + 255) / 256), 256, 0, s>>>(a, mu);
     } else if (mu == SF || mu == SB) {
         k4_straight<<<dim3((unsigned)((a.g.nx + 255) / 256), (unsigned)a.g.nt), 256, 0, s>>>(a, mu, level);
@@ -300,6 +323,7 @@ Layer4 layer_args(const plan_s* p) {
     a.dx = p->d_cdx;
     a.dy = p->d_cdy;
     a.dth = p->d_cdth;
+    a.dxy = p->d_cdxy;
     return a;
 }
 
@@ -312,6 +336,8 @@ void curv4_release(plan_s* p) {
     p->dfree(p->d_cdx, p->cdx.size() * 2);
     p->dfree(p->d_cdy, p->cdy.size() * 2);
     p->dfree(p->d_cdth, p->cdth.size() * 4);
+    p->dfree(p->d_cdxy, p->cdx.size() * 4);
+    p->d_cdxy = nullptr;
     p->dfree(p->d_qd4, 3 * sizeof(QueryDesc));
     p->d_qd4 = nullptr;
     p->d_V4 = nullptr;
@@ -353,7 +379,8 @@ int plan_set_curvature_levels(plan_t* p, int levels_per_side, double arc_per_lev
     p->d_cdy = (int16_t*)p->dalloc(p->cdy.size() * 2);
     p->d_cdth = (int32_t*)p->dalloc(p->cdth.size() * 4);
     p->d_qd4 = (QueryDesc*)p->dalloc(3 * sizeof(QueryDesc));
-    if (!p->d_V4 || !p->d_L4 || !p->d_cdx || !p->d_cdy || !p->d_cdth || !p->d_qd4) {
+    p->d_cdxy = (int32_t*)p->dalloc(p->cdx.size() * 4);
+    if (!p->d_V4 || !p->d_L4 || !p->d_cdx || !p->d_cdy || !p->d_cdth || !p->d_qd4 || !p->d_cdxy) {
         curv4_release(p);
         return PLAN_ENOMEM;
     }
@@ -362,6 +389,11 @@ int plan_set_curvature_levels(plan_t* p, int levels_per_side, double arc_per_lev
         e = cudaMemcpyAsync(p->d_cdy, p->cdy.data(), p->cdy.size() * 2, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_cdth, p->cdth.data(), p->cdth.size() * 4, cudaMemcpyHostToDevice, p->stream);
+    std::vector<int32_t> dxy(p->cdx.size());
+    for (size_t i = 0; i < dxy.size(); i++)
+        dxy[i] = (int32_t)(((uint32_t)(uint16_t)p->cdy[i] << 16) | (uint32_t)(uint16_t)p->cdx[i]);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_cdxy, dxy.data(), dxy.size() * 4, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // the host tables may change with the next call
     if (e != cudaSuccess) {
         curv4_release(p);  // no half-built levels

@@ -237,6 +237,7 @@ struct Layer4 {
     int64_t nr;
     int nk;
     const int16_t *dx, *dy;
+    const int32_t* dxy;     // (dy << 16) | (dx & 0xFFFF), the same entries in one word
     const int32_t* dth;
     uint32_t w, cin, cout;  // step weight of the layer's maneuver; entering, leaving
     bool th;                // finite costs stay below TH: clothoids in the plain sweeps' value domain

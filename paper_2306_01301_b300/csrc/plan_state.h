@@ -36,6 +36,7 @@ struct plan_s {
     nhp::QueryDesc* d_qdc = nullptr;
     uint16_t* d_L4 = nullptr;
     int16_t *d_cdx = nullptr, *d_cdy = nullptr;
+    int32_t* d_cdxy = nullptr;  // dx and dy packed in one word
     int32_t* d_cdth = nullptr;
     std::vector<int16_t> cdx, cdy;
     std::vector<int32_t> cdth;
