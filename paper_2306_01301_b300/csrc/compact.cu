@@ -33,6 +33,7 @@ struct CompactLayer {
     uint32_t *Vs, *Vl, *Vr;
     uint16_t *Ls, *Ll, *Lr;
     uint32_t ct;
+    int32_t* err;  // the bounds-check build's error word (QueryDesc::err)
 };
 
 namespace {
@@ -211,8 +212,13 @@ kc_scan(const CompactLayer a, int mu1, int mu2) {
     for (int k = 0; k < K; k++) {
         const int2 c = sm.cell[sec * K + k];
         const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
-        const uint16_t b = __ldg(a.B + id);
-        const uint32_t xt = min(__ldg(Vt + id), TH), xs = min(__ldg(a.Vs + id), TH);
+        uint16_t b = HARD;
+        uint32_t xt = TH, xs = TH;
+        if (NHP_IN(id, nxy * g.nt, a.err, 36)) {
+            b = __ldg(a.B + id);
+            xt = min(__ldg(Vt + id), TH);
+            xs = min(__ldg(a.Vs + id), TH);
+        }
         const bool hard = b == HARD;
         u[k] = hard ? 0u : xt;
         s[k] = hard ? 0u : xs;
@@ -234,6 +240,7 @@ kc_scan(const CompactLayer a, int mu1, int mu2) {
             if (chg & (1u << k)) {
                 const int2 c = sm.cell[sec * K + k];
                 const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
+                if (!NHP_IN(id, nxy * g.nt, a.err, 37)) continue;
                 const uint16_t lab = sm.sh.lab[k][tid];
                 if (u[k] < min(Vt[id], TH)) { Vt[id] = u[k]; Lt[id] = lab; }
                 if (s[k] < min(a.Vs[id], TH)) { a.Vs[id] = s[k]; a.Ls[id] = lab; }
@@ -342,6 +349,7 @@ CompactLayer layer_args(const plan_s* p) {
     a.Ll = p->d_Lcl;
     a.Lr = p->d_Lcr;
     a.ct = p->costs.transition;
+    a.err = p->d_status + 3;
     return a;
 }
 
@@ -448,9 +456,10 @@ int plan_extract_compact(plan_t* p, plan_pose goal, plan_segment* out, int cap, 
     kc_extract<<<1, 32, 0, p->stream>>>(layer_args(p), cell_index(p, goal), p->d_seg, kDevSegCap, p->d_status);
     NHP_CK(cudaGetLastError());
     p->launches++;
-    int32_t status[2] = {0, 0};
+    int32_t status[4] = {0, 0, 0, 0};  // [3]: the bounds-check build's error word
     NHP_CK(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
     NHP_CK(cudaStreamSynchronize(p->stream));
+    if (status[3] != 0) return check_failed(p, status[3]);
     if (status[0] == -1) return PLAN_EUNREACHABLE;
     if (status[0] < 0) return PLAN_EINTERNAL;
     *cost = (uint32_t)status[1];
@@ -472,8 +481,7 @@ int plan_copy_compact_volumes(plan_t* p, uint32_t* VL, uint16_t* LL, uint32_t* V
     if (LL) NHP_CK(cudaMemcpyAsync(LL, p->d_Lcl, n * 2, cudaMemcpyDeviceToHost, p->stream));
     if (VR) NHP_CK(cudaMemcpyAsync(VR, p->d_Vcr, n * 4, cudaMemcpyDeviceToHost, p->stream));
     if (LR) NHP_CK(cudaMemcpyAsync(LR, p->d_Lcr, n * 2, cudaMemcpyDeviceToHost, p->stream));
-    NHP_CK(cudaStreamSynchronize(p->stream));
-    return PLAN_OK;
+    return check_error_word(p);
 }
 
 }  // extern "C"

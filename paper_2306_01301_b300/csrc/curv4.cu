@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(256) k4_clothoid_th(const Layer4 a, int mu) {
         for (int j = 0; j < J; j++) {
             const uint32_t y = (uint32_t)(yb + (j << lq) + dy) & (uint32_t)g.mx;
             const uint32_t c = base | (y << g.lx);
+            if (!NHP_IN((int64_t)(dir > 0 ? q : a.nk - 1 - q) * a.nr + c, (int64_t)a.nk * a.nr, a.err, 38)) continue;
             const uint16_t b = __ldg(a.B + c);
             const bool hard = b == HARD;
             const uint32_t u = hard ? 0u : min(Vk[c], TH);
@@ -324,6 +325,7 @@ Layer4 layer_args(const plan_s* p) {
     a.dy = p->d_cdy;
     a.dth = p->d_cdth;
     a.dxy = p->d_cdxy;
+    a.err = p->d_status + 3;
     return a;
 }
 
@@ -490,9 +492,10 @@ int plan_extract4(plan_t* p, plan_pose goal, int goal_level, plan_segment4* out,
     NHP_CK(launch4_extract(layer_args(p), goal4, reinterpret_cast<plan_segment4*>(p->d_seg), cap4, p->d_status,
                            p->stream));
     p->launches++;
-    int32_t status[2] = {0, 0};
+    int32_t status[4] = {0, 0, 0, 0};  // [3]: the bounds-check build's error word
     NHP_CK(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
     NHP_CK(cudaStreamSynchronize(p->stream));
+    if (status[3] != 0) return check_failed(p, status[3]);
     if (status[0] == -1) return PLAN_EUNREACHABLE;
     if (status[0] < 0) return PLAN_EINTERNAL;
     *cost = (uint32_t)status[1];
@@ -512,8 +515,7 @@ int plan_copy_volumes4(plan_t* p, uint32_t* V, uint16_t* L) {
     const size_t n4 = (size_t)p->nr * p->curv_nk;
     if (V) NHP_CK(cudaMemcpyAsync(V, p->d_V4, n4 * 4, cudaMemcpyDeviceToHost, p->stream));
     if (L) NHP_CK(cudaMemcpyAsync(L, p->d_L4, n4 * 2, cudaMemcpyDeviceToHost, p->stream));
-    NHP_CK(cudaStreamSynchronize(p->stream));
-    return PLAN_OK;
+    return check_error_word(p);
 }
 
 int plan_clothoid_tables(plan_t* p, int16_t* dx, int16_t* dy, int32_t* dth) {

@@ -182,8 +182,13 @@ k_gear_scan(const GearLayer a, int mu1, int mu2, uint32_t ct1, uint32_t ct2) {
     for (int k = 0; k < K; k++) {
         const int2 c = sm.cell[sec * K + k];
         const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
-        const uint16_t b = __ldg(a.B + id);
-        const uint32_t x1 = min(__ldg(V1 + id), TH), x2 = min(__ldg(V2 + id), TH);
+        uint16_t b = HARD;
+        uint32_t x1 = TH, x2 = TH;
+        if (NHP_IN(id, nxy * g.nt, a.err, 30)) {
+            b = __ldg(a.B + id);
+            x1 = min(__ldg(V1 + id), TH);
+            x2 = min(__ldg(V2 + id), TH);
+        }
         const bool hard = b == HARD;
         v1[k] = hard ? 0u : x1;
         v2[k] = hard ? 0u : x2;
@@ -198,6 +203,7 @@ k_gear_scan(const GearLayer a, int mu1, int mu2, uint32_t ct1, uint32_t ct2) {
             if (chg & (1u << k)) {
                 const int2 c = sm.cell[sec * K + k];
                 const uint32_t id = (uint32_t)c.x + (uint32_t)((c.y + lane) & g.mx);
+                if (!NHP_IN(id, nxy * g.nt, a.err, 31)) continue;
                 V[id] = v[k];
                 L[id] = sm.sh.lab[k][tid];
             }

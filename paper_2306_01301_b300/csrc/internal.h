@@ -211,6 +211,7 @@ struct GearLayer {
     uint16_t *Lf, *Lr;
     uint32_t pen, cin, cout;  // gear change; entering and leaving the layer's maneuver
     bool scan;                // finite costs stay below TH: turn layers may run the sections scan
+    int32_t* err;             // the bounds-check build's error word (QueryDesc::err)
 };
 cudaError_t launch_gear_init(uint32_t* Vf, uint32_t* Vr, uint16_t* Lf, uint16_t* Lr, int64_t nr, int64_t start,
                              int start_gear, cudaStream_t s);
@@ -241,6 +242,7 @@ struct Layer4 {
     const int32_t* dth;
     uint32_t w, cin, cout;  // step weight of the layer's maneuver; entering, leaving
     bool th;                // finite costs stay below TH: clothoids in the plain sweeps' value domain
+    int32_t* err;           // the bounds-check build's error word (QueryDesc::err)
 };
 cudaError_t launch4_init(uint32_t* V, uint16_t* L, int64_t n4, int64_t start4, cudaStream_t s);
 cudaError_t launch4_layer(const Layer4& a, int mu, int level, cudaStream_t s);

@@ -199,6 +199,19 @@ int check_sweep(const plan_s* p, plan_pose start, int n_cycles) {
     return range_check(p, n_cycles);
 }
 
+int check_error_word(plan_s* p) {
+    int32_t err = 0;
+    int rc = cuda_rc(cudaMemcpyAsync(&err, p->d_status + 3, 4, cudaMemcpyDeviceToHost, p->stream));
+    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
+    return rc == PLAN_OK && err != 0 ? check_failed(p, err) : rc;
+}
+
+int check_failed(plan_s* p, int32_t site) {
+    record_check_failure(site);
+    cudaMemsetAsync(p->d_status + 3, 0, 4, p->stream);
+    return PLAN_EINTERNAL;
+}
+
 int upload_desc(plan_s* p) {
     return cuda_rc(cudaMemcpyAsync(p->d_qd, &p->qd, sizeof(QueryDesc), cudaMemcpyHostToDevice, p->stream));
 }
@@ -447,13 +460,7 @@ int sweep_impl(plan_s* p, plan_pose start, int n_cycles, const uint32_t* entry) 
     return rc;
 }
 
-// A failed index check of the bounds-check build (site recorded in the
-// error word): reported once as PLAN_EINTERNAL, the word cleared.
-int device_check_failed(plan_s* p, int32_t site) {
-    record_check_failure(site);
-    cudaMemsetAsync(p->d_status + 3, 0, 4, p->stream);
-    return PLAN_EINTERNAL;
-}
+int device_check_failed(plan_s* p, int32_t site) { return check_failed(p, site); }
 
 // Status of the label walk just launched: segment count, V(goal); copies the
 // segments in driving order.  Synchronises.
@@ -561,6 +568,7 @@ int plan_sweep_gear(plan_t* p, plan_pose start, int start_gear, int n_cycles) {
     a.Lf = p->d_L;
     a.Lr = p->d_Lr;
     a.pen = p->gear_pen;
+    a.err = p->d_status + 3;
     // every layer adds at most one segment and one gear change
     a.scan = range_check_layers(p, 6 * n_cycles) == PLAN_OK &&
              (double)6 * n_cycles * (double)p->gear_pen + (double)6 * n_cycles * 65536.0 < (double)(1u << 29);
@@ -604,11 +612,12 @@ int plan_extract_gear(plan_t* p, plan_pose goal, plan_segment* out, int cap, int
     a.Lr = p->d_Lr;
     int rc = cuda_rc(launch_gear_extract(a, cell_index(p, goal), p->d_seg, kDevSegCap, p->d_status, p->stream));
     p->launches++;
-    int32_t status[3] = {0, 0, 0};
+    int32_t status[4] = {0, 0, 0, 0};  // [3]: the bounds-check build's error word
     if (rc == PLAN_OK)
         rc = cuda_rc(cudaMemcpyAsync(status, p->d_status, sizeof(status), cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
     if (rc != PLAN_OK) return rc;
+    if (status[3] != 0) return check_failed(p, status[3]);
     if (status[0] == -1) return PLAN_EUNREACHABLE;
     if (status[0] < 0) return PLAN_EINTERNAL;
     *cost = (uint32_t)status[1];
@@ -632,8 +641,7 @@ int plan_copy_reverse_volumes(plan_t* p, uint32_t* V, uint16_t* L) {
     if (V) rc = cuda_rc(cudaMemcpyAsync(V, p->d_Vr, (size_t)p->nr * 4, cudaMemcpyDeviceToHost, p->stream));
     if (rc == PLAN_OK && L)
         rc = cuda_rc(cudaMemcpyAsync(L, p->d_Lr, (size_t)p->nr * 2, cudaMemcpyDeviceToHost, p->stream));
-    if (rc == PLAN_OK) rc = cuda_rc(cudaStreamSynchronize(p->stream));
-    return rc;
+    return rc == PLAN_OK ? check_error_word(p) : rc;
 }
 
 int plan_set_direction_field(plan_t* p, const uint16_t* heading, int tolerance, uint32_t penalty_q8) {

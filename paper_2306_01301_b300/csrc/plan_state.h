@@ -138,6 +138,11 @@ uint64_t obstacle_bound(const plan_s* p);
 void set_transition(plan_s* p, const uint32_t* cin, const uint32_t* cout);
 void curv4_release(plan_s* p);  // the curvature levels' buffers
 void compact_release(plan_s* p);  // the Compact graph's L and R volumes
+// The bounds-check build's error word (the plan's d_status[3]): after the
+// work queued so far (synchronises), PLAN_EINTERNAL when an index check
+// failed, reported once with its site (plan_last_error) and cleared.
+int check_error_word(plan_s* p);
+int check_failed(plan_s* p, int32_t site);
 // Copy the plan's QueryDesc to the device (async on the plan's stream).
 int upload_desc(plan_s* p);
 // plan_create, optionally without the V and L volumes (a cached scene).

@@ -548,21 +548,26 @@ struct __align__(16) GearStage {
 // The other gear's chunk tile, copied like the own gear's values.
 template <bool STEEP>
 __device__ __forceinline__ void gear_issue_other(uint32_t* vo, const ChunkGeom& c, const uint32_t* Vop, int lx,
-                                                 int mx) {
+                                                 int mx, int32_t* err) {
     const int t = threadIdx.x, nt = blockDim.x;
+    const int64_t plane = (int64_t)1 << (2 * lx);
     if (!STEEP) {
         const int jv = t & 3;
         for (int r = t >> 2; r < c.span; r += nt >> 2) {
             const uint32_t row = ((uint32_t)((c.base + r) & mx) << lx) + (uint32_t)c.y0;
-            cp_async16(&vo[shv(r, 4 * jv)], Vop + row + 4 * jv);
+            if (NHP_IN(row + 4 * jv + 3, plane, err, 32) && NHP_IN(shv(r, 4 * jv) + 3, kVWords, err, 33))
+                cp_async16(&vo[shv(r, 4 * jv)], Vop + row + 4 * jv);
         }
     } else {
         const int a4 = c.base & ~3, nv = ((c.base & 3) + c.span + 3) >> 2;
         const int rpp = max(1, nt / nv);
         const int s0 = t / nv, j = t - s0 * nv;
         if (s0 < rpp)
-            for (int s = s0; s < kSteps; s += rpp)
-                cp_async16(&vo[s * kStV + 4 * j], Vop + ((uint32_t)(c.y0 + s) << lx) + ((a4 + 4 * j) & mx));
+            for (int s = s0; s < kSteps; s += rpp) {
+                const uint32_t gi = ((uint32_t)(c.y0 + s) << lx) + ((a4 + 4 * j) & mx);
+                if (NHP_IN(gi + 3, plane, err, 32) && NHP_IN(s * kStV + 4 * j + 3, kVWords, err, 33))
+                    cp_async16(&vo[s * kStV + 4 * j], Vop + gi);
+            }
     }
 }
 
@@ -588,13 +593,13 @@ __device__ __forceinline__ void gear_straight_body(const GearLayer& a, int mu, i
     uint32_t pvo = 0;  // the carried segment was entered from the other gear
     const int nch = g.nx / kSteps;
     ChunkGeom geo0 = chunk_geom(bs, 0, dir, g.nx, X0, lines, g.mx), geo1 = geo0;
-    straight_issue<STEEP>(stage[0].s, geo0, bs, Vp, Bp, g.lx, g.mx, nullptr);
-    gear_issue_other<STEEP>(stage[0].vo, geo0, Vop, g.lx, g.mx);
+    straight_issue<STEEP>(stage[0].s, geo0, bs, Vp, Bp, g.lx, g.mx, a.err);
+    gear_issue_other<STEEP>(stage[0].vo, geo0, Vop, g.lx, g.mx, a.err);
     cp_async_commit();
     if (nch > 1) {
         geo1 = chunk_geom(bs, 1, dir, g.nx, X0, lines, g.mx);
-        straight_issue<STEEP>(stage[1].s, geo1, bs, Vp, Bp, g.lx, g.mx, nullptr);
-        gear_issue_other<STEEP>(stage[1].vo, geo1, Vop, g.lx, g.mx);
+        straight_issue<STEEP>(stage[1].s, geo1, bs, Vp, Bp, g.lx, g.mx, a.err);
+        gear_issue_other<STEEP>(stage[1].vo, geo1, Vop, g.lx, g.mx, a.err);
     }
     cp_async_commit();
     for (int ch = 0; ch < nch; ch++) {
@@ -611,6 +616,7 @@ __device__ __forceinline__ void gear_straight_body(const GearLayer& a, int mu, i
             const int s = FWD ? kk : kSteps - 1 - kk;
             const int ai = t + st.bs[s];
             const int vi = vidx<STEEP>(s, ai, c.base), bi = bidx<STEEP>(s, ai, c.base);
+            if (!NHP_IN(vi, kVWords, a.err, 34) || !NHP_IN(bi, kBHalves, a.err, 34)) continue;
             const uint16_t ob = st.b[bi];
             const bool hard = ob == HARD;
             const uint32_t e = edge_cost(ob, w);
@@ -637,6 +643,7 @@ __device__ __forceinline__ void gear_straight_body(const GearLayer& a, int mu, i
                         const uint32_t x = st.v[shv(r, s2)];
                         if ((x >> 30) == 2u) {
                             const uint32_t id = ((uint32_t)((c.base + r) & g.mx) << g.lx) + c.y0 + s2;
+                            if (!NHP_IN(id, nxy, a.err, 35)) continue;
                             Vp[id] = x & ~kMark;
                             Lp[id] = st.b[shb(r, s2)];
                         }
@@ -650,6 +657,7 @@ __device__ __forceinline__ void gear_straight_body(const GearLayer& a, int mu, i
                         const uint32_t x = st.v[vidx<true>(s2, xx, c.base)];
                         if ((x >> 30) == 2u) {
                             const uint32_t id = ((uint32_t)(c.y0 + s2) << g.lx) + ((c.base + xx) & g.mx);
+                            if (!NHP_IN(id, nxy, a.err, 35)) continue;
                             Vp[id] = x & ~kMark;
                             Lp[id] = st.b[bidx<true>(s2, xx, c.base)];
                         }
@@ -662,8 +670,8 @@ __device__ __forceinline__ void gear_straight_body(const GearLayer& a, int mu, i
             const ChunkGeom nxt = chunk_geom(bs, ch + 2, dir, g.nx, X0, lines, g.mx);
             if (sb) geo1 = nxt;
             else geo0 = nxt;
-            straight_issue<STEEP>(stage[sb].s, nxt, bs, Vp, Bp, g.lx, g.mx, nullptr);
-            gear_issue_other<STEEP>(stage[sb].vo, nxt, Vop, g.lx, g.mx);
+            straight_issue<STEEP>(stage[sb].s, nxt, bs, Vp, Bp, g.lx, g.mx, a.err);
+            gear_issue_other<STEEP>(stage[sb].vo, nxt, Vop, g.lx, g.mx, a.err);
         }
         cp_async_commit();
     }
