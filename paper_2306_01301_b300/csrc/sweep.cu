@@ -550,7 +550,7 @@ template <bool STEEP>
 __device__ __forceinline__ void gear_issue_other(uint32_t* vo, const ChunkGeom& c, const uint32_t* Vop, int lx,
                                                  int mx, int32_t* err) {
     const int t = threadIdx.x, nt = blockDim.x;
-    const int64_t plane = (int64_t)1 << (2 * lx);
+    [[maybe_unused]] const int64_t plane = (int64_t)1 << (2 * lx);  // bounds-check build only
     if (!STEEP) {
         const int jv = t & 3;
         for (int r = t >> 2; r < c.span; r += nt >> 2) {
