@@ -1,7 +1,7 @@
 """The Compact graph (Section V.A, Fig. 12) on the GPU, through the C ABI,
 against the oracle: the values and labels of all three vertex types bit for
 bit and the back-tracked plans segment for segment on grids from 8^2 x 8 to
-128^2 x 512, and one cycle of the 512^3 parking scene."""
+128^2 x 512, and two cycles of the 512^3 parking scene."""
 import numpy as np
 import pytest
 
@@ -80,7 +80,8 @@ def test_compact_calls_are_checked():
     p.close()
 
 
-def test_parking_512cubed_compact_graph_one_cycle():
+def test_parking_512cubed_compact_graph_two_cycles():
+    """Full size, two cycles: the fused turn pairs within and across cycles."""
     sc = scenes.parallel_parking()
     img = sc.hard_image()
     o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
@@ -88,9 +89,9 @@ def test_parking_512cubed_compact_graph_one_cycle():
     p = planner(sc, img)
     p.set_compact_graph(True)
     p.render()
-    p.sweep_compact(sc.start, 1)
+    p.sweep_compact(sc.start, 2)
     got = p.compact_volumes()
-    Vo, Lo = o.sweep_compact(Bo, o.cell(sc.start), 1)
+    Vo, Lo = o.sweep_compact(Bo, o.cell(sc.start), 2)
     nr = o.nr
     want = (Vo[:nr], Lo[:nr], Vo[nr:2 * nr], Lo[nr:2 * nr], Vo[2 * nr:], Lo[2 * nr:])
     for name, a, b in zip(("V_S", "L_S", "V_L", "L_L", "V_R", "L_R"), got, want):

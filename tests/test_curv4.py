@@ -2,8 +2,9 @@
 the oracle: the library's clothoid tables equal the oracle's (both built
 from the clothoid integrals, each with its own code), and the 4D values,
 labels and back-tracked plans are bit for bit the oracle's, from start
-curvatures across the levels, on grids up to 128^2 x 128 with up to 9
-levels."""
+curvatures across the levels, on grids up to 128^2 x 256 with up to 9
+levels, and the values and labels of the 256^2 x 256 parking scene over 9
+levels and two cycles."""
 import numpy as np
 import pytest
 
@@ -84,4 +85,24 @@ def test_curvature_calls_are_checked():
     p.set_curvature_levels(0)
     with pytest.raises(binding.PlanError):
         p.sweep4(sc.start, 0, 1)
+    p.close()
+
+
+def test_curvature_levels_parking_256_bit_exact():
+    """The parking scene at 256^2 x 256 over 9 levels, two cycles: the plain
+    kernels' persistent shapes on a level and the clothoid layer at a size
+    where its four chains per thread span many blocks."""
+    sc = scenes.parallel_parking(nx_log2=8, nt_log2=8, n_cycles=2)
+    img = sc.hard_image()
+    o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
+    q = O.Oracle4(o, 4, 1.0, 500)
+    Bo = o.render_rows(img, sc.footprint)
+    p = planner(sc, img)
+    p.set_curvature_levels(4, 1.0, 500)
+    p.render()
+    p.sweep4(sc.start, 0, 2)
+    V, Lb = p.volumes4()
+    Vo, Lo = q.sweep(Bo, q.cell(sc.start, 0), 2)
+    assert np.array_equal(V, Vo), f"values differ at {np.flatnonzero(V != Vo)[:5]}"
+    assert np.array_equal(Lb, Lo), f"labels differ at {np.flatnonzero(Lb != Lo)[:5]}"
     p.close()

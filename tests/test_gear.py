@@ -1,7 +1,7 @@
 """Two gear states on the GPU, through the C ABI, against the oracle: both
 states' values and labels bit for bit for vehicles standing in forward or
 reverse gear or at rest, with and without per-maneuver transition costs,
-back-tracked plans segment for segment, and one cycle of the 512^3 parking
+back-tracked plans segment for segment, and two cycles of the 512^3 parking
 scene."""
 import numpy as np
 import pytest
@@ -99,7 +99,8 @@ def test_gear_calls_are_checked():
     p.close()
 
 
-def test_parking_512cubed_gear_states_one_cycle():
+def test_parking_512cubed_gear_states_two_cycles():
+    """Full size, two cycles: the fused turn pairs within and across cycles."""
     sc = scenes.parallel_parking()
     img = sc.hard_image()
     o = O.Oracle(sc.nx_log2, sc.nt_log2, sc.turn_radius, transition=sc.transition)
@@ -107,10 +108,10 @@ def test_parking_512cubed_gear_states_one_cycle():
     p = planner(sc, img)
     p.set_gear_penalty(3000)
     p.render()
-    p.sweep_gear(sc.start, 0, 1)
+    p.sweep_gear(sc.start, 0, 2)
     Vf, Lf, _ = p.volumes(B=False)
     Vr, Lr = p.reverse_volumes()
-    Vo, Lo = o.sweep_gear(Bo, o.cell(sc.start), 0, 3000, 1)
+    Vo, Lo = o.sweep_gear(Bo, o.cell(sc.start), 0, 3000, 2)
     nr = o.nr
     assert np.array_equal(Vf, Vo[:nr]) and np.array_equal(Vr, Vo[nr:])
     assert np.array_equal(Lf, Lo[:nr]) and np.array_equal(Lr, Lo[nr:])
