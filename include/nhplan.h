@@ -448,8 +448,8 @@ const char* plan_last_error(void);
  * loads this library holds until the process exits, so Nx is limited to 512
  * (larger grids return PLAN_ERANGE before any work) and the footprint to 65536
  * row runs over all headings.  The first call on a device looks up that
- * array's device address with the device current; make it before any stream
- * capture.  All calls share the one array: two calls whose work overlaps on a
+ * array's device address with the device current.  All calls share the one
+ * array: two calls whose work overlaps on a
  * GPU (other streams, other host threads) race and may produce wrong volumes.
  * Returns PLAN_EINVAL for bad arguments and PLAN_ECUDA if a CUDA call fails. */
 int plan_render_cspace_static(const uint16_t* image_dev, int nx_log2, int ntheta_log2,
