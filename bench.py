@@ -535,16 +535,36 @@ def run_extensions(args, torch):
     p.set_compact_graph(False)
     p.close()
     dir_ms = max(render_dir - render_plain, 1e-6)
+    # Algorithmic bytes read per plan (the stores of improved cells are left
+    # out: a few per cent): every sweep launch reads its volumes once per
+    # cell.  Gear states: each turn launch (a fused pair or a lone turn) and
+    # each straight reads B and both gears' values, 10 B per cell.  Compact
+    # graph: a turn launch reads B, its turn state and S (10 B); a straight B
+    # and S (6 B).  Curvature levels: a clothoid layer reads V and B on every
+    # level (6 B per cell and level), a 3D pass V and B on its level (6 B).
+    peak, peak_kind = load_peaks()
+    turns, straights = 4 * sc.n_cycles + 1 - 2 * sc.n_cycles, 2 * sc.n_cycles
+
+    def hbm(nbytes, ms):
+        gbs = nbytes / (ms * 1e6)
+        return {"algorithmic_gb_read": nbytes / 1e9, "GBps": gbs, "frac_of_hbm": gbs / peak, "peak": peak,
+                "peak_kind": peak_kind}
+    gear_bytes = (turns + straights) * 10 * sc.cells
+    compact_bytes = (turns * 10 + straights * 6) * sc.cells
+    curv_bytes = sc.n_cycles * (4 * nk * 6 + 5 * 6) * sc.cells
     return {"direction_pass_ms": dir_ms, "direction_pass_gbs": 4 * sc.cells / (dir_ms * 1e6),
             "render_ms_with_field": render_dir, "render_ms": render_plain,
             "start_layer_ms": max(init_seed - init_only, 0.0),
             "goal_set_extract_ms": goal_set, "single_goal_extract_ms": walk,
             "gear_states_sweep_ms": gear_plan, "gear_states_updates_per_s": 6 * sc.n_cycles * sc.cells / (gear_plan / 1e3),
+            "gear_states_roofline": hbm(gear_bytes, gear_plan),
             "gear_states_plan_cost": gear_res[0].cost if gear_res else None,
             "compact_graph": {"sweep_ms": compact_plan, "updates_per_s": 6 * sc.n_cycles * sc.cells / (compact_plan / 1e3),
+                              "roofline": hbm(compact_bytes, compact_plan),
                               "plan_cost": compact_res.cost if compact_res else None,
                               "plan_maneuvers": len(compact_res.segments) if compact_res else None},
             "curvature_levels": {"levels": nk, "sweep_ms": curv_plan, "updates_per_s": curv_updates / (curv_plan / 1e3),
+                                 "roofline": hbm(curv_bytes, curv_plan),
                                  "plan_cost": curv_res.cost if curv_res else None,
                                  "plan_maneuvers": len(curv_res.segments) if curv_res else None},
             "note": "direction pass moves 4 B per pose (read and write B); the other two are latency-bound one-block kernels"}
