@@ -177,7 +177,7 @@ __device__ __forceinline__ void turn_tile(const QueryDesc& Q, const PassInfo& ps
         e[k] = edge_cost(ob, w);
         u[k] = ob == HARD ? 0u : min(vv, TH);
         a = min(a + e[k], TH);
-        live |= ob != HARD && vv < TH;
+        live |= vv < TH;  // a hard cell's value stays INF (never stored; the start is not hard)
     }
     uint32_t chg = 0;
     // the launch's costs (kernel parameters), else this query's own
