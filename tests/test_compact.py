@@ -97,3 +97,25 @@ def test_parking_512cubed_compact_graph_two_cycles():
     for name, a, b in zip(("V_S", "L_S", "V_L", "L_L", "V_R", "L_R"), got, want):
         assert np.array_equal(a, b), f"{name} differs at {np.flatnonzero(a != b)[:5]}"
     p.close()
+
+
+def test_compact_graph_costs_beyond_the_scan_range():
+    """A transition cost whose sums could reach 2^30: the two-loop walks on a
+    grid the scan would otherwise take, against the oracle."""
+    lx, lt, R, fp, N = 5, 7, 7.5, (2, 1, 1), 3
+    sc, img = scenes.tiny(1077, lx, lt, fill=0.06, turn_radius=R, footprint=fp, soft=True, transition=1 << 26)
+    o = O.Oracle(lx, lt, R, transition=sc.transition)
+    Bo = o.render(img, fp)
+    start = next(c for c in sc.pose_candidates if Bo[o.cell(c)] != O.HARD)
+    p = planner(sc, img)
+    p.set_compact_graph(True)
+    p.render()
+    p.sweep_compact(start, N)
+    got = p.compact_volumes()
+    Vo, Lo = o.sweep_compact(Bo, o.cell(start), N)
+    nr = o.nr
+    want = (Vo[:nr], Lo[:nr], Vo[nr:2 * nr], Lo[nr:2 * nr], Vo[2 * nr:], Lo[2 * nr:])
+    for name, a, b in zip(("V_S", "L_S", "V_L", "L_L", "V_R", "L_R"), got, want):
+        assert np.array_equal(a, b), f"{name} differs at {np.flatnonzero(a != b)[:5]}"
+    assert (Vo[:nr][Vo[:nr] != O.INF] >= 1 << 26).sum() > 0
+    p.close()

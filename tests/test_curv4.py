@@ -29,6 +29,8 @@ CASES = [
     (7, 7, 14.0, (4, 1, 2), 4, 1.0, 400, 1, 3),
     # several cycles on a grid whose 3D layers take the persistent turn shape
     (7, 8, 12.0, (3, 1, 1), 4, 1.0, 350, 3, -1),
+    # a clothoid cost whose sums could reach 2^30: the saturating walks
+    (5, 6, 6.0, (2, 1, 1), 2, 1.0, 1 << 27, 2, 0),
 ]
 
 

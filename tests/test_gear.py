@@ -29,6 +29,8 @@ CASES = [
     # the fused turn pairs across cycles (LB, then the next cycle's LF)
     (5, 8, 6.0, (2, 1, 1), 2, 1100, 2, ([200, 80, 500, 150, 600, 450], [40, 0, 90, 30, 20, 70])),
     (6, 7, 9.0, (3, 1, 1), 3, 600, 0, None),
+    # a penalty whose sums could reach 2^30: the two-loop walks on a grid the scan would take
+    (5, 7, 7.5, (2, 1, 1), 2, 1 << 27, 1, None),
 ]
 
 
