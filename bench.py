@@ -464,9 +464,21 @@ def run_reach(args, torch):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        # the 8 cycles alone: each reads R_m and H and writes R_{m+1}, 3 bits per pose
+        e0.record(stream)
+        for _ in range(steps):
+            p.reach_sweep(sc_start, 8)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cycles_ms = e0.elapsed_time(e1) / steps
+        peak, peak_kind = load_peaks()
+        gbs = 8 * 3 * sc.cells / 8 / (cycles_ms * 1e6)
         out[name] = {"ms_per_plan": ms, "plans_per_s": 1e3 / ms,
                      "pose_cycles_per_s": 8 * 6 * sc.cells / (ms / 1e3),
-                     "maneuvers_to_goal": res[0] if res else None}
+                     "maneuvers_to_goal": res[0] if res else None,
+                     "cycles_ms": cycles_ms,
+                     "roofline": {"bound": "hbm", "algorithmic_mb_per_cycle": 3 * sc.cells / 8 / 1e6, "GBps": gbs,
+                                  "frac_of_hbm": gbs / peak, "peak": peak, "peak_kind": peak_kind}}
         p.close()
     out["paper_context"] = "Table 9: 2 ms for render + 8 cycles + back-track at 128^2 x 512 on its larger GPU"
     return out
