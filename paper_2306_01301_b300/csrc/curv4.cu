@@ -10,10 +10,15 @@
 // heading offset that depends only on kappa (Appendix F), so for one level
 // the map is a permutation of the 3D cells and consecutive threads (x0) touch
 // consecutive cells.  Clothoid chains are open (the curvature runs from one
-// limit to the other): one pass from the first level.  The 3D maneuvers
-// walk their cyclic chains twice on their level, as the paper's two loops.
-// Feature path: one thread per chain, saturating arithmetic, labels
+// limit to the other): one pass from the first level.  Labels are
 // (maneuver << 12) | d.
+//
+// When the finite costs stay below TH (checked on the host), the 3D layers
+// are passes of the plain turn and straight kernels on their level, and the
+// clothoid layer (k4_clothoid_th) carries four chains per thread in 32-bit
+// arithmetic.  Otherwise every layer is one thread per chain with saturating
+// arithmetic, the 3D maneuvers walking their cyclic chains twice on their
+// level, as the paper's two loops.
 #include <algorithm>
 #include <cmath>
 #include <vector>

@@ -7,16 +7,21 @@
 // the other one; leaving costs cost_out[mu] and returns to mu's gear's
 // state.  Each maneuver layer reads both states and writes its own gear's.
 //
-// A turn layer walks every chain twice around its cycle (one thread per
-// chain over N_theta headings), as the paper's two sequential loops do: the
-// first loop warms the carried value up, the second stores; a straight layer
-// walks each line once from its wall cell (one thread per line).  A cell is read once per step before its possible store,
-// so the values used for entering are those before the layer (only this
-// thread writes the cell, and only in the second loop).  Arithmetic
-// saturates at PLAN_INF.  Labels are (mu << 13) | (other << 12) | d with
-// d <= n (a whole turn circle can now pay off: it changes the gear state),
-// so grids are limited to 2048.  A feature path, not a tuned one: it streams
-// both value volumes, B and the labels twice per layer.
+// When the finite costs stay below TH (checked on the host), turn layers run
+// on the sections scan of turn_scan.cuh, RB with RF and LB with the next
+// cycle's LF fused into one launch (k_gear_scan), and straight layers on the
+// staged tiles of the plain straight kernel with a third tile for the other
+// gear (k_gear_straight_tiled, sweep.cu).  Otherwise, and on grids the scan
+// does not take, a turn layer walks every chain twice around its cycle (one
+// thread per chain over N_theta headings), as the paper's two sequential
+// loops do: the first loop warms the carried value up, the second stores; a
+// straight layer walks each line once from its wall cell (one thread per
+// line).  A cell is read once per step before its possible store, so the
+// values used for entering are those before the layer (only this thread
+// writes the cell, and only in the second loop); that arithmetic saturates
+// at PLAN_INF.  Labels are (mu << 13) | (other << 12) | d with d <= n (a
+// whole turn circle can pay off: it changes the gear state), so grids are
+// limited to 2048.
 #include "curve.cuh"
 #include "internal.h"
 #include "turn_scan.cuh"
