@@ -262,7 +262,7 @@ k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restr
 // warp's lanes are 32 / W sections of W words; SEC sections of K steps.  SF
 // and SB walk the line in opposite directions; what either reaches counts.
 template <int K>
-__global__ void __launch_bounds__(512, 1) k_reach_straight(const DevGrid g, const uint32_t* __restrict__ Rm,
+__global__ void __launch_bounds__(512, 2) k_reach_straight(const DevGrid g, const uint32_t* __restrict__ Rm,
                                  const uint32_t* __restrict__ H, const uint32_t* __restrict__ RmT,
                                  const uint32_t* __restrict__ HT, uint32_t* __restrict__ Rn,
                                  uint32_t* __restrict__ OT) {
@@ -314,24 +314,24 @@ __global__ void __launch_bounds__(512, 1) k_reach_straight(const DevGrid g, cons
         }
     }
     __syncthreads();
-    uint32_t o[K];
+    // forward sweep into shared memory (this thread's slots), then the
+    // backward sweep, each word stored as soon as both directions have it
+    // (a third register array would push the kernel past two blocks per SM)
+    uint32_t* sF = sC + 2 * W * P;  // [k][thread]
+    const int nth = blockDim.x;
     uint32_t v = sA[l * P + sec];
 #pragma unroll
     for (int k = 0; k < K; k++) {
         v = (v & vi[k]) | hb[k];
-        o[k] = ~v;
+        sF[k * nth + threadIdx.x] = v;
     }
     v = sA[(W + l) * P + sec];
 #pragma unroll
     for (int k = K - 1; k >= 0; k--) {
         v = (v & vi[k]) | hb[k];
-        o[k] |= ~v;
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) {
         const int y = sec * K + k;
         const int64_t ix = (int64_t)T * nplane + (int64_t)y * W + l;
-        const uint32_t word = scatter_bits(~o[k], l, bs[y] & g.mx, W);
+        const uint32_t word = scatter_bits(sF[k * nth + threadIdx.x] & v, l, bs[y] & g.mx, W);
         if (steep) Rn[ix] &= word;
         else OT[ix] = word;
     }
@@ -412,7 +412,8 @@ cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const ui
     const int SEC = g.nx / K;
     const int threads = SEC * W;
     if (g.nx < 64 || g.nx > 512 || threads % 32 != 0 || threads > 512) return cudaErrorInvalidValue;
-    const size_t smem = 4 * (size_t)(SEC + 1) * W * sizeof(uint32_t);
+    // section maps and carries (4 W (SEC + 1) words) + the forward sweep (K words per thread)
+    const size_t smem = (4 * (size_t)(SEC + 1) * W + (size_t)K * threads) * sizeof(uint32_t);
     if (K == 4) k_reach_straight<4><<<(unsigned)g.nt, threads, smem, s>>>(g, Rm, H, RmT, HT, Rn, OT);
     else k_reach_straight<16><<<(unsigned)g.nt, threads, smem, s>>>(g, Rm, H, RmT, HT, Rn, OT);
     return cudaGetLastError();
