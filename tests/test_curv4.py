@@ -22,6 +22,7 @@ def planner(sc, img):
 
 CASES = [
     # lx, lt, R, footprint, M, L, clothoid cost, N, start level
+    (2, 3, 1.5, (0, 0, 0), 1, 1.0, 150, 2, 0),  # Nx = 4: one row per chain group of the clothoid layer
     (3, 3, 2.0, (0, 0, 0), 1, 1.0, 150, 1, 0),
     (4, 4, 3.0, (1, 0, 0), 2, 1.0, 200, 2, 1),
     (5, 6, 6.0, (2, 1, 1), 3, 0.75, 300, 2, -2),
