@@ -274,10 +274,14 @@ cudaError_t launch_hard_bits(const uint16_t* B, uint32_t* H, int64_t nr, cudaStr
 cudaError_t launch_reach_init(uint32_t* R, int64_t nr, int64_t start, cudaStream_t s);
 cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32_t* planes, int nplanes, int lx,
                                  bool and_into, cudaStream_t s);
+// mode: 0 AND into Rn, 1 Rn = Rm AND result, 2 Rn = result
 cudaError_t launch_reach_turn(const DevGrid& g, const uint32_t* Rm, uint32_t* Rn, const uint32_t* H, int family,
-                              bool assign, cudaStream_t s);
+                              int mode, cudaStream_t s);
+// Steep planes' results stored into Out, shallow planes' (transposed) into OT.
 cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const uint32_t* H, const uint32_t* RmT,
-                                  const uint32_t* HT, uint32_t* Rn, uint32_t* OT, cudaStream_t s);
+                                  const uint32_t* HT, uint32_t* Out, uint32_t* OT, cudaStream_t s);
+// Rn &= X1 & X2 over all words.
+cudaError_t launch_reach_combine(uint32_t* Rn, const uint32_t* X1, const uint32_t* X2, int64_t nr, cudaStream_t s);
 cudaError_t launch_reach_counts(const uint32_t* R, int n, int64_t nr, uint8_t* count, cudaStream_t s);
 cudaError_t launch_reach_extract(const DevGrid& g, const uint32_t* R, int n, int64_t words, const uint32_t* H,
                                  int64_t goal, plan_segment* seg, int cap, int32_t* status, cudaStream_t s);

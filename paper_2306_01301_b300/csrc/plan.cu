@@ -246,6 +246,12 @@ void release(plan_s* p) {
     p->dfree(p->d_hbt, bits);
     p->dfree(p->d_rt, bits);
     p->dfree(p->d_ot, bits);
+    p->dfree(p->d_x1, bits);
+    p->dfree(p->d_x2, bits);
+    for (auto& st : p->reach_side)
+        if (st) cudaStreamDestroy(st);
+    for (auto& e : p->reach_ev)
+        if (e) cudaEventDestroy(e);
     p->dfree(p->d_shallow, sizeof(int32_t) * (size_t)p->nt);
     p->dfree(p->d_reach, bits * (size_t)p->reach_cap);
     for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }

@@ -87,6 +87,12 @@ struct plan_s {
     uint32_t* d_hbt = nullptr;
     uint32_t* d_rt = nullptr;
     uint32_t* d_ot = nullptr;
+    // the second turn family's and the straights' results of a cycle, written
+    // on two side streams while the first family runs, then ANDed into R_{m+1}
+    uint32_t* d_x1 = nullptr;
+    uint32_t* d_x2 = nullptr;
+    cudaStream_t reach_side[2] = {nullptr, nullptr};
+    cudaEvent_t reach_ev[3] = {nullptr, nullptr, nullptr};  // fork, join of each side stream
     uint32_t* d_reach = nullptr;
     int32_t* d_shallow = nullptr;
     std::vector<int32_t> shallow;

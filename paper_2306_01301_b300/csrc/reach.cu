@@ -168,13 +168,14 @@ __device__ __forceinline__ uint32_t ripple(uint32_t A, uint32_t C, int p, int n,
 
 // One turn family (LEFT: LF up, LB down; RIGHT: RB up, RF down).  Block: SEC
 // warps = sections of K headings; a warp's lanes are G = 32 / W chain rows
-// of W words.  Both maneuvers read R_m; what they reach is ANDed into
-// R_{m+1}, or with `assign` stored as R_m AND it (the first writer of a
-// cycle, so that R_{m+1} needs no copy of R_m first).
+// of W words.  Both maneuvers read R_m; what they reach goes to Rn by
+// `mode`: 0 ANDed into it, 1 stored as R_m AND it (the first writer of a
+// cycle, so that R_{m+1} needs no copy of R_m first), 2 stored as it is (a
+// family running beside the others writes its own volume).
 template <int K, int SEC>
 __global__ void __launch_bounds__(32 * SEC, 1)
 k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restrict__ Rn,
-             const uint32_t* __restrict__ H, int family, int assign) {
+             const uint32_t* __restrict__ H, int family, int mode) {
     // [direction][chain word][section]: the section maps, then what enters
     // each section; the odd pitch keeps both access patterns conflict-free
     __shared__ uint32_t sA[2][32][SEC + 1], sC[2][32][SEC + 1];
@@ -251,13 +252,15 @@ k_reach_turn(const DevGrid g, const uint32_t* __restrict__ Rm, uint32_t* __restr
         int off;
         const uint32_t ix = where(sec * K + k, off);
         const uint32_t word = scatter_bits(~o[k], l, off, W);
-        if (assign) Rn[ix] = rd(Rm + ix) & word;
+        if (mode == 2) Rn[ix] = word;
+        else if (mode == 1) Rn[ix] = rd(Rm + ix) & word;
         else Rn[ix] &= word;
     }
 }
 
 // Straight lines of one plane per block (steep planes in place, shallow
-// planes through their transposed copies): lines x' packed 32 per word,
+// planes through their transposed copies); results stored (steep into Rn,
+// shallow into OT), not combined: lines x' packed 32 per word,
 // steps y' along the view's rows, row y' shifted by Bs(y') (eq. 23).  A
 // warp's lanes are 32 / W sections of W words; SEC sections of K steps.  SF
 // and SB walk the line in opposite directions; what either reaches counts.
@@ -332,8 +335,17 @@ __global__ void __launch_bounds__(512, 2) k_reach_straight(const DevGrid g, cons
         const int y = sec * K + k;
         const int64_t ix = (int64_t)T * nplane + (int64_t)y * W + l;
         const uint32_t word = scatter_bits(sF[k * nth + threadIdx.x] & v, l, bs[y] & g.mx, W);
-        if (steep) Rn[ix] &= word;
+        if (steep) Rn[ix] = word;
         else OT[ix] = word;
+    }
+}
+
+// R_{m+1} &= (second turn family) & (straights), 16 bytes per thread.
+__global__ void k_reach_combine(uint4* __restrict__ Rn, const uint4* __restrict__ X1, const uint4* __restrict__ X2,
+                                int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 a = Rn[i], b = __ldg(X1 + i), c = __ldg(X2 + i);
+        Rn[i] = make_uint4(a.x & b.x & c.x, a.y & b.y & c.y, a.z & b.z & c.z, a.w & b.w & c.w);
     }
 }
 
@@ -389,15 +401,15 @@ cudaError_t launch_bit_transpose(const uint32_t* src, uint32_t* dst, const int32
 }
 
 cudaError_t launch_reach_turn(const DevGrid& g, const uint32_t* Rm, uint32_t* Rn, const uint32_t* H, int family,
-                              bool assign, cudaStream_t s) {
+                              int mode, cudaStream_t s) {
     const int W = 1 << (g.lx - 5), G = 32 / W;
     const unsigned blocks = (unsigned)(g.nx / G);
     switch (g.lt) {  // K = 16 headings per section
-        case 5: k_reach_turn<16, 2><<<blocks, 32 * 2, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
-        case 6: k_reach_turn<16, 4><<<blocks, 32 * 4, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
-        case 7: k_reach_turn<16, 8><<<blocks, 32 * 8, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
-        case 8: k_reach_turn<16, 16><<<blocks, 32 * 16, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
-        case 9: k_reach_turn<16, 32><<<blocks, 32 * 32, 0, s>>>(g, Rm, Rn, H, family, assign ? 1 : 0); break;
+        case 5: k_reach_turn<16, 2><<<blocks, 32 * 2, 0, s>>>(g, Rm, Rn, H, family, mode); break;
+        case 6: k_reach_turn<16, 4><<<blocks, 32 * 4, 0, s>>>(g, Rm, Rn, H, family, mode); break;
+        case 7: k_reach_turn<16, 8><<<blocks, 32 * 8, 0, s>>>(g, Rm, Rn, H, family, mode); break;
+        case 8: k_reach_turn<16, 16><<<blocks, 32 * 16, 0, s>>>(g, Rm, Rn, H, family, mode); break;
+        case 9: k_reach_turn<16, 32><<<blocks, 32 * 32, 0, s>>>(g, Rm, Rn, H, family, mode); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -419,6 +431,14 @@ cudaError_t launch_reach_straight(const DevGrid& g, const uint32_t* Rm, const ui
     return cudaGetLastError();
 }
 
+cudaError_t launch_reach_combine(uint32_t* Rn, const uint32_t* X1, const uint32_t* X2, int64_t nr, cudaStream_t s) {
+    const int64_t n4 = nr / 128;  // 32 poses per word, 4 words per thread (Nx >= 64)
+    const int64_t blocks = std::min<int64_t>((n4 + 255) / 256, 148 * 8);
+    k_reach_combine<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<uint4*>(Rn), reinterpret_cast<const uint4*>(X1),
+                                                      reinterpret_cast<const uint4*>(X2), n4);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reach_counts(const uint32_t* R, int n, int64_t nr, uint8_t* count, cudaStream_t s) {
     const int64_t words = nr / 32;
     const int64_t blocks = std::min<int64_t>((words + 255) / 256, 148 * 16);
@@ -436,15 +456,19 @@ int reach_alloc(plan_s* p, int n_cycles) {
         p->d_hbt = (uint32_t*)p->dalloc(vol);
         p->d_rt = (uint32_t*)p->dalloc(vol);
         p->d_ot = (uint32_t*)p->dalloc(vol);
+        p->d_x1 = (uint32_t*)p->dalloc(vol);
+        p->d_x2 = (uint32_t*)p->dalloc(vol);
         p->d_shallow = (int32_t*)p->dalloc(sizeof(int32_t) * (size_t)p->nt);
-        if (!p->d_hb || !p->d_hbt || !p->d_rt || !p->d_ot || !p->d_shallow) {
+        if (!p->d_hb || !p->d_hbt || !p->d_rt || !p->d_ot || !p->d_x1 || !p->d_x2 || !p->d_shallow) {
             // give back what was taken: the next call starts from nothing
             p->dfree(p->d_hb, vol);
             p->dfree(p->d_hbt, vol);
             p->dfree(p->d_rt, vol);
             p->dfree(p->d_ot, vol);
+            p->dfree(p->d_x1, vol);
+            p->dfree(p->d_x2, vol);
             p->dfree(p->d_shallow, sizeof(int32_t) * (size_t)p->nt);
-            p->d_hb = p->d_hbt = p->d_rt = p->d_ot = nullptr;
+            p->d_hb = p->d_hbt = p->d_rt = p->d_ot = p->d_x1 = p->d_x2 = nullptr;
             p->d_shallow = nullptr;
             return PLAN_ENOMEM;
         }
@@ -457,6 +481,10 @@ int reach_alloc(plan_s* p, int n_cycles) {
             NHP_CK(cudaMemcpyAsync(p->d_shallow, p->shallow.data(), sizeof(int32_t) * sh.size(),
                                    cudaMemcpyHostToDevice, p->stream));
     }
+    for (auto& st : p->reach_side)
+        if (!st) NHP_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& e : p->reach_ev)
+        if (!e) NHP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (n_cycles + 1 > p->reach_cap) {
         p->dfree(p->d_reach, vol * (size_t)p->reach_cap);
         p->d_reach = (uint32_t*)p->dalloc(vol * (size_t)(n_cycles + 1));
@@ -487,15 +515,29 @@ int plan_reach_sweep(plan_t* p, plan_pose start, int n_cycles) {
     NHP_CK(launch_bit_transpose(p->d_hb, p->d_hbt, p->d_shallow, p->n_shallow, p->lx, false, s));
     NHP_CK(launch_reach_init(p->d_reach, p->nr, cell_index(p, start), s));
     p->launches += 3;
+    // A cycle's maneuvers all read R_m, so they run side by side: the first
+    // turn family writes R_{m+1} = R_m AND its result on the plan's stream,
+    // the second family its own volume on one side stream, the straights
+    // (shallow planes through their transposes) theirs on the other; then
+    // R_{m+1} &= both.
+    cudaStream_t a1 = p->reach_side[0], a2 = p->reach_side[1];
     for (int m = 0; m < n_cycles; m++) {
         const uint32_t* Rm = p->d_reach + (size_t)m * words;
         uint32_t* Rn = p->d_reach + (size_t)(m + 1) * words;
-        NHP_CK(launch_bit_transpose(Rm, p->d_rt, p->d_shallow, p->n_shallow, p->lx, false, s));
-        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 0, true, s));
-        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 1, false, s));
-        NHP_CK(launch_reach_straight(g, Rm, p->d_hb, p->d_rt, p->d_hbt, Rn, p->d_ot, s));
-        NHP_CK(launch_bit_transpose(p->d_ot, Rn, p->d_shallow, p->n_shallow, p->lx, true, s));
-        p->launches += 5;
+        NHP_CK(cudaEventRecord(p->reach_ev[0], s));
+        NHP_CK(cudaStreamWaitEvent(a1, p->reach_ev[0], 0));
+        NHP_CK(cudaStreamWaitEvent(a2, p->reach_ev[0], 0));
+        NHP_CK(launch_bit_transpose(Rm, p->d_rt, p->d_shallow, p->n_shallow, p->lx, false, a1));
+        NHP_CK(launch_reach_straight(g, Rm, p->d_hb, p->d_rt, p->d_hbt, p->d_x2, p->d_ot, a1));
+        NHP_CK(launch_bit_transpose(p->d_ot, p->d_x2, p->d_shallow, p->n_shallow, p->lx, false, a1));
+        NHP_CK(launch_reach_turn(g, Rm, p->d_x1, p->d_hb, 1, 2, a2));
+        NHP_CK(launch_reach_turn(g, Rm, Rn, p->d_hb, 0, 1, s));
+        NHP_CK(cudaEventRecord(p->reach_ev[1], a1));
+        NHP_CK(cudaEventRecord(p->reach_ev[2], a2));
+        NHP_CK(cudaStreamWaitEvent(s, p->reach_ev[1], 0));
+        NHP_CK(cudaStreamWaitEvent(s, p->reach_ev[2], 0));
+        NHP_CK(launch_reach_combine(Rn, p->d_x1, p->d_x2, p->nr, s));
+        p->launches += 6;
     }
     p->reach_n = n_cycles;
     p->reach_ready = true;
